@@ -1,0 +1,366 @@
+"""Pins of the oracle's SA-AMG setup and solve (Sec. 3) against mathematics.
+
+MIS-2 is checked against brute force and against a different algorithm (synchronous
+rounds) that provably returns the same set; P and the Galerkin operator against dense
+linear algebra; the Chebyshev smoother against its closed-form error polynomial; the
+coarse LU against a library solve; the V-cycle against symmetry and the exact inverse;
+PCG against a sparse direct solve.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sps
+import scipy.sparse.linalg as spla
+
+from oracle import oracle as O
+from paper_0907_4863_gb300 import inputs as I
+from tests.oracle_cases import oracle_hierarchy, oracle_operator, small_workloads
+
+SEED0 = 0x9E3779B9
+
+
+def _key(ids, seed):
+    h = np.array([O.fmix32(int(v) ^ seed) for v in ids], dtype=np.uint64)
+    return (h << np.uint64(32)) | ids.astype(np.uint64)
+
+
+def _random_graph(n, p, rng):
+    """Symmetric random graph in CSR with the diagonal included."""
+    m = rng.random((n, n)) < p
+    m = np.triu(m, 1)
+    m = m | m.T | np.eye(n, dtype=bool)
+    A = sps.csr_matrix(m.astype(float))
+    A.sort_indices()
+    return A.indptr.astype(np.int32), A.indices.astype(np.int32), m
+
+
+def _dist(m):
+    """All-pairs graph distance by BFS on a dense adjacency (brute force)."""
+    n = len(m)
+    D = np.full((n, n), 99, int)
+    for s in range(n):
+        D[s, s] = 0
+        front = [s]
+        while front:
+            nxt = []
+            for v in front:
+                for u in np.nonzero(m[v])[0]:
+                    if D[s, u] > D[s, v] + 1:
+                        D[s, u] = D[s, v] + 1
+                        nxt.append(u)
+            front = nxt
+    return D
+
+
+def _rounds_mis2(indptr, idx, key):
+    """Synchronous rounds: an undecided node joins when its key is the largest among the
+    undecided nodes within distance 2; nodes within distance 2 of a joined node leave."""
+    n = len(indptr) - 1
+    state = np.zeros(n, int)  # 0 undecided, 1 in, 2 out
+    nb = [idx[indptr[i]:indptr[i + 1]] for i in range(n)]
+    while np.any(state == 0):
+        m1 = np.array([max([key[u] for u in nb[j] if state[u] == 0], default=0) for j in range(n)],
+                      dtype=np.uint64)
+        m2 = np.array([max([m1[j] for j in nb[i]], default=0) for i in range(n)], dtype=np.uint64)
+        join = (state == 0) & (m2 == key)
+        state[join] = 1
+        o1 = np.array([any(state[u] == 1 for u in nb[j]) for j in range(n)])
+        o2 = np.array([any(o1[j] for j in nb[i]) for i in range(n)])
+        state[(state == 0) & o2] = 2
+    return (state == 1).astype(np.uint8)
+
+
+def test_fmix32_is_a_bijection_sample():
+    assert O.fmix32(0) == 0
+    vals = {O.fmix32(v) for v in range(1 << 14)}
+    assert len(vals) == 1 << 14
+
+
+@pytest.mark.parametrize("trial", range(12))
+def test_mis2_bruteforce_and_rounds(trial):
+    rng = np.random.default_rng(trial)
+    n = int(rng.integers(5, 40))
+    indptr, idx, m = _random_graph(n, float(rng.uniform(0.03, 0.25)), rng)
+    ids = rng.permutation(1000)[:n].astype(np.uint32)
+    seed = int(rng.integers(0, 2 ** 32))
+    root = O.mis2(indptr, idx, ids, seed)
+    D = _dist(m)
+    R = np.nonzero(root)[0]
+    # independence at distance >= 3
+    for a in R:
+        for b in R:
+            if a != b:
+                assert D[a, b] >= 3
+    # maximality: every node within distance 2 of some root
+    assert np.all(D[:, R].min(axis=1) <= 2)
+    # greedy by decreasing key: a node is out only if a higher-key root is within distance 2
+    key = _key(ids, seed)
+    for v in range(n):
+        if not root[v]:
+            assert any(D[v, r] <= 2 and key[r] > key[v] for r in R)
+    # the synchronous-round algorithm gives the identical set
+    assert np.array_equal(_rounds_mis2(indptr, idx, key), root)
+
+
+@pytest.mark.parametrize("w", small_workloads()[:4], ids=lambda w: w.name)
+def test_aggregates_partition_and_structure(w):
+    op = oracle_operator(w)
+    ids = op.node_of_row.astype(np.uint32)
+    root = O.mis2(op.rowptr, op.col, ids, SEED0)
+    agg, nagg = O.aggregate(op.rowptr, op.col, ids, SEED0, root)
+    assert nagg == int(root.sum()) and nagg > 0
+    assert agg.min() == 0 and agg.max() == nagg - 1
+    # numbering by ascending root row
+    roots = np.nonzero(root)[0]
+    assert np.array_equal(agg[roots], np.arange(nagg))
+    A = op.scipy()
+    # every neighbour of a root belongs to the root's aggregate (phase 1)
+    for r in roots:
+        nbrs = A.indices[A.indptr[r]:A.indptr[r + 1]]
+        assert np.all(agg[nbrs] == agg[r])
+    # every aggregate is connected in G
+    for J in range(nagg):
+        members = set(np.nonzero(agg == J)[0].tolist())
+        seen = {int(roots[J])}
+        front = [int(roots[J])]
+        while front:
+            v = front.pop()
+            for u in A.indices[A.indptr[v]:A.indptr[v + 1]]:
+                if int(u) in members and int(u) not in seen:
+                    seen.add(int(u))
+                    front.append(int(u))
+        assert seen == members
+
+
+def test_aggregates_identical_across_boundary_modes():
+    """G_0 is the structural graph of A, the same for all three extrapolations."""
+    aggs = []
+    for mode in (I.CONSTANT, I.LINEAR, I.QUADRATIC):
+        w = I.pipe_workload(20, mode)
+        op = oracle_operator(w)
+        h = oracle_hierarchy(op, max_coarse=50)
+        aggs.append([h.agg(l)[0] for l in range(h.levels - 1)])
+    for l in range(len(aggs[0])):
+        assert np.array_equal(aggs[0][l], aggs[1][l]) and np.array_equal(aggs[0][l], aggs[2][l])
+
+
+def test_power_lambda_bounds_spectrum():
+    w = I.cylinder_workload(12, I.LINEAR)
+    op = oracle_operator(w)
+    A = op.scipy().toarray()
+    Dinv = 1.0 / np.diag(A)
+    lam_max = np.linalg.eigvalsh(0.5 * (A + A.T) * np.sqrt(Dinv)[:, None] * np.sqrt(Dinv)[None, :]).max()
+    ids = op.node_of_row.astype(np.uint32)
+    lam10 = O.power_lambda(op.rowptr, op.col, op.ahat, ids, 10)
+    lam400 = O.power_lambda(op.rowptr, op.col, op.ahat, ids, 400)
+    assert lam10 <= lam_max * (1 + 1e-12)
+    assert lam10 > 0.8 * lam_max
+    assert abs(lam400 - lam_max) < 2e-3 * lam_max
+
+
+def _dense(rowptr, col, val, n, m):
+    return sps.csr_matrix((val, col, rowptr), shape=(n, m)).toarray()
+
+
+@pytest.mark.parametrize("mode", [I.CONSTANT, I.LINEAR, I.QUADRATIC])
+def test_prolongator_and_galerkin_dense(mode):
+    """P = T - omega D^-1 A T and A_{l+1} = P^T A_l P by dense matrix products (<= 8^3)."""
+    w = I.Workload("e8", I.cell_centred_grid(8), I.Domain(0.45, 0.35, taper=0.9), mode)
+    op = oracle_operator(w)
+    h = oracle_hierarchy(op, max_coarse=4)
+    assert h.levels >= 3
+    for l in range(h.levels - 1):
+        n, nc = h.n(l), h.n(l + 1)
+        A = _dense(*h.A(l), n, n)
+        agg, _ = h.agg(l)
+        T = np.zeros((n, nc))
+        T[np.arange(n), agg] = 1.0
+        omega = h.omega(l)
+        assert omega == pytest.approx(4.0 / (3.0 * h.lam(l)), rel=1e-15)
+        P_ref = T - omega * (A @ T) / np.diag(A)[:, None]
+        P = _dense(*h.P(l), n, nc)
+        assert np.allclose(P, P_ref, rtol=1e-13, atol=1e-13)
+        Rm = _dense(*h.R(l), nc, n)
+        assert np.array_equal(Rm, P.T)
+        Ac = _dense(*h.A(l + 1), nc, nc)
+        Ac_ref = P.T @ A @ P
+        assert np.allclose(Ac, Ac_ref, rtol=1e-12, atol=1e-12 * abs(Ac_ref).max())
+        # structural pattern: contains every nonzero of the dense product
+        rp, cc, _ = h.A(l + 1)
+        pat = np.zeros((nc, nc), bool)
+        for i in range(nc):
+            pat[i, cc[rp[i]:rp[i + 1]]] = True
+        assert np.all(pat[np.abs(Ac_ref) > 1e-14 * abs(Ac_ref).max()])
+
+
+def test_chebyshev_error_polynomial():
+    """Saad Alg. 12.1: after k steps from x0 = 0 the error is T_k((theta - lam)/delta) /
+    T_k(theta/delta) applied to each eigencomponent of D^-1 A."""
+    w = I.cylinder_workload(8, I.LINEAR)
+    op = oracle_operator(w)
+    A = op.scipy(scaled=False).toarray()  # unscaled: D != I, exercises D^-1
+    n = A.shape[0]
+    rp = op.rowptr
+    invd = 1.0 / np.diag(A)
+    rng = np.random.default_rng(3)
+    xs = rng.standard_normal(n)
+    b = A @ xs
+    lam_hat = 1.7 * np.max(np.abs(np.linalg.eigvals(invd[:, None] * A)).real) / 1.1 / 1.5
+    for k in (1, 2, 3, 4):
+        x = O.cheb_smooth(rp, op.col, op.aval, invd, lam_hat, b, degree=k, ratio=30.0, safety=1.1)
+        hi = 1.1 * lam_hat
+        lo = hi / 30.0
+        th, de = (hi + lo) / 2, (hi - lo) / 2
+        # D^-1 A = D^-1/2 (D^-1/2 A D^-1/2) D^1/2 with a symmetric middle factor
+        Sd = np.sqrt(invd)
+        lam, V = np.linalg.eigh(Sd[:, None] * A * Sd[None, :])
+        Tk = np.polynomial.chebyshev.chebval((th - lam) / de, [0] * k + [1])
+        Tk0 = np.polynomial.chebyshev.chebval(th / de, [0] * k + [1])
+        E = (V * (Tk / Tk0)) @ V.T
+        err_ref = (E @ (xs / Sd)) * Sd
+        assert np.allclose(xs - x, err_ref, rtol=1e-9, atol=1e-9 * np.abs(xs).max())
+
+
+def test_dense_lu_against_library_and_pivoting():
+    rng = np.random.default_rng(0)
+    for n in (1, 2, 7, 40):
+        a = rng.standard_normal((n, n))
+        b = rng.standard_normal(n)
+        assert np.allclose(O.dense_lu_solve(a, b), np.linalg.solve(a, b), rtol=1e-10, atol=1e-12)
+    a = np.array([[0.0, 2.0, 1.0], [1.0, 1.0, 0.0], [3.0, 0.0, 1.0]])  # needs pivoting
+    b = np.array([1.0, 2.0, 3.0])
+    assert np.allclose(O.dense_lu_solve(a, b), np.linalg.solve(a, b), rtol=1e-14)
+    with pytest.raises(ZeroDivisionError):
+        O.dense_lu_solve(np.zeros((3, 3)), b)
+
+
+@pytest.mark.parametrize("mode", [I.CONSTANT, I.LINEAR])
+def test_vcycle_symmetric_positive(mode):
+    """Sec. 3.2: same pre- and post-smoother and R = P^T give a symmetric preconditioner."""
+    w = I.cylinder_workload(14, mode)
+    op = oracle_operator(w)
+    h = oracle_hierarchy(op, max_coarse=30)
+    assert h.levels >= 3
+    rng = np.random.default_rng(1)
+    x, y = rng.standard_normal(op.n), rng.standard_normal(op.n)
+    Mx, My = h.vcycle(x), h.vcycle(y)
+    assert abs(Mx @ y - x @ My) <= 1e-12 * abs(Mx @ y)
+    assert Mx @ x > 0 and My @ y > 0
+
+
+def test_vcycle_single_level_is_exact_inverse():
+    w = I.cylinder_workload(8, I.QUADRATIC)
+    op = oracle_operator(w)
+    h = oracle_hierarchy(op, max_coarse=10 ** 6)
+    assert h.levels == 1
+    r = np.random.default_rng(2).standard_normal(op.n)
+    z = h.vcycle(r)
+    assert np.allclose(z, np.linalg.solve(op.scipy().toarray(), r), rtol=1e-11, atol=1e-13)
+
+
+@pytest.mark.parametrize("w", [I.cylinder_workload(12, I.CONSTANT), I.pipe_workload(12, I.LINEAR),
+                               I.pipe_workload(12, I.QUADRATIC),
+                               I.taper_workload(10, 9, 14, I.QUADRATIC)], ids=lambda w: w.name)
+def test_pcg_matches_direct_solve(w):
+    op = oracle_operator(w)
+    h = oracle_hierarchy(op, max_coarse=40)
+    rho = I.gaussian_bunch(w.grid, w.centre, w.sigma, seed=1)
+    phi, info = h.solve(rho, rtol=1e-12)
+    assert info["rc"] == 0
+    b = op.bfac * rho[op.node_of_row]
+    x_ref = spla.spsolve(op.scipy(scaled=False).tocsc(), b)
+    x = phi[op.node_of_row]
+    assert np.max(np.abs(x - x_ref)) <= 1e-10 * np.max(np.abs(x_ref))
+    outside = np.ones(w.grid.nbox, bool)
+    outside[op.node_of_row] = False
+    assert np.all(phi[outside] == 0.0)
+
+
+def test_pcg_edge_cases_and_warm_start():
+    w = I.pipe_workload(16, I.LINEAR)
+    op = oracle_operator(w)
+    h = oracle_hierarchy(op, max_coarse=100)
+    zero = np.zeros(w.grid.nbox)
+    phi, info = h.solve(zero, rtol=1e-8)
+    assert info["rc"] == 0 and info["iters"] == 0 and np.all(phi == 0)
+    rho = I.gaussian_bunch(w.grid, w.centre, w.sigma, seed=0)
+    phi, info = h.solve(rho, rtol=1e-8, maxit=2)
+    assert info["rc"] == 1 and info["iters"] == 2
+    phi, info = h.solve(rho, rtol=1e-8)
+    assert info["rc"] == 0
+    cold = info["iters"]
+    # exact warm start needs no iteration
+    _, info2 = h.solve(rho, phi0_box=phi, rtol=1e-8)
+    assert info2["iters"] == 0
+    # a drifted bunch (next time step) started from the previous solution needs fewer
+    # iterations (Sec. 5.2 reports about 30 % fewer)
+    rho2 = I.gaussian_bunch(w.grid, (w.centre[0], w.centre[1], w.centre[2] + 0.005), w.sigma, seed=0)
+    _, info3 = h.solve(rho2, phi0_box=phi, rtol=1e-8)
+    assert info3["rc"] == 0 and info3["iters"] < cold
+
+
+def test_iterations_roughly_grid_independent():
+    its = []
+    for n in (16, 32, 48):
+        w = I.pipe_workload(n, I.LINEAR)
+        op = oracle_operator(w)
+        h = oracle_hierarchy(op, max_coarse=200)
+        _, info = h.solve(I.gaussian_bunch(w.grid, w.centre, w.sigma, 0), rtol=1e-8)
+        assert info["rc"] == 0
+        its.append(info["iters"])
+    assert max(its) <= 1.6 * min(its) and max(its) <= 30, its
+
+
+def test_polak_ribiere_matches_fletcher_reeves_for_fixed_preconditioner():
+    w = I.pipe_workload(16, I.LINEAR)
+    op = oracle_operator(w)
+    h = oracle_hierarchy(op, max_coarse=100)
+    rho = I.gaussian_bunch(w.grid, w.centre, w.sigma, 0)
+    p0, i0 = h.solve(rho, rtol=1e-10, beta_rule=0)
+    p1, i1 = h.solve(rho, rtol=1e-10, beta_rule=1)
+    assert abs(i0["iters"] - i1["iters"]) <= 1
+    assert np.max(np.abs(p0 - p1)) <= 1e-8 * np.max(np.abs(p0))
+
+
+@pytest.mark.parametrize("mode", [I.LINEAR, I.QUADRATIC])
+def test_two_level_vcycle_closed_form(mode):
+    """Algorithm 1 with two levels: the error propagator of one V-cycle is
+    E (I - P A_c^-1 P^T A) E with E = p(D^-1 A) the Chebyshev error polynomial, so
+    z = M r = (I - E (I - P A_c^-1 P^T A) E) A^-1 r."""
+    w = I.Workload("e9", I.cell_centred_grid(9), I.Domain(0.45, 0.35), mode)
+    op = oracle_operator(w)
+    h = oracle_hierarchy(op, max_levels=2, max_coarse=1)
+    assert h.levels == 2
+    n, nc = h.n(0), h.n(1)
+    A = _dense(*h.A(0), n, n)
+    P = _dense(*h.P(0), n, nc)
+    Ac = _dense(*h.A(1), nc, nc)
+    invd = 1.0 / np.diag(A)
+    hi = 1.1 * h.lam(0)
+    lo = hi / 30.0
+    th, de = (hi + lo) / 2, (hi - lo) / 2
+    lam, V = np.linalg.eig(invd[:, None] * A)
+    pk = (np.polynomial.chebyshev.chebval((th - lam) / de, [0, 0, 1])
+          / np.polynomial.chebyshev.chebval(th / de, [0, 0, 1]))
+    E = np.real((V * pk) @ np.linalg.inv(V))
+    K = np.eye(n) - P @ np.linalg.solve(Ac, P.T @ A)
+    r = np.random.default_rng(5).standard_normal(n)
+    z_ref = np.linalg.solve(A, r) - E @ K @ E @ np.linalg.solve(A, r)
+    assert np.allclose(h.vcycle(r), z_ref, rtol=1e-9, atol=1e-10 * np.abs(z_ref).max())
+
+
+def test_phase2_nodes_join_highest_key_root():
+    w = I.pipe_workload(14, I.LINEAR)
+    op = oracle_operator(w)
+    ids = op.node_of_row.astype(np.uint32)
+    root = O.mis2(op.rowptr, op.col, ids, SEED0)
+    agg, nagg = O.aggregate(op.rowptr, op.col, ids, SEED0, root)
+    key = _key(ids, SEED0)
+    roots = np.nonzero(root)[0]
+    phase1 = -np.ones(op.n, int)
+    for r in roots:
+        phase1[op.col[op.rowptr[r]:op.rowptr[r + 1]]] = r
+    for i in np.nonzero(phase1 < 0)[0]:
+        cand = {phase1[u] for u in op.col[op.rowptr[i]:op.rowptr[i + 1]] if phase1[u] >= 0}
+        assert cand, i
+        best = max(cand, key=lambda r: key[r])
+        assert agg[i] == agg[best]
