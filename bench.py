@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""SAAMG-PCG benchmark: solves/s to relative residual 1e-8 on the 256^3 elliptic pipe.
+
+One step = one pass of the whole method on a new seeded Gaussian-bunch charge density:
+build the operator (inside test, boundary rows, scaling), set up the SA-AMG hierarchy
+(MIS-2 aggregation, prolongators, Galerkin products, coarse LU) and solve with PCG to
+||r|| <= 1e-8 ||b||.  Prints one JSON line (see the README of the measurement contract in
+the design doc).  --impl reference times the FP64 CPU oracle instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_0907_4863_gb300 import inputs as I  # noqa: E402
+
+RTOL = 1e-8
+METRIC = "solves/s to rel-residual 1e-8 at 256^3 (mixed/batched vs FP64 GPU); HBM GB/s; p99"
+UNIT = "solves/s"
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=256, help="grid size of the elliptic pipe workload")
+    ap.add_argument("--precision", choices=list(PREC), default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the mixed-precision and reuse legs")
+    return ap.parse_args()
+
+
+def workload(n):
+    w = I.pipe_workload(n, I.LINEAR)
+    return w
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    from paper_0907_4863_gb300 import saamg as S
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    S.use_torch_allocator()
+    w = workload(args.n)
+    dom, grid = S.make_domain(w.domain), S.make_grid(w.grid)
+    prec = PREC[args.precision]
+    params = S.params_default(max_coarse=4096, precision=prec, beta_rule=1 if prec else 0)
+    nsteps = args.warmup + args.steps
+    # every step gets its own seeded right-hand side, resident in HBM before timing
+    rhs = [torch.from_numpy(I.gaussian_bunch(w.grid, w.centre, w.sigma, seed=1000 * rank + k)).cuda()
+           for k in range(nsteps)]
+    phis = [torch.zeros_like(r) for r in rhs]
+    stream = torch.cuda.current_stream()
+    infos = []
+
+    def step(k):
+        op = S.build_operator(dom, grid, w.mode)
+        h = S.setup(op, params)
+        phis[k].zero_()
+        info = S.solve(h, rhs[k], phis[k], rtol=RTOL)
+        infos.append((info, h.info()))
+        h.free()
+        op.free()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for k in range(args.warmup):
+        step(k)
+    S.kernel_timing(True)
+    for c in range(len(S.KT_NAMES)):
+        S.kernel_timing_read(c)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    launches0 = S.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_host0 = time.perf_counter()
+    e0.record(stream)
+    for k in range(args.warmup, nsteps):
+        step(k)
+    e1.record(stream)
+    barrier()
+    t_host = time.perf_counter() - t_host0
+    launches = S.kernel_launches() - launches0
+    clk = clocks.stop()
+    S.kernel_timing(False)
+    ktime = {S.KT_NAMES[c]: S.kernel_timing_read(c) for c in range(len(S.KT_NAMES))}
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    timed = infos[args.warmup:]
+    iters = [i["iters"] for i, _ in timed]
+    relres = max(i["relres_true"] for i, _ in timed)
+    assert all(i["converged"] == 1 for i, _ in timed), "a timed solve did not converge"
+    hinfo = timed[-1][1]
+    value = world * args.steps / (ms / 1e3)
+
+    # --- roofline of the dominant kernel class (live, CUDA events on the launching stream)
+    dom_name = max(ktime, key=lambda k: ktime[k][0])
+    roof = roofline(dom_name, ktime[dom_name], prec)
+
+    # --- end to end through the public API with host buffers (pinned), copies in the region
+    nbox = w.grid.nbox
+    host_rho = [torch.from_numpy(I.gaussian_bunch(w.grid, w.centre, w.sigma, seed=5000 + k)).pin_memory()
+                for k in range(args.steps)]
+    host_phi = torch.zeros(nbox, dtype=torch.float64).pin_memory()
+
+    def e2e_step(k):
+        op = S.build_operator(dom, grid, w.mode)
+        h = S.setup(op, params)
+        host_phi.zero_()
+        info = S.solve_host(h, host_rho[k].numpy(), host_phi.numpy(), rtol=RTOL)
+        assert info["converged"] == 1
+        h.free()
+        op.free()
+
+    e2e_step(0)
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        e2e_step(k)
+    barrier()
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": world * args.steps / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * nbox * 8, "d2h_bytes_per_step": nbox * 8}
+
+    extra = {}
+    if not args.no_extra:
+        extra = extra_legs(S, torch, w, dom, grid, rhs[args.warmup], args)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32+f64",
+        "data": "synthetic (seeded Gaussian bunch, no dataset)",
+        "config": {"workload": f"{w.name}, linear extrapolation, Robin ends, rtol 1e-8, coarse <= 4096, "
+                               f"{args.precision} V-cycle; step = build operator + AMG setup + PCG solve",
+                   "grid": list(w.grid.n), "unknowns": hinfo["n"][0], "levels": hinfo["n"],
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (rho 134 MB, hierarchy > 1 GB)"},
+        "iters": iters, "relres_true_max": relres,
+        "host_wall_ms_per_step": 1e3 * t_host / args.steps,
+        "kernel_classes_ms_per_step": {k: v[0] / args.steps for k, v in ktime.items()},
+        "roofline": roof, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
+    }
+    out.update(extra)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(w, iters[-1])
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def roofline(name, rec, prec):
+    """Algorithmic work per launch / average launch duration for the dominant class."""
+    total_ms, launches, rows = rec
+    if launches == 0 or total_ms <= 0:
+        return None
+    avg_s = total_ms / launches / 1e3
+    rows_per_launch = rows / launches
+    if prec == 0 and name in ("stencil_smooth", "stencil_apply"):
+        # FP64 issue-bound: 19 flops per row for a Chebyshev step fused with the residual
+        # (13 for A x, 1 for b - A x, 4 for the direction update, 1 for x + d); 13 for A x
+        flops = (19 if name == "stencil_smooth" else 13) * rows_per_launch
+        ach = flops / avg_s / 1e12
+        return {"bound": "alu", "kernel": name, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                "avg_launch_us": avg_s * 1e6, "launches": launches}
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    w = 8 if prec == 0 else 4
+    per_row = {"stencil_smooth": 5 * w, "stencil_apply": 2 * w}.get(name, 2 * w)
+    ach = per_row * rows_per_launch / avg_s / 1e9
+    return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm, "traffic": None,
+            "peak_source": "measured" if peaks else "fallback",
+            "avg_launch_us": avg_s * 1e6, "launches": launches}
+
+
+def extra_legs(S, torch, w, dom, grid, rho, args):
+    """Hierarchy reuse (Sec. 5.2, reusing the preconditioner) and the mixed-precision path."""
+    out = {}
+    for name, prec in (("fp64", 0), ("fp32", 1), ("bf16", 2)):
+        params = S.params_default(max_coarse=4096, precision=prec, beta_rule=1 if prec else 0)
+        op = S.build_operator(dom, grid, w.mode)
+        h = S.setup(op, params)
+        phi = torch.zeros_like(rho)
+        S.solve(h, rho, phi, rtol=RTOL)
+        S.kernel_timing(True)
+        for c in range(len(S.KT_NAMES)):
+            S.kernel_timing_read(c)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        its = []
+        for k in range(args.steps):
+            phi.zero_()
+            its.append(S.solve(h, rho, phi, rtol=RTOL))
+        e1.record()
+        torch.cuda.synchronize()
+        S.kernel_timing(False)
+        kt = {S.KT_NAMES[c]: S.kernel_timing_read(c) for c in range(len(S.KT_NAMES))}
+        ms = e0.elapsed_time(e1) / args.steps
+        # whole pipeline in this precision
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            op2 = S.build_operator(dom, grid, w.mode)
+            h2 = S.setup(op2, params)
+            phi.zero_()
+            S.solve(h2, rho, phi, rtol=RTOL)
+            h2.free()
+            op2.free()
+        torch.cuda.synchronize()
+        full_ms = 1e3 * (time.perf_counter() - t0) / args.steps
+        dom_name = "stencil_smooth"
+        out[f"{name}_vcycle"] = {
+            "solve_only_solves_per_s": 1e3 / ms, "solve_ms": ms,
+            "full_pipeline_solves_per_s": 1e3 / full_ms, "setup_ms": h.info()["setup_ms"],
+            "iters": its[-1]["iters"], "relres_true": its[-1]["relres_true"],
+            "roofline_stencil_smooth": roofline(dom_name, kt[dom_name], prec),
+            "kernel_classes_ms_per_solve": {k: v[0] / args.steps for k, v in kt.items()},
+        }
+        h.free()
+        op.free()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(w, iters_needed, capped_iters=4):
+    """Oracle on the full workload: build + setup + `capped_iters` PCG iterations, the solve
+    time scaled to the iterations the solve needs.  Returns seconds per solve."""
+    from oracle import oracle as O
+    d, g = w.domain, w.grid
+    rho = I.gaussian_bunch(g, w.centre, w.sigma, seed=0)
+    t0 = time.perf_counter()
+    op = O.Operator(g.n, g.h, g.origin, d.a, d.b, d.taper, d.cx, d.cy, d.zbc, d.symmetrize, w.mode)
+    h = O.Hierarchy(op, max_coarse=4096)
+    t1 = time.perf_counter()
+    _, info = h.solve(rho, rtol=RTOL, maxit=capped_iters)
+    t2 = time.perf_counter()
+    per_iter = (t2 - t1) / max(1, info["iters"])
+    return (t1 - t0) + per_iter * iters_needed, (t1 - t0), per_iter
+
+
+def cpu_baseline(w, iters_needed):
+    sec, setup_s, per_iter = oracle_sample(w, iters_needed)
+    return {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"single-thread FP64 oracle on {w.name}: build + setup + 4 PCG iterations, "
+                      f"solve scaled to {iters_needed} iterations (setup {setup_s:.1f} s, "
+                      f"{per_iter:.2f} s/iteration)"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    w = workload(args.n)
+    iters_needed = 21 if args.n == 256 else 20
+    for _ in range(args.warmup):
+        oracle_sample(w, iters_needed, capped_iters=1)
+    secs = []
+    for _ in range(args.steps):
+        s, _, _ = oracle_sample(w, iters_needed, capped_iters=2)
+        secs.append(s)
+    total = sum(secs)
+    value = args.steps / total
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded Gaussian bunch, no dataset)",
+           "config": {"workload": f"{w.name}, linear extrapolation, Robin ends, rtol 1e-8, coarse <= 4096; "
+                                  "step = build operator + AMG setup + PCG solve",
+                      "grid": list(w.grid.n), "parallelism": "single CPU thread"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "each step: FP64 oracle build + setup + 2 PCG iterations on the full "
+                                      f"workload, solve scaled to {iters_needed} iterations"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

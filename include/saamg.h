@@ -1,0 +1,232 @@
+/*
+ * saamg.h -- C ABI of the GB300 (sm_103a) SAAMG-PCG library.
+ *
+ * Conjugate gradients on the finite-difference Poisson system of an irregular 3-D
+ * pipe domain, preconditioned by one smoothed-aggregation AMG V-cycle per iteration
+ * (Adelmann, Arbenz, Ineichen, "A Fast Parallel Poisson Solver on Irregular Domains
+ * Applied to Beam Dynamic Simulations").
+ *
+ * Conventions for every call:
+ *   - Every function returns a saamg_status (0 = OK, 1 = not converged, < 0 = error),
+ *     never aborts, throws or exits.  saamg_last_error() gives a message for the
+ *     calling thread's last failure.
+ *   - Device pointers are caller-owned and must stay valid until the work enqueued on
+ *     `stream` has finished.  `stream` is a cudaStream_t (NULL = legacy default
+ *     stream); all GPU work of a call is enqueued on it.  Calls that must return a
+ *     host-visible result (sizes, iteration counts) synchronise that stream.
+ *   - Handles (saamg_operator, saamg_hierarchy) are library-owned and released by
+ *     saamg_free().  An operator must outlive every hierarchy set up from it.
+ *   - Box arrays: nx*ny*nz doubles, node (i,j,k) at index i + nx*(j + ny*k), node
+ *     position origin + (i*h[0], j*h[1], k*h[2]).  Compact arrays: one entry per
+ *     unknown, unknowns numbered in ascending box index.
+ *   - Device memory is taken from the allocator installed by saamg_set_allocator
+ *     (cudaMalloc/cudaFree when none is installed).
+ */
+#ifndef SAAMG_H
+#define SAAMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SAAMG_MAX_LEVELS 16
+
+typedef enum {
+  SAAMG_OK = 0,
+  SAAMG_NOT_CONVERGED = 1,   /* maxit reached; the best iterate is returned */
+  SAAMG_EINVAL = -1,         /* invalid argument */
+  SAAMG_ENOMEM = -2,         /* the allocator returned NULL */
+  SAAMG_ECUDA = -3,          /* a CUDA runtime call failed */
+  SAAMG_NUMERICAL = -4,      /* NaN/Inf or a zero pivot / breakdown */
+  SAAMG_DEVICE_TIMEOUT = -5, /* a bounded device-side wait gave up */
+  SAAMG_UNIMPLEMENTED = -6
+} saamg_status;
+
+/* Dirichlet treatment on the pipe wall Gamma_1 (Sec. 2, Eqs. (7), (8), (9)-(10)). */
+typedef enum {
+  SAAMG_BC_CONSTANT = 0,
+  SAAMG_BC_LINEAR = 1,
+  SAAMG_BC_QUADRATIC = 2
+} saamg_boundary_mode;
+
+/* Treatment of the two end planes Gamma_2: Robin (Eq. (5), Eq. (11)) or zero Dirichlet. */
+typedef enum { SAAMG_Z_ROBIN = 0, SAAMG_Z_DIRICHLET = 1 } saamg_zbc;
+
+/* Arithmetic of the V-cycle.  The outer CG, its residual, dot products, search
+ * direction and the coarsest-level solve are FP64 in every mode. */
+typedef enum {
+  SAAMG_PREC_FP64 = 0,      /* whole method in FP64 */
+  SAAMG_PREC_FP32 = 1,      /* V-cycle in FP32, coarse operators stored FP32 */
+  SAAMG_PREC_FP32_BF16 = 2  /* V-cycle in FP32, coarse operators stored BF16 */
+} saamg_precision;
+
+/* Domain Omega (Sec. 2, Sec. 4.1): an elliptic pipe along z, cross-section
+ * ((x-cx)/(a s))^2 + ((y-cy)/(b s))^2 < 1 where s = 1 at the first z-plane of the grid
+ * and s = taper at the last, linear in between (taper = 1: straight pipe).  The first
+ * and last z-planes of the grid are Gamma_2. */
+typedef struct {
+  double a, b;
+  double taper;
+  double cx, cy;
+  int zbc;               /* saamg_zbc */
+  int symmetrize_gamma2; /* 1: halve Robin rows (and rhs) so that constant and linear
+                            modes give a symmetric matrix; 0: the raw rows */
+} saamg_domain;
+
+typedef struct {
+  int n[3];
+  double h[3];
+  double origin[3];
+} saamg_grid;
+
+typedef struct {
+  int cheb_degree;    /* Chebyshev steps per pre- and post-smoothing (default 2) */
+  double cheb_ratio;  /* lambda_hi / lambda_lo of the smoothing interval (30) */
+  double cheb_safety; /* lambda_hi = safety * lambda_hat (1.1) */
+  int max_coarse;     /* stop coarsening at <= max_coarse unknowns (1000, Table 1) */
+  int max_levels;     /* including the finest level (10) */
+  int power_iters;    /* power-iteration steps for lambda_hat (10) */
+  int precision;      /* saamg_precision (FP64) */
+  int beta_rule;      /* 0: r'z ratio (Fletcher-Reeves form), 1: Polak-Ribiere (0) */
+  int maxit;          /* PCG iteration limit (1000) */
+} saamg_params;
+
+typedef struct {
+  int iters;          /* products A p */
+  int converged;      /* 1 when ||r|| <= rtol ||b|| */
+  double relres;      /* recursive residual ||r||/||b|| of the scaled system */
+  double relres_true; /* recomputed ||b - A x|| / ||b|| of the scaled system */
+  double solve_ms;    /* wall time of the call */
+} saamg_solve_info;
+
+typedef struct {
+  int levels;
+  int n[SAAMG_MAX_LEVELS];          /* unknowns per level */
+  long long nnz[SAAMG_MAX_LEVELS];  /* nonzeros of A_l (level 0: explicit CSR) */
+  long long nnz_p[SAAMG_MAX_LEVELS];/* nonzeros of P_l (0 on the coarsest level) */
+  double lambda[SAAMG_MAX_LEVELS];  /* power-iteration estimate of lambda_max(D^-1 A_l) */
+  long long device_bytes;           /* device memory held by the hierarchy */
+  double setup_ms;                  /* wall time of saamg_setup */
+} saamg_hierarchy_info;
+
+typedef struct saamg_operator saamg_operator;
+typedef struct saamg_hierarchy saamg_hierarchy;
+
+/* Allocator hook: alloc(bytes, stream, ctx) -> device pointer or NULL; free(ptr, stream, ctx). */
+typedef void *(*saamg_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*saamg_free_fn)(void *ptr, void *stream, void *ctx);
+
+/* Fills *p with the defaults listed above.  EINVAL if p is NULL. */
+saamg_status saamg_params_default(saamg_params *p);
+
+/* Installs a process-wide device allocator (both NULL: back to cudaMalloc/cudaFree).
+ * Handles keep the allocator that created them.  Not thread-safe against concurrent
+ * allocation. */
+saamg_status saamg_set_allocator(saamg_alloc_fn alloc, saamg_free_fn free_fn, void *ctx);
+
+/* Builds the scaled operator D^-1/2 A D^-1/2 of Sec. 2 (Eqs. (5)-(12) and the scaling
+ * paragraph after Eq. (12)) on the device: inside test and boundary fractions of every
+ * lattice node, the rows of the constant / linear / quadratic extrapolation, Robin rows
+ * on Gamma_2, the diagonal scaling, a matrix-free stencil description and an explicit
+ * CSR copy for the AMG setup.  mode: saamg_boundary_mode.
+ * Errors: EINVAL (NULL pointers, sizes < 1, nz < 2 (Robin) or < 3 (Dirichlet), h <= 0,
+ * a, b, taper <= 0, more than 2^31 nonzeros, a lattice line whose inside nodes are not
+ * contiguous), ENOMEM, ECUDA. */
+saamg_status saamg_build_operator(const saamg_domain *domain, const saamg_grid *grid,
+                                  int mode, void *stream, saamg_operator **out);
+
+/* Number of unknowns and nonzeros of the scaled operator. */
+saamg_status saamg_operator_size(const saamg_operator *op, int *n_unknowns, long long *nnz);
+
+/* Copies the operator to HOST buffers (any may be NULL): node_of_row[n] (box index),
+ * scale[n] (s_i = a_ii^-1/2), rowptr[n+1], col[nnz], val[nnz] (scaled values), and
+ * is_regular[n] (1 when the row is applied with the constant interior stencil). */
+saamg_status saamg_operator_copy(const saamg_operator *op, int *node_of_row, double *scale,
+                                 int *rowptr, int *col, double *val, unsigned char *is_regular,
+                                 void *stream);
+
+/* y = Ahat x on compact device vectors (matrix-free stencil, Eq. (6) with the boundary rows). */
+saamg_status saamg_operator_apply(const saamg_operator *op, const double *x, double *y,
+                                  void *stream);
+
+/* Sets up the SA-AMG hierarchy of Sec. 3.2 on the device: MIS-2 aggregation of the
+ * adjacency graph of A_l, tentative prolongator, lambda_hat by power iteration, damped-
+ * Jacobi smoothed prolongator P_l, R_l = P_l^T, Galerkin A_{l+1} = R_l A_l P_l, and a
+ * dense LU (partial pivoting) with explicit inverse of the coarsest matrix.
+ * params NULL = defaults.  Errors: EINVAL, ENOMEM, ECUDA, NUMERICAL (zero pivot,
+ * coarsest level larger than 16384 because coarsening stalled). */
+saamg_status saamg_setup(const saamg_operator *op, const saamg_params *params, void *stream,
+                         saamg_hierarchy **out);
+
+saamg_status saamg_hierarchy_get_info(const saamg_hierarchy *h, saamg_hierarchy_info *info);
+
+/* Copies level l to HOST buffers (any may be NULL): A_l as CSR (rowptr[n_l+1], col, val),
+ * aggregate index agg[n_l] and root flags root[n_l] (levels below the coarsest), P_l as
+ * CSR (p_rowptr[n_l+1], p_col, p_val) and R_l (r_rowptr[n_{l+1}+1], r_col, r_val). */
+saamg_status saamg_hierarchy_copy_level(const saamg_hierarchy *h, int l, int *rowptr, int *col,
+                                        double *val, int *agg, unsigned char *root,
+                                        int *p_rowptr, int *p_col, double *p_val,
+                                        int *r_rowptr, int *r_col, double *r_val, void *stream);
+
+/* z = M r: one V-cycle (Algorithm 1) on compact device vectors of level 0. */
+saamg_status saamg_vcycle(const saamg_hierarchy *h, const double *r, double *z, void *stream);
+
+/* Solves A phi = rho (Sec. 3.1, PCG preconditioned by one V-cycle per iteration) on BOX
+ * device arrays: rho = rho/epsilon_0 sampled at the nodes (read at unknowns only), phi
+ * holds the initial guess on entry (warm start, Sec. 4) and the solution on exit, zero
+ * at non-unknowns.  Stops when ||r||_2 <= rtol ||b||_2 for the scaled system.
+ * Returns OK, NOT_CONVERGED (maxit reached), NUMERICAL (NaN/Inf or breakdown), EINVAL. */
+saamg_status saamg_solve(saamg_hierarchy *h, const double *rho, double *phi, double rtol,
+                         void *stream, saamg_solve_info *info);
+
+/* Same as saamg_solve with HOST box arrays; the host<->device copies are part of the call. */
+saamg_status saamg_solve_host(saamg_hierarchy *h, const double *rho_host, double *phi_host,
+                              double rtol, void *stream, saamg_solve_info *info);
+
+/* Deterministic MIS-2 aggregation of a symmetric graph given as CSR on the device
+ * (rowptr[n+1], col[nnz], self loops allowed), distinct node ids ids[n] (NULL: the row
+ * index) and a 32-bit seed.  The priority of node v is fmix32(id_v ^ seed), a bijection,
+ * so distinct ids never tie.  Outputs (device):
+ * root[n] (1 = aggregate root) and agg[n] (aggregate index, roots numbered by ascending
+ * row).  *n_agg receives the number of aggregates.  Same rule as the hierarchy's setup. */
+saamg_status saamg_mis2_aggregate(int n, const int *rowptr, const int *col, const uint32_t *ids,
+                                  uint32_t seed, unsigned char *root, int *agg, int *n_agg,
+                                  void *stream);
+
+/* Kernel classes for saamg_kernel_timing_read. */
+typedef enum {
+  SAAMG_KT_STENCIL_SMOOTH = 0, /* level-0 Chebyshev step fused with the residual */
+  SAAMG_KT_STENCIL_APPLY = 1,  /* level-0 A x, residual, A p with p'Ap */
+  SAAMG_KT_COARSE = 2,         /* CSR smoother / residual on levels >= 1 */
+  SAAMG_KT_TRANSFER = 3,       /* restriction R r and prolongation x += P v */
+  SAAMG_KT_SPGEMM = 4,         /* sparse products of the setup */
+  SAAMG_KT_COUNT = 5
+} saamg_kernel_class;
+
+/* Number of kernels this library has launched in the calling process. */
+long long saamg_kernel_launches(void);
+
+/* enable != 0: record a CUDA event pair on the launching stream around every launch of
+ * the classes above (adds two event records per launch); 0: stop recording. */
+saamg_status saamg_kernel_timing(int enable);
+
+/* Waits for the recorded events of class kclass and returns their summed duration, the
+ * number of launches and the rows they processed since the last read; then resets the
+ * class.  EINVAL for an unknown class. */
+saamg_status saamg_kernel_timing_read(int kclass, double *total_ms, long long *launches,
+                                      long long *rows);
+
+/* Releases an operator or a hierarchy (NULL is ignored).  Waits for the handle's
+ * outstanding work first. */
+void saamg_free(void *handle);
+
+/* Message of the calling thread's last error ("" if none). */
+const char *saamg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SAAMG_H */

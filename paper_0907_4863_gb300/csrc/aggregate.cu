@@ -1,0 +1,285 @@
+// Aggregation for the tentative prolongator (Sec. 3.2, "Prolongation operator"):
+// aggregates seeded by a deterministic distance-2 maximal independent set (MIS-2) of the
+// adjacency graph G_l of A_l, computed in synchronous rounds.
+//
+// Priority of node v: (fmix32(id_v ^ seed), v) compared lexicographically.  Rows are
+// numbered in ascending id, so this is the same order as (fmix32(id ^ seed), id).
+// Round: an undecided node joins when its priority is the largest among the undecided
+// nodes within graph distance 2; afterwards every undecided node within distance 2 of a
+// member leaves.  With fixed priorities these rounds select exactly the set of the
+// sequential greedy rule (visit by decreasing priority, join unless a member is within
+// distance 2) -- the determinism result for parallel greedy MIS of Blelloch, Fineman and
+// Shun (2012), applied to the square of the graph.
+#include "aggregate.cuh"
+
+namespace saamg {
+
+namespace {
+
+// MurmurHash3 32-bit finaliser (public domain): xor-shift 16, multiply 0x85ebca6b,
+// xor-shift 13, multiply 0xc2b2ae35, xor-shift 16.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+__device__ __forceinline__ unsigned long long prio(const unsigned* ids, int row, uint32_t seed) {
+  uint32_t id = ids ? ids[row] : (uint32_t)row;
+  // +1 keeps 0 free as "no candidate"; rows < 2^31 so this never wraps
+  return (((unsigned long long)fmix32(id ^ seed) << 32) | (unsigned long long)(uint32_t)row) + 1ull;
+}
+
+template <class T>
+__device__ __forceinline__ T group_max(T v, int G) {
+  for (int o = G / 2; o > 0; o >>= 1) {
+    T w = __shfl_xor_sync(0xffffffffu, v, o, G);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+__device__ __forceinline__ int group_or(int v, int G) {
+  for (int o = G / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o, G);
+  return v;
+}
+
+// Loop shared by the kernels below: 32/G rows per warp, uniform trip count per warp.
+#define SAAMG_ROW_LOOP(G)                                                          \
+  const int lane = threadIdx.x & 31;                                               \
+  const int gl = lane % (G);                                                       \
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;                   \
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;                                \
+  for (int wbase = warp * (32 / (G)); wbase < n; wbase += nwarps * (32 / (G)))
+
+// m1[j] = max priority of the undecided nodes in N[j] (0 if none)
+template <int G>
+__global__ void mis_max1_k(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                           const unsigned char* __restrict__ state, const unsigned* __restrict__ ids,
+                           uint32_t seed, unsigned long long* __restrict__ m1) {
+  SAAMG_ROW_LOOP(G) {
+    int row = wbase + lane / G;
+    unsigned long long acc = 0;
+    if (row < n && gl == 0 && state[row] == 0) acc = prio(ids, row, seed);  // closed N[j]
+    if (row < n)
+      for (int p = rowptr[row] + gl; p < rowptr[row + 1]; p += G) {
+        int u = col[p];
+        if (state[u] == 0) {
+          unsigned long long k = prio(ids, u, seed);
+          acc = k > acc ? k : acc;
+        }
+      }
+    acc = group_max(acc, G);
+    if (row < n && gl == 0) m1[row] = acc;
+  }
+}
+
+// an undecided node whose priority is the maximum over N[N[i]] joins
+template <int G>
+__global__ void mis_max2_k(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                           unsigned char* __restrict__ state, const unsigned* __restrict__ ids,
+                           uint32_t seed, const unsigned long long* __restrict__ m1) {
+  SAAMG_ROW_LOOP(G) {
+    int row = wbase + lane / G;
+    bool und = row < n && state[row] == 0;
+    unsigned long long acc = (und && gl == 0) ? m1[row] : 0ull;
+    if (und)
+      for (int p = rowptr[row] + gl; p < rowptr[row + 1]; p += G) {
+        unsigned long long k = m1[col[p]];
+        acc = k > acc ? k : acc;
+      }
+    acc = group_max(acc, G);
+    if (und && gl == 0 && acc == prio(ids, row, seed)) state[row] = 1;
+  }
+}
+
+// o1[j] = 1 if N[j] holds a member
+template <int G>
+__global__ void mis_or1_k(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                          const unsigned char* __restrict__ state, unsigned char* __restrict__ o1) {
+  SAAMG_ROW_LOOP(G) {
+    int row = wbase + lane / G;
+    int any = (row < n && gl == 0) ? (state[row] == 1) : 0;
+    if (row < n)
+      for (int p = rowptr[row] + gl; p < rowptr[row + 1]; p += G) any |= (state[col[p]] == 1);
+    any = group_or(any, G);
+    if (row < n && gl == 0) o1[row] = (unsigned char)any;
+  }
+}
+
+// undecided nodes within distance 2 of a member leave; count the rest
+template <int G>
+__global__ void mis_or2_k(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                          unsigned char* __restrict__ state, const unsigned char* __restrict__ o1,
+                          int* __restrict__ undecided) {
+  int cnt = 0;
+  SAAMG_ROW_LOOP(G) {
+    int row = wbase + lane / G;
+    bool und = row < n && state[row] == 0;
+    int any = (und && gl == 0) ? o1[row] : 0;
+    if (und)
+      for (int p = rowptr[row] + gl; p < rowptr[row + 1]; p += G) any |= o1[col[p]];
+    any = group_or(any, G);
+    if (und && gl == 0) {
+      if (any) state[row] = 2;
+      else ++cnt;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(undecided, cnt);
+}
+
+__global__ void roots_from_state_k(int n, const unsigned char* __restrict__ state,
+                                   unsigned char* __restrict__ root) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) root[i] = state[i] == 1;
+}
+
+// phase 1: a root claims itself and its neighbours (disjoint for distinct roots)
+__global__ void agg_phase1_k(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                             const unsigned char* __restrict__ root, int* __restrict__ root1) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !root[i]) return;
+  for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) root1[col[p]] = i;
+  root1[i] = i;
+}
+
+// phase 2: other nodes join the phase-1 aggregate whose root has the largest priority
+template <int G>
+__global__ void agg_phase2_k(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                             const unsigned* __restrict__ ids, uint32_t seed,
+                             const int* __restrict__ root1, int* __restrict__ aggroot,
+                             int* __restrict__ err) {
+  SAAMG_ROW_LOOP(G) {
+    int row = wbase + lane / G;
+    bool need = row < n && root1[row] < 0;
+    unsigned long long best = 0;
+    if (need)
+      for (int p = rowptr[row] + gl; p < rowptr[row + 1]; p += G) {
+        int r = root1[col[p]];
+        if (r >= 0) {
+          unsigned long long k = prio(ids, r, seed);
+          best = k > best ? k : best;
+        }
+      }
+    best = group_max(best, G);
+    if (row < n && gl == 0) {
+      if (!need) {
+        aggroot[row] = root1[row];
+      } else if (best == 0) {
+        aggroot[row] = -1;
+        atomicOr(err, 1);
+      } else {
+        aggroot[row] = (int)(uint32_t)((best - 1ull) & 0xffffffffull);
+      }
+    }
+  }
+}
+
+__global__ void agg_number_k(int n, const int* __restrict__ aggroot, const int* __restrict__ rank,
+                             int* __restrict__ agg) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) agg[i] = aggroot[i] >= 0 ? rank[aggroot[i]] : -1;
+}
+
+template <int G>
+int rounds(int n, const int* rowptr, const int* col, const unsigned* ids, uint32_t seed,
+           unsigned char* state, unsigned long long* m1, unsigned char* o1, int* counter,
+           cudaStream_t s) {
+  long long need = ((long long)n * G + 255) / 256;
+  int blocks = (int)(need < 152 * 16 ? (need > 0 ? need : 1) : 152 * 16);
+  int rounds_done = 0;
+  for (;;) {
+    mis_max1_k<G><<<blocks, 256, 0, s>>>(n, rowptr, col, state, ids, seed, m1);
+    SAAMG_LAUNCH();
+    mis_max2_k<G><<<blocks, 256, 0, s>>>(n, rowptr, col, state, ids, seed, m1);
+    SAAMG_LAUNCH();
+    mis_or1_k<G><<<blocks, 256, 0, s>>>(n, rowptr, col, state, o1);
+    SAAMG_LAUNCH();
+    SAAMG_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
+    mis_or2_k<G><<<blocks, 256, 0, s>>>(n, rowptr, col, state, o1, counter);
+    SAAMG_LAUNCH();
+    ++rounds_done;
+    int left = 0;
+    d2h_sync(&left, counter, sizeof(int), s);
+    if (left == 0) break;
+    // every round removes at least the undecided node of largest priority
+    if (rounds_done > n + 1) fail(SAAMG_NUMERICAL, "MIS-2 rounds did not terminate");
+  }
+  return rounds_done;
+}
+
+template <int G>
+void phase2(int n, const int* rowptr, const int* col, const unsigned* ids, uint32_t seed,
+            const int* root1, int* aggroot, int* err, cudaStream_t s) {
+  long long need = ((long long)n * G + 255) / 256;
+  int blocks = (int)(need < 152 * 16 ? (need > 0 ? need : 1) : 152 * 16);
+  agg_phase2_k<G><<<blocks, 256, 0, s>>>(n, rowptr, col, ids, seed, root1, aggroot, err);
+  SAAMG_LAUNCH();
+}
+
+}  // namespace
+
+int mis2_aggregate(int n, const int* rowptr, const int* col, long long nnz, const unsigned* ids,
+                   uint32_t seed, unsigned char* root, int* agg, const AggScratch& w,
+                   cudaStream_t s) {
+  if (n <= 0) return 0;
+  double avg = (double)nnz / (double)n;
+  SAAMG_CUDA(cudaMemsetAsync(w.state, 0, (size_t)n, s));
+  if (avg <= 8.0)
+    rounds<4>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, s);
+  else if (avg <= 24.0)
+    rounds<8>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, s);
+  else if (avg <= 64.0)
+    rounds<16>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, s);
+  else
+    rounds<32>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, s);
+  roots_from_state_k<<<(n + 255) / 256, 256, 0, s>>>(n, w.state, root);
+  SAAMG_LAUNCH();
+  fill_int(w.root1, -1, (size_t)n, s);
+  agg_phase1_k<<<(n + 255) / 256, 256, 0, s>>>(n, rowptr, col, root, w.root1);
+  SAAMG_LAUNCH();
+  SAAMG_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(int), s));
+  if (avg <= 8.0)
+    phase2<4>(n, rowptr, col, ids, seed, w.root1, w.aggroot, w.counter, s);
+  else if (avg <= 24.0)
+    phase2<8>(n, rowptr, col, ids, seed, w.root1, w.aggroot, w.counter, s);
+  else if (avg <= 64.0)
+    phase2<16>(n, rowptr, col, ids, seed, w.root1, w.aggroot, w.counter, s);
+  else
+    phase2<32>(n, rowptr, col, ids, seed, w.root1, w.aggroot, w.counter, s);
+  long long nagg = exclusive_scan_u8(root, w.rank, n, s);
+  agg_number_k<<<(n + 255) / 256, 256, 0, s>>>(n, w.aggroot, w.rank, agg);
+  SAAMG_LAUNCH();
+  int err = 0;
+  d2h_sync(&err, w.counter, sizeof(int), s);
+  if (err) fail(SAAMG_NUMERICAL, "aggregation left a node without an aggregate");
+  return (int)nagg;
+}
+
+void AggScratchBufs::alloc(int n, cudaStream_t s) {
+  state.alloc(n, s);
+  o1.alloc(n, s);
+  m1.alloc(n, s);
+  counter.alloc(1, s);
+  root1.alloc(n, s);
+  aggroot.alloc(n, s);
+  rank.alloc(n, s);
+}
+
+AggScratch AggScratchBufs::view() const {
+  AggScratch w;
+  w.state = state.p;
+  w.o1 = o1.p;
+  w.m1 = m1.p;
+  w.counter = counter.p;
+  w.root1 = root1.p;
+  w.aggroot = aggroot.p;
+  w.rank = rank.p;
+  return w;
+}
+
+}  // namespace saamg

@@ -1,0 +1,34 @@
+// MIS-2 aggregation (internal).
+#pragma once
+
+#include "common.cuh"
+
+namespace saamg {
+
+// Device scratch of the aggregation: n bytes x2, 8n bytes, 3 n ints and one counter.
+struct AggScratch {
+  unsigned char* state;
+  unsigned char* o1;
+  unsigned long long* m1;
+  int* counter;
+  int* root1;
+  int* aggroot;
+  int* rank;
+};
+
+struct AggScratchBufs {
+  Buf<unsigned char> state, o1;
+  Buf<unsigned long long> m1;
+  Buf<int> counter, root1, aggroot, rank;
+  void alloc(int n, cudaStream_t s);
+  AggScratch view() const;
+};
+
+// Root flags and aggregate index (roots numbered by ascending row) of the graph given by
+// the CSR pattern (rowptr, col); ids = node ids (NULL: the row index).  Returns the number
+// of aggregates.  Synchronises the stream once per round.
+int mis2_aggregate(int n, const int* rowptr, const int* col, long long nnz, const unsigned* ids,
+                   uint32_t seed, unsigned char* root, int* agg, const AggScratch& w,
+                   cudaStream_t s);
+
+}  // namespace saamg

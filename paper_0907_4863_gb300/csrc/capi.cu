@@ -1,0 +1,893 @@
+// C ABI of libsaamg: handles, the setup of the SA-AMG hierarchy (Sec. 3.2), the V-cycle
+// (Algorithm 1) and the PCG driver (Sec. 3.1).  Host code here only orchestrates; every
+// arithmetic step runs in the kernels of the other translation units.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "aggregate.cuh"
+#include "coarse.cuh"
+#include "csr.cuh"
+#include "galerkin.cuh"
+#include "operator.cuh"
+#include "pcg.cuh"
+
+namespace saamg {
+
+// ---------------------------------------------------------------------------
+// errors and allocation
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+void fail(saamg_status st, const std::string& msg) { throw Error{st, msg}; }
+
+void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
+  if (e == cudaSuccess) return;
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" +
+                  std::to_string(line) + ")";
+  if (e == cudaErrorMemoryAllocation) throw Error{SAAMG_ENOMEM, m};
+  throw Error{SAAMG_ECUDA, m};
+}
+
+static AllocHook g_alloc;
+
+AllocHook current_allocator() { return g_alloc; }
+
+void* dev_alloc(const AllocHook& h, size_t bytes, cudaStream_t s) {
+  void* p = nullptr;
+  if (h.alloc) {
+    p = h.alloc(bytes, (void*)s, h.ctx);
+    if (!p) fail(SAAMG_ENOMEM, "allocator hook returned NULL for " + std::to_string(bytes) + " bytes");
+    return p;
+  }
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(e == cudaErrorMemoryAllocation ? SAAMG_ENOMEM : SAAMG_ECUDA,
+         std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  return p;
+}
+
+void dev_free(const AllocHook& h, void* p, cudaStream_t s) {
+  if (!p) return;
+  if (h.free) {
+    h.free(p, (void*)s, h.ctx);
+    return;
+  }
+  // cudaFree synchronises the device: pending work that reads p finishes first
+  cudaFree(p);
+}
+
+HostScratch::~HostScratch() {
+  if (p) cudaFreeHost(p);
+}
+
+void* HostScratch::need(size_t b) {
+  if (b > bytes) {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    SAAMG_CUDA(cudaMallocHost(&p, b));
+    bytes = b;
+  }
+  return p;
+}
+
+void d2h_sync(void* host, const void* dev, size_t bytes, cudaStream_t s) {
+  SAAMG_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, s));
+  SAAMG_CUDA(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------------------
+// optional phase timing (SAAMG_PROFILE=1): synchronises at phase ends, prints to stderr
+// ---------------------------------------------------------------------------
+struct PhaseTimer {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  std::chrono::steady_clock::time_point t;
+  std::string out;
+  explicit PhaseTimer(cudaStream_t st) : s(st) {
+    const char* e = std::getenv("SAAMG_PROFILE");
+    on = e && e[0] == '1';
+    t = std::chrono::steady_clock::now();
+  }
+  void mark(const std::string& name) {
+    if (!on) return;
+    cudaStreamSynchronize(s);
+    auto now = std::chrono::steady_clock::now();
+    char buf[96];
+    std::snprintf(buf, sizeof(buf), " %s=%.2f", name.c_str(),
+                  std::chrono::duration<double, std::milli>(now - t).count());
+    out += buf;
+    t = now;
+  }
+  void flush(const char* what) {
+    if (on) std::fprintf(stderr, "[saamg %s ms]%s\n", what, out.c_str());
+  }
+};
+
+// ---------------------------------------------------------------------------
+// hierarchy
+// ---------------------------------------------------------------------------
+struct ChebCoef {
+  std::vector<double> c1, c2;
+};
+
+// Chebyshev steps on [hi/ratio, hi], hi = safety * lambda (Saad, Alg. 12.1 on D^-1 A):
+// step 0: c1 = 0, c2 = 1/theta; step k: rho_k = 1/(2 sigma - rho_{k-1}),
+// c1 = rho_k rho_{k-1}, c2 = 2 rho_k / delta.
+static ChebCoef cheb_coefficients(double lambda, double ratio, double safety, int degree) {
+  ChebCoef c;
+  const double hi = safety * lambda;
+  const double lo = hi / ratio;
+  const double theta = 0.5 * (hi + lo);
+  const double delta = 0.5 * (hi - lo);
+  const double sigma = theta / delta;
+  double rho_prev = 1.0 / sigma;
+  for (int k = 0; k < degree; ++k) {
+    if (k == 0) {
+      c.c1.push_back(0.0);
+      c.c2.push_back(1.0 / theta);
+    } else {
+      const double rho = 1.0 / (2.0 * sigma - rho_prev);
+      c.c1.push_back(rho * rho_prev);
+      c.c2.push_back((2.0 * rho) / delta);
+      rho_prev = rho;
+    }
+  }
+  return c;
+}
+
+struct Level {
+  int n = 0;
+  long long nnz = 0;
+  double avg = 0;
+  DevCsr A;                     // levels >= 1 (level 0 uses the operator's CSR / stencil)
+  Buf<double> invd;
+  Buf<float> invd32;
+  Buf<int> agg;
+  Buf<unsigned char> root;
+  DevCsr P, R;                  // to the next level
+  double lambda = 0, omega = 0;
+  ChebCoef cheb;
+  // V-cycle work vectors (FP64 and FP32 sets; only the one for the precision is allocated)
+  Buf<double> x0, x1, b, d, r;
+  Buf<float> fx0, fx1, fb, fd, fr;
+  Buf<float> P32, R32;          // FP32 values of P and R
+};
+
+}  // namespace saamg
+
+using namespace saamg;
+
+static const uint32_t kOpMagic = 0x5341504fu;    // "SAPO"
+static const uint32_t kHierMagic = 0x53414852u;  // "SAHR"
+
+struct saamg_operator {
+  uint32_t magic = kOpMagic;
+  OperatorData d;
+  cudaStream_t stream = nullptr;
+};
+
+struct saamg_hierarchy {
+  uint32_t magic = kHierMagic;
+  const saamg_operator* op = nullptr;
+  saamg_params prm{};
+  std::vector<std::unique_ptr<Level>> lev;
+  CoarseSolver coarse;
+  double setup_ms = 0;
+  // PCG state
+  Buf<double> bhat, xhat, r, z, p, q;
+  Buf<float> z32, r32;
+  Buf<double> part0, part1, part2;
+  Buf<PcgCtl> ctl;
+  HostScratch host;
+  Buf<double> scratch;
+  long long bytes = 0;
+};
+
+namespace saamg {
+
+static int status_of(const Error& e, const char* where) {
+  g_last_error = std::string(where) + ": " + e.msg;
+  return e.status;
+}
+
+template <class F>
+static saamg_status guard(const char* where, F&& f) {
+  try {
+    f();
+    return SAAMG_OK;
+  } catch (const Error& e) {
+    return (saamg_status)status_of(e, where);
+  } catch (const std::bad_alloc&) {
+    g_last_error = std::string(where) + ": host allocation failed";
+    return SAAMG_ENOMEM;
+  } catch (...) {
+    g_last_error = std::string(where) + ": unexpected exception";
+    return SAAMG_ECUDA;
+  }
+}
+
+static bool mixed(const saamg_hierarchy* h) { return h->prm.precision != SAAMG_PREC_FP64; }
+
+// Matrix of level l (level 0 = the operator's CSR)
+static const DevCsr& level_matrix(const saamg_hierarchy* h, int l) {
+  return l == 0 ? h->op->d.A : h->lev[l]->A;
+}
+
+static void alloc_level_vectors(saamg_hierarchy* h, Level& L, bool is0, cudaStream_t s) {
+  if (!mixed(h)) {
+    L.x0.alloc(L.n, s);
+    if (!is0) L.x1.alloc(L.n, s);
+    L.b.alloc(L.n, s);
+    L.d.alloc(L.n, s);
+    L.r.alloc(L.n, s);
+  } else {
+    L.fx0.alloc(L.n, s);
+    if (!is0) L.fx1.alloc(L.n, s);
+    L.fb.alloc(L.n, s);
+    L.fd.alloc(L.n, s);
+    L.fr.alloc(L.n, s);
+  }
+}
+
+static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaStream_t s,
+                       saamg_hierarchy* h) {
+  auto t0 = std::chrono::steady_clock::now();
+  PhaseTimer pt(s);
+  h->op = op;
+  h->prm = prm;
+  const OperatorData& od = op->d;
+  {
+    auto L0 = std::make_unique<Level>();
+    L0->n = od.n;
+    L0->nnz = od.nnz;
+    L0->avg = od.n ? (double)od.nnz / od.n : 0.0;
+    L0->invd.alloc(od.n, s);
+    L0->invd32.alloc(od.n, s);
+    csr_diag_inverse(od.A, L0->invd.p, L0->invd32.p, s);
+    h->lev.push_back(std::move(L0));
+  }
+  int l = 0;
+  AggScratchBufs agg_scratch;
+  agg_scratch.alloc(od.n > 0 ? od.n : 1, s);
+  for (;;) {
+    Level& L = *h->lev[l];
+    const DevCsr& A = level_matrix(h, l);
+    if (L.n <= prm.max_coarse || l == prm.max_levels - 1 || l == SAAMG_MAX_LEVELS - 1) break;
+    const unsigned seed = 0x9E3779B9u * (unsigned)(l + 1);
+    L.root.alloc(L.n, s);
+    L.agg.alloc(L.n, s);
+    const unsigned* ids = (l == 0) ? od.ids.p : nullptr;
+    pt.mark("L" + std::to_string(l) + ".pre");
+    int nagg = mis2_aggregate(L.n, A.rowptr.p, A.col.p, A.nnz, ids, seed, L.root.p, L.agg.p,
+                              agg_scratch.view(), s);
+    pt.mark("L" + std::to_string(l) + ".mis2agg");
+    if (10LL * nagg > 9LL * L.n) {  // coarsening stalled
+      L.root.release();
+      L.agg.release();
+      break;
+    }
+    L.lambda = power_lambda(A, L.invd.p, ids, prm.power_iters, s);
+    L.omega = 4.0 / (3.0 * L.lambda);
+    pt.mark("L" + std::to_string(l) + ".lambda");
+    DevCsr T, AT, AP;
+    tentative(L.agg.p, L.n, nagg, T, s);
+    spgemm(A, T, AT, s);
+    smoothed_prolongator(AT, L.agg.p, L.invd.p, L.omega, L.P, s);
+    pt.mark("L" + std::to_string(l) + ".P");
+    transpose(L.P, L.R, s);
+    pt.mark("L" + std::to_string(l) + ".R");
+    spgemm(A, L.P, AP, s);
+    pt.mark("L" + std::to_string(l) + ".AP");
+    auto N = std::make_unique<Level>();
+    spgemm(L.R, AP, N->A, s);
+    pt.mark("L" + std::to_string(l) + ".RAP");
+    N->n = N->A.n;
+    N->nnz = N->A.nnz;
+    N->avg = N->n ? (double)N->nnz / N->n : 0.0;
+    N->invd.alloc(N->n, s);
+    N->invd32.alloc(N->n, s);
+    csr_diag_inverse(N->A, N->invd.p, N->invd32.p, s);
+    h->lev.push_back(std::move(N));
+    ++l;
+  }
+  const int nl = (int)h->lev.size();
+  Level& C = *h->lev[nl - 1];
+  if (C.n > 16384) fail(SAAMG_NUMERICAL, "coarsest level has more than 16384 unknowns");
+  pt.mark("levels");
+  coarse_factor(level_matrix(h, nl - 1), h->coarse, s);
+  pt.mark("coarseLU");
+  for (int q = 0; q < nl; ++q) {
+    Level& L = *h->lev[q];
+    if (q < nl - 1) L.cheb = cheb_coefficients(L.lambda, prm.cheb_ratio, prm.cheb_safety, prm.cheb_degree);
+    alloc_level_vectors(h, L, q == 0, s);
+    if (mixed(h)) {
+      if (q >= 1) {
+        if (prm.precision == SAAMG_PREC_FP32) {
+          L.A.val32.alloc(L.A.nnz, s);
+          to_float(L.A.val.p, L.A.val32.p, L.A.nnz, s);
+        } else {
+          L.A.val16.alloc(L.A.nnz, s);
+          to_bf16(L.A.val.p, L.A.val16.p, L.A.nnz, s);
+        }
+      }
+      if (q < nl - 1) {
+        L.P32.alloc(L.P.nnz, s);
+        to_float(L.P.val.p, L.P32.p, L.P.nnz, s);
+        L.R32.alloc(L.R.nnz, s);
+        to_float(L.R.val.p, L.R32.p, L.R.nnz, s);
+      }
+    }
+  }
+  const int n = od.n;
+  h->bhat.alloc(n, s);
+  h->xhat.alloc(n, s);
+  h->r.alloc(n, s);
+  h->z.alloc(n, s);
+  h->p.alloc(n, s);
+  h->q.alloc(n, s);
+  if (mixed(h)) {
+    h->z32.alloc(n, s);
+    h->r32.alloc(n, s);
+  }
+  h->part0.alloc(kRedBlocks, s);
+  h->part1.alloc(kRedBlocks, s);
+  h->part2.alloc(kRedBlocks, s);
+  h->ctl.alloc(1, s);
+  SAAMG_CUDA(cudaStreamSynchronize(s));
+  pt.mark("finish");
+  pt.flush("setup");
+  long long bytes = 0;
+  for (auto& L : h->lev) {
+    bytes += L->A.bytes() + L->P.bytes() + L->R.bytes() + L->invd.bytes() + L->invd32.bytes() +
+             L->agg.bytes() + L->root.bytes() + L->x0.bytes() + L->x1.bytes() + L->b.bytes() +
+             L->d.bytes() + L->r.bytes() + L->fx0.bytes() + L->fx1.bytes() + L->fb.bytes() +
+             L->fd.bytes() + L->fr.bytes() + L->P32.bytes() + L->R32.bytes();
+  }
+  bytes += h->coarse.inv.bytes() + 6LL * n * 8 + (mixed(h) ? 8LL * n : 0);
+  h->bytes = bytes;
+  h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// --- V-cycle (Algorithm 1) -------------------------------------------------
+// Level l smooths b_l -> x_l; the final iterate lands in `out` (length n_l).  The
+// Chebyshev steps ping-pong between two buffers: with nu pre- and nu post-steps there are
+// 2 nu - 1 swaps after the first step, so starting in `tmp` ends in `out`.
+template <class T>
+struct LevelVecs;
+
+template <>
+struct LevelVecs<double> {
+  static double* x0(Level& L) { return L.x0.p; }
+  static double* x1(Level& L) { return L.x1.p; }
+  static double* b(Level& L) { return L.b.p; }
+  static double* d(Level& L) { return L.d.p; }
+  static double* r(Level& L) { return L.r.p; }
+};
+template <>
+struct LevelVecs<float> {
+  static float* x0(Level& L) { return L.fx0.p; }
+  static float* x1(Level& L) { return L.fx1.p; }
+  static float* b(Level& L) { return L.fb.p; }
+  static float* d(Level& L) { return L.fd.p; }
+  static float* r(Level& L) { return L.fr.p; }
+};
+
+template <class T>
+static const T* invd_of(Level& L);
+template <>
+const double* invd_of<double>(Level& L) {
+  return L.invd.p;
+}
+template <>
+const float* invd_of<float>(Level& L) {
+  return L.invd32.p;
+}
+
+// y (+)= M x for a coarse matrix in the working precision
+template <class T>
+static void level_csr(saamg_hierarchy* h, int l, int mode, const T* x, T* y, const T* b, T* d,
+                      T c1, T c2, cudaStream_t s);
+
+template <>
+void level_csr<double>(saamg_hierarchy* h, int l, int mode, const double* x, double* y,
+                       const double* b, double* d, double c1, double c2, cudaStream_t s) {
+  Level& L = *h->lev[l];
+  csr_apply<double, double>(mode, L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, L.avg, x, y, b, d,
+                            L.invd.p, c1, c2, nullptr, s, SAAMG_KT_COARSE);
+}
+
+template <>
+void level_csr<float>(saamg_hierarchy* h, int l, int mode, const float* x, float* y,
+                      const float* b, float* d, float c1, float c2, cudaStream_t s) {
+  Level& L = *h->lev[l];
+  if (h->prm.precision == SAAMG_PREC_FP32)
+    csr_apply<float, float>(mode, L.n, L.A.rowptr.p, L.A.col.p, L.A.val32.p, L.avg, x, y, b, d,
+                            L.invd32.p, c1, c2, nullptr, s, SAAMG_KT_COARSE);
+  else
+    csr_apply<float, __nv_bfloat16>(mode, L.n, L.A.rowptr.p, L.A.col.p, L.A.val16.p, L.avg, x, y,
+                                    b, d, L.invd32.p, c1, c2, nullptr, s, SAAMG_KT_COARSE);
+}
+
+template <class T>
+static void transfer(saamg_hierarchy* h, int l, bool restrict_, const T* x, T* y, cudaStream_t s);
+
+template <>
+void transfer<double>(saamg_hierarchy* h, int l, bool restrict_, const double* x, double* y,
+                      cudaStream_t s) {
+  Level& L = *h->lev[l];
+  const DevCsr& M = restrict_ ? L.R : L.P;
+  csr_apply<double, double>(restrict_ ? CSR_SPMV : CSR_ADD, M.n, M.rowptr.p, M.col.p, M.val.p,
+                            M.n ? (double)M.nnz / M.n : 0.0, x, y, nullptr, nullptr, nullptr, 0.0,
+                            0.0, nullptr, s, SAAMG_KT_TRANSFER);
+}
+
+template <>
+void transfer<float>(saamg_hierarchy* h, int l, bool restrict_, const float* x, float* y,
+                     cudaStream_t s) {
+  Level& L = *h->lev[l];
+  const DevCsr& M = restrict_ ? L.R : L.P;
+  const float* v = restrict_ ? L.R32.p : L.P32.p;
+  csr_apply<float, float>(restrict_ ? CSR_SPMV : CSR_ADD, M.n, M.rowptr.p, M.col.p, v,
+                          M.n ? (double)M.nnz / M.n : 0.0, x, y, nullptr, nullptr, nullptr, 0.0f,
+                          0.0f, nullptr, s, SAAMG_KT_TRANSFER);
+}
+
+template <class T>
+static void smooth_step(saamg_hierarchy* h, int l, int mode0, const T* x, T* y, const T* b, T* d,
+                        T c1, T c2, cudaStream_t s) {
+  if (l == 0) {
+    StencilDev<T> S = h->op->d.template view<T>();
+    stencil_apply<T>(S, mode0 == CSR_CHEB0 ? ST_CHEB0 : (mode0 == CSR_RESID ? ST_RESID : ST_CHEB),
+                     x, y, b, d, c1, c2, nullptr, s);
+  } else {
+    level_csr<T>(h, l, mode0, x, y, b, d, c1, c2, s);
+  }
+}
+
+template <class T>
+static void vcycle_level(saamg_hierarchy* h, int l, const T* b, T* out, cudaStream_t s) {
+  const int nl = (int)h->lev.size();
+  Level& L = *h->lev[l];
+  if (l == nl - 1) {
+    coarse_apply<T>(h->coarse, b, out, s);
+    return;
+  }
+  const int nu = (int)L.cheb.c1.size();
+  T* bufs[2] = {LevelVecs<T>::x0(L), out};
+  T* d = LevelVecs<T>::d(L);
+  int cur = 0;
+  // presmoothing from x = 0
+  smooth_step<T>(h, l, CSR_CHEB0, nullptr, bufs[cur], b, d, T(0), (T)L.cheb.c2[0], s);
+  for (int k = 1; k < nu; ++k) {
+    smooth_step<T>(h, l, CSR_CHEB, bufs[cur], bufs[1 - cur], b, d, (T)L.cheb.c1[k],
+                   (T)L.cheb.c2[k], s);
+    cur = 1 - cur;
+  }
+  // residual, restriction, coarse correction
+  T* r = LevelVecs<T>::r(L);
+  smooth_step<T>(h, l, CSR_RESID, bufs[cur], r, b, nullptr, T(0), T(0), s);
+  Level& N = *h->lev[l + 1];
+  T* bc = LevelVecs<T>::b(N);
+  T* vc = (l + 1 == nl - 1) ? LevelVecs<T>::x0(N) : LevelVecs<T>::x1(N);
+  transfer<T>(h, l, true, r, bc, s);
+  vcycle_level<T>(h, l + 1, bc, vc, s);
+  transfer<T>(h, l, false, vc, bufs[cur], s);
+  // postsmoothing with the same polynomial
+  for (int k = 0; k < nu; ++k) {
+    smooth_step<T>(h, l, CSR_CHEB, bufs[cur], bufs[1 - cur], b, d, (T)L.cheb.c1[k],
+                   (T)L.cheb.c2[k], s);
+    cur = 1 - cur;
+  }
+  if (bufs[cur] != out) {
+    SAAMG_CUDA(cudaMemcpyAsync(out, bufs[cur], sizeof(T) * L.n, cudaMemcpyDeviceToDevice, s));
+  }
+}
+
+// z = M r on level 0, FP64 in and out (FP32 inside in mixed mode)
+static void apply_preconditioner(saamg_hierarchy* h, const double* r, double* z, float* z32,
+                                 cudaStream_t s) {
+  const int n = h->op->d.n;
+  if (!mixed(h)) {
+    vcycle_level<double>(h, 0, r, z, s);
+  } else {
+    to_float(r, h->r32.p, n, s);
+    vcycle_level<float>(h, 0, h->r32.p, z32, s);
+  }
+}
+
+// --- PCG --------------------------------------------------------------------
+static int pcg_impl(saamg_hierarchy* h, double rtol, cudaStream_t s, saamg_solve_info* info) {
+  const OperatorData& od = h->op->d;
+  const int n = od.n;
+  const bool mx = mixed(h);
+  double* x = h->xhat.p;
+  double* r = h->r.p;
+  double* p = h->p.p;
+  double* q = h->q.p;
+  double* z = h->z.p;
+  PcgCtl* ctl = h->ctl.p;
+  PcgCtl* hc = static_cast<PcgCtl*>(h->host.need(sizeof(PcgCtl)));
+  const StencilDev<double> S = od.view<double>();
+  info->iters = 0;
+  info->converged = 0;
+  info->relres = 0;
+  info->relres_true = 0;
+  if (n == 0) {
+    info->converged = 1;
+    return SAAMG_OK;
+  }
+  // ||b||
+  dot_partials<double, double>(n, h->bhat.p, h->bhat.p, h->part0.p, s);
+  Buf<double>& sc = h->scratch;
+  if (!sc.p) sc.alloc(4, s);
+  sum_partials(h->part0.p, kRedBlocks, sc.p, s);
+  double bb = 0;
+  d2h_sync(&bb, sc.p, sizeof(double), s);
+  if (!std::isfinite(bb)) fail(SAAMG_NUMERICAL, "right-hand side holds NaN or Inf");
+  if (bb == 0.0) {
+    SAAMG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    info->converged = 1;
+    return SAAMG_OK;
+  }
+  const double bnorm = std::sqrt(bb);
+  // r = b - A x
+  stencil_apply<double>(S, ST_RESID, x, r, h->bhat.p, nullptr, 0.0, 0.0, nullptr, s);
+  PcgCtl init{};
+  init.tol2 = (rtol * bnorm) * (rtol * bnorm);
+  SAAMG_CUDA(cudaMemcpyAsync(ctl, &init, sizeof(PcgCtl), cudaMemcpyHostToDevice, s));
+  dot_partials<double, double>(n, r, r, h->part0.p, s);
+  pcg_check(h->part0.p, ctl, s);  // counts one; reset below
+  d2h_sync(hc, ctl, sizeof(PcgCtl), s);
+  double rr = hc->rr;
+  if (!std::isfinite(rr)) fail(SAAMG_NUMERICAL, "initial residual holds NaN or Inf");
+  init.rr = rr;
+  init.iters = 0;
+  SAAMG_CUDA(cudaMemcpyAsync(ctl, &init, sizeof(PcgCtl), cudaMemcpyHostToDevice, s));
+  int status = SAAMG_NOT_CONVERGED;
+  if (rr <= init.tol2) {
+    status = SAAMG_OK;
+    info->converged = 1;
+  } else {
+    apply_preconditioner(h, r, z, h->z32.p, s);
+    if (mx) {
+      vec_copy_to_double<float>(n, h->z32.p, p, s);
+      dot_partials<double, float>(n, r, h->z32.p, h->part0.p, s);
+    } else {
+      vec_copy_to_double<double>(n, z, p, s);
+      dot_partials<double, double>(n, r, z, h->part0.p, s);
+    }
+    pcg_beta(h->part0.p, nullptr, -1, ctl, s);  // rz of the first direction
+    for (int it = 1; it <= h->prm.maxit; ++it) {
+      stencil_apply<double>(S, ST_SPMV_DOT, p, q, nullptr, nullptr, 0.0, 0.0, h->part0.p, s);
+      pcg_alpha(h->part0.p, ctl, s);
+      pcg_update(n, x, r, p, q, ctl, h->part1.p, s);
+      pcg_check(h->part1.p, ctl, s);
+      d2h_sync(hc, ctl, sizeof(PcgCtl), s);
+      info->iters = hc->iters;
+      if (hc->breakdown) {
+        status = SAAMG_NUMERICAL;
+        break;
+      }
+      if (hc->converged) {
+        status = SAAMG_OK;
+        info->converged = 1;
+        break;
+      }
+      apply_preconditioner(h, r, z, h->z32.p, s);
+      if (mx) {
+        dot_partials<double, float>(n, r, h->z32.p, h->part0.p, s);
+        if (h->prm.beta_rule == 1) dot_partials<float, double>(n, h->z32.p, q, h->part2.p, s);
+        pcg_beta(h->part0.p, h->prm.beta_rule == 1 ? h->part2.p : nullptr, h->prm.beta_rule, ctl, s);
+        pcg_direction<float>(n, h->z32.p, p, ctl, s);
+      } else {
+        dot_partials<double, double>(n, r, z, h->part0.p, s);
+        if (h->prm.beta_rule == 1) dot_partials<double, double>(n, z, q, h->part2.p, s);
+        pcg_beta(h->part0.p, h->prm.beta_rule == 1 ? h->part2.p : nullptr, h->prm.beta_rule, ctl, s);
+        pcg_direction<double>(n, z, p, ctl, s);
+      }
+    }
+  }
+  d2h_sync(hc, ctl, sizeof(PcgCtl), s);
+  info->relres = std::sqrt(hc->rr) / bnorm;
+  // true residual of the scaled system
+  stencil_apply<double>(S, ST_RESID, x, q, h->bhat.p, nullptr, 0.0, 0.0, nullptr, s);
+  dot_partials<double, double>(n, q, q, h->part0.p, s);
+  sum_partials(h->part0.p, kRedBlocks, sc.p, s);
+  double tr = 0;
+  d2h_sync(&tr, sc.p, sizeof(double), s);
+  info->relres_true = std::sqrt(tr) / bnorm;
+  if (status == SAAMG_NUMERICAL) g_last_error = "saamg_solve: breakdown (NaN/Inf or p'Ap = 0)";
+  return status;
+}
+
+}  // namespace saamg
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+saamg_status saamg_params_default(saamg_params* p) {
+  if (!p) return SAAMG_EINVAL;
+  p->cheb_degree = 2;
+  p->cheb_ratio = 30.0;
+  p->cheb_safety = 1.1;
+  p->max_coarse = 1000;
+  p->max_levels = 10;
+  p->power_iters = 10;
+  p->precision = SAAMG_PREC_FP64;
+  p->beta_rule = 0;
+  p->maxit = 1000;
+  return SAAMG_OK;
+}
+
+saamg_status saamg_set_allocator(saamg_alloc_fn alloc, saamg_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) {
+    g_last_error = "saamg_set_allocator: alloc and free must both be set or both be NULL";
+    return SAAMG_EINVAL;
+  }
+  g_alloc.alloc = alloc;
+  g_alloc.free = free_fn;
+  g_alloc.ctx = ctx;
+  return SAAMG_OK;
+}
+
+const char* saamg_last_error(void) { return g_last_error.c_str(); }
+
+saamg_status saamg_build_operator(const saamg_domain* domain, const saamg_grid* grid, int mode,
+                                  void* stream, saamg_operator** out) {
+  return guard("saamg_build_operator", [&] {
+    if (!domain || !grid || !out) fail(SAAMG_EINVAL, "NULL argument");
+    *out = nullptr;
+    GeomParams g{};
+    g.nx = grid->n[0];
+    g.ny = grid->n[1];
+    g.nz = grid->n[2];
+    for (int d = 0; d < 3; ++d) {
+      g.h[d] = grid->h[d];
+      g.o[d] = grid->origin[d];
+      if (!(grid->h[d] > 0.0) || !std::isfinite(grid->h[d]) || !std::isfinite(grid->origin[d]))
+        fail(SAAMG_EINVAL, "grid spacing must be positive and finite");
+    }
+    if (g.nx < 1 || g.ny < 1 || g.nz < 2) fail(SAAMG_EINVAL, "grid needs n >= 1 and nz >= 2");
+    if (domain->zbc != SAAMG_Z_ROBIN && domain->zbc != SAAMG_Z_DIRICHLET)
+      fail(SAAMG_EINVAL, "unknown z boundary");
+    if (domain->zbc == SAAMG_Z_DIRICHLET && g.nz < 3) fail(SAAMG_EINVAL, "Dirichlet ends need nz >= 3");
+    if (!(domain->a > 0) || !(domain->b > 0) || !(domain->taper > 0) || !std::isfinite(domain->a) ||
+        !std::isfinite(domain->b) || !std::isfinite(domain->taper) || !std::isfinite(domain->cx) ||
+        !std::isfinite(domain->cy))
+      fail(SAAMG_EINVAL, "domain semi-axes and taper must be positive and finite");
+    if (mode < SAAMG_BC_CONSTANT || mode > SAAMG_BC_QUADRATIC) fail(SAAMG_EINVAL, "unknown boundary mode");
+    if ((long long)g.nx * g.ny * g.nz > (1LL << 31) - 1) fail(SAAMG_EINVAL, "box larger than 2^31 nodes");
+    g.a = domain->a;
+    g.b = domain->b;
+    g.taper = domain->taper;
+    g.cx = domain->cx;
+    g.cy = domain->cy;
+    g.zbc = domain->zbc;
+    g.sym = domain->symmetrize_gamma2 ? 1 : 0;
+    g.mode = mode;
+    auto op = std::make_unique<saamg_operator>();
+    op->stream = (cudaStream_t)stream;
+    build_operator_data(g, (cudaStream_t)stream, op->d);
+    *out = op.release();
+  });
+}
+
+saamg_status saamg_operator_size(const saamg_operator* op, int* n, long long* nnz) {
+  return guard("saamg_operator_size", [&] {
+    if (!op || op->magic != kOpMagic) fail(SAAMG_EINVAL, "not an operator handle");
+    if (n) *n = op->d.n;
+    if (nnz) *nnz = op->d.nnz;
+  });
+}
+
+saamg_status saamg_operator_copy(const saamg_operator* op, int* node_of_row, double* scale,
+                                 int* rowptr, int* col, double* val, unsigned char* is_regular,
+                                 void* stream) {
+  return guard("saamg_operator_copy", [&] {
+    if (!op || op->magic != kOpMagic) fail(SAAMG_EINVAL, "not an operator handle");
+    cudaStream_t s = (cudaStream_t)stream;
+    const OperatorData& d = op->d;
+    auto cp = [&](void* dst, const void* src, size_t b) {
+      if (dst && b) SAAMG_CUDA(cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToHost, s));
+    };
+    cp(node_of_row, d.ids.p, sizeof(int) * d.n);
+    cp(scale, d.scale.p, sizeof(double) * d.n);
+    cp(rowptr, d.A.rowptr.p, sizeof(int) * (d.n + 1));
+    cp(col, d.A.col.p, sizeof(int) * d.nnz);
+    cp(val, d.A.val.p, sizeof(double) * d.nnz);
+    cp(is_regular, d.regular.p, d.n);
+    SAAMG_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+saamg_status saamg_operator_apply(const saamg_operator* op, const double* x, double* y,
+                                  void* stream) {
+  return guard("saamg_operator_apply", [&] {
+    if (!op || op->magic != kOpMagic) fail(SAAMG_EINVAL, "not an operator handle");
+    if (op->d.n > 0 && (!x || !y)) fail(SAAMG_EINVAL, "NULL vector");
+    stencil_apply<double>(op->d.view<double>(), ST_SPMV, x, y, nullptr, nullptr, 0.0, 0.0, nullptr,
+                          (cudaStream_t)stream);
+  });
+}
+
+saamg_status saamg_setup(const saamg_operator* op, const saamg_params* params, void* stream,
+                         saamg_hierarchy** out) {
+  return guard("saamg_setup", [&] {
+    if (!op || op->magic != kOpMagic || !out) fail(SAAMG_EINVAL, "NULL or invalid argument");
+    *out = nullptr;
+    saamg_params prm;
+    saamg_params_default(&prm);
+    if (params) prm = *params;
+    if (prm.cheb_degree < 1 || prm.cheb_degree > 16) fail(SAAMG_EINVAL, "cheb_degree must be in 1..16");
+    if (!(prm.cheb_ratio > 1.0) || !(prm.cheb_safety > 0.0)) fail(SAAMG_EINVAL, "bad Chebyshev interval");
+    if (prm.max_coarse < 1 || prm.max_levels < 1 || prm.power_iters < 1 || prm.maxit < 0)
+      fail(SAAMG_EINVAL, "max_coarse, max_levels, power_iters must be >= 1");
+    if (prm.precision < SAAMG_PREC_FP64 || prm.precision > SAAMG_PREC_FP32_BF16)
+      fail(SAAMG_EINVAL, "unknown precision");
+    if (prm.beta_rule != 0 && prm.beta_rule != 1) fail(SAAMG_EINVAL, "beta_rule must be 0 or 1");
+    auto h = std::make_unique<saamg_hierarchy>();
+    setup_impl(op, prm, (cudaStream_t)stream, h.get());
+    *out = h.release();
+  });
+}
+
+saamg_status saamg_hierarchy_get_info(const saamg_hierarchy* h, saamg_hierarchy_info* info) {
+  return guard("saamg_hierarchy_get_info", [&] {
+    if (!h || h->magic != kHierMagic || !info) fail(SAAMG_EINVAL, "NULL or invalid argument");
+    std::memset(info, 0, sizeof(*info));
+    info->levels = (int)h->lev.size();
+    for (int l = 0; l < info->levels; ++l) {
+      info->n[l] = h->lev[l]->n;
+      info->nnz[l] = h->lev[l]->nnz;
+      info->nnz_p[l] = h->lev[l]->P.nnz;
+      info->lambda[l] = h->lev[l]->lambda;
+    }
+    info->device_bytes = h->bytes;
+    info->setup_ms = h->setup_ms;
+  });
+}
+
+saamg_status saamg_hierarchy_copy_level(const saamg_hierarchy* h, int l, int* rowptr, int* col,
+                                        double* val, int* agg, unsigned char* root, int* p_rowptr,
+                                        int* p_col, double* p_val, int* r_rowptr, int* r_col,
+                                        double* r_val, void* stream) {
+  return guard("saamg_hierarchy_copy_level", [&] {
+    if (!h || h->magic != kHierMagic) fail(SAAMG_EINVAL, "not a hierarchy handle");
+    if (l < 0 || l >= (int)h->lev.size()) fail(SAAMG_EINVAL, "level out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Level& L = *h->lev[l];
+    const DevCsr& A = level_matrix(h, l);
+    auto cp = [&](void* dst, const void* src, size_t b) {
+      if (dst && src && b) SAAMG_CUDA(cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToHost, s));
+    };
+    cp(rowptr, A.rowptr.p, sizeof(int) * (A.n + 1));
+    cp(col, A.col.p, sizeof(int) * A.nnz);
+    cp(val, A.val.p, sizeof(double) * A.nnz);
+    cp(agg, L.agg.p, sizeof(int) * (L.agg.p ? L.n : 0));
+    cp(root, L.root.p, L.root.p ? L.n : 0);
+    if (L.P.rowptr.p) {
+      cp(p_rowptr, L.P.rowptr.p, sizeof(int) * (L.P.n + 1));
+      cp(p_col, L.P.col.p, sizeof(int) * L.P.nnz);
+      cp(p_val, L.P.val.p, sizeof(double) * L.P.nnz);
+      cp(r_rowptr, L.R.rowptr.p, sizeof(int) * (L.R.n + 1));
+      cp(r_col, L.R.col.p, sizeof(int) * L.R.nnz);
+      cp(r_val, L.R.val.p, sizeof(double) * L.R.nnz);
+    }
+    SAAMG_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+saamg_status saamg_vcycle(const saamg_hierarchy* hc, const double* r, double* z, void* stream) {
+  return guard("saamg_vcycle", [&] {
+    if (!hc || hc->magic != kHierMagic) fail(SAAMG_EINVAL, "not a hierarchy handle");
+    saamg_hierarchy* h = const_cast<saamg_hierarchy*>(hc);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = h->op->d.n;
+    if (n == 0) return;
+    if (!r || !z) fail(SAAMG_EINVAL, "NULL vector");
+    if (!mixed(h)) {
+      vcycle_level<double>(h, 0, r, z, s);
+    } else {
+      apply_preconditioner(h, r, nullptr, h->z32.p, s);
+      to_double(h->z32.p, z, n, s);
+    }
+  });
+}
+
+saamg_status saamg_solve(saamg_hierarchy* h, const double* rho, double* phi, double rtol,
+                         void* stream, saamg_solve_info* info) {
+  saamg_solve_info local{};
+  if (!info) info = &local;
+  int st = SAAMG_OK;
+  auto t0 = std::chrono::steady_clock::now();
+  saamg_status g = guard("saamg_solve", [&] {
+    if (!h || h->magic != kHierMagic) fail(SAAMG_EINVAL, "not a hierarchy handle");
+    if (!rho || !phi) fail(SAAMG_EINVAL, "NULL rho or phi");
+    if (!(rtol > 0.0) || !std::isfinite(rtol)) fail(SAAMG_EINVAL, "rtol must be positive");
+    cudaStream_t s = (cudaStream_t)stream;
+    const OperatorData& od = h->op->d;
+    gather_rhs(od, rho, phi, h->bhat.p, h->xhat.p, s);
+    st = pcg_impl(h, rtol, s, info);
+    scatter_solution(od, h->xhat.p, phi, s);
+    SAAMG_CUDA(cudaStreamSynchronize(s));
+  });
+  info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return g != SAAMG_OK ? g : (saamg_status)st;
+}
+
+saamg_status saamg_solve_host(saamg_hierarchy* h, const double* rho_host, double* phi_host,
+                              double rtol, void* stream, saamg_solve_info* info) {
+  saamg_solve_info local{};
+  if (!info) info = &local;
+  int st = SAAMG_OK;
+  auto t0 = std::chrono::steady_clock::now();
+  saamg_status g = guard("saamg_solve_host", [&] {
+    if (!h || h->magic != kHierMagic) fail(SAAMG_EINVAL, "not a hierarchy handle");
+    if (!rho_host || !phi_host) fail(SAAMG_EINVAL, "NULL rho or phi");
+    if (!(rtol > 0.0) || !std::isfinite(rtol)) fail(SAAMG_EINVAL, "rtol must be positive");
+    cudaStream_t s = (cudaStream_t)stream;
+    const OperatorData& od = h->op->d;
+    size_t nbox = (size_t)od.g.nx * od.g.ny * od.g.nz;
+    Buf<double> rho, phi;
+    rho.alloc(nbox, s);
+    phi.alloc(nbox, s);
+    SAAMG_CUDA(cudaMemcpyAsync(rho.p, rho_host, nbox * 8, cudaMemcpyHostToDevice, s));
+    SAAMG_CUDA(cudaMemcpyAsync(phi.p, phi_host, nbox * 8, cudaMemcpyHostToDevice, s));
+    gather_rhs(od, rho.p, phi.p, h->bhat.p, h->xhat.p, s);
+    st = pcg_impl(h, rtol, s, info);
+    scatter_solution(od, h->xhat.p, phi.p, s);
+    SAAMG_CUDA(cudaMemcpyAsync(phi_host, phi.p, nbox * 8, cudaMemcpyDeviceToHost, s));
+    SAAMG_CUDA(cudaStreamSynchronize(s));
+  });
+  info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return g != SAAMG_OK ? g : (saamg_status)st;
+}
+
+saamg_status saamg_mis2_aggregate(int n, const int* rowptr, const int* col, const uint32_t* ids,
+                                  uint32_t seed, unsigned char* root, int* agg, int* n_agg,
+                                  void* stream) {
+  return guard("saamg_mis2_aggregate", [&] {
+    if (n < 0 || !n_agg) fail(SAAMG_EINVAL, "bad size or NULL n_agg");
+    *n_agg = 0;
+    if (n == 0) return;
+    if (!rowptr || !col || !root || !agg) fail(SAAMG_EINVAL, "NULL array");
+    cudaStream_t s = (cudaStream_t)stream;
+    int nnz = 0;
+    d2h_sync(&nnz, rowptr + n, sizeof(int), s);
+    AggScratchBufs w;
+    w.alloc(n, s);
+    *n_agg = mis2_aggregate(n, rowptr, col, nnz, ids, seed, root, agg, w.view(), s);
+    SAAMG_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+void saamg_free(void* handle) {
+  if (!handle) return;
+  uint32_t magic = *static_cast<uint32_t*>(handle);
+  try {
+    if (magic == kOpMagic) {
+      saamg_operator* op = static_cast<saamg_operator*>(handle);
+      cudaStreamSynchronize(op->stream);
+      op->magic = 0;
+      delete op;
+    } else if (magic == kHierMagic) {
+      saamg_hierarchy* h = static_cast<saamg_hierarchy*>(handle);
+      cudaDeviceSynchronize();
+      h->magic = 0;
+      delete h;
+    }
+  } catch (...) {
+  }
+}
+
+}  // extern "C"

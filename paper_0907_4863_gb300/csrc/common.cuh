@@ -1,0 +1,171 @@
+// Internal declarations shared by the translation units of libsaamg (not part of the ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <utility>
+
+#include "saamg.h"
+
+namespace saamg {
+
+// ---------------------------------------------------------------------------
+// Errors: every internal failure throws Error; the C ABI converts it to a status.
+// ---------------------------------------------------------------------------
+struct Error {
+  saamg_status status;
+  std::string msg;
+};
+
+[[noreturn]] void fail(saamg_status st, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what, const char* file, int line);
+
+void count_launch();
+
+#define SAAMG_CUDA(x) ::saamg::check_cuda((x), #x, __FILE__, __LINE__)
+#define SAAMG_LAUNCH()                                                                  \
+  do {                                                                                  \
+    ::saamg::count_launch();                                                            \
+    ::saamg::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__);       \
+  } while (0)
+
+// Opt-in timing of kernel classes with CUDA events recorded on the launching stream.
+// KernelTimer t(cls, rows, stream); <launch>; -- records a start event on construction
+// and a stop event on destruction when timing is enabled; otherwise does nothing.
+struct KernelTimer {
+  int cls;
+  long long rows;
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr;
+  KernelTimer(int kclass, long long nrows, cudaStream_t stream);
+  ~KernelTimer();
+};
+
+// ---------------------------------------------------------------------------
+// Device memory through the installed allocator hook.
+// ---------------------------------------------------------------------------
+struct AllocHook {
+  saamg_alloc_fn alloc = nullptr;
+  saamg_free_fn free = nullptr;
+  void* ctx = nullptr;
+};
+AllocHook current_allocator();
+void* dev_alloc(const AllocHook& h, size_t bytes, cudaStream_t s);
+void dev_free(const AllocHook& h, void* p, cudaStream_t s);
+
+// Owning device array (move-only).  Memory comes from the hook captured at allocation.
+template <class T>
+struct Buf {
+  T* p = nullptr;
+  size_t n = 0;
+  AllocHook hook;
+  cudaStream_t stream = nullptr;
+
+  Buf() = default;
+  Buf(const Buf&) = delete;
+  Buf& operator=(const Buf&) = delete;
+  Buf(Buf&& o) noexcept { swap(o); }
+  Buf& operator=(Buf&& o) noexcept {
+    if (this != &o) {
+      release();
+      swap(o);
+    }
+    return *this;
+  }
+  ~Buf() { release(); }
+  void swap(Buf& o) noexcept {
+    std::swap(p, o.p);
+    std::swap(n, o.n);
+    std::swap(hook, o.hook);
+    std::swap(stream, o.stream);
+  }
+  void alloc(size_t count, cudaStream_t s) {
+    release();
+    hook = current_allocator();
+    stream = s;
+    n = count;
+    p = static_cast<T*>(dev_alloc(hook, (count > 0 ? count : 1) * sizeof(T), s));
+  }
+  void release() noexcept {
+    if (p) {
+      try {
+        dev_free(hook, p, stream);
+      } catch (...) {
+      }
+    }
+    p = nullptr;
+    n = 0;
+  }
+  size_t bytes() const { return n * sizeof(T); }
+  T* get() const { return p; }
+};
+
+// Pinned host scratch used to read small device results back.
+struct HostScratch {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~HostScratch();
+  void* need(size_t b);
+};
+
+// ---------------------------------------------------------------------------
+// Level-0 stencil description (matrix-free operator)
+// ---------------------------------------------------------------------------
+// One record per x-line (j,k), line index L = j + ny*k.  The unknowns of a line form
+// the contiguous run i in [lo, hi] and occupy compact rows start .. start+hi-lo.  Rows
+// with i in [rlo, rhi] are applied with the constant interior coefficients; the others
+// read 7 scaled coefficients and 1/diag from the table at tstart + (their rank among
+// the line's table rows).
+struct __align__(32) LineInfo {
+  int lo, hi, start, rlo, rhi, tstart, pad0, pad1;
+};
+
+template <class T>
+struct StencilDev {
+  const LineInfo* lines;
+  const int2* chunks;  // (line, offset of the first of <= 32 consecutive unknowns)
+  int nchunks;
+  int n;               // unknowns
+  int nx, ny, nz;
+  const T* table;      // 8 per table row: self, -x, +x, -y, +y, -z, +z, 1/self
+  T c0, cx, cy, cz, invd0;  // regular-row coefficients (scaled)
+};
+
+// ---------------------------------------------------------------------------
+// CSR matrix on the device
+// ---------------------------------------------------------------------------
+struct DevCsr {
+  int n = 0, m = 0;
+  long long nnz = 0;
+  Buf<int> rowptr, col;
+  Buf<double> val;
+  Buf<float> val32;           // FP32 copy (mixed precision)
+  Buf<__nv_bfloat16> val16;   // BF16 copy (mixed precision, BF16 storage)
+  size_t bytes() const {
+    return rowptr.bytes() + col.bytes() + val.bytes() + val32.bytes() + val16.bytes();
+  }
+};
+
+// Reduction partials: kernels that reduce write one double per block into a fixed
+// array, and a single block adds them in index order, so results do not depend on
+// scheduling.
+constexpr int kRedBlocks = 608;  // 4 x 152 SMs
+constexpr int kRedThreads = 256;
+
+// ---------------------------------------------------------------------------
+// Host launchers (implemented in the .cu files; each file owns its kernels)
+// ---------------------------------------------------------------------------
+// scan.cu
+long long exclusive_scan(const int* in, int* out, int n, cudaStream_t s);  // returns the total
+long long exclusive_scan_u8(const unsigned char* in, int* out, int n, cudaStream_t s);
+void fill_int(int* p, int v, size_t n, cudaStream_t s);
+void fill_double(double* p, double v, size_t n, cudaStream_t s);
+void sum_partials(const double* partials, int count, double* out, cudaStream_t s);
+// Copies `bytes` from device to host and waits.
+void d2h_sync(void* host, const void* dev, size_t bytes, cudaStream_t s);
+
+}  // namespace saamg

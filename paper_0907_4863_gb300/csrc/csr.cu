@@ -1,0 +1,208 @@
+// CSR kernels: coarse-level operator, Chebyshev smoother fused with the residual,
+// restriction R r and prolongation x += P v (Algorithm 1), and D^-1 A x for the
+// power iteration.  G lanes cooperate on one row (G chosen from the mean row length),
+// partial row sums are combined with shuffles inside the G-lane group.
+#include "csr.cuh"
+
+namespace saamg {
+
+namespace {
+
+__device__ __forceinline__ double ld(const double* p, size_t i) { return p[i]; }
+__device__ __forceinline__ float ld(const float* p, size_t i) { return p[i]; }
+__device__ __forceinline__ float ld(const __nv_bfloat16* p, size_t i) {
+  return __bfloat162float(p[i]);
+}
+
+template <class TV, class TM, int G, int MODE>
+__global__ void __launch_bounds__(256) csr_k(int n, const int* __restrict__ rowptr,
+                                             const int* __restrict__ col,
+                                             const TM* __restrict__ val, const TV* __restrict__ x,
+                                             TV* __restrict__ y, const TV* __restrict__ b,
+                                             TV* __restrict__ d, const TV* __restrict__ invd,
+                                             TV c1, TV c2, double* __restrict__ partials) {
+  const int lane = threadIdx.x & 31;
+  const int gl = lane % G;
+  constexpr int kRowsPerWarp = 32 / G;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  double dacc = 0.0;
+  // the trip count is uniform across the warp, so the group shuffles see all 32 lanes
+  for (int wbase = warp * kRowsPerWarp; wbase < n; wbase += nwarps * kRowsPerWarp) {
+    const int row = wbase + lane / G;
+    const bool active = row < n;
+    TV acc = TV(0);
+    if (MODE != CSR_CHEB0 && active) {
+      const int p0 = rowptr[row], p1 = rowptr[row + 1];
+      for (int p = p0 + gl; p < p1; p += G) acc += (TV)ld(val, p) * x[col[p]];
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
+    if (active && gl == 0) {
+      if (MODE == CSR_SPMV) {
+        y[row] = acc;
+      } else if (MODE == CSR_RESID) {
+        y[row] = b[row] - acc;
+      } else if (MODE == CSR_ADD) {
+        y[row] = y[row] + acc;
+      } else if (MODE == CSR_CHEB) {
+        const TV r = b[row] - acc;
+        const TV dprev = (c1 == TV(0)) ? TV(0) : c1 * d[row];
+        const TV dv = dprev + c2 * (invd[row] * r);
+        d[row] = dv;
+        y[row] = x[row] + dv;
+      } else if (MODE == CSR_CHEB0) {
+        const TV dv = c2 * (invd[row] * b[row]);
+        d[row] = dv;
+        y[row] = dv;
+      } else {  // CSR_SPMV_DINV_DOT
+        const TV w = invd[row] * acc;
+        y[row] = w;
+        dacc += (double)w * (double)w;
+      }
+    }
+  }
+  if (MODE == CSR_SPMV_DINV_DOT) {
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = dacc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+      partials[blockIdx.x] = t;
+    }
+  }
+}
+
+template <class TV, class TM, int G>
+void launch_g(int mode, int n, const int* rowptr, const int* col, const TM* val, const TV* x,
+              TV* y, const TV* b, TV* d, const TV* invd, TV c1, TV c2, double* partials,
+              cudaStream_t s) {
+  int blocks;
+  if (mode == CSR_SPMV_DINV_DOT) {
+    blocks = kRedBlocks;
+  } else {
+    long long need = ((long long)n * G + 255) / 256;
+    blocks = (int)(need < 152 * 16 ? (need > 0 ? need : 1) : 152 * 16);
+  }
+#define SAAMG_CSR_CASE(M)                                                                  \
+  case M:                                                                                  \
+    csr_k<TV, TM, G, M><<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y, b, d, invd, c1, c2, \
+                                                partials);                                 \
+    break;
+  switch (mode) {
+    SAAMG_CSR_CASE(CSR_SPMV)
+    SAAMG_CSR_CASE(CSR_RESID)
+    SAAMG_CSR_CASE(CSR_CHEB)
+    SAAMG_CSR_CASE(CSR_CHEB0)
+    SAAMG_CSR_CASE(CSR_ADD)
+    SAAMG_CSR_CASE(CSR_SPMV_DINV_DOT)
+    default:
+      fail(SAAMG_EINVAL, "bad csr mode");
+  }
+#undef SAAMG_CSR_CASE
+  SAAMG_LAUNCH();
+}
+
+__global__ void diag_inverse_k(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                               const double* __restrict__ val, double* __restrict__ invd,
+                               float* __restrict__ invd32) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double dgl = 0.0;
+  for (int p = rowptr[i]; p < rowptr[i + 1]; ++p)
+    if (col[p] == i) dgl = val[p];
+  double v = 1.0 / dgl;
+  invd[i] = v;
+  if (invd32) invd32[i] = (float)v;
+}
+
+template <class TI, class TO>
+__global__ void convert_k(const TI* __restrict__ in, TO* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (TO)in[i];
+}
+
+__global__ void to_bf16_k(const double* __restrict__ in, __nv_bfloat16* __restrict__ out,
+                          size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = __double2bfloat16(in[i]);
+}
+
+inline int grid_for(size_t n) {
+  size_t b = (n + 255) / 256;
+  return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+}  // namespace
+
+template <class TV, class TM>
+void csr_apply(int mode, int n, const int* rowptr, const int* col, const TM* val, double avg_nnz,
+               const TV* x, TV* y, const TV* b, TV* d, const TV* invd, TV c1, TV c2,
+               double* partials, cudaStream_t s, int kclass) {
+  if (n <= 0) {
+    if (mode == CSR_SPMV_DINV_DOT) fill_double(partials, 0.0, kRedBlocks, s);
+    return;
+  }
+  KernelTimer kt(kclass, n, s);
+  // FP64 shuffle-adds are as costly as the row's multiply-adds on this part: few lanes per
+  // row for double vectors; FP32 can afford wider groups for better coalescing.
+  if (sizeof(TV) == 8) {
+    if (avg_nnz <= 10.0)
+      launch_g<TV, TM, 2>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
+    else if (avg_nnz <= 48.0)
+      launch_g<TV, TM, 4>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
+    else
+      launch_g<TV, TM, 8>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
+  } else {
+    if (avg_nnz <= 6.0)
+      launch_g<TV, TM, 4>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
+    else if (avg_nnz <= 16.0)
+      launch_g<TV, TM, 8>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
+    else if (avg_nnz <= 48.0)
+      launch_g<TV, TM, 16>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
+    else
+      launch_g<TV, TM, 32>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
+  }
+}
+
+template void csr_apply<double, double>(int, int, const int*, const int*, const double*, double,
+                                        const double*, double*, const double*, double*,
+                                        const double*, double, double, double*, cudaStream_t, int);
+template void csr_apply<float, float>(int, int, const int*, const int*, const float*, double,
+                                      const float*, float*, const float*, float*, const float*,
+                                      float, float, double*, cudaStream_t, int);
+template void csr_apply<float, __nv_bfloat16>(int, int, const int*, const int*,
+                                              const __nv_bfloat16*, double, const float*, float*,
+                                              const float*, float*, const float*, float, float,
+                                              double*, cudaStream_t, int);
+
+void csr_diag_inverse(const DevCsr& A, double* invd, float* invd32, cudaStream_t s) {
+  if (A.n == 0) return;
+  diag_inverse_k<<<(A.n + 255) / 256, 256, 0, s>>>(A.n, A.rowptr.p, A.col.p, A.val.p, invd,
+                                                   invd32);
+  SAAMG_LAUNCH();
+}
+
+void to_float(const double* in, float* out, size_t n, cudaStream_t s) {
+  if (!n) return;
+  convert_k<double, float><<<grid_for(n), 256, 0, s>>>(in, out, n);
+  SAAMG_LAUNCH();
+}
+
+void to_double(const float* in, double* out, size_t n, cudaStream_t s) {
+  if (!n) return;
+  convert_k<float, double><<<grid_for(n), 256, 0, s>>>(in, out, n);
+  SAAMG_LAUNCH();
+}
+
+void to_bf16(const double* in, __nv_bfloat16* out, size_t n, cudaStream_t s) {
+  if (!n) return;
+  to_bf16_k<<<grid_for(n), 256, 0, s>>>(in, out, n);
+  SAAMG_LAUNCH();
+}
+
+}  // namespace saamg

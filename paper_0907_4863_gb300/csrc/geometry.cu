@@ -1,0 +1,566 @@
+// Domain classification and operator assembly on the device (Sec. 2 of the paper).
+//
+// This file is compiled with --fmad=false: the inside test F < 0 and the boundary
+// fractions s, t decide which lattice nodes are unknowns and how rows are formed, so
+// they are evaluated with the plain IEEE multiply/add/divide/sqrt sequence written
+// below and never with fused multiply-adds.
+#include <climits>
+
+#include "operator.cuh"
+
+namespace saamg {
+
+namespace {
+
+__device__ __forceinline__ double node_coord(double o, int i, double h) { return o + (double)i * h; }
+
+__device__ __forceinline__ double zlo(const GeomParams& g) { return g.o[2]; }
+__device__ __forceinline__ double zhi(const GeomParams& g) {
+  return g.o[2] + (double)(g.nz - 1) * g.h[2];
+}
+
+// Cross-section scale: 1 at the first z-plane, `taper` at the last, linear in z.
+__device__ double taper_sigma(const GeomParams& g, double z) {
+  if (g.taper == 1.0 || g.nz < 2) return 1.0;
+  double tau = (z - zlo(g)) / (zhi(g) - zlo(g));
+  return 1.0 + (g.taper - 1.0) * tau;
+}
+
+// Implicit function of the elliptic wall Gamma_1 (Sec. 4.1); F < 0 inside.
+__device__ double wall_F(const GeomParams& g, double x, double y, double z) {
+  double sg = taper_sigma(g, z);
+  double u = (x - g.cx) / (g.a * sg);
+  double v = (y - g.cy) / (g.b * sg);
+  return (u * u + v * v) - 1.0;
+}
+
+// Omega_h of Sec. 2: lattice nodes of Omega plus the Robin planes; Dirichlet end
+// planes carry known zeros.
+__device__ bool node_inside(const GeomParams& g, int i, int j, int k) {
+  if (i < 0 || j < 0 || k < 0 || i >= g.nx || j >= g.ny || k >= g.nz) return false;
+  if (g.zbc == SAAMG_Z_DIRICHLET && (k == 0 || k == g.nz - 1)) return false;
+  double x = node_coord(g.o[0], i, g.h[0]);
+  double y = node_coord(g.o[1], j, g.h[1]);
+  double z = node_coord(g.o[2], k, g.h[2]);
+  return wall_F(g, x, y, z) < 0.0;
+}
+
+// 0 < s <= 1; the lower clamp 2^-20 only guards against rounding.
+__device__ double clamp_frac(double s) {
+  const double smin = 9.5367431640625e-07;
+  if (s < smin) s = smin;
+  if (s > 1.0) s = 1.0;
+  return s;
+}
+
+// Fraction s of Sec. 2 (Fig. 2): the wall point x* = x -/+ s h e_dir nearest to the node.
+// dir 0..5 = -x, +x, -y, +y, -z, +z.
+__device__ double boundary_fraction(const GeomParams& g, int i, int j, int k, int dir) {
+  double x = node_coord(g.o[0], i, g.h[0]);
+  double y = node_coord(g.o[1], j, g.h[1]);
+  double z = node_coord(g.o[2], k, g.h[2]);
+  double sg = taper_sigma(g, z);
+  if (dir < 2) {
+    double v = (y - g.cy) / (g.b * sg);
+    double w = (g.a * sg) * sqrt(1.0 - v * v);
+    double s = (dir == 0) ? (x - (g.cx - w)) / g.h[0] : ((g.cx + w) - x) / g.h[0];
+    return clamp_frac(s);
+  }
+  if (dir < 4) {
+    double u = (x - g.cx) / (g.a * sg);
+    double w = (g.b * sg) * sqrt(1.0 - u * u);
+    double s = (dir == 2) ? (y - (g.cy - w)) / g.h[1] : ((g.cy + w) - y) / g.h[1];
+    return clamp_frac(s);
+  }
+  // z: only a taper's cone crosses a z-line, where sigma(z*) = q
+  if (g.taper == 1.0 || g.nz < 2) return 1.0;
+  double u0 = (x - g.cx) / g.a;
+  double v0 = (y - g.cy) / g.b;
+  double q = sqrt(u0 * u0 + v0 * v0);
+  double tstar = (q - 1.0) / (g.taper - 1.0);
+  double zstar = zlo(g) + tstar * (zhi(g) - zlo(g));
+  if (dir == 4) return (zstar < z) ? clamp_frac((z - zstar) / g.h[2]) : 1.0;
+  return (zstar > z) ? clamp_frac((zstar - z) / g.h[2]) : 1.0;
+}
+
+// One direction of a row after substituting the extrapolated outside value into the
+// difference star Eq. (6) (g = 0): constant Eq. (7), linear Eq. (8), quadratic Eqs. (9)
+// and (10).  dd: diagonal contribution; om/opl: couplings to the minus/plus neighbour.
+__device__ void direction_row(int mode, double c, bool in_m, bool in_p, double s, double t,
+                              double& dd, double& om, double& opl) {
+  om = 0.0;
+  opl = 0.0;
+  if (in_m && in_p) {
+    dd = 2.0 * c;
+    om = -c;
+    opl = -c;
+    return;
+  }
+  if (!in_m && !in_p) {
+    if (mode == SAAMG_BC_CONSTANT) dd = 2.0 * c;
+    else if (mode == SAAMG_BC_LINEAR) dd = (1.0 / s + 1.0 / t) * c;
+    else dd = (2.0 / (s * t)) * c;
+    return;
+  }
+  double f = in_m ? t : s;
+  double off;
+  if (mode == SAAMG_BC_CONSTANT) {
+    dd = 2.0 * c;
+    off = -c;
+  } else if (mode == SAAMG_BC_LINEAR) {
+    dd = (1.0 + 1.0 / f) * c;
+    off = -c;
+  } else {
+    dd = (2.0 / f) * c;
+    off = -(2.0 / (f + 1.0)) * c;
+  }
+  if (in_m) om = off;
+  else opl = off;
+}
+
+// Neighbour lookup through the line records: row of (i, line Ln), or -1.
+__device__ __forceinline__ int row_in_line(const LineInfo* lines, int Ln, int i) {
+  LineInfo l = lines[Ln];
+  return (i >= l.lo && i <= l.hi) ? l.start + (i - l.lo) : -1;
+}
+
+// Rows of the 6 neighbours (-x,+x,-y,+y,-z,+z) of unknown (i, L), -1 if not an unknown.
+__device__ void neighbour_rows(const GeomParams& g, const LineInfo* lines, int L, int i, int row,
+                               const LineInfo& me, int nb[6]) {
+  int j = L % g.ny, k = L / g.ny;
+  nb[0] = (i - 1 >= me.lo) ? row - 1 : -1;
+  nb[1] = (i + 1 <= me.hi) ? row + 1 : -1;
+  nb[2] = (j > 0) ? row_in_line(lines, L - 1, i) : -1;
+  nb[3] = (j < g.ny - 1) ? row_in_line(lines, L + 1, i) : -1;
+  nb[4] = (k > 0) ? row_in_line(lines, L - g.ny, i) : -1;
+  nb[5] = (k < g.nz - 1) ? row_in_line(lines, L + g.ny, i) : -1;
+}
+
+// --- kernels ---------------------------------------------------------------
+
+// Warp per x-line: first/last inside node and count; flags a non-contiguous line.
+__global__ void classify_lines_k(GeomParams g, int nlines, LineInfo* lines, int* count,
+                                 int* err) {
+  int L = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (L >= nlines) return;
+  int j = L % g.ny, k = L / g.ny;
+  int first = INT_MAX, last = -1, cnt = 0;
+  for (int base = 0; base < g.nx; base += 32) {
+    int i = base + lane;
+    bool in = (i < g.nx) && node_inside(g, i, j, k);
+    unsigned m = __ballot_sync(0xffffffffu, in);
+    if (m) {
+      if (first == INT_MAX) first = base + __ffs(m) - 1;
+      last = base + 31 - __clz(m);
+      cnt += __popc(m);
+    }
+  }
+  if (lane == 0) {
+    LineInfo l;
+    l.lo = cnt ? first : 0;
+    l.hi = cnt ? last : -1;
+    l.start = 0;
+    l.rlo = l.hi + 1;
+    l.rhi = l.hi;
+    l.tstart = 0;
+    l.pad0 = l.pad1 = 0;
+    lines[L] = l;
+    count[L] = cnt;
+    if (cnt && cnt != last - first + 1) atomicOr(err, 1);
+  }
+}
+
+__global__ void chunk_counts_k(const int* count, int nlines, int* nch) {
+  int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L < nlines) nch[L] = (count[L] + 31) >> 5;
+}
+
+__global__ void set_start_and_chunks_k(LineInfo* lines, const int* start, const int* chunk_start,
+                                       const int* count, int nlines, int2* chunks) {
+  int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= nlines) return;
+  lines[L].start = start[L];
+  int c0 = chunk_start[L], cnt = count[L];
+  for (int off = 0, c = c0; off < cnt; off += 32, ++c) chunks[c] = make_int2(L, off);
+}
+
+// Regular interior row: all six couplings -c_dir, diagonal 2(cx+cy+cz), scaled.
+__global__ void regular_consts_k(GeomParams g, double* out) {
+  double dd[3], om, opl;
+  for (int ax = 0; ax < 3; ++ax) {
+    double c = 1.0 / (g.h[ax] * g.h[ax]);
+    direction_row(g.mode, c, true, true, 1.0, 1.0, dd[ax], om, opl);
+  }
+  double diag = (dd[0] + dd[1]) + dd[2];
+  double s = 1.0 / sqrt(diag);
+  double ss = s * s;
+  out[0] = diag * ss;
+  out[1] = (-(1.0 / (g.h[0] * g.h[0]))) * ss;
+  out[2] = (-(1.0 / (g.h[1] * g.h[1]))) * ss;
+  out[3] = (-(1.0 / (g.h[2] * g.h[2]))) * ss;
+  out[4] = 1.0 / out[0];
+}
+
+// Warp per chunk, lane per unknown: unscaled row (diag + 6 couplings), s_i, row length.
+__global__ void assemble_unscaled_k(GeomParams g, const LineInfo* __restrict__ lines,
+                                    const int2* __restrict__ chunks, int nchunks,
+                                    double* __restrict__ coef, double* __restrict__ scale,
+                                    int* __restrict__ rowlen, unsigned* __restrict__ ids) {
+  int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (c >= nchunks) return;
+  int2 ch = chunks[c];
+  int L = ch.x;
+  LineInfo me = lines[L];
+  int i = me.lo + ch.y + lane;
+  if (i > me.hi) return;
+  int row = me.start + ch.y + lane;
+  int j = L % g.ny, k = L / g.ny;
+  int nb[6];
+  neighbour_rows(g, lines, L, i, row, me, nb);
+  double off[6] = {0, 0, 0, 0, 0, 0};
+  double dd[3];
+  bool gamma2 = (g.zbc == SAAMG_Z_ROBIN) && (k == 0 || k == g.nz - 1);
+  const double dist = 0.5 * ((double)(g.nz - 1) * g.h[2]);
+  for (int ax = 0; ax < 3; ++ax) {
+    double cdir = 1.0 / (g.h[ax] * g.h[ax]);
+    int dm = 2 * ax, dp = 2 * ax + 1;
+    bool in_m = nb[dm] >= 0, in_p = nb[dp] >= 0;
+    if (ax == 2 && gamma2) {
+      // Robin plane, Eq. (11): virtual point u(x') = u(x'') - (2h/d) u(x)
+      bool inner_is_p = (k == 0);
+      bool in_inner = inner_is_p ? in_p : in_m;
+      if (in_inner) {
+        dd[2] = (2.0 + (2.0 * g.h[2]) / dist) * cdir;
+        off[inner_is_p ? dp : dm] = -2.0 * cdir;
+      } else {
+        // inner neighbour outside the wall: replaced by its one-sided extrapolation
+        double t = boundary_fraction(g, i, j, k, inner_is_p ? dp : dm);
+        if (g.mode == SAAMG_BC_CONSTANT) dd[2] = (2.0 + (2.0 * g.h[2]) / dist) * cdir;
+        else dd[2] = ((2.0 * g.h[2]) / dist + 2.0 / t) * cdir;
+      }
+      continue;
+    }
+    double s = 1.0, t = 1.0;
+    if (!in_m) s = boundary_fraction(g, i, j, k, dm);
+    if (!in_p) t = boundary_fraction(g, i, j, k, dp);
+    direction_row(g.mode, cdir, in_m, in_p, s, t, dd[ax], off[dm], off[dp]);
+  }
+  double diag = (dd[0] + dd[1]) + dd[2];
+  if (gamma2 && g.sym) {
+    diag *= 0.5;
+    for (int q = 0; q < 6; ++q) off[q] *= 0.5;
+  }
+  double* cr = coef + 8 * (size_t)row;
+  cr[0] = diag;
+  int len = 1;
+  for (int q = 0; q < 6; ++q) {
+    cr[1 + q] = off[q];
+    len += nb[q] >= 0;
+  }
+  cr[7] = 0.0;
+  scale[row] = 1.0 / sqrt(diag);
+  rowlen[row] = len;
+  ids[row] = (unsigned)i + (unsigned)g.nx * (unsigned)L;
+}
+
+// Warp per chunk: scaled row ahat_ij = a_ij (s_i s_j), CSR fill in ascending column order
+// (-z, -y, -x, self, +x, +y, +z), the row kept in `coef` for the stencil table, and the
+// regular flag (all six neighbours present and the coefficients equal the interior ones).
+__global__ void assemble_scaled_k(GeomParams g, const LineInfo* __restrict__ lines,
+                                  const int2* __restrict__ chunks, int nchunks,
+                                  double* __restrict__ coef, const double* __restrict__ scale,
+                                  const int* __restrict__ rowptr, int* __restrict__ col,
+                                  double* __restrict__ val, unsigned char* __restrict__ regular,
+                                  const double* __restrict__ rc) {
+  int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (c >= nchunks) return;
+  int2 ch = chunks[c];
+  int L = ch.x;
+  LineInfo me = lines[L];
+  int i = me.lo + ch.y + lane;
+  if (i > me.hi) return;
+  int row = me.start + ch.y + lane;
+  int nb[6];
+  neighbour_rows(g, lines, L, i, row, me, nb);
+  double si = scale[row];
+  double* cr = coef + 8 * (size_t)row;
+  double sc[7];
+  sc[0] = cr[0] * (si * si);
+  bool reg = true;
+  for (int q = 0; q < 6; ++q) {
+    if (nb[q] >= 0) {
+      sc[1 + q] = cr[1 + q] * (si * scale[nb[q]]);
+    } else {
+      sc[1 + q] = 0.0;
+      reg = false;
+    }
+  }
+  reg = reg && sc[0] == rc[0] && sc[1] == rc[1] && sc[2] == rc[1] && sc[3] == rc[2] &&
+        sc[4] == rc[2] && sc[5] == rc[3] && sc[6] == rc[3];
+  const int order[7] = {4, 2, 0, -1, 1, 3, 5};
+  int p = rowptr[row];
+  for (int o = 0; o < 7; ++o) {
+    int q = order[o];
+    if (q < 0) {
+      col[p] = row;
+      val[p] = sc[0];
+      ++p;
+    } else if (nb[q] >= 0) {
+      col[p] = nb[q];
+      val[p] = sc[1 + q];
+      ++p;
+    }
+  }
+  for (int q = 0; q < 7; ++q) cr[q] = sc[q];
+  cr[7] = 1.0 / sc[0];
+  regular[row] = reg ? 1 : 0;
+}
+
+// Thread per line: longest run of regular rows -> [rlo, rhi]; table rows = the rest.
+__global__ void line_runs_k(LineInfo* lines, int nlines, const unsigned char* regular,
+                            int* ntab) {
+  int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= nlines) return;
+  LineInfo l = lines[L];
+  int cnt = l.hi - l.lo + 1;
+  int best_lo = 0, best_len = 0, cur_lo = 0, cur_len = 0;
+  for (int t = 0; t < cnt; ++t) {
+    if (regular[l.start + t]) {
+      if (cur_len == 0) cur_lo = t;
+      ++cur_len;
+      if (cur_len > best_len) {
+        best_len = cur_len;
+        best_lo = cur_lo;
+      }
+    } else {
+      cur_len = 0;
+    }
+  }
+  if (best_len > 0) {
+    lines[L].rlo = l.lo + best_lo;
+    lines[L].rhi = l.lo + best_lo + best_len - 1;
+  } else {
+    lines[L].rlo = l.hi + 1;
+    lines[L].rhi = l.hi;
+  }
+  ntab[L] = cnt - best_len;
+}
+
+__global__ void set_tstart_k(LineInfo* lines, const int* tstart, int nlines) {
+  int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L < nlines) lines[L].tstart = tstart[L];
+}
+
+// Warp per chunk: table rows copy their 7 scaled coefficients and 1/diag.
+__global__ void fill_table_k(const LineInfo* __restrict__ lines, const int2* __restrict__ chunks,
+                             int nchunks, const double* __restrict__ coef,
+                             double* __restrict__ table, float* __restrict__ table32) {
+  int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (c >= nchunks) return;
+  int2 ch = chunks[c];
+  LineInfo me = lines[ch.x];
+  int i = me.lo + ch.y + lane;
+  if (i > me.hi) return;
+  if (i >= me.rlo && i <= me.rhi) return;
+  int row = me.start + ch.y + lane;
+  int t = me.tstart + (i < me.rlo ? i - me.lo : (me.rlo - me.lo) + (i - me.rhi - 1));
+  for (int q = 0; q < 8; ++q) {
+    double v = coef[8 * (size_t)row + q];
+    table[8 * (size_t)t + q] = v;
+    table32[8 * (size_t)t + q] = (float)v;
+  }
+}
+
+// Box -> compact right-hand side and initial guess.
+__global__ void gather_k(GeomParams g, const LineInfo* __restrict__ lines,
+                         const int2* __restrict__ chunks, int nchunks,
+                         const double* __restrict__ scale, const double* __restrict__ rho,
+                         const double* __restrict__ phi0, double* __restrict__ bhat,
+                         double* __restrict__ xhat) {
+  int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (c >= nchunks) return;
+  int2 ch = chunks[c];
+  int L = ch.x;
+  LineInfo me = lines[L];
+  int i = me.lo + ch.y + lane;
+  if (i > me.hi) return;
+  int row = me.start + ch.y + lane;
+  int k = L / g.ny;
+  size_t box = (size_t)i + (size_t)g.nx * (size_t)L;
+  bool gamma2 = (g.zbc == SAAMG_Z_ROBIN) && (k == 0 || k == g.nz - 1);
+  double bf = (gamma2 && g.sym) ? 0.5 : 1.0;
+  double si = scale[row];
+  bhat[row] = si * (bf * rho[box]);
+  if (xhat) xhat[row] = phi0 ? phi0[box] / si : 0.0;
+}
+
+__global__ void scatter_k(const GeomParams g, const LineInfo* __restrict__ lines,
+                          const int2* __restrict__ chunks, int nchunks,
+                          const double* __restrict__ scale, const double* __restrict__ xhat,
+                          double* __restrict__ phi) {
+  int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (c >= nchunks) return;
+  int2 ch = chunks[c];
+  int L = ch.x;
+  LineInfo me = lines[L];
+  int i = me.lo + ch.y + lane;
+  if (i > me.hi) return;
+  int row = me.start + ch.y + lane;
+  phi[(size_t)i + (size_t)g.nx * (size_t)L] = scale[row] * xhat[row];
+}
+
+inline int warp_blocks(long long warps) { return (int)((warps * 32 + 255) / 256); }
+
+}  // namespace
+
+void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op) {
+  op.g = g;
+  long long nl = (long long)g.ny * g.nz;
+  if (nl > INT_MAX / 32) fail(SAAMG_EINVAL, "grid too large");
+  int nlines = (int)nl;
+  op.nlines = nlines;
+  op.lines.alloc(nlines, s);
+  Buf<int> count, start, nch, chstart, err;
+  count.alloc(nlines, s);
+  start.alloc(nlines, s);
+  nch.alloc(nlines, s);
+  chstart.alloc(nlines, s);
+  err.alloc(1, s);
+  fill_int(err.p, 0, 1, s);
+  classify_lines_k<<<warp_blocks(nlines), 256, 0, s>>>(g, nlines, op.lines.p, count.p, err.p);
+  SAAMG_LAUNCH();
+  int herr = 0;
+  d2h_sync(&herr, err.p, sizeof(int), s);
+  if (herr) fail(SAAMG_EINVAL, "a lattice line meets the domain in more than one interval");
+  long long n = exclusive_scan(count.p, start.p, nlines, s);
+  if (n > INT_MAX / 8) fail(SAAMG_EINVAL, "too many unknowns for 32-bit indices");
+  op.n = (int)n;
+  chunk_counts_k<<<(nlines + 255) / 256, 256, 0, s>>>(count.p, nlines, nch.p);
+  SAAMG_LAUNCH();
+  long long nchunks = exclusive_scan(nch.p, chstart.p, nlines, s);
+  op.nchunks = (int)nchunks;
+  op.chunks.alloc(nchunks, s);
+  set_start_and_chunks_k<<<(nlines + 255) / 256, 256, 0, s>>>(op.lines.p, start.p, chstart.p,
+                                                               count.p, nlines, op.chunks.p);
+  SAAMG_LAUNCH();
+
+  Buf<double> rc;
+  rc.alloc(5, s);
+  regular_consts_k<<<1, 1, 0, s>>>(g, rc.p);
+  SAAMG_LAUNCH();
+  double hrc[5];
+  d2h_sync(hrc, rc.p, sizeof(hrc), s);
+  op.c0 = hrc[0];
+  op.cx = hrc[1];
+  op.cy = hrc[2];
+  op.cz = hrc[3];
+  op.invd0 = hrc[4];
+
+  op.scale.alloc(op.n, s);
+  op.ids.alloc(op.n, s);
+  op.regular.alloc(op.n, s);
+  Buf<double> coef;
+  coef.alloc((size_t)op.n * 8, s);
+  Buf<int> rowlen;
+  rowlen.alloc(op.n + 1, s);
+  if (op.n > 0) {
+    assemble_unscaled_k<<<warp_blocks(nchunks), 256, 0, s>>>(g, op.lines.p, op.chunks.p,
+                                                              op.nchunks, coef.p, op.scale.p,
+                                                              rowlen.p, op.ids.p);
+    SAAMG_LAUNCH();
+  }
+  fill_int(rowlen.p + op.n, 0, 1, s);
+  op.A.n = op.A.m = op.n;
+  op.A.rowptr.alloc(op.n + 1, s);
+  long long nnz = exclusive_scan(rowlen.p, op.A.rowptr.p, op.n + 1, s);
+  if (nnz > INT_MAX) fail(SAAMG_EINVAL, "more than 2^31 nonzeros");
+  op.nnz = op.A.nnz = nnz;
+  op.A.col.alloc(nnz, s);
+  op.A.val.alloc(nnz, s);
+  if (op.n > 0) {
+    assemble_scaled_k<<<warp_blocks(nchunks), 256, 0, s>>>(
+        g, op.lines.p, op.chunks.p, op.nchunks, coef.p, op.scale.p, op.A.rowptr.p, op.A.col.p,
+        op.A.val.p, op.regular.p, rc.p);
+    SAAMG_LAUNCH();
+  }
+  Buf<int> ntab, tstart;
+  ntab.alloc(nlines, s);
+  tstart.alloc(nlines, s);
+  line_runs_k<<<(nlines + 255) / 256, 256, 0, s>>>(op.lines.p, nlines, op.regular.p, ntab.p);
+  SAAMG_LAUNCH();
+  long long nt = exclusive_scan(ntab.p, tstart.p, nlines, s);
+  op.ntable = (int)nt;
+  set_tstart_k<<<(nlines + 255) / 256, 256, 0, s>>>(op.lines.p, tstart.p, nlines);
+  SAAMG_LAUNCH();
+  op.table.alloc((size_t)nt * 8, s);
+  op.table32.alloc((size_t)nt * 8, s);
+  if (op.n > 0) {
+    fill_table_k<<<warp_blocks(nchunks), 256, 0, s>>>(op.lines.p, op.chunks.p, op.nchunks, coef.p,
+                                                       op.table.p, op.table32.p);
+    SAAMG_LAUNCH();
+  }
+  SAAMG_CUDA(cudaStreamSynchronize(s));
+}
+
+template <>
+StencilDev<double> OperatorData::view<double>() const {
+  StencilDev<double> v;
+  v.lines = lines.p;
+  v.chunks = chunks.p;
+  v.nchunks = nchunks;
+  v.n = n;
+  v.nx = g.nx;
+  v.ny = g.ny;
+  v.nz = g.nz;
+  v.table = table.p;
+  v.c0 = c0;
+  v.cx = cx;
+  v.cy = cy;
+  v.cz = cz;
+  v.invd0 = invd0;
+  return v;
+}
+
+template <>
+StencilDev<float> OperatorData::view<float>() const {
+  StencilDev<float> v;
+  v.lines = lines.p;
+  v.chunks = chunks.p;
+  v.nchunks = nchunks;
+  v.n = n;
+  v.nx = g.nx;
+  v.ny = g.ny;
+  v.nz = g.nz;
+  v.table = table32.p;
+  v.c0 = (float)c0;
+  v.cx = (float)cx;
+  v.cy = (float)cy;
+  v.cz = (float)cz;
+  v.invd0 = (float)invd0;
+  return v;
+}
+
+void gather_rhs(const OperatorData& op, const double* rho, const double* phi0, double* bhat,
+                double* xhat, cudaStream_t s) {
+  if (op.n == 0) return;
+  gather_k<<<warp_blocks(op.nchunks), 256, 0, s>>>(op.g, op.lines.p, op.chunks.p, op.nchunks,
+                                                    op.scale.p, rho, phi0, bhat, xhat);
+  SAAMG_LAUNCH();
+}
+
+void scatter_solution(const OperatorData& op, const double* xhat, double* phi, cudaStream_t s) {
+  size_t nbox = (size_t)op.g.nx * op.g.ny * op.g.nz;
+  SAAMG_CUDA(cudaMemsetAsync(phi, 0, nbox * sizeof(double), s));
+  if (op.n == 0) return;
+  scatter_k<<<warp_blocks(op.nchunks), 256, 0, s>>>(op.g, op.lines.p, op.chunks.p, op.nchunks,
+                                                     op.scale.p, xhat, phi);
+  SAAMG_LAUNCH();
+}
+
+}  // namespace saamg

@@ -1,0 +1,65 @@
+// Level-0 operator data and the launchers that build and apply it (internal).
+#pragma once
+
+#include "common.cuh"
+
+namespace saamg {
+
+struct GeomParams {
+  int nx, ny, nz;
+  double h[3], o[3];
+  double a, b, taper, cx, cy;
+  int zbc, sym, mode;
+};
+
+// Scaled operator Ahat = D^-1/2 A D^-1/2 on the unknowns of the box grid.
+struct OperatorData {
+  GeomParams g{};
+  int n = 0;            // unknowns
+  long long nnz = 0;    // nonzeros of the explicit CSR
+  int nlines = 0;       // ny * nz
+  Buf<LineInfo> lines;
+  Buf<int2> chunks;
+  int nchunks = 0;
+  Buf<double> table;    // 8 doubles per table row
+  Buf<float> table32;
+  int ntable = 0;
+  double c0 = 0, cx = 0, cy = 0, cz = 0, invd0 = 0;  // regular-row coefficients
+  Buf<double> scale;    // s_i = a_ii^-1/2 (unscaled diagonal)
+  Buf<unsigned> ids;    // box index of each unknown
+  Buf<unsigned char> regular;
+  DevCsr A;             // explicit scaled CSR (used by the AMG setup)
+  size_t bytes() const {
+    return lines.bytes() + chunks.bytes() + table.bytes() + table32.bytes() + scale.bytes() +
+           ids.bytes() + regular.bytes() + A.bytes();
+  }
+  template <class T>
+  StencilDev<T> view() const;
+};
+
+template <>
+StencilDev<double> OperatorData::view<double>() const;
+template <>
+StencilDev<float> OperatorData::view<float>() const;
+
+// geometry.cu
+void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op);
+// rho (box) -> bhat (compact) = s_i * (bfac_i * rho); phi0 (box) -> xhat0 = phi0 / s_i (if given)
+void gather_rhs(const OperatorData& op, const double* rho, const double* phi0, double* bhat,
+                double* xhat, cudaStream_t s);
+// xhat (compact) -> phi (box) = s_i * xhat at unknowns, 0 elsewhere
+void scatter_solution(const OperatorData& op, const double* xhat, double* phi, cudaStream_t s);
+
+// stencil.cu -- matrix-free level-0 kernels.  MODE selects the fused operation.
+enum StencilMode {
+  ST_SPMV = 0,      // y = A x
+  ST_SPMV_DOT = 1,  // y = A x, partials of x.y
+  ST_RESID = 2,     // y = b - A x
+  ST_CHEB = 3,      // r = b - A x; d = c1 d + c2 D^-1 r; y = x + d
+  ST_CHEB0 = 4      // d = c2 D^-1 b; y = d   (Chebyshev step 0 from x = 0)
+};
+template <class T>
+void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* b, T* d, T c1,
+                   T c2, double* partials, cudaStream_t s);
+
+}  // namespace saamg

@@ -1,0 +1,187 @@
+// Conjugate-gradient recursion (Sec. 3.1) on the scaled system: fused axpy + norm,
+// direction update, dot products.  Every reduction writes one partial per block of a
+// fixed grid and a single block adds the partials in index order, so a run is
+// reproducible bit for bit.  The CG scalars stay on the device.
+#include "pcg.cuh"
+
+namespace saamg {
+
+namespace {
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  return t;  // valid in thread 0
+}
+
+// single-block ordered sum of kRedBlocks partials
+__device__ __forceinline__ double sum_fixed(const double* part) {
+  __shared__ double sh[kRedThreads];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) acc += part[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+template <class TA, class TB>
+__global__ void dot_k(int n, const TA* __restrict__ a, const TB* __restrict__ b,
+                      double* __restrict__ part) {
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    acc += (double)a[i] * (double)b[i];
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void alpha_k(const double* __restrict__ part, PcgCtl* ctl) {
+  double pq = sum_fixed(part);
+  if (threadIdx.x == 0) {
+    ctl->pq = pq;
+    double a = ctl->rz / pq;
+    if (!(pq != 0.0) || !isfinite(a)) {
+      ctl->breakdown = 1;
+      a = 0.0;
+    }
+    ctl->alpha = a;
+  }
+}
+
+__global__ void update_k(int n, double* __restrict__ x, double* __restrict__ r,
+                         const double* __restrict__ p, const double* __restrict__ q,
+                         const PcgCtl* __restrict__ ctl, double* __restrict__ part) {
+  const double a = ctl->alpha;
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    x[i] = x[i] + a * p[i];
+    double ri = r[i] - a * q[i];
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void check_k(const double* __restrict__ part, PcgCtl* ctl) {
+  double rr = sum_fixed(part);
+  if (threadIdx.x == 0) {
+    ctl->rr = rr;
+    ctl->iters += 1;
+    if (!isfinite(rr)) ctl->breakdown = 1;
+    ctl->converged = rr <= ctl->tol2;
+  }
+}
+
+__global__ void beta_k(const double* __restrict__ part_rz, const double* __restrict__ part_zq,
+                       int rule, PcgCtl* ctl) {
+  double rz = sum_fixed(part_rz);
+  double zq = part_zq ? sum_fixed(part_zq) : 0.0;
+  if (threadIdx.x == 0 && rule < 0) {  // first direction: only r'z
+    ctl->rz = rz;
+    if (!isfinite(rz)) ctl->breakdown = 1;
+    return;
+  }
+  if (threadIdx.x == 0) {
+    double b = (rule == 1) ? (-ctl->alpha * zq) / ctl->rz : rz / ctl->rz;
+    if (!isfinite(b) || !isfinite(rz)) {
+      ctl->breakdown = 1;
+      b = 0.0;
+    }
+    ctl->rz_new = rz;
+    ctl->zq = zq;
+    ctl->beta = b;
+    ctl->rz = rz;
+  }
+}
+
+template <class TZ>
+__global__ void direction_k(int n, const TZ* __restrict__ z, double* __restrict__ p,
+                            const PcgCtl* __restrict__ ctl) {
+  const double b = ctl->beta;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    p[i] = (double)z[i] + b * p[i];
+}
+
+__global__ void sub_k(int n, const double* __restrict__ b, const double* __restrict__ q,
+                      double* __restrict__ r) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    r[i] = b[i] - q[i];
+}
+
+template <class TZ>
+__global__ void copy_k(int n, const TZ* __restrict__ z, double* __restrict__ p) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    p[i] = (double)z[i];
+}
+
+inline int vec_blocks(int n) {
+  int b = (n + 255) / 256;
+  return b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8;
+}
+
+}  // namespace
+
+template <class TA, class TB>
+void dot_partials(int n, const TA* a, const TB* b, double* partials, cudaStream_t s) {
+  dot_k<TA, TB><<<kRedBlocks, kRedThreads, 0, s>>>(n, a, b, partials);
+  SAAMG_LAUNCH();
+}
+template void dot_partials<double, double>(int, const double*, const double*, double*, cudaStream_t);
+template void dot_partials<double, float>(int, const double*, const float*, double*, cudaStream_t);
+template void dot_partials<float, double>(int, const float*, const double*, double*, cudaStream_t);
+
+void pcg_alpha(const double* partials, PcgCtl* ctl, cudaStream_t s) {
+  alpha_k<<<1, kRedThreads, 0, s>>>(partials, ctl);
+  SAAMG_LAUNCH();
+}
+
+void pcg_update(int n, double* x, double* r, const double* p, const double* q, const PcgCtl* ctl,
+                double* partials, cudaStream_t s) {
+  update_k<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, p, q, ctl, partials);
+  SAAMG_LAUNCH();
+}
+
+void pcg_check(const double* partials, PcgCtl* ctl, cudaStream_t s) {
+  check_k<<<1, kRedThreads, 0, s>>>(partials, ctl);
+  SAAMG_LAUNCH();
+}
+
+void pcg_beta(const double* part_rz, const double* part_zq, int rule, PcgCtl* ctl,
+              cudaStream_t s) {
+  beta_k<<<1, kRedThreads, 0, s>>>(part_rz, part_zq, rule, ctl);
+  SAAMG_LAUNCH();
+}
+
+template <class TZ>
+void pcg_direction(int n, const TZ* z, double* p, const PcgCtl* ctl, cudaStream_t s) {
+  direction_k<TZ><<<vec_blocks(n), 256, 0, s>>>(n, z, p, ctl);
+  SAAMG_LAUNCH();
+}
+template void pcg_direction<double>(int, const double*, double*, const PcgCtl*, cudaStream_t);
+template void pcg_direction<float>(int, const float*, double*, const PcgCtl*, cudaStream_t);
+
+void vec_sub(int n, const double* b, const double* q, double* r, cudaStream_t s) {
+  sub_k<<<vec_blocks(n), 256, 0, s>>>(n, b, q, r);
+  SAAMG_LAUNCH();
+}
+
+template <class TZ>
+void vec_copy_to_double(int n, const TZ* z, double* p, cudaStream_t s) {
+  copy_k<TZ><<<vec_blocks(n), 256, 0, s>>>(n, z, p);
+  SAAMG_LAUNCH();
+}
+template void vec_copy_to_double<double>(int, const double*, double*, cudaStream_t);
+template void vec_copy_to_double<float>(int, const float*, double*, cudaStream_t);
+
+}  // namespace saamg

@@ -1,0 +1,171 @@
+// Matrix-free level-0 operator: the 7-point star of Eq. (6) with the boundary rows of
+// Sec. 2, scaled by D^-1/2 on both sides, applied on compact vectors.
+//
+// One warp per chunk of <= 32 consecutive unknowns of one x-line.  The x-neighbours are
+// the adjacent compact rows; the y- and z-neighbours of lane i are the rows start' +
+// (i - lo') of the neighbouring lines, so every warp load is a contiguous run.  Rows
+// inside the line's regular run use the four interior coefficients held in registers;
+// the remaining rows (near-boundary rows and their neighbours, about 5-8 % of all
+// rows) read their 7 coefficients and 1/diag from the table.
+#include "operator.cuh"
+
+namespace saamg {
+
+namespace {
+
+template <class T>
+__device__ __forceinline__ double to_d(T v) {
+  return (double)v;
+}
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __restrict__ x,
+                                                 T* __restrict__ y, const T* __restrict__ b,
+                                                 T* __restrict__ d, T c1, T c2,
+                                                 double* __restrict__ partials) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int nw = gridDim.x * wpb;
+  const T c2invd0 = c2 * S.invd0;
+  double dacc = 0.0;
+  for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < S.nchunks; c += nw) {
+    const int2 ch = S.chunks[c];
+    const int L = ch.x;
+    const LineInfo me = S.lines[L];
+    const int i = me.lo + ch.y + lane;
+    if (i > me.hi) continue;
+    const int row = me.start + ch.y + lane;
+    const bool reg = (i >= me.rlo) && (i <= me.rhi);
+    T invd;
+    const T* tb = nullptr;
+    if (reg) {
+      invd = S.invd0;
+    } else {
+      const int t = me.tstart + (i < me.rlo ? i - me.lo : (me.rlo - me.lo) + (i - me.rhi - 1));
+      tb = S.table + 8 * (size_t)t;
+      invd = tb[7];
+    }
+    if (MODE == ST_CHEB0) {
+      T dv = (reg ? c2invd0 : c2 * invd) * b[row];
+      d[row] = dv;
+      y[row] = dv;
+      continue;
+    }
+    const int j = L % S.ny, k = L / S.ny;
+    const T xc = x[row];
+    // SPMV modes accumulate A x; RESID / CHEB accumulate r = b - A x directly (FP64 issue
+    // slots bound this kernel in double precision, so every add is folded into an FMA)
+    constexpr bool kResid = (MODE == ST_RESID || MODE == ST_CHEB);
+    T acc;
+    if (reg) {
+      // all six neighbours are unknowns
+      const LineInfo ym = S.lines[L - 1], yp = S.lines[L + 1];
+      const LineInfo zm = S.lines[L - S.ny], zp = S.lines[L + S.ny];
+      const T sx = x[row - 1] + x[row + 1];
+      const T sy = x[ym.start + (i - ym.lo)] + x[yp.start + (i - yp.lo)];
+      const T sz = x[zm.start + (i - zm.lo)] + x[zp.start + (i - zp.lo)];
+      if (kResid) {
+        acc = fma(-S.c0, xc, b[row]);
+        acc = fma(-S.cx, sx, acc);
+        acc = fma(-S.cy, sy, acc);
+        acc = fma(-S.cz, sz, acc);
+      } else {
+        acc = S.c0 * xc;
+        acc = fma(S.cx, sx, acc);
+        acc = fma(S.cy, sy, acc);
+        acc = fma(S.cz, sz, acc);
+      }
+    } else {
+      const T sg = kResid ? T(-1) : T(1);
+      acc = kResid ? fma(-tb[0], xc, b[row]) : tb[0] * xc;
+      if (i - 1 >= me.lo) acc = fma(sg * tb[1], x[row - 1], acc);
+      if (i + 1 <= me.hi) acc = fma(sg * tb[2], x[row + 1], acc);
+      if (j > 0) {
+        const LineInfo l = S.lines[L - 1];
+        if (i >= l.lo && i <= l.hi) acc = fma(sg * tb[3], x[l.start + (i - l.lo)], acc);
+      }
+      if (j < S.ny - 1) {
+        const LineInfo l = S.lines[L + 1];
+        if (i >= l.lo && i <= l.hi) acc = fma(sg * tb[4], x[l.start + (i - l.lo)], acc);
+      }
+      if (k > 0) {
+        const LineInfo l = S.lines[L - S.ny];
+        if (i >= l.lo && i <= l.hi) acc = fma(sg * tb[5], x[l.start + (i - l.lo)], acc);
+      }
+      if (k < S.nz - 1) {
+        const LineInfo l = S.lines[L + S.ny];
+        if (i >= l.lo && i <= l.hi) acc = fma(sg * tb[6], x[l.start + (i - l.lo)], acc);
+      }
+    }
+    if (MODE == ST_SPMV || MODE == ST_SPMV_DOT) {
+      y[row] = acc;
+      if (MODE == ST_SPMV_DOT) dacc = fma(to_d(xc), to_d(acc), dacc);
+    } else if (MODE == ST_RESID) {
+      y[row] = acc;
+    } else {  // ST_CHEB: d = c1 d + c2 D^-1 r; x_out = x + d
+      const T c2i = reg ? c2invd0 : c2 * invd;
+      const T dv = (c1 == T(0)) ? acc * c2i : fma(c1, d[row], acc * c2i);
+      d[row] = dv;
+      y[row] = xc + dv;
+    }
+  }
+  if (MODE == ST_SPMV_DOT) {
+    __shared__ double sh[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+    if (lane == 0) sh[threadIdx.x >> 5] = dacc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < wpb; ++w) t += sh[w];
+      partials[blockIdx.x] = t;
+    }
+  }
+}
+
+}  // namespace
+
+template <class T>
+void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* b, T* d, T c1,
+                   T c2, double* partials, cudaStream_t s) {
+  if (S.nchunks == 0) {
+    if (mode == ST_SPMV_DOT) fill_double(partials, 0.0, kRedBlocks, s);
+    return;
+  }
+  KernelTimer kt(mode == ST_CHEB || mode == ST_CHEB0 ? SAAMG_KT_STENCIL_SMOOTH : SAAMG_KT_STENCIL_APPLY,
+                 S.n, s);
+  // Reductions use the fixed grid so that partial sums are always taken the same way.
+  int blocks = kRedBlocks;
+  if (mode != ST_SPMV_DOT) {
+    long long need = ((long long)S.nchunks + 7) / 8;
+    blocks = (int)(need < 152 * 16 ? need : 152 * 16);
+  }
+  switch (mode) {
+    case ST_SPMV:
+      stencil_k<T, ST_SPMV><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      break;
+    case ST_SPMV_DOT:
+      stencil_k<T, ST_SPMV_DOT><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      break;
+    case ST_RESID:
+      stencil_k<T, ST_RESID><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      break;
+    case ST_CHEB:
+      stencil_k<T, ST_CHEB><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      break;
+    case ST_CHEB0:
+      stencil_k<T, ST_CHEB0><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      break;
+    default:
+      fail(SAAMG_EINVAL, "bad stencil mode");
+  }
+  SAAMG_LAUNCH();
+}
+
+template void stencil_apply<double>(const StencilDev<double>&, int, const double*, double*,
+                                    const double*, double*, double, double, double*,
+                                    cudaStream_t);
+template void stencil_apply<float>(const StencilDev<float>&, int, const float*, float*,
+                                   const float*, float*, float, float, double*, cudaStream_t);
+
+}  // namespace saamg

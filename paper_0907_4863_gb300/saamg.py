@@ -1,0 +1,357 @@
+"""Thin Python binding of libsaamg (include/saamg.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts torch tensors to
+device pointers, passes torch's current CUDA stream, and routes the library's device
+allocations to torch's caching allocator.  There is no fallback: if libsaamg.so is
+missing or fails to load, every call raises.
+"""
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(PKG, "libsaamg.so")
+
+OK, NOT_CONVERGED = 0, 1
+EINVAL, ENOMEM, ECUDA, NUMERICAL, DEVICE_TIMEOUT, UNIMPLEMENTED = -1, -2, -3, -4, -5, -6
+BC_CONSTANT, BC_LINEAR, BC_QUADRATIC = 0, 1, 2
+Z_ROBIN, Z_DIRICHLET = 0, 1
+PREC_FP64, PREC_FP32, PREC_FP32_BF16 = 0, 1, 2
+KT_STENCIL_SMOOTH, KT_STENCIL_APPLY, KT_COARSE, KT_TRANSFER, KT_SPGEMM = 0, 1, 2, 3, 4
+KT_NAMES = ["stencil_smooth", "stencil_apply", "coarse_csr", "transfer", "spgemm"]
+MAX_LEVELS = 16
+
+
+class SaamgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"saamg status {status}: {msg}")
+        self.status = status
+
+
+class Domain(C.Structure):
+    _fields_ = [("a", C.c_double), ("b", C.c_double), ("taper", C.c_double), ("cx", C.c_double),
+                ("cy", C.c_double), ("zbc", C.c_int), ("symmetrize_gamma2", C.c_int)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("h", C.c_double * 3), ("origin", C.c_double * 3)]
+
+
+class Params(C.Structure):
+    _fields_ = [("cheb_degree", C.c_int), ("cheb_ratio", C.c_double), ("cheb_safety", C.c_double),
+                ("max_coarse", C.c_int), ("max_levels", C.c_int), ("power_iters", C.c_int),
+                ("precision", C.c_int), ("beta_rule", C.c_int), ("maxit", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("relres", C.c_double),
+                ("relres_true", C.c_double), ("solve_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class HierarchyInfo(C.Structure):
+    _fields_ = [("levels", C.c_int), ("n", C.c_int * MAX_LEVELS),
+                ("nnz", C.c_longlong * MAX_LEVELS), ("nnz_p", C.c_longlong * MAX_LEVELS),
+                ("lambda_", C.c_double * MAX_LEVELS), ("device_bytes", C.c_longlong),
+                ("setup_ms", C.c_double)]
+
+    def as_dict(self):
+        L = self.levels
+        return dict(levels=L, n=list(self.n[:L]), nnz=list(self.nnz[:L]), nnz_p=list(self.nnz_p[:L]),
+                    lam=list(self.lambda_[:L]), device_bytes=self.device_bytes, setup_ms=self.setup_ms)
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+_lib = None
+_hooks = None
+
+_p = C.c_void_p
+_i = C.c_int
+
+
+def lib():
+    """Load libsaamg.so (raises if it is missing: there is no other implementation)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIBPATH):
+        raise ImportError(f"{LIBPATH} is missing; build it with paper_0907_4863_gb300.build.build()")
+    L = C.CDLL(LIBPATH)
+    sig = {
+        "saamg_params_default": [C.POINTER(Params)],
+        "saamg_set_allocator": [ALLOC_FN, FREE_FN, _p],
+        "saamg_build_operator": [C.POINTER(Domain), C.POINTER(Grid), _i, _p, C.POINTER(_p)],
+        "saamg_operator_size": [_p, C.POINTER(_i), C.POINTER(C.c_longlong)],
+        "saamg_operator_copy": [_p, _p, _p, _p, _p, _p, _p, _p],
+        "saamg_operator_apply": [_p, _p, _p, _p],
+        "saamg_setup": [_p, C.POINTER(Params), _p, C.POINTER(_p)],
+        "saamg_hierarchy_get_info": [_p, C.POINTER(HierarchyInfo)],
+        "saamg_hierarchy_copy_level": [_p, _i] + [_p] * 12,
+        "saamg_vcycle": [_p, _p, _p, _p],
+        "saamg_solve": [_p, _p, _p, C.c_double, _p, C.POINTER(SolveInfo)],
+        "saamg_solve_host": [_p, _p, _p, C.c_double, _p, C.POINTER(SolveInfo)],
+        "saamg_mis2_aggregate": [_i, _p, _p, _p, C.c_uint32, _p, _p, C.POINTER(_i), _p],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    L.saamg_kernel_launches.argtypes = []
+    L.saamg_kernel_launches.restype = C.c_longlong
+    L.saamg_kernel_timing.argtypes = [_i]
+    L.saamg_kernel_timing.restype = C.c_int
+    L.saamg_kernel_timing_read.argtypes = [_i, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                                           C.POINTER(C.c_longlong)]
+    L.saamg_kernel_timing_read.restype = C.c_int
+    L.saamg_free.argtypes = [_p]
+    L.saamg_free.restype = None
+    L.saamg_last_error.argtypes = []
+    L.saamg_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def last_error():
+    return lib().saamg_last_error().decode()
+
+
+def _check(status, allow_not_converged=False):
+    if status == OK or (allow_not_converged and status == NOT_CONVERGED):
+        return status
+    raise SaamgError(status, last_error())
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def use_torch_allocator():
+    """Route the library's device allocations to torch's caching allocator."""
+    global _hooks
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      stream or 0)
+        except Exception:
+            return None
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    _hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _check(lib().saamg_set_allocator(_hooks[0], _hooks[1], None))
+
+
+def use_cuda_malloc():
+    global _hooks
+    _check(lib().saamg_set_allocator(ALLOC_FN(), FREE_FN(), None))
+    _hooks = None
+
+
+def params_default(**overrides):
+    p = Params()
+    _check(lib().saamg_params_default(C.byref(p)))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+class Operator:
+    """Handle of saamg_build_operator."""
+
+    def __init__(self, handle, grid_n):
+        self.handle = handle
+        self.grid_n = tuple(grid_n)
+
+    def size(self):
+        n = C.c_int(0)
+        nnz = C.c_longlong(0)
+        _check(lib().saamg_operator_size(self.handle, C.byref(n), C.byref(nnz)))
+        return n.value, nnz.value
+
+    def free(self):
+        if self.handle:
+            lib().saamg_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Hierarchy:
+    """Handle of saamg_setup (keeps its operator alive)."""
+
+    def __init__(self, handle, op):
+        self.handle = handle
+        self.op = op
+
+    def info(self):
+        hi = HierarchyInfo()
+        _check(lib().saamg_hierarchy_get_info(self.handle, C.byref(hi)))
+        return hi.as_dict()
+
+    def free(self):
+        if self.handle:
+            lib().saamg_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_operator(domain: Domain, grid: Grid, mode: int, stream=None) -> Operator:
+    h = C.c_void_p()
+    _check(lib().saamg_build_operator(C.byref(domain), C.byref(grid), int(mode), _stream(stream),
+                                      C.byref(h)))
+    return Operator(h, tuple(grid.n))
+
+
+def operator_size(op: Operator):
+    return op.size()
+
+
+def operator_copy(op: Operator, stream=None):
+    """Host copies: node_of_row, scale, rowptr, col, val, is_regular (numpy)."""
+    import numpy as np
+    n, nnz = op.size()
+    out = dict(node_of_row=np.empty(n, np.int32), scale=np.empty(n, np.float64),
+               rowptr=np.empty(n + 1, np.int32), col=np.empty(nnz, np.int32),
+               val=np.empty(nnz, np.float64), is_regular=np.empty(n, np.uint8))
+    P = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    _check(lib().saamg_operator_copy(op.handle, P(out["node_of_row"]), P(out["scale"]),
+                                     P(out["rowptr"]), P(out["col"]), P(out["val"]),
+                                     P(out["is_regular"]), _stream(stream)))
+    return out
+
+
+def operator_apply(op: Operator, x, y, stream=None):
+    _check(lib().saamg_operator_apply(op.handle, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def setup(op: Operator, params: Params = None, stream=None) -> Hierarchy:
+    h = C.c_void_p()
+    _check(lib().saamg_setup(op.handle, C.byref(params) if params is not None else None,
+                             _stream(stream), C.byref(h)))
+    return Hierarchy(h, op)
+
+
+def hierarchy_get_info(h: Hierarchy):
+    return h.info()
+
+
+def hierarchy_copy_level(h: Hierarchy, l: int, stream=None):
+    """Host copies of level l: A (rowptr, col, val), agg, root, P and R (numpy)."""
+    import numpy as np
+    info = h.info()
+    n = info["n"][l]
+    nnz = info["nnz"][l]
+    has_next = l + 1 < info["levels"]
+    nn = info["n"][l + 1] if has_next else 0
+    np_ = info["nnz_p"][l] if has_next else 0
+    out = dict(rowptr=np.empty(n + 1, np.int32), col=np.empty(nnz, np.int32),
+               val=np.empty(nnz, np.float64))
+    if has_next:
+        out.update(agg=np.empty(n, np.int32), root=np.empty(n, np.uint8),
+                   p_rowptr=np.empty(n + 1, np.int32), p_col=np.empty(np_, np.int32),
+                   p_val=np.empty(np_, np.float64), r_rowptr=np.empty(nn + 1, np.int32),
+                   r_col=np.empty(np_, np.int32), r_val=np.empty(np_, np.float64))
+    P = lambda k: out[k].ctypes.data_as(C.c_void_p) if k in out else None  # noqa: E731
+    _check(lib().saamg_hierarchy_copy_level(h.handle, int(l), P("rowptr"), P("col"), P("val"),
+                                            P("agg"), P("root"), P("p_rowptr"), P("p_col"),
+                                            P("p_val"), P("r_rowptr"), P("r_col"), P("r_val"),
+                                            _stream(stream)))
+    return out
+
+
+def vcycle(h: Hierarchy, r, z, stream=None):
+    _check(lib().saamg_vcycle(h.handle, _ptr(r), _ptr(z), _stream(stream)))
+
+
+def solve(h: Hierarchy, rho, phi, rtol=1e-8, stream=None):
+    """rho, phi: float64 CUDA tensors over the whole box; phi = initial guess in, solution out."""
+    info = SolveInfo()
+    st = lib().saamg_solve(h.handle, _ptr(rho), _ptr(phi), float(rtol), _stream(stream),
+                           C.byref(info))
+    _check(st, allow_not_converged=True)
+    d = info.as_dict()
+    d["status"] = st
+    return d
+
+
+def solve_host(h: Hierarchy, rho, phi, rtol=1e-8, stream=None):
+    """Host (numpy float64) box arrays; the copies to and from the device are in the call."""
+    info = SolveInfo()
+    st = lib().saamg_solve_host(h.handle, rho.ctypes.data_as(C.c_void_p),
+                                phi.ctypes.data_as(C.c_void_p), float(rtol), _stream(stream),
+                                C.byref(info))
+    _check(st, allow_not_converged=True)
+    d = info.as_dict()
+    d["status"] = st
+    return d
+
+
+def mis2_aggregate(rowptr, col, ids, seed, root, agg, stream=None):
+    """Device CSR (int32 tensors), ids (int32/uint32 tensor or None) -> root (uint8), agg (int32)."""
+    nagg = C.c_int(0)
+    n = rowptr.numel() - 1
+    _check(lib().saamg_mis2_aggregate(int(n), _ptr(rowptr), _ptr(col), _ptr(ids),
+                                      int(seed) & 0xFFFFFFFF, _ptr(root), _ptr(agg),
+                                      C.byref(nagg), _stream(stream)))
+    return nagg.value
+
+
+def free(handle):
+    if isinstance(handle, (Operator, Hierarchy)):
+        handle.free()
+    elif handle:
+        lib().saamg_free(handle)
+
+
+def make_domain(d) -> Domain:
+    """From paper_0907_4863_gb300.inputs.Domain (or any object with the same fields)."""
+    return Domain(d.a, d.b, d.taper, d.cx, d.cy, d.zbc, d.symmetrize)
+
+
+def make_grid(g) -> Grid:
+    gr = Grid()
+    for k in range(3):
+        gr.n[k] = g.n[k]
+        gr.h[k] = g.h[k]
+        gr.origin[k] = g.origin[k]
+    return gr
+
+
+def kernel_launches():
+    """Number of kernels libsaamg has launched in this process."""
+    return int(lib().saamg_kernel_launches())
+
+
+def kernel_timing(enable: bool):
+    _check(lib().saamg_kernel_timing(1 if enable else 0))
+
+
+def kernel_timing_read(kclass: int):
+    """(total_ms, launches, rows) of a kernel class since the last read; resets it."""
+    ms = C.c_double(0)
+    n = C.c_longlong(0)
+    rows = C.c_longlong(0)
+    _check(lib().saamg_kernel_timing_read(int(kclass), C.byref(ms), C.byref(n), C.byref(rows)))
+    return ms.value, n.value, rows.value
