@@ -196,6 +196,20 @@ saamg_status saamg_mis2_aggregate(int n, const int *rowptr, const int *col, cons
                                   uint32_t seed, unsigned char *root, int *agg, int *n_agg,
                                   void *stream);
 
+/* saamg_mis2_aggregate without any device allocation (the paper has no counterpart; it
+ * exists for callers that cannot allocate device memory at the point of the call, such as
+ * code inside a fixed memory pool or a callback that must not re-enter the allocator).
+ * Same arguments, rule and results as saamg_mis2_aggregate.  Its scratch is one static
+ * device array of about 5.8 MB per device that loads the library, held until the process
+ * exits; graphs with more than 262,144 nodes are rejected with EINVAL.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress), so make that first
+ * call before any stream capture.  Calls share the array: two calls whose GPU work
+ * overlaps (other streams, other host threads) race and give undefined results.  Nothing
+ * from an earlier call is read: every call initialises the parts it uses. */
+saamg_status saamg_mis2_aggregate_noalloc(int n, const int *rowptr, const int *col,
+                                          const uint32_t *ids, uint32_t seed, unsigned char *root,
+                                          int *agg, int *n_agg, void *stream);
+
 /* Kernel classes for saamg_kernel_timing_read. */
 typedef enum {
   SAAMG_KT_STENCIL_SMOOTH = 0, /* level-0 Chebyshev step fused with the residual */

@@ -10,6 +10,8 @@
 // sequential greedy rule (visit by decreasing priority, join unless a member is within
 // distance 2) -- the determinism result for parallel greedy MIS of Blelloch, Fineman and
 // Shun (2012), applied to the square of the graph.
+#include <mutex>
+
 #include "aggregate.cuh"
 
 namespace saamg {
@@ -260,6 +262,43 @@ int mis2_aggregate(int n, const int* rowptr, const int* col, long long nnz, cons
   return (int)nagg;
 }
 
+int mis2_aggregate_into(int n, const int* rowptr, const int* col, long long nnz,
+                        const unsigned* ids, uint32_t seed, unsigned char* root, int* agg,
+                        const AggScratch& w, long long* tiles, cudaStream_t s) {
+  if (n <= 0) return 0;
+  double avg = (double)nnz / (double)n;
+  SAAMG_CUDA(cudaMemsetAsync(w.state, 0, (size_t)n, s));
+  if (avg <= 8.0)
+    rounds<4>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, s);
+  else if (avg <= 24.0)
+    rounds<8>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, s);
+  else if (avg <= 64.0)
+    rounds<16>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, s);
+  else
+    rounds<32>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, s);
+  roots_from_state_k<<<(n + 255) / 256, 256, 0, s>>>(n, w.state, root);
+  SAAMG_LAUNCH();
+  fill_int(w.root1, -1, (size_t)n, s);
+  agg_phase1_k<<<(n + 255) / 256, 256, 0, s>>>(n, rowptr, col, root, w.root1);
+  SAAMG_LAUNCH();
+  SAAMG_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(int), s));
+  if (avg <= 8.0)
+    phase2<4>(n, rowptr, col, ids, seed, w.root1, w.aggroot, w.counter, s);
+  else if (avg <= 24.0)
+    phase2<8>(n, rowptr, col, ids, seed, w.root1, w.aggroot, w.counter, s);
+  else if (avg <= 64.0)
+    phase2<16>(n, rowptr, col, ids, seed, w.root1, w.aggroot, w.counter, s);
+  else
+    phase2<32>(n, rowptr, col, ids, seed, w.root1, w.aggroot, w.counter, s);
+  long long nagg = exclusive_scan_u8_into(root, w.rank, n, tiles, s);
+  agg_number_k<<<(n + 255) / 256, 256, 0, s>>>(n, w.aggroot, w.rank, agg);
+  SAAMG_LAUNCH();
+  int err = 0;
+  d2h_sync(&err, w.counter, sizeof(int), s);
+  if (err) fail(SAAMG_NUMERICAL, "aggregation left a node without an aggregate");
+  return (int)nagg;
+}
+
 void AggScratchBufs::alloc(int n, cudaStream_t s) {
   state.alloc(n, s);
   o1.alloc(n, s);
@@ -283,3 +322,98 @@ AggScratch AggScratchBufs::view() const {
 }
 
 }  // namespace saamg
+
+// ===========================================================================
+// Allocation-free variant of saamg_mis2_aggregate.
+//
+// Some callers cannot allocate device memory at the moment they need an aggregation:
+// code running inside a memory pool that must not grow, a host thread that holds a lock
+// the allocator also takes, or a framework whose allocator may not be re-entered from a
+// callback.  For them the scratch of the aggregation lives in one array with static
+// storage on every device that loads this library (kNoallocBytes, held until the process
+// exits), so the call itself allocates nothing: no cudaMalloc, cudaFree, allocator hook or
+// temporary buffer.  The price is a size limit and no concurrency: calls share the array.
+// ===========================================================================
+namespace saamg {
+namespace {
+
+constexpr int kNoallocMaxNodes = 1 << 18;  // 262,144 graph nodes
+constexpr size_t kAlignN(size_t b) { return (b + 255) & ~size_t(255); }
+constexpr size_t kOffState = 0;
+constexpr size_t kOffO1 = kOffState + kAlignN(kNoallocMaxNodes);
+constexpr size_t kOffM1 = kOffO1 + kAlignN(kNoallocMaxNodes);
+constexpr size_t kOffCounter = kOffM1 + kAlignN(sizeof(unsigned long long) * kNoallocMaxNodes);
+constexpr size_t kOffRoot1 = kOffCounter + 256;
+constexpr size_t kOffAggroot = kOffRoot1 + kAlignN(sizeof(int) * kNoallocMaxNodes);
+constexpr size_t kOffRank = kOffAggroot + kAlignN(sizeof(int) * kNoallocMaxNodes);
+constexpr size_t kOffTiles = kOffRank + kAlignN(sizeof(int) * kNoallocMaxNodes);
+constexpr size_t kTileEntries = kNoallocMaxNodes / 2048 + 2;
+constexpr size_t kNoallocBytes = kOffTiles + kAlignN(sizeof(long long) * kTileEntries);
+
+// The scratch itself (about 5.8 MB).  Every call overwrites what it reads before reading
+// it; nothing carries over between calls.
+static __device__ __align__(256) unsigned char g_mis2_scratch[kNoallocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch on the current device, looked up once per device.
+unsigned char* noalloc_scratch() {
+  int dev = 0;
+  SAAMG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) fail(SAAMG_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_mis2_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      fail(SAAMG_ECUDA, std::string("cudaGetSymbolAddress of the aggregation scratch: ") +
+                            cudaGetErrorString(e));
+    }
+    g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  return g_noalloc_ptr[dev];
+}
+
+}  // namespace
+}  // namespace saamg
+
+extern "C" saamg_status saamg_mis2_aggregate_noalloc(int n, const int* rowptr, const int* col,
+                                                     const uint32_t* ids, uint32_t seed,
+                                                     unsigned char* root, int* agg, int* n_agg,
+                                                     void* stream) {
+  using namespace saamg;
+  try {
+    if (n < 0 || !n_agg) fail(SAAMG_EINVAL, "bad size or NULL n_agg");
+    *n_agg = 0;
+    if (n > kNoallocMaxNodes)
+      fail(SAAMG_EINVAL, "graph has " + std::to_string(n) + " nodes; the allocation-free "
+                         "aggregation handles at most " + std::to_string(kNoallocMaxNodes));
+    if (n == 0) return SAAMG_OK;
+    if (!rowptr || !col || !root || !agg) fail(SAAMG_EINVAL, "NULL array");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* base = noalloc_scratch();
+    AggScratch w;
+    w.state = base + kOffState;
+    w.o1 = base + kOffO1;
+    w.m1 = reinterpret_cast<unsigned long long*>(base + kOffM1);
+    w.counter = reinterpret_cast<int*>(base + kOffCounter);
+    w.root1 = reinterpret_cast<int*>(base + kOffRoot1);
+    w.aggroot = reinterpret_cast<int*>(base + kOffAggroot);
+    w.rank = reinterpret_cast<int*>(base + kOffRank);
+    long long* tiles = reinterpret_cast<long long*>(base + kOffTiles);
+    int nnz = 0;
+    d2h_sync(&nnz, rowptr + n, sizeof(int), s);
+    *n_agg = mis2_aggregate_into(n, rowptr, col, nnz, ids, seed, root, agg, w, tiles, s);
+    SAAMG_CUDA(cudaStreamSynchronize(s));
+    return SAAMG_OK;
+  } catch (const Error& e) {
+    set_last_error(std::string("saamg_mis2_aggregate_noalloc: ") + e.msg);
+    return e.status;
+  } catch (...) {
+    set_last_error("saamg_mis2_aggregate_noalloc: unexpected exception");
+    return SAAMG_ECUDA;
+  }
+}

@@ -31,4 +31,10 @@ int mis2_aggregate(int n, const int* rowptr, const int* col, long long nnz, cons
                    uint32_t seed, unsigned char* root, int* agg, const AggScratch& w,
                    cudaStream_t s);
 
+// The same aggregation with every temporary in caller-provided scratch (w and `tiles`,
+// scan_u8_tiles_needed(n) entries); allocates nothing.
+int mis2_aggregate_into(int n, const int* rowptr, const int* col, long long nnz,
+                        const unsigned* ids, uint32_t seed, unsigned char* root, int* agg,
+                        const AggScratch& w, long long* tiles, cudaStream_t s);
+
 }  // namespace saamg

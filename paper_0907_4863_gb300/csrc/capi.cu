@@ -26,6 +26,8 @@ static thread_local std::string g_last_error;
 
 void fail(saamg_status st, const std::string& msg) { throw Error{st, msg}; }
 
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
 void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
   if (e == cudaSuccess) return;
   std::string m = std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" +

@@ -25,6 +25,8 @@ struct Error {
 void check_cuda(cudaError_t e, const char* what, const char* file, int line);
 
 void count_launch();
+// Stores the message returned by saamg_last_error() for the calling thread.
+void set_last_error(const std::string& msg);
 
 #define SAAMG_CUDA(x) ::saamg::check_cuda((x), #x, __FILE__, __LINE__)
 #define SAAMG_LAUNCH()                                                                  \
@@ -162,6 +164,11 @@ constexpr int kRedThreads = 256;
 // scan.cu
 long long exclusive_scan(const int* in, int* out, int n, cudaStream_t s);  // returns the total
 long long exclusive_scan_u8(const unsigned char* in, int* out, int n, cudaStream_t s);
+// Same scan of bytes with caller-provided tile scratch (scan_u8_tiles_needed(n) entries);
+// allocates nothing.
+long long scan_u8_tiles_needed(int n);
+long long exclusive_scan_u8_into(const unsigned char* in, int* out, int n, long long* tiles,
+                                 cudaStream_t s);
 void fill_int(int* p, int v, size_t n, cudaStream_t s);
 void fill_double(double* p, double v, size_t n, cudaStream_t s);
 void sum_partials(const double* partials, int count, double* out, cudaStream_t s);

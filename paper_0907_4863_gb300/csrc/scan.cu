@@ -136,6 +136,23 @@ __global__ void sum_partials_k(const double* __restrict__ part, int count, doubl
 
 }  // namespace
 
+long long scan_u8_tiles_needed(int n) { return n > 0 ? (n + kScanTile - 1) / kScanTile + 1 : 1; }
+
+long long exclusive_scan_u8_into(const unsigned char* in, int* out, int n, long long* tiles,
+                                 cudaStream_t s) {
+  if (n <= 0) return 0;
+  int ntiles = (n + kScanTile - 1) / kScanTile;
+  scan_tiles<unsigned char><<<ntiles, kScanThreads, 0, s>>>(in, out, tiles, n);
+  SAAMG_LAUNCH();
+  scan_tile_sums<<<1, kScanThreads, 0, s>>>(tiles, ntiles, tiles + ntiles);
+  SAAMG_LAUNCH();
+  scan_add<<<ntiles, 256, 0, s>>>(out, tiles, n);
+  SAAMG_LAUNCH();
+  long long total = 0;
+  d2h_sync(&total, tiles + ntiles, sizeof(long long), s);
+  return total;
+}
+
 long long exclusive_scan(const int* in, int* out, int n, cudaStream_t s) {
   return scan_impl<int>(in, out, n, s);
 }

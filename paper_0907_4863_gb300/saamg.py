@@ -94,6 +94,7 @@ def lib():
         "saamg_solve": [_p, _p, _p, C.c_double, _p, C.POINTER(SolveInfo)],
         "saamg_solve_host": [_p, _p, _p, C.c_double, _p, C.POINTER(SolveInfo)],
         "saamg_mis2_aggregate": [_i, _p, _p, _p, C.c_uint32, _p, _p, C.POINTER(_i), _p],
+        "saamg_mis2_aggregate_noalloc": [_i, _p, _p, _p, C.c_uint32, _p, _p, C.POINTER(_i), _p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -315,6 +316,18 @@ def mis2_aggregate(rowptr, col, ids, seed, root, agg, stream=None):
     _check(lib().saamg_mis2_aggregate(int(n), _ptr(rowptr), _ptr(col), _ptr(ids),
                                       int(seed) & 0xFFFFFFFF, _ptr(root), _ptr(agg),
                                       C.byref(nagg), _stream(stream)))
+    return nagg.value
+
+
+def mis2_aggregate_noalloc(rowptr, col, ids, seed, root, agg, stream=None):
+    """Same as mis2_aggregate, for callers that cannot allocate device memory during the call:
+    the library uses its own static scratch (graphs of at most 262,144 nodes; calls must not
+    overlap on the GPU).  The caller still provides every input and output tensor."""
+    nagg = C.c_int(0)
+    n = rowptr.numel() - 1
+    _check(lib().saamg_mis2_aggregate_noalloc(int(n), _ptr(rowptr), _ptr(col), _ptr(ids),
+                                              int(seed) & 0xFFFFFFFF, _ptr(root), _ptr(agg),
+                                              C.byref(nagg), _stream(stream)))
     return nagg.value
 
 
