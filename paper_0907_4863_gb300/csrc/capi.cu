@@ -276,7 +276,8 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
       L.agg.release();
       break;
     }
-    L.lambda = power_lambda(A, L.invd.p, ids, prm.power_iters, s);
+    const StencilDev<double> S0 = od.view<double>();
+    L.lambda = power_lambda(A, L.invd.p, ids, prm.power_iters, s, l == 0 ? &S0 : nullptr);
     L.omega = 4.0 / (3.0 * L.lambda);
     pt.mark("L" + std::to_string(l) + ".lambda");
     DevCsr T, AT, AP;
@@ -677,6 +678,9 @@ saamg_status saamg_build_operator(const saamg_domain* domain, const saamg_grid* 
     g.zbc = domain->zbc;
     g.sym = domain->symmetrize_gamma2 ? 1 : 0;
     g.mode = mode;
+    for (int d = 0; d < 3; ++d) g.cdir[d] = 1.0 / (g.h[d] * g.h[d]);
+    const double dist = 0.5 * ((double)(g.nz - 1) * g.h[2]);  // Robin distance d
+    g.robin = (2.0 * g.h[2]) / dist;
     auto op = std::make_unique<saamg_operator>();
     op->stream = (cudaStream_t)stream;
     build_operator_data(g, (cudaStream_t)stream, op->d);

@@ -11,6 +11,7 @@
 
 #include "csr.cuh"
 #include "galerkin.cuh"
+#include "operator.cuh"
 
 namespace saamg {
 
@@ -34,9 +35,9 @@ __global__ void power_init_k(int n, const unsigned* __restrict__ ids, double* __
 
 __global__ void power_normalize_k(int n, const double* __restrict__ w,
                                   const double* __restrict__ nrm2, double* __restrict__ v) {
-  double nrm = sqrt(*nrm2);
+  const double inv = 1.0 / sqrt(*nrm2);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    v[i] = w[i] / nrm;
+    v[i] = w[i] * inv;
 }
 
 // --- sparse product --------------------------------------------------------
@@ -73,36 +74,55 @@ __device__ __forceinline__ int hash_find(const int* keys, int logcap, int key) {
   return -1;
 }
 
-// Symbolic pass: number of distinct columns of each listed row (-1 on overflow).
-__global__ void spgemm_symbolic_k(const int* __restrict__ list, int nlist, int logcap,
-                                  int* __restrict__ gkeys, CsrView X, CsrView Y,
-                                  int* __restrict__ count, int* __restrict__ overflow) {
+// Warp-wide exclusive prefix of v; *total gets the sum over the warp.
+__device__ __forceinline__ int warp_excl_scan(int v, int lane, int* total) {
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  *total = __shfl_sync(0xffffffffu, inc, 31);
+  return inc - v;
+}
+
+// Hash path, symbolic: distinct columns of each listed row (-1 and an overflow count when a
+// row does not fit half of the table).  Lanes take 32 entries of X's row at a time and
+// insert the columns of their Y rows; insertion order does not matter for the count.
+__global__ void __launch_bounds__(128) spgemm_hash_symbolic_k(const int* __restrict__ list,
+                                                              int nlist, int logcap, CsrView X,
+                                                              CsrView Y, int* __restrict__ count,
+                                                              int* __restrict__ overflow) {
   extern __shared__ int smem_i[];
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
   const int cap = 1 << logcap;
+  int* keys = smem_i + (threadIdx.x >> 5) * cap;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  int* keys = gkeys ? gkeys + (size_t)gw * cap : smem_i + wib * cap;
   for (int t = gw; t < nlist; t += nw) {
     const int i = list[t];
     for (int q = lane; q < cap; q += 32) keys[q] = -1;
     __syncwarp();
     int cnt = 0, full = 0;
-    for (int p = X.rowptr[i]; p < X.rowptr[i + 1]; ++p) {
-      const int k = X.col[p];
-      for (int q = Y.rowptr[k] + lane; q < Y.rowptr[k + 1]; q += 32) {
-        int r = hash_insert(keys, logcap, Y.col[q]);
-        if (r > 0) ++cnt;
-        if (r < 0) full = 1;
+    const int p1 = X.rowptr[i + 1];
+    for (int pb = X.rowptr[i]; pb < p1; pb += 32) {
+      const int p = pb + lane;
+      if (p < p1) {
+        const int k = X.col[p];
+        for (int q = Y.rowptr[k]; q < Y.rowptr[k + 1]; ++q) {
+          const int r = hash_insert(keys, logcap, Y.col[q]);
+          cnt += r > 0;
+          full |= r < 0;
+        }
       }
     }
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
       full |= __shfl_xor_sync(0xffffffffu, full, o);
     }
     if (lane == 0) {
-      bool over = full || 2 * cnt > cap;
+      const bool over = full || 2 * cnt > cap;
       count[i] = over ? -1 : cnt;
       if (over) atomicAdd(overflow, 1);
     }
@@ -110,27 +130,29 @@ __global__ void spgemm_symbolic_k(const int* __restrict__ list, int nlist, int l
   }
 }
 
-// Numeric pass: fixed-order accumulation, then rank-sort of the distinct columns.
-__global__ void spgemm_numeric_k(const int* __restrict__ list, int nlist, int logcap,
-                                 int* __restrict__ gkeys, double* __restrict__ gvals, CsrView X,
-                                 CsrView Y, const int* __restrict__ crowptr,
-                                 int* __restrict__ ccol, double* __restrict__ cval) {
+// Hash path, numeric.  1) insert every column (lane-parallel); 2) compact the distinct
+// columns and give each its rank in ascending order; 3) accumulate the products one X
+// entry at a time (lanes over the distinct columns of one Y row: no two lanes share a
+// slot), which fixes the summation order; 4) write the row in ascending column order.
+// Per warp: cap keys, cap ranks, cap/2 compacted keys (ints) and cap values (doubles).
+__global__ void __launch_bounds__(128) spgemm_hash_numeric_k(const int* __restrict__ list,
+                                                             int nlist, int logcap, CsrView X,
+                                                             CsrView Y,
+                                                             const int* __restrict__ crowptr,
+                                                             int* __restrict__ ccol,
+                                                             double* __restrict__ cval) {
   extern __shared__ double smem_d[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
   const int cap = 1 << logcap;
+  double* vals = smem_d + (size_t)wib * cap;
+  int* ibase = reinterpret_cast<int*>(smem_d + (size_t)wpb * cap) + (size_t)wib * (cap * 5 / 2);
+  int* keys = ibase;
+  int* rank = ibase + cap;
+  int* uniq = ibase + 2 * cap;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  double* vals;
-  int* keys;
-  if (gkeys) {
-    vals = gvals + (size_t)gw * cap;
-    keys = gkeys + (size_t)gw * cap;
-  } else {
-    vals = smem_d + (size_t)wib * cap;
-    keys = reinterpret_cast<int*>(smem_d + (size_t)wpb * cap) + wib * cap;
-  }
   for (int t = gw; t < nlist; t += nw) {
     const int i = list[t];
     for (int q = lane; q < cap; q += 32) {
@@ -139,32 +161,46 @@ __global__ void spgemm_numeric_k(const int* __restrict__ list, int nlist, int lo
     }
     __syncwarp();
     const int p0 = X.rowptr[i], p1 = X.rowptr[i + 1];
-    for (int p = p0; p < p1; ++p) {
-      const int k = X.col[p];
-      for (int q = Y.rowptr[k] + lane; q < Y.rowptr[k + 1]; q += 32) hash_insert(keys, logcap, Y.col[q]);
+    for (int pb = p0; pb < p1; pb += 32) {
+      const int p = pb + lane;
+      if (p < p1) {
+        const int k = X.col[p];
+        for (int q = Y.rowptr[k]; q < Y.rowptr[k + 1]; ++q) hash_insert(keys, logcap, Y.col[q]);
+      }
+    }
+    __syncwarp();
+    // compact the distinct columns
+    int nu = 0;
+    for (int q0 = 0; q0 < cap; q0 += 32) {
+      const int key = keys[q0 + lane];
+      const unsigned bm = __ballot_sync(0xffffffffu, key >= 0);
+      if (key >= 0) uniq[nu + __popc(bm & ((1u << lane) - 1u))] = key;
+      nu += __popc(bm);
+    }
+    __syncwarp();
+    for (int q = lane; q < cap; q += 32) {
+      const int key = keys[q];
+      if (key < 0) continue;
+      int r = 0;
+      for (int u = 0; u < nu; ++u) r += uniq[u] < key;
+      rank[q] = r;
     }
     __syncwarp();
     for (int p = p0; p < p1; ++p) {
       const int k = X.col[p];
       const double xv = X.val[p];
-      // the columns of one Y row are distinct: every lane owns a different slot
       for (int q = Y.rowptr[k] + lane; q < Y.rowptr[k + 1]; q += 32) {
-        int slot = hash_find(keys, logcap, Y.col[q]);
+        const int slot = hash_find(keys, logcap, Y.col[q]);
         if (slot >= 0) vals[slot] += xv * Y.val[q];
       }
       __syncwarp();
     }
     const int base = crowptr[i];
     for (int q = lane; q < cap; q += 32) {
-      int key = keys[q];
+      const int key = keys[q];
       if (key < 0) continue;
-      int rank = 0;
-      for (int u = 0; u < cap; ++u) {
-        int ku = keys[u];
-        rank += (ku >= 0 && ku < key);
-      }
-      ccol[base + rank] = key;
-      cval[base + rank] = vals[q];
+      ccol[base + rank[q]] = key;
+      cval[base + rank[q]] = vals[q];
     }
     __syncwarp();
   }
@@ -192,8 +228,6 @@ __global__ void __launch_bounds__(128) spgemm_esc_k(const int* __restrict__ list
     const int i = list[t];
     const int p1 = X.rowptr[i + 1];
     int nprod = 0;
-    // lanes take 32 entries of X's row at a time; a warp scan of the Y-row lengths gives
-    // every product its index (X entry order, then Y entry order)
     for (int pb = X.rowptr[i]; pb < p1; pb += 32) {
       const int p = pb + lane;
       const bool ok = p < p1;
@@ -201,14 +235,8 @@ __global__ void __launch_bounds__(128) spgemm_esc_k(const int* __restrict__ list
       const double xv = (NUMERIC && ok) ? X.val[p] : 0.0;
       const int q0 = ok ? Y.rowptr[k] : 0;
       const int len = ok ? Y.rowptr[k + 1] - q0 : 0;
-      int off = len;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, off, o);
-        if (lane >= o) off += v;
-      }
-      const int total = __shfl_sync(0xffffffffu, off, 31);
-      off -= len;
+      int total;
+      const int off = warp_excl_scan(len, lane, &total);
       for (int q = 0; q < len; ++q) {
         const int idx = nprod + off + q;
         keys[idx] = ((unsigned long long)(uint32_t)Y.col[q0 + q] << 32) | (uint32_t)idx;
@@ -220,11 +248,11 @@ __global__ void __launch_bounds__(128) spgemm_esc_k(const int* __restrict__ list
     while (m < nprod) m <<= 1;
     for (int idx = nprod + lane; idx < m; idx += 32) keys[idx] = ~0ull;
     __syncwarp();
-    // bitonic sort, ascending
+    // bitonic sort, ascending; pairs (lo, lo + stride) with bit `stride` of lo clear
     for (int size = 2; size <= m; size <<= 1) {
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
         for (int e = lane; e < (m >> 1); e += 32) {
-          const int lo = (e / stride) * 2 * stride + (e % stride);
+          const int lo = e + (e & ~(stride - 1));
           const int hi = lo + stride;
           const bool asc = (lo & size) == 0;
           const unsigned long long ka = keys[lo], kb = keys[hi];
@@ -241,7 +269,6 @@ __global__ void __launch_bounds__(128) spgemm_esc_k(const int* __restrict__ list
         __syncwarp();
       }
     }
-    // compress: one output entry per run of equal columns
     const int outbase = NUMERIC ? crowptr[i] : 0;
     int run = 0;
     for (int c0 = 0; c0 < nprod; c0 += 32) {
@@ -318,26 +345,44 @@ __global__ void __launch_bounds__(128) spgemm_row_k(const int* __restrict__ list
   }
 }
 
-// Row classes: 0..5 = ESC with 32 << class product slots, 6 = hash table.
-constexpr int kEscClasses = 6;
-constexpr int kClasses = kEscClasses + 1;
+// Row classes.  0: <= 32 products (thread per row); 1: <= 64 products (warp ESC);
+// 2 + (log2(table) - kHashMinLog): hash table of 2^log2 slots, log2 in [kHashMinLog, kHashMaxLog].
+constexpr int kHashMinLog = 6;
+constexpr int kHashMaxLog = 12;
+constexpr int kClasses = 2 + (kHashMaxLog - kHashMinLog + 1);
 
-// Class of every row from its number of products; per-block counts in shared memory,
-// one global atomic per class and block.
-__global__ void classify_rows_k(int n, CsrView X, CsrView Y, int* __restrict__ cls,
-                                int* __restrict__ hist) {
+__global__ void row_products_k(int n, CsrView X, CsrView Y, int* __restrict__ nprod) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  long long t = 0;
+  for (int p = X.rowptr[i]; p < X.rowptr[i + 1]; ++p) {
+    int k = X.col[p];
+    t += Y.rowptr[k + 1] - Y.rowptr[k];
+  }
+  nprod[i] = (int)(t < 0x7fffffffLL ? t : 0x7fffffffLL);
+}
+
+// Class of every row (symbolic: table sized from min(products, m); numeric: from the exact
+// count); block-aggregated histogram.
+__global__ void classify_rows_k(int n, const int* __restrict__ nprod, const int* __restrict__ cnt,
+                                int m, int* __restrict__ cls, int* __restrict__ hist) {
   __shared__ int sh[kClasses];
   if (threadIdx.x < kClasses) sh[threadIdx.x] = 0;
   __syncthreads();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
-    long long t = 0;
-    for (int p = X.rowptr[i]; p < X.rowptr[i + 1]; ++p) {
-      int k = X.col[p];
-      t += Y.rowptr[k + 1] - Y.rowptr[k];
+    const int np = nprod[i];
+    int c;
+    if (np <= 32) {
+      c = 0;
+    } else if (np <= 64) {
+      c = 1;
+    } else {
+      long long need = cnt ? cnt[i] : (np < m ? np : m);
+      int lg = kHashMinLog;
+      while (lg < kHashMaxLog && (1LL << lg) < 2 * need) ++lg;
+      c = 2 + lg - kHashMinLog;
     }
-    int c = 0;
-    while (c < kEscClasses && (32LL << c) < t) ++c;
     cls[i] = c;
     atomicAdd(&sh[c], 1);
   }
@@ -428,8 +473,6 @@ __global__ void rank_rows_k(int n, const int* __restrict__ rowptr, const int* __
 
 inline int blocks_for(long long n, int t = 256) { return (int)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1); }
 
-constexpr int kMinLog = 5;    // 32 slots
-constexpr int kMaxSmemLog = 11;  // 2048 slots in shared memory
 constexpr int kSpgemmWarps = 4;
 
 CsrView view(const DevCsr& a) { return CsrView{a.rowptr.p, a.col.p, a.val.p}; }
@@ -437,7 +480,7 @@ CsrView view(const DevCsr& a) { return CsrView{a.rowptr.p, a.col.p, a.val.p}; }
 }  // namespace
 
 double power_lambda(const DevCsr& A, const double* invd, const unsigned* ids, int iters,
-                    cudaStream_t s) {
+                    cudaStream_t s, const StencilDev<double>* S) {
   int n = A.n;
   if (n == 0) return 1.0;
   Buf<double> v, w, part, nrm2;
@@ -449,8 +492,11 @@ double power_lambda(const DevCsr& A, const double* invd, const unsigned* ids, in
   SAAMG_LAUNCH();
   double avg = (double)A.nnz / n;
   for (int it = 0; it <= iters; ++it) {
-    csr_apply<double, double>(CSR_SPMV_DINV_DOT, n, A.rowptr.p, A.col.p, A.val.p, avg, v.p, w.p,
-                              nullptr, nullptr, invd, 0.0, 0.0, part.p, s);
+    if (S)
+      stencil_apply<double>(*S, ST_DINV_DOT, v.p, w.p, nullptr, nullptr, 0.0, 0.0, part.p, s);
+    else
+      csr_apply<double, double>(CSR_SPMV_DINV_DOT, n, A.rowptr.p, A.col.p, A.val.p, avg, v.p,
+                                w.p, nullptr, nullptr, invd, 0.0, 0.0, part.p, s);
     sum_partials(part.p, kRedBlocks, nrm2.p, s);
     if (it == iters) break;
     power_normalize_k<<<std::min(blocks_for(n), 4096), 256, 0, s>>>(n, w.p, nrm2.p, v.p);
@@ -472,42 +518,67 @@ void tentative(const int* agg, int n, int nagg, DevCsr& T, cudaStream_t s) {
   SAAMG_LAUNCH();
 }
 
-template <int CAP, bool NUMERIC>
-static void launch_esc(const int* list, int nl, CsrView X, CsrView Y, const int* crowptr,
-                       int* count, int* ccol, double* cval, cudaStream_t s) {
-  const int warps = 4;
-  const size_t sm = (size_t)warps * CAP * (NUMERIC ? 16 : 8);
-  if (sm > 48 * 1024)
-    SAAMG_CUDA(cudaFuncSetAttribute(spgemm_esc_k<CAP, NUMERIC>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  const int blocks = std::min((nl + warps - 1) / warps, 152 * 16);
-  spgemm_esc_k<CAP, NUMERIC><<<blocks, 32 * warps, sm, s>>>(list, nl, X, Y, crowptr, count, ccol,
-                                                             cval);
+namespace {
+
+// Bins rows into per-class lists; returns the per-class counts and list offsets.
+void bin_rows(int n, const int* nprod, const int* cnt, int m, int* cls, int* list, int* ctl,
+              int hist[kClasses], int start[kClasses + 1], cudaStream_t s) {
+  SAAMG_CUDA(cudaMemsetAsync(ctl, 0, sizeof(int) * 2 * kClasses, s));
+  classify_rows_k<<<blocks_for(n), 256, 0, s>>>(n, nprod, cnt, m, cls, ctl);
   SAAMG_LAUNCH();
+  d2h_sync(hist, ctl, sizeof(int) * kClasses, s);
+  start[0] = 0;
+  for (int c = 0; c < kClasses; ++c) start[c + 1] = start[c] + hist[c];
+  SAAMG_CUDA(cudaMemcpyAsync(ctl + kClasses, start, sizeof(int) * kClasses, cudaMemcpyHostToDevice, s));
+  scatter_rows_k<<<blocks_for(n), 256, 0, s>>>(n, cls, ctl + kClasses, list);
+  SAAMG_LAUNCH();
+  SAAMG_CUDA(cudaStreamSynchronize(s));  // `start` lives on this frame
 }
 
 template <bool NUMERIC>
-static void esc_class(int c, const int* list, int nl, CsrView X, CsrView Y, const int* crowptr,
-                      int* count, int* ccol, double* cval, cudaStream_t s) {
-  switch (c) {
-    case 0: {
-      const int blocks = std::max(1, std::min((nl + 127) / 128, 152 * 16));
-      spgemm_row_k<NUMERIC><<<blocks, 128, 0, s>>>(list, nl, X, Y, crowptr, count, ccol, cval);
-      SAAMG_LAUNCH();
-      break;
-    }
-    case 1: launch_esc<64, NUMERIC>(list, nl, X, Y, crowptr, count, ccol, cval, s); break;
-    case 2: launch_esc<128, NUMERIC>(list, nl, X, Y, crowptr, count, ccol, cval, s); break;
-    case 3: launch_esc<256, NUMERIC>(list, nl, X, Y, crowptr, count, ccol, cval, s); break;
-    case 4: launch_esc<512, NUMERIC>(list, nl, X, Y, crowptr, count, ccol, cval, s); break;
-    case 5: launch_esc<1024, NUMERIC>(list, nl, X, Y, crowptr, count, ccol, cval, s); break;
-    default: fail(SAAMG_EINVAL, "bad product class");
+void run_class(int c, const int* list, int nl, CsrView X, CsrView Y, const int* crowptr, int* count,
+               int* overflow, int* ccol, double* cval, cudaStream_t s) {
+  if (nl == 0) return;
+  KernelTimer kt(SAAMG_KT_SPGEMM, nl, s);
+  const int threads = 32 * kSpgemmWarps;
+  if (c == 0) {
+    const int blocks = std::max(1, std::min((nl + 127) / 128, 152 * 16));
+    spgemm_row_k<NUMERIC><<<blocks, 128, 0, s>>>(list, nl, X, Y, crowptr, count, ccol, cval);
+    SAAMG_LAUNCH();
+    return;
   }
+  const int blocks = std::max(1, std::min((nl + kSpgemmWarps - 1) / kSpgemmWarps, 152 * 16));
+  if (c == 1) {
+    const size_t sm = (size_t)kSpgemmWarps * 64 * (NUMERIC ? 16 : 8);
+    spgemm_esc_k<64, NUMERIC><<<blocks, threads, sm, s>>>(list, nl, X, Y, crowptr, count, ccol, cval);
+    SAAMG_LAUNCH();
+    return;
+  }
+  const int lg = kHashMinLog + (c - 2);
+  const int cap = 1 << lg;
+  if (!NUMERIC) {
+    const size_t sm = (size_t)kSpgemmWarps * cap * sizeof(int);
+    if (sm > 48 * 1024)
+      SAAMG_CUDA(cudaFuncSetAttribute(spgemm_hash_symbolic_k,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    spgemm_hash_symbolic_k<<<blocks, threads, sm, s>>>(list, nl, lg, X, Y, count, overflow);
+  } else {
+    // 18 bytes per slot and warp: the 4096-slot table runs 2 warps per block (147 KB)
+    const int wpb = cap >= 4096 ? 2 : kSpgemmWarps;
+    const size_t sm = (size_t)wpb * cap * (sizeof(double) + sizeof(int) * 5 / 2);
+    if (sm > 48 * 1024)
+      SAAMG_CUDA(cudaFuncSetAttribute(spgemm_hash_numeric_k,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int nb = std::max(1, std::min((nl + wpb - 1) / wpb, 152 * 16));
+    spgemm_hash_numeric_k<<<nb, 32 * wpb, sm, s>>>(list, nl, lg, X, Y, crowptr, ccol, cval);
+  }
+  SAAMG_LAUNCH();
 }
+
+}  // namespace
 
 void spgemm(const DevCsr& X, const DevCsr& Y, DevCsr& C, cudaStream_t s) {
   const int n = X.n;
-  KernelTimer kt(SAAMG_KT_SPGEMM, n, s);
   C.n = n;
   C.m = Y.m;
   C.rowptr.alloc(n + 1, s);
@@ -518,68 +589,36 @@ void spgemm(const DevCsr& X, const DevCsr& Y, DevCsr& C, cudaStream_t s) {
     C.val.alloc(0, s);
     return;
   }
-  // classify rows by their number of products; one list per class
-  Buf<int> cls, list, cnt, ctl;
+  Buf<int> nprod, cls, list, cnt, ctl;
+  nprod.alloc(n, s);
   cls.alloc(n, s);
   list.alloc(n, s);
   cnt.alloc(n + 1, s);
-  ctl.alloc(2 * kClasses + 1, s);  // histogram, cursors, overflow flag
-  SAAMG_CUDA(cudaMemsetAsync(ctl.p, 0, sizeof(int) * (2 * kClasses + 1), s));
-  classify_rows_k<<<blocks_for(n), 256, 0, s>>>(n, view(X), view(Y), cls.p, ctl.p);
-  SAAMG_LAUNCH();
-  int hist[kClasses];
-  d2h_sync(hist, ctl.p, sizeof(hist), s);
-  int start[kClasses + 1];
-  start[0] = 0;
-  for (int c = 0; c < kClasses; ++c) start[c + 1] = start[c] + hist[c];
-  SAAMG_CUDA(cudaMemcpyAsync(ctl.p + kClasses, start, sizeof(int) * kClasses,
-                             cudaMemcpyHostToDevice, s));
-  scatter_rows_k<<<blocks_for(n), 256, 0, s>>>(n, cls.p, ctl.p + kClasses, list.p);
-  SAAMG_LAUNCH();
+  ctl.alloc(2 * kClasses + 1, s);
   int* overflow = ctl.p + 2 * kClasses;
-  const int threads = 32 * kSpgemmWarps;
-  const int lc_hash = kMaxSmemLog;
+  SAAMG_CUDA(cudaMemsetAsync(overflow, 0, sizeof(int), s));
+  row_products_k<<<blocks_for(n), 256, 0, s>>>(n, view(X), view(Y), nprod.p);
+  SAAMG_LAUNCH();
+  int hist[kClasses], start[kClasses + 1];
   // symbolic: distinct columns per row
-  for (int c = 0; c < kClasses; ++c) {
-    if (hist[c] == 0) continue;
-    const int* lp = list.p + start[c];
-    if (c < kEscClasses) {
-      esc_class<false>(c, lp, hist[c], view(X), view(Y), nullptr, cnt.p, nullptr, nullptr, s);
-    } else {
-      size_t sm = (size_t)kSpgemmWarps * (1u << lc_hash) * sizeof(int);
-      int blocks = std::min((hist[c] + kSpgemmWarps - 1) / kSpgemmWarps, 152 * 8);
-      spgemm_symbolic_k<<<blocks, threads, sm, s>>>(lp, hist[c], lc_hash, nullptr, view(X),
-                                                    view(Y), cnt.p, overflow);
-      SAAMG_LAUNCH();
-    }
-  }
-  if (hist[kEscClasses] > 0) {
-    int nover = 0;
-    d2h_sync(&nover, overflow, sizeof(int), s);
-    if (nover) fail(SAAMG_UNIMPLEMENTED, "sparse product row longer than 1024 distinct columns");
-  }
+  bin_rows(n, nprod.p, nullptr, Y.m, cls.p, list.p, ctl.p, hist, start, s);
+  for (int c = 0; c < kClasses; ++c)
+    run_class<false>(c, list.p + start[c], hist[c], view(X), view(Y), nullptr, cnt.p, overflow,
+                     nullptr, nullptr, s);
+  int nover = 0;
+  d2h_sync(&nover, overflow, sizeof(int), s);
+  if (nover) fail(SAAMG_UNIMPLEMENTED, "sparse product row with more than 2048 distinct columns");
   fill_int(cnt.p + n, 0, 1, s);
   long long nnz = exclusive_scan(cnt.p, C.rowptr.p, n + 1, s);
   if (nnz > 0x7fffffffLL) fail(SAAMG_EINVAL, "more than 2^31 nonzeros in a coarse operator");
   C.nnz = nnz;
   C.col.alloc(nnz, s);
   C.val.alloc(nnz, s);
-  for (int c = 0; c < kClasses; ++c) {
-    if (hist[c] == 0) continue;
-    const int* lp = list.p + start[c];
-    if (c < kEscClasses) {
-      esc_class<true>(c, lp, hist[c], view(X), view(Y), C.rowptr.p, nullptr, C.col.p, C.val.p, s);
-    } else {
-      size_t sm = (size_t)kSpgemmWarps * (1u << lc_hash) * (sizeof(int) + sizeof(double));
-      if (sm > 48 * 1024)
-        SAAMG_CUDA(cudaFuncSetAttribute(spgemm_numeric_k,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      int blocks = std::min((hist[c] + kSpgemmWarps - 1) / kSpgemmWarps, 152 * 8);
-      spgemm_numeric_k<<<blocks, threads, sm, s>>>(lp, hist[c], lc_hash, nullptr, nullptr,
-                                                   view(X), view(Y), C.rowptr.p, C.col.p, C.val.p);
-      SAAMG_LAUNCH();
-    }
-  }
+  // numeric: tables sized from the exact counts
+  bin_rows(n, nprod.p, cnt.p, Y.m, cls.p, list.p, ctl.p, hist, start, s);
+  for (int c = 0; c < kClasses; ++c)
+    run_class<true>(c, list.p + start[c], hist[c], view(X), view(Y), C.rowptr.p, nullptr, nullptr,
+                    C.col.p, C.val.p, s);
 }
 
 void smoothed_prolongator(DevCsr& AT, const int* agg, const double* invd, double omega,

@@ -6,9 +6,12 @@
 namespace saamg {
 
 // lambda_hat of D^-1 A by `iters` power-iteration steps from v_i = 0.5 + fmix32(id ^
-// 0xA5A5A5A5)/2^32 (ids NULL: the row index).  Returns lambda_hat (synchronises).
+// 0xA5A5A5A5)/2^32 (ids NULL: the row index).  Returns lambda_hat (synchronises).  With S
+// given, D^-1 A is applied by the matrix-free level-0 stencil instead of the CSR.
+template <class T>
+struct StencilDev;
 double power_lambda(const DevCsr& A, const double* invd, const unsigned* ids, int iters,
-                    cudaStream_t s);
+                    cudaStream_t s, const StencilDev<double>* S = nullptr);
 
 // C = X Y with a structural pattern (entries that cancel are kept), columns ascending in
 // every row, each entry summed in the order X's row (ascending columns) then Y's row.

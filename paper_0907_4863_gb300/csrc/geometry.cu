@@ -188,17 +188,14 @@ __global__ void set_start_and_chunks_k(LineInfo* lines, const int* start, const 
 // Regular interior row: all six couplings -c_dir, diagonal 2(cx+cy+cz), scaled.
 __global__ void regular_consts_k(GeomParams g, double* out) {
   double dd[3], om, opl;
-  for (int ax = 0; ax < 3; ++ax) {
-    double c = 1.0 / (g.h[ax] * g.h[ax]);
-    direction_row(g.mode, c, true, true, 1.0, 1.0, dd[ax], om, opl);
-  }
+  for (int ax = 0; ax < 3; ++ax) direction_row(g.mode, g.cdir[ax], true, true, 1.0, 1.0, dd[ax], om, opl);
   double diag = (dd[0] + dd[1]) + dd[2];
   double s = 1.0 / sqrt(diag);
   double ss = s * s;
   out[0] = diag * ss;
-  out[1] = (-(1.0 / (g.h[0] * g.h[0]))) * ss;
-  out[2] = (-(1.0 / (g.h[1] * g.h[1]))) * ss;
-  out[3] = (-(1.0 / (g.h[2] * g.h[2]))) * ss;
+  out[1] = (-g.cdir[0]) * ss;
+  out[2] = (-g.cdir[1]) * ss;
+  out[3] = (-g.cdir[2]) * ss;
   out[4] = 1.0 / out[0];
 }
 
@@ -222,9 +219,8 @@ __global__ void assemble_unscaled_k(GeomParams g, const LineInfo* __restrict__ l
   double off[6] = {0, 0, 0, 0, 0, 0};
   double dd[3];
   bool gamma2 = (g.zbc == SAAMG_Z_ROBIN) && (k == 0 || k == g.nz - 1);
-  const double dist = 0.5 * ((double)(g.nz - 1) * g.h[2]);
   for (int ax = 0; ax < 3; ++ax) {
-    double cdir = 1.0 / (g.h[ax] * g.h[ax]);
+    const double cdir = g.cdir[ax];
     int dm = 2 * ax, dp = 2 * ax + 1;
     bool in_m = nb[dm] >= 0, in_p = nb[dp] >= 0;
     if (ax == 2 && gamma2) {
@@ -232,13 +228,13 @@ __global__ void assemble_unscaled_k(GeomParams g, const LineInfo* __restrict__ l
       bool inner_is_p = (k == 0);
       bool in_inner = inner_is_p ? in_p : in_m;
       if (in_inner) {
-        dd[2] = (2.0 + (2.0 * g.h[2]) / dist) * cdir;
+        dd[2] = (2.0 + g.robin) * cdir;
         off[inner_is_p ? dp : dm] = -2.0 * cdir;
       } else {
         // inner neighbour outside the wall: replaced by its one-sided extrapolation
         double t = boundary_fraction(g, i, j, k, inner_is_p ? dp : dm);
-        if (g.mode == SAAMG_BC_CONSTANT) dd[2] = (2.0 + (2.0 * g.h[2]) / dist) * cdir;
-        else dd[2] = ((2.0 * g.h[2]) / dist + 2.0 / t) * cdir;
+        if (g.mode == SAAMG_BC_CONSTANT) dd[2] = (2.0 + g.robin) * cdir;
+        else dd[2] = (g.robin + 2.0 / t) * cdir;
       }
       continue;
     }

@@ -10,6 +10,9 @@ struct GeomParams {
   double h[3], o[3];
   double a, b, taper, cx, cy;
   int zbc, sym, mode;
+  // derived once on the host (plain IEEE multiply / divide, no rounding differences):
+  double cdir[3];   // 1 / h_i^2
+  double robin;     // 2 h_z / d with d = (nz - 1) h_z / 2
 };
 
 // Scaled operator Ahat = D^-1/2 A D^-1/2 on the unknowns of the box grid.
@@ -56,7 +59,8 @@ enum StencilMode {
   ST_SPMV_DOT = 1,  // y = A x, partials of x.y
   ST_RESID = 2,     // y = b - A x
   ST_CHEB = 3,      // r = b - A x; d = c1 d + c2 D^-1 r; y = x + d
-  ST_CHEB0 = 4      // d = c2 D^-1 b; y = d   (Chebyshev step 0 from x = 0)
+  ST_CHEB0 = 4,     // d = c2 D^-1 b; y = d   (Chebyshev step 0 from x = 0)
+  ST_DINV_DOT = 5   // y = D^-1 A x, partials of y.y (power iteration)
 };
 template <class T>
 void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* b, T* d, T c1,

@@ -97,7 +97,11 @@ __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __res
         if (i >= l.lo && i <= l.hi) acc = fma(sg * tb[6], x[l.start + (i - l.lo)], acc);
       }
     }
-    if (MODE == ST_SPMV || MODE == ST_SPMV_DOT) {
+    if (MODE == ST_DINV_DOT) {
+      const T w = invd * acc;
+      y[row] = w;
+      dacc = fma(to_d(w), to_d(w), dacc);
+    } else if (MODE == ST_SPMV || MODE == ST_SPMV_DOT) {
       y[row] = acc;
       if (MODE == ST_SPMV_DOT) dacc = fma(to_d(xc), to_d(acc), dacc);
     } else if (MODE == ST_RESID) {
@@ -109,7 +113,7 @@ __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __res
       y[row] = xc + dv;
     }
   }
-  if (MODE == ST_SPMV_DOT) {
+  if (MODE == ST_SPMV_DOT || MODE == ST_DINV_DOT) {
     __shared__ double sh[32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
@@ -129,14 +133,16 @@ template <class T>
 void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* b, T* d, T c1,
                    T c2, double* partials, cudaStream_t s) {
   if (S.nchunks == 0) {
-    if (mode == ST_SPMV_DOT) fill_double(partials, 0.0, kRedBlocks, s);
+    if (mode == ST_SPMV_DOT || mode == ST_DINV_DOT) fill_double(partials, 0.0, kRedBlocks, s);
     return;
   }
-  KernelTimer kt(mode == ST_CHEB || mode == ST_CHEB0 ? SAAMG_KT_STENCIL_SMOOTH : SAAMG_KT_STENCIL_APPLY,
+  KernelTimer kt(mode == ST_CHEB || mode == ST_CHEB0 ? SAAMG_KT_STENCIL_SMOOTH
+                 : mode == ST_DINV_DOT                 ? -1
+                                                       : SAAMG_KT_STENCIL_APPLY,
                  S.n, s);
   // Reductions use the fixed grid so that partial sums are always taken the same way.
   int blocks = kRedBlocks;
-  if (mode != ST_SPMV_DOT) {
+  if (mode != ST_SPMV_DOT && mode != ST_DINV_DOT) {
     long long need = ((long long)S.nchunks + 7) / 8;
     blocks = (int)(need < 152 * 16 ? need : 152 * 16);
   }
@@ -155,6 +161,9 @@ void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* 
       break;
     case ST_CHEB0:
       stencil_k<T, ST_CHEB0><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      break;
+    case ST_DINV_DOT:
+      stencil_k<T, ST_DINV_DOT><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
       break;
     default:
       fail(SAAMG_EINVAL, "bad stencil mode");
