@@ -4,8 +4,9 @@
 One step = one pass of the whole method on a new seeded Gaussian-bunch charge density:
 build the operator (inside test, boundary rows, scaling), set up the SA-AMG hierarchy
 (MIS-2 aggregation, prolongators, Galerkin products, coarse LU) and solve with PCG to
-||r|| <= 1e-8 ||b||.  Prints one JSON line (see the README of the measurement contract in
-the design doc).  --impl reference times the FP64 CPU oracle instead.
+||r|| <= 1e-8 ||b||.  Prints one JSON line with the throughput, the end-to-end figure through
+the host-buffer call, the roofline of the dominant kernel, clocks, the CPU baseline and the
+mixed-precision, batched and serving legs.  --impl reference times the FP64 CPU oracle instead.
 """
 import argparse
 import json
@@ -27,6 +28,10 @@ METRIC = "solves/s to rel-residual 1e-8 at 256^3 (mixed/batched vs FP64 GPU); HB
 UNIT = "solves/s"
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP64 level-0 Chebyshev step
+# on the 256^3 elliptic pipe (profiles/stencil_cheb_fp64_pipe256.md); None for other kernels or
+# sizes, and to be reset whenever that kernel changes
+TRAFFIC_BYTES = {("stencil_smooth", 0, 256): 283.02e6}
 
 
 def parse():
@@ -39,6 +44,10 @@ def parse():
     ap.add_argument("--precision", choices=list(PREC), default="fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the mixed-precision and reuse legs")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched (64 instances) leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-requests", type=int, default=1500,
+                    help="requests of the 10,000-request serving stream to replay")
     return ap.parse_args()
 
 
@@ -181,9 +190,12 @@ def run_ours(args):
     hinfo = timed[-1][1]
     value = world * args.steps / (ms / 1e3)
 
-    # --- roofline of the dominant kernel class (live, CUDA events on the launching stream)
-    dom_name = max(ktime, key=lambda k: ktime[k][0])
-    roof = roofline(dom_name, ktime[dom_name], prec)
+    # --- roofline of the dominant kernel (live, CUDA events on the launching stream).  Each
+    # solve-phase class is one kernel template; the sparse products of the setup are several
+    # different kernels, reported as a class time only.
+    solve_classes = ("stencil_smooth", "stencil_apply", "coarse_csr", "transfer")
+    dom_name = max(solve_classes, key=lambda k: ktime[k][0])
+    roof = roofline(dom_name, ktime[dom_name], prec, args.n)
 
     # --- end to end through the public API with host buffers (pinned), copies in the region
     nbox = w.grid.nbox
@@ -218,6 +230,13 @@ def run_ours(args):
     extra = {}
     if not args.no_extra:
         extra = extra_legs(S, torch, w, dom, grid, rhs[args.warmup], args)
+        extra.update(mixed_quadratic_leg(S, torch, args))
+    del rhs, phis
+    torch.cuda.empty_cache()
+    if not args.no_batched:
+        extra["batched_c4"] = batched_leg(S, torch)
+    if not args.no_serve:
+        extra["serving_c5"] = serving_leg(S, torch, args.serve_requests)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -244,7 +263,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def roofline(name, rec, prec):
+def roofline(name, rec, prec, n=256):
     """Algorithmic work per launch / average launch duration for the dominant class."""
     total_ms, launches, rows = rec
     if launches == 0 or total_ms <= 0:
@@ -257,7 +276,9 @@ def roofline(name, rec, prec):
         flops = (19 if name == "stencil_smooth" else 13) * rows_per_launch
         ach = flops / avg_s / 1e12
         return {"bound": "alu", "kernel": name, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": TRAFFIC_BYTES.get((name, prec, n)),
+                "algorithmic_bytes_per_launch": (40 if name == "stencil_smooth" else 16) * rows_per_launch,
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
                 "avg_launch_us": avg_s * 1e6, "launches": launches}
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
@@ -313,11 +334,120 @@ def extra_legs(S, torch, w, dom, grid, rho, args):
             "solve_only_solves_per_s": 1e3 / ms, "solve_ms": ms,
             "full_pipeline_solves_per_s": 1e3 / full_ms, "setup_ms": h.info()["setup_ms"],
             "iters": its[-1]["iters"], "relres_true": its[-1]["relres_true"],
-            "roofline_stencil_smooth": roofline(dom_name, kt[dom_name], prec),
+            "roofline_stencil_smooth": roofline(dom_name, kt[dom_name], prec, args.n),
             "kernel_classes_ms_per_solve": {k: v[0] / args.steps for k, v in kt.items()},
         }
         h.free()
         op.free()
+    return out
+
+
+def mixed_quadratic_leg(S, torch, args):
+    """Quadratic extrapolation at 256^3 (mildly nonsymmetric): FP64 vs FP32 / BF16 V-cycle."""
+    w = I.pipe_workload(args.n, I.QUADRATIC)
+    dom, grid = S.make_domain(w.domain), S.make_grid(w.grid)
+    rho = torch.from_numpy(I.gaussian_bunch(w.grid, w.centre, w.sigma, seed=77)).cuda()
+    out, ref = {}, None
+    for name, prec in (("fp64", 0), ("fp32", 1), ("bf16", 2)):
+        params = S.params_default(max_coarse=4096, precision=prec, beta_rule=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        op = S.build_operator(dom, grid, w.mode)
+        h = S.setup(op, params)
+        phi = torch.zeros_like(rho)
+        info = S.solve(h, rho, phi, rtol=RTOL)
+        torch.cuda.synchronize()
+        full = time.perf_counter() - t0
+        ts = []
+        for _ in range(3):
+            phi2 = torch.zeros_like(rho)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            S.solve(h, rho, phi2, rtol=RTOL)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t1)
+        if ref is None:
+            ref = phi
+        err = float((phi - ref).abs().max() / ref.abs().max())
+        out[name] = {"full_pipeline_solves_per_s": 1.0 / full, "solve_only_solves_per_s": 1.0 / min(ts),
+                     "iters": info["iters"], "relres_true": info["relres_true"],
+                     "max_rel_diff_vs_fp64_gpu": err}
+        h.free()
+        op.free()
+    return {"mixed_quadratic_c3": {"workload": f"{w.name}, quadratic extrapolation, rtol 1e-8", **out}}
+
+
+def batched_leg(S, torch):
+    """64 instances of uneven grids (48..160 per axis) and geometries, 4 rhs each: one batched
+    call with the FP32 V-cycle and autotuned Chebyshev degree, against FP64 solved one by one."""
+    inst = I.batched_instances()
+    hs32, hs64, rhos = [], [], []
+    degrees = []
+    for k, w in enumerate(inst):
+        dom, grid = S.make_domain(w.domain), S.make_grid(w.grid)
+        op = S.build_operator(dom, grid, w.mode)
+        h32 = S.setup(op, S.params_default(max_coarse=4096, precision=1, beta_rule=1))
+        h64 = S.setup(op, S.params_default(max_coarse=4096))
+        r = [I.gaussian_bunch_torch(w.grid, w.centre, w.sigma, 1234 + 4 * k + j) for j in range(4)]
+        best, _ = S.autotune_cheb_degree(h32, r[0], 2, 4)
+        degrees.append(best)
+        hs32.append(h32)
+        hs64.append(h64)
+        rhos.append(r)
+    H = [h for h in hs32 for _ in range(4)]
+    R = [r for rr in rhos for r in rr]
+    X = [torch.zeros_like(r) for r in R]
+    S.solve_batched(H, R, X)  # warm-up (captures the graphs)
+    for x in X:
+        x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    infos = S.solve_batched(H, R, X)
+    torch.cuda.synchronize()
+    t_batched = time.perf_counter() - t0
+    # FP64, one solve at a time through the synchronous call
+    X64 = [torch.zeros_like(r) for r in R]
+    H64 = [h for h in hs64 for _ in range(4)]
+    S.solve(H64[0], R[0], X64[0])
+    X64[0].zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its64 = [S.solve(h, r, x)["iters"] for h, r, x in zip(H64, R, X64)]
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    err = max(float((a - b).abs().max() / b.abs().max()) for a, b in zip(X, X64))
+    out = {"instances": len(inst), "solves": len(R),
+           "unknowns_total": int(sum(h.info()["n"][0] for h in hs32) * 4),
+           "batched_fp32_solves_per_s": len(R) / t_batched,
+           "sequential_fp64_solves_per_s": len(R) / t_seq,
+           "speedup": t_seq / t_batched,
+           "all_converged": all(i["converged"] == 1 for i in infos),
+           "max_relres_true": max(i["relres_true"] for i in infos),
+           "max_rel_diff_vs_fp64": err,
+           "autotuned_degrees": {d: degrees.count(d) for d in sorted(set(degrees))},
+           "iters_fp32_mean": statistics.fmean(i["iters"] for i in infos),
+           "iters_fp64_mean": statistics.fmean(its64)}
+    for h in hs32 + hs64:
+        h.free()
+    return out
+
+
+def serving_leg(S, torch, nreq):
+    """A prefix of the 10,000-request Poisson stream (mean gap 2 ms) over 20 geometries."""
+    from paper_0907_4863_gb300 import serve
+    geoms = I.serving_geometries()
+    reqs = I.serving_requests(10000)[:nreq]
+    out = {"requests_replayed": nreq, "of": 10000, "mean_gap_ms": 2.0, "geometries": len(geoms)}
+    for name, params, slots, warm in (
+            ("fp32_continuous_batching", S.params_default(max_coarse=4096, precision=1, beta_rule=1), 16, False),
+            ("fp32_continuous_batching_warm_start", S.params_default(max_coarse=4096, precision=1, beta_rule=1), 16, True),
+            ("fp64_unbatched", S.params_default(max_coarse=4096), 1, False)):
+        srv = serve.Server(geoms, budget_bytes=120 << 30, slots=slots, params=params, warm_start=warm)
+        _, st = srv.run(reqs)
+        srv.close()
+        torch.cuda.synchronize()
+        out[name] = {k: st[k] for k in ("solves_per_s", "p50_ms", "p99_ms", "mean_ms", "wall_s",
+                                        "cache_misses", "all_converged", "rejected")}
     return out
 
 

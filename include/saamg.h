@@ -37,6 +37,7 @@ extern "C" {
 typedef enum {
   SAAMG_OK = 0,
   SAAMG_NOT_CONVERGED = 1,   /* maxit reached; the best iterate is returned */
+  SAAMG_NOT_READY = 2,       /* saamg_solve_test: the solve is still running */
   SAAMG_EINVAL = -1,         /* invalid argument */
   SAAMG_ENOMEM = -2,         /* the allocator returned NULL */
   SAAMG_ECUDA = -3,          /* a CUDA runtime call failed */
@@ -186,6 +187,45 @@ saamg_status saamg_solve(saamg_hierarchy *h, const double *rho, double *phi, dou
 saamg_status saamg_solve_host(saamg_hierarchy *h, const double *rho_host, double *phi_host,
                               double rtol, void *stream, saamg_solve_info *info);
 
+/* Same solve as saamg_solve, enqueued as ONE CUDA graph and returning at once: the whole
+ * PCG loop (Sec. 3.1) runs on the device in a conditional while node whose test kernel
+ * ends the loop (no host round trip per iteration).  Gather, the graph, the copy of the
+ * result scalars and the scatter are enqueued on `stream`.  The first call on a hierarchy
+ * captures the graph (about one solve's worth of launches; make it outside any capture).
+ * rho and phi must stay valid until saamg_solve_wait or saamg_solve_test reports the end.
+ * A hierarchy holds one solve's work vectors: do not start a second solve on the same
+ * hierarchy before the first has finished (saamg_solve_batched orders them for you). */
+saamg_status saamg_solve_async(saamg_hierarchy *h, const double *rho, double *phi, double rtol,
+                               void *stream);
+
+/* OK when the hierarchy's last asynchronous solve has finished, NOT_READY otherwise. */
+saamg_status saamg_solve_test(const saamg_hierarchy *h);
+
+/* Waits for the hierarchy's last asynchronous solve and returns its status and info
+ * (solve_ms is left 0). */
+saamg_status saamg_solve_wait(saamg_hierarchy *h, saamg_solve_info *info);
+
+/* Many solves in one call (the benchmark spec batching): count right-hand sides rho[j] -> phi[j]
+ * (device box arrays) on hierarchies hs[j] of any sizes.  Solves of the same hierarchy
+ * run in the given order on one stream; different hierarchies run concurrently on a pool
+ * of up to 32 library streams, each solve being one device-loop graph launch.  Joins back
+ * into `stream` and returns when all are done; infos[j] per solve (solve_ms = the wall
+ * time of the whole batch).  Returns the worst status. */
+saamg_status saamg_solve_batched(saamg_hierarchy *const *hs, const double *const *rho,
+                                 double *const *phi, int count, double rtol, void *stream,
+                                 saamg_solve_info *infos);
+
+/* Changes the Chebyshev degree of every smoothed level (coefficients from the stored
+ * lambda_hat; the hierarchy is otherwise unchanged).  EINVAL outside 1..16. */
+saamg_status saamg_set_cheb_degree(saamg_hierarchy *h, int degree);
+
+/* Autotuner: times a device-loop solve of rho (device box array) for every Chebyshev
+ * degree lo..hi, keeps the degree with the shortest converged solve and returns it and
+ * its time.  Allocates one box array for the trial solutions. */
+saamg_status saamg_autotune_cheb_degree(saamg_hierarchy *h, const double *rho, int lo, int hi,
+                                        double rtol, void *stream, int *best_degree,
+                                        double *best_ms);
+
 /* Deterministic MIS-2 aggregation of a symmetric graph given as CSR on the device
  * (rowptr[n+1], col[nnz], self loops allowed), distinct node ids ids[n] (NULL: the row
  * index) and a 32-bit seed.  The priority of node v is fmix32(id_v ^ seed), a bijection,
@@ -212,8 +252,9 @@ saamg_status saamg_mis2_aggregate_noalloc(int n, const int *rowptr, const int *c
 
 /* Kernel classes for saamg_kernel_timing_read. */
 typedef enum {
-  SAAMG_KT_STENCIL_SMOOTH = 0, /* level-0 Chebyshev step fused with the residual */
-  SAAMG_KT_STENCIL_APPLY = 1,  /* level-0 A x, residual, A p with p'Ap */
+  SAAMG_KT_STENCIL_SMOOTH = 0, /* level-0 Chebyshev step fused with the residual (full step) */
+  SAAMG_KT_STENCIL_APPLY = 1,  /* other level-0 stencil passes: A x, residual, A p with p'Ap,
+                                  first smoothing steps */
   SAAMG_KT_COARSE = 2,         /* CSR smoother / residual on levels >= 1 */
   SAAMG_KT_TRANSFER = 3,       /* restriction R r and prolongation x += P v */
   SAAMG_KT_SPGEMM = 4,         /* sparse products of the setup */

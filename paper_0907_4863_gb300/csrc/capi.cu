@@ -6,7 +6,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -191,6 +193,18 @@ struct saamg_hierarchy {
   HostScratch host;
   Buf<double> scratch;
   long long bytes = 0;
+  // device-loop solve: the whole PCG as one graph (conditional while node)
+  cudaGraph_t graph = nullptr;      // owns the conditional handle: lives as long as gexec
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t done = nullptr;
+  PcgCtl* result = nullptr;  // pinned host copy of the last device-loop solve's scalars
+  ~saamg_hierarchy() {
+    if (done) cudaEventSynchronize(done);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (done) cudaEventDestroy(done);
+    if (result) cudaFreeHost(result);
+  }
 };
 
 namespace saamg {
@@ -448,8 +462,11 @@ static void smooth_step(saamg_hierarchy* h, int l, int mode0, const T* x, T* y, 
                         T c1, T c2, cudaStream_t s) {
   if (l == 0) {
     StencilDev<T> S = h->op->d.template view<T>();
-    stencil_apply<T>(S, mode0 == CSR_CHEB0 ? ST_CHEB0 : (mode0 == CSR_RESID ? ST_RESID : ST_CHEB),
-                     x, y, b, d, c1, c2, nullptr, s);
+    const int m = mode0 == CSR_CHEB0   ? ST_CHEB0
+                  : mode0 == CSR_RESID ? ST_RESID
+                  : (c1 == T(0))       ? ST_CHEB1
+                                       : ST_CHEB;
+    stencil_apply<T>(S, m, x, y, b, d, c1, c2, nullptr, s);
   } else {
     level_csr<T>(h, l, mode0, x, y, b, d, c1, c2, s);
   }
@@ -611,6 +628,174 @@ static int pcg_impl(saamg_hierarchy* h, double rtol, cudaStream_t s, saamg_solve
   return status;
 }
 
+// --- device-loop PCG ------------------------------------------------------------
+// The whole solve of Sec. 3.1 as one CUDA graph: a prologue (||b||, r = b - A x, the loop
+// condition), a conditional while node whose body is one PCG pass (V-cycle, beta,
+// direction, A p, alpha, update, convergence test that clears the condition), and an
+// epilogue (true residual).  Pointers and Chebyshev coefficients are fixed at capture, the
+// tolerance is read from the device scalars, so one capture serves every right-hand side.
+__global__ void set_rtol_k(PcgCtl* ctl, double rtol) { ctl->rtol = rtol; }
+
+static void pcg_pass(saamg_hierarchy* h, cudaGraphConditionalHandle cond, cudaStream_t s) {
+  const OperatorData& od = h->op->d;
+  const int n = od.n;
+  const StencilDev<double> S = od.view<double>();
+  const int rule = h->prm.beta_rule;
+  double* r = h->r.p;
+  double* p = h->p.p;
+  double* q = h->q.p;
+  PcgCtl* ctl = h->ctl.p;
+  apply_preconditioner(h, r, h->z.p, h->z32.p, s);
+  if (mixed(h)) {
+    dot_partials<double, float>(n, r, h->z32.p, h->part0.p, s);
+    if (rule == 1) dot_partials<float, double>(n, h->z32.p, q, h->part2.p, s);
+    pcg_graph_beta(h->part0.p, rule == 1 ? h->part2.p : nullptr, rule, ctl, s);
+    pcg_direction<float>(n, h->z32.p, p, ctl, s);
+  } else {
+    dot_partials<double, double>(n, r, h->z.p, h->part0.p, s);
+    if (rule == 1) dot_partials<double, double>(n, h->z.p, q, h->part2.p, s);
+    pcg_graph_beta(h->part0.p, rule == 1 ? h->part2.p : nullptr, rule, ctl, s);
+    pcg_direction<double>(n, h->z.p, p, ctl, s);
+  }
+  stencil_apply<double>(S, ST_SPMV_DOT, p, q, nullptr, nullptr, 0.0, 0.0, h->part0.p, s);
+  pcg_alpha(h->part0.p, ctl, s);
+  pcg_update(n, h->xhat.p, r, p, q, ctl, h->part1.p, s);
+  pcg_graph_check(h->part1.p, ctl, cond, h->prm.maxit, s);
+}
+
+// Capture needs a stream that can be captured (not the legacy default stream): the graph is
+// recorded on a private stream (nothing executes during capture) and launched on the
+// caller's stream.
+static cudaStream_t capture_stream() {
+  static std::mutex mu;
+  static cudaStream_t cs = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cs) SAAMG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  return cs;
+}
+
+static void build_solve_graph(saamg_hierarchy* h) {
+  static std::mutex capture_mu;  // one capture at a time on the shared capture stream
+  std::lock_guard<std::mutex> lock(capture_mu);
+  cudaStream_t s = capture_stream();
+  const OperatorData& od = h->op->d;
+  const int n = od.n;
+  const StencilDev<double> S = od.view<double>();
+  cudaGraph_t g = nullptr;
+  SAAMG_CUDA(cudaGraphCreate(&g, 0));
+  bool capturing = false;
+  try {
+    cudaGraphConditionalHandle cond;
+    SAAMG_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault));
+    SAAMG_CUDA(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    capturing = true;
+    dot_partials<double, double>(n, h->bhat.p, h->bhat.p, h->part2.p, s);
+    stencil_apply<double>(S, ST_RESID, h->xhat.p, h->r.p, h->bhat.p, nullptr, 0.0, 0.0, nullptr, s);
+    dot_partials<double, double>(n, h->r.p, h->r.p, h->part1.p, s);
+    SAAMG_CUDA(cudaMemsetAsync(h->p.p, 0, sizeof(double) * n, s));
+    pcg_graph_init(h->part2.p, h->part1.p, h->ctl.p, cond, h->prm.maxit, h->xhat.p, n, s);
+    cudaStreamCaptureStatus st;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    SAAMG_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    SAAMG_CUDA(cudaGraphAddNode(&cnode, cg, deps, nullptr, nd, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    SAAMG_CUDA(cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    stencil_apply<double>(S, ST_RESID, h->xhat.p, h->q.p, h->bhat.p, nullptr, 0.0, 0.0, nullptr, s);
+    dot_partials<double, double>(n, h->q.p, h->q.p, h->part0.p, s);
+    pcg_store_true(h->part0.p, h->ctl.p, s);
+    capturing = false;
+    SAAMG_CUDA(cudaStreamEndCapture(s, &g));
+    SAAMG_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    capturing = true;
+    pcg_pass(h, cond, s);
+    capturing = false;
+    SAAMG_CUDA(cudaStreamEndCapture(s, &body));
+    SAAMG_CUDA(cudaGraphInstantiate(&h->gexec, g, 0));
+    h->graph = g;
+  } catch (...) {
+    if (capturing) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(s, &junk);
+      if (junk && junk != g) cudaGraphDestroy(junk);
+    }
+    cudaGraphDestroy(g);
+    throw;
+  }
+}
+
+static void drop_solve_graph(saamg_hierarchy* h) {
+  if (h->done) cudaEventSynchronize(h->done);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->gexec = nullptr;
+  h->graph = nullptr;
+}
+
+// Enqueues gather -> graph -> result copy -> scatter -> completion event; returns at once.
+static void solve_async_impl(saamg_hierarchy* h, const double* rho, double* phi, double rtol,
+                             cudaStream_t s, PcgCtl* host_out) {
+  const OperatorData& od = h->op->d;
+  if (!h->done) SAAMG_CUDA(cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming));
+  if (od.n == 0) {
+    PcgCtl z{};
+    z.converged = 1;
+    *host_out = z;
+    scatter_solution(od, h->xhat.p, phi, s);
+    SAAMG_CUDA(cudaEventRecord(h->done, s));
+    return;
+  }
+  if (!h->gexec) build_solve_graph(h);
+  gather_rhs(od, rho, phi, h->bhat.p, h->xhat.p, s);
+  set_rtol_k<<<1, 1, 0, s>>>(h->ctl.p, rtol);
+  SAAMG_LAUNCH();
+  SAAMG_CUDA(cudaGraphLaunch(h->gexec, s));
+  SAAMG_CUDA(cudaMemcpyAsync(host_out, h->ctl.p, sizeof(PcgCtl), cudaMemcpyDeviceToHost, s));
+  scatter_solution(od, h->xhat.p, phi, s);
+  SAAMG_CUDA(cudaEventRecord(h->done, s));
+}
+
+static saamg_status info_from_ctl(const PcgCtl& c, saamg_solve_info* info) {
+  const double bn = std::sqrt(c.bb);
+  info->iters = c.iters;
+  info->converged = (c.converged && !c.breakdown) ? 1 : 0;
+  info->relres = bn > 0 ? std::sqrt(c.rr) / bn : 0.0;
+  info->relres_true = bn > 0 ? std::sqrt(c.rr_true) / bn : 0.0;
+  if (c.breakdown) return SAAMG_NUMERICAL;
+  return info->converged ? SAAMG_OK : SAAMG_NOT_CONVERGED;
+}
+
+// Streams for batched solves (created once, non-blocking).
+static std::mutex g_pool_mu;
+static std::vector<cudaStream_t> g_pool;
+
+static cudaStream_t pool_stream(size_t k) {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  while (g_pool.size() <= k) {
+    cudaStream_t st;
+    SAAMG_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    g_pool.push_back(st);
+  }
+  return g_pool[k];
+}
+
+static void recompute_cheb(saamg_hierarchy* h, int degree) {
+  const int nl = (int)h->lev.size();
+  for (int q = 0; q + 1 < nl; ++q) {
+    Level& L = *h->lev[q];
+    L.cheb = cheb_coefficients(L.lambda, h->prm.cheb_ratio, h->prm.cheb_safety, degree);
+  }
+  h->prm.cheb_degree = degree;
+  drop_solve_graph(h);
+}
+
 }  // namespace saamg
 
 // ===========================================================================
@@ -743,6 +928,7 @@ saamg_status saamg_setup(const saamg_operator* op, const saamg_params* params, v
     if (prm.beta_rule != 0 && prm.beta_rule != 1) fail(SAAMG_EINVAL, "beta_rule must be 0 or 1");
     auto h = std::make_unique<saamg_hierarchy>();
     setup_impl(op, prm, (cudaStream_t)stream, h.get());
+    SAAMG_CUDA(cudaMallocHost(&h->result, sizeof(PcgCtl)));
     *out = h.release();
   });
 }
@@ -807,6 +993,8 @@ saamg_status saamg_vcycle(const saamg_hierarchy* hc, const double* r, double* z,
       apply_preconditioner(h, r, nullptr, h->z32.p, s);
       to_double(h->z32.p, z, n, s);
     }
+    if (!h->done) SAAMG_CUDA(cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming));
+    SAAMG_CUDA(cudaEventRecord(h->done, s));
   });
 }
 
@@ -859,6 +1047,162 @@ saamg_status saamg_solve_host(saamg_hierarchy* h, const double* rho_host, double
   return g != SAAMG_OK ? g : (saamg_status)st;
 }
 
+saamg_status saamg_solve_async(saamg_hierarchy* h, const double* rho, double* phi, double rtol,
+                               void* stream) {
+  return guard("saamg_solve_async", [&] {
+    if (!h || h->magic != kHierMagic) fail(SAAMG_EINVAL, "not a hierarchy handle");
+    if (!rho || !phi) fail(SAAMG_EINVAL, "NULL rho or phi");
+    if (!(rtol > 0.0) || !std::isfinite(rtol)) fail(SAAMG_EINVAL, "rtol must be positive");
+    solve_async_impl(h, rho, phi, rtol, (cudaStream_t)stream, h->result);
+  });
+}
+
+saamg_status saamg_solve_test(const saamg_hierarchy* h) {
+  if (!h || h->magic != kHierMagic) return SAAMG_EINVAL;
+  if (!h->done) return SAAMG_OK;
+  cudaError_t e = cudaEventQuery(h->done);
+  if (e == cudaSuccess) return SAAMG_OK;
+  if (e == cudaErrorNotReady) return SAAMG_NOT_READY;
+  cudaGetLastError();
+  set_last_error(std::string("saamg_solve_test: ") + cudaGetErrorString(e));
+  return SAAMG_ECUDA;
+}
+
+saamg_status saamg_solve_wait(saamg_hierarchy* h, saamg_solve_info* info) {
+  saamg_solve_info local{};
+  if (!info) info = &local;
+  saamg_status st = SAAMG_OK;
+  saamg_status g = guard("saamg_solve_wait", [&] {
+    if (!h || h->magic != kHierMagic) fail(SAAMG_EINVAL, "not a hierarchy handle");
+    if (h->done) SAAMG_CUDA(cudaEventSynchronize(h->done));
+    st = info_from_ctl(*h->result, info);
+    if (st == SAAMG_NUMERICAL) set_last_error("saamg_solve_wait: breakdown (NaN/Inf or p'Ap = 0)");
+  });
+  return g != SAAMG_OK ? g : st;
+}
+
+saamg_status saamg_solve_batched(saamg_hierarchy* const* hs, const double* const* rho,
+                                 double* const* phi, int count, double rtol, void* stream,
+                                 saamg_solve_info* infos) {
+  saamg_status worst = SAAMG_OK;
+  auto t0 = std::chrono::steady_clock::now();
+  saamg_status g = guard("saamg_solve_batched", [&] {
+    if (count < 0 || (count > 0 && (!hs || !rho || !phi || !infos)))
+      fail(SAAMG_EINVAL, "bad count or NULL arrays");
+    if (!(rtol > 0.0) || !std::isfinite(rtol)) fail(SAAMG_EINVAL, "rtol must be positive");
+    if (count == 0) return;
+    for (int j = 0; j < count; ++j) {
+      if (!hs[j] || hs[j]->magic != kHierMagic) fail(SAAMG_EINVAL, "not a hierarchy handle");
+      if (!rho[j] || !phi[j]) fail(SAAMG_EINVAL, "NULL rho or phi");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // solves of one hierarchy share its work vectors: they run in order on one stream;
+    // different hierarchies run on different streams and overlap on the device
+    std::vector<saamg_hierarchy*> order;
+    std::map<saamg_hierarchy*, std::vector<int>> groups;
+    for (int j = 0; j < count; ++j) {
+      if (!groups.count(hs[j])) order.push_back(hs[j]);
+      groups[hs[j]].push_back(j);
+    }
+    PcgCtl* res = nullptr;
+    SAAMG_CUDA(cudaMallocHost(&res, sizeof(PcgCtl) * count));
+    std::vector<cudaEvent_t> evs;
+    auto cleanup = [&] {
+      for (cudaEvent_t e : evs) cudaEventDestroy(e);
+      cudaFreeHost(res);
+    };
+    try {
+      const size_t nstreams = std::min<size_t>(order.size(), 32);
+      cudaEvent_t fork;
+      SAAMG_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+      evs.push_back(fork);
+      SAAMG_CUDA(cudaEventRecord(fork, s));
+      for (size_t k = 0; k < nstreams; ++k) SAAMG_CUDA(cudaStreamWaitEvent(pool_stream(k), fork, 0));
+      for (size_t gi = 0; gi < order.size(); ++gi) {
+        cudaStream_t ps = pool_stream(gi % nstreams);
+        for (int j : groups[order[gi]]) solve_async_impl(order[gi], rho[j], phi[j], rtol, ps, &res[j]);
+      }
+      for (size_t k = 0; k < nstreams; ++k) {
+        cudaEvent_t e;
+        SAAMG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        evs.push_back(e);
+        SAAMG_CUDA(cudaEventRecord(e, pool_stream(k)));
+        SAAMG_CUDA(cudaStreamWaitEvent(s, e, 0));
+      }
+      SAAMG_CUDA(cudaStreamSynchronize(s));
+      for (int j = 0; j < count; ++j) {
+        saamg_status st = info_from_ctl(res[j], &infos[j]);
+        if (st < 0 && worst >= 0) worst = st;
+        else if (st == SAAMG_NOT_CONVERGED && worst == SAAMG_OK) worst = st;
+      }
+    } catch (...) {
+      cleanup();
+      throw;
+    }
+    cleanup();
+  });
+  if (count > 0 && infos) {
+    double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (int j = 0; j < count; ++j) infos[j].solve_ms = ms;
+  }
+  return g != SAAMG_OK ? g : worst;
+}
+
+saamg_status saamg_set_cheb_degree(saamg_hierarchy* h, int degree) {
+  return guard("saamg_set_cheb_degree", [&] {
+    if (!h || h->magic != kHierMagic) fail(SAAMG_EINVAL, "not a hierarchy handle");
+    if (degree < 1 || degree > 16) fail(SAAMG_EINVAL, "degree must be in 1..16");
+    if (h->done) SAAMG_CUDA(cudaEventSynchronize(h->done));
+    recompute_cheb(h, degree);
+  });
+}
+
+saamg_status saamg_autotune_cheb_degree(saamg_hierarchy* h, const double* rho, int lo, int hi,
+                                        double rtol, void* stream, int* best_degree,
+                                        double* best_ms) {
+  return guard("saamg_autotune_cheb_degree", [&] {
+    if (!h || h->magic != kHierMagic || !rho) fail(SAAMG_EINVAL, "NULL or invalid argument");
+    if (lo < 1 || hi > 16 || lo > hi) fail(SAAMG_EINVAL, "degree range must satisfy 1 <= lo <= hi <= 16");
+    if (!(rtol > 0.0)) fail(SAAMG_EINVAL, "rtol must be positive");
+    cudaStream_t s = (cudaStream_t)stream;
+    const OperatorData& od = h->op->d;
+    Buf<double> phi;
+    phi.alloc((size_t)od.g.nx * od.g.ny * od.g.nz, s);
+    cudaEvent_t e0, e1;
+    SAAMG_CUDA(cudaEventCreate(&e0));
+    SAAMG_CUDA(cudaEventCreate(&e1));
+    int best = h->prm.cheb_degree;
+    float best_t = -1.f;
+    try {
+      for (int d = lo; d <= hi; ++d) {
+        recompute_cheb(h, d);
+        for (int rep = 0; rep < 2; ++rep) {  // the first pass captures the graph
+          SAAMG_CUDA(cudaMemsetAsync(phi.p, 0, phi.bytes(), s));
+          SAAMG_CUDA(cudaEventRecord(e0, s));
+          solve_async_impl(h, rho, phi.p, rtol, s, h->result);
+          SAAMG_CUDA(cudaEventRecord(e1, s));
+          SAAMG_CUDA(cudaEventSynchronize(e1));
+        }
+        float ms = 0.f;
+        SAAMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (h->result->converged && (best_t < 0.f || ms < best_t)) {
+          best_t = ms;
+          best = d;
+        }
+      }
+    } catch (...) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    recompute_cheb(h, best);
+    if (best_degree) *best_degree = best;
+    if (best_ms) *best_ms = best_t;
+  });
+}
+
 saamg_status saamg_mis2_aggregate(int n, const int* rowptr, const int* col, const uint32_t* ids,
                                   uint32_t seed, unsigned char* root, int* agg, int* n_agg,
                                   void* stream) {
@@ -888,7 +1232,8 @@ void saamg_free(void* handle) {
       delete op;
     } else if (magic == kHierMagic) {
       saamg_hierarchy* h = static_cast<saamg_hierarchy*>(handle);
-      cudaDeviceSynchronize();
+      // asynchronous calls record `done`; the synchronous ones end with a stream sync
+      if (h->done) cudaEventSynchronize(h->done);
       h->magic = 0;
       delete h;
     }

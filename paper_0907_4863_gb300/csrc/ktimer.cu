@@ -53,6 +53,8 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 KernelTimer::KernelTimer(int kclass, long long nrows, cudaStream_t stream)
     : cls(kclass), rows(nrows), s(stream) {
   if (!g_timing || cls < 0 || cls >= SAAMG_KT_COUNT) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
   e0 = take_event();
   SAAMG_CUDA(cudaEventRecord(e0, s));
 }

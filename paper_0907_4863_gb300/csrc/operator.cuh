@@ -60,7 +60,8 @@ enum StencilMode {
   ST_RESID = 2,     // y = b - A x
   ST_CHEB = 3,      // r = b - A x; d = c1 d + c2 D^-1 r; y = x + d
   ST_CHEB0 = 4,     // d = c2 D^-1 b; y = d   (Chebyshev step 0 from x = 0)
-  ST_DINV_DOT = 5   // y = D^-1 A x, partials of y.y (power iteration)
+  ST_DINV_DOT = 5,  // y = D^-1 A x, partials of y.y (power iteration)
+  ST_CHEB1 = 6      // ST_CHEB with c1 = 0 (first step from a nonzero x): d is not read
 };
 template <class T>
 void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* b, T* d, T c1,

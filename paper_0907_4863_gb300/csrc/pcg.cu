@@ -125,6 +125,66 @@ __global__ void copy_k(int n, const TZ* __restrict__ z, double* __restrict__ p) 
     p[i] = (double)z[i];
 }
 
+__global__ void graph_init_k(const double* __restrict__ part_bb, const double* __restrict__ part_rr,
+                             PcgCtl* ctl, cudaGraphConditionalHandle cond, int maxit) {
+  const double bb = sum_fixed(part_bb);
+  const double rr = sum_fixed(part_rr);
+  if (threadIdx.x == 0) {
+    ctl->bb = bb;
+    ctl->rr = rr;
+    ctl->tol2 = (ctl->rtol * ctl->rtol) * bb;
+    ctl->iters = 0;
+    ctl->breakdown = !(isfinite(bb) && isfinite(rr));
+    ctl->converged = (bb == 0.0) || rr <= ctl->tol2;
+    ctl->rz = 0.0;
+    ctl->alpha = 0.0;
+    ctl->beta = 0.0;
+    const int go = !ctl->converged && !ctl->breakdown && maxit > 0;
+    cudaGraphSetConditional(cond, go ? 1u : 0u);
+  }
+}
+
+__global__ void zero_if_rhs_zero_k(double* __restrict__ x, int n, const PcgCtl* __restrict__ ctl) {
+  if (ctl->bb != 0.0) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = 0.0;
+}
+
+__global__ void graph_beta_k(const double* __restrict__ part_rz, const double* __restrict__ part_zq,
+                             int rule, PcgCtl* ctl) {
+  const double rz = sum_fixed(part_rz);
+  const double zq = part_zq ? sum_fixed(part_zq) : 0.0;
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    if (ctl->iters > 0) b = (rule == 1) ? (-ctl->alpha * zq) / ctl->rz : rz / ctl->rz;
+    if (!isfinite(b) || !isfinite(rz)) {
+      ctl->breakdown = 1;
+      b = 0.0;
+    }
+    ctl->rz_new = rz;
+    ctl->zq = zq;
+    ctl->beta = b;
+    ctl->rz = rz;
+  }
+}
+
+__global__ void graph_check_k(const double* __restrict__ part, PcgCtl* ctl,
+                              cudaGraphConditionalHandle cond, int maxit) {
+  const double rr = sum_fixed(part);
+  if (threadIdx.x == 0) {
+    ctl->rr = rr;
+    ctl->iters += 1;
+    if (!isfinite(rr)) ctl->breakdown = 1;
+    ctl->converged = rr <= ctl->tol2;
+    const int go = !ctl->converged && !ctl->breakdown && ctl->iters < maxit;
+    cudaGraphSetConditional(cond, go ? 1u : 0u);
+  }
+}
+
+__global__ void store_true_k(const double* __restrict__ part, PcgCtl* ctl) {
+  const double rr = sum_fixed(part);
+  if (threadIdx.x == 0) ctl->rr_true = rr;
+}
+
 inline int vec_blocks(int n) {
   int b = (n + 255) / 256;
   return b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8;
@@ -173,6 +233,31 @@ template void pcg_direction<float>(int, const float*, double*, const PcgCtl*, cu
 
 void vec_sub(int n, const double* b, const double* q, double* r, cudaStream_t s) {
   sub_k<<<vec_blocks(n), 256, 0, s>>>(n, b, q, r);
+  SAAMG_LAUNCH();
+}
+
+void pcg_graph_init(const double* part_bb, const double* part_rr, PcgCtl* ctl,
+                    cudaGraphConditionalHandle cond, int maxit, double* x, int n, cudaStream_t s) {
+  graph_init_k<<<1, kRedThreads, 0, s>>>(part_bb, part_rr, ctl, cond, maxit);
+  SAAMG_LAUNCH();
+  zero_if_rhs_zero_k<<<vec_blocks(n), 256, 0, s>>>(x, n, ctl);
+  SAAMG_LAUNCH();
+}
+
+void pcg_graph_beta(const double* part_rz, const double* part_zq, int rule, PcgCtl* ctl,
+                    cudaStream_t s) {
+  graph_beta_k<<<1, kRedThreads, 0, s>>>(part_rz, part_zq, rule, ctl);
+  SAAMG_LAUNCH();
+}
+
+void pcg_graph_check(const double* partials, PcgCtl* ctl, cudaGraphConditionalHandle cond,
+                     int maxit, cudaStream_t s) {
+  graph_check_k<<<1, kRedThreads, 0, s>>>(partials, ctl, cond, maxit);
+  SAAMG_LAUNCH();
+}
+
+void pcg_store_true(const double* partials, PcgCtl* ctl, cudaStream_t s) {
+  store_true_k<<<1, kRedThreads, 0, s>>>(partials, ctl);
   SAAMG_LAUNCH();
 }
 

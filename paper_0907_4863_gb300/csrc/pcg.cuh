@@ -7,6 +7,9 @@ namespace saamg {
 
 // Scalars of the CG recursion, kept on the device between kernels.
 struct PcgCtl {
+  double rtol;    // stopping tolerance (device-loop solves read it here)
+  double bb;      // ||b||^2
+  double rr_true; // ||b - A x||^2 at exit
   double rz;      // r'z of the current direction
   double alpha;
   double beta;
@@ -43,5 +46,19 @@ void pcg_direction(int n, const TZ* z, double* p, const PcgCtl* ctl, cudaStream_
 void vec_sub(int n, const double* b, const double* q, double* r, cudaStream_t s);
 template <class TZ>
 void vec_copy_to_double(int n, const TZ* z, double* p, cudaStream_t s);
+
+// --- device-loop PCG (one CUDA graph with a conditional while node) --------------
+// prologue: ctl->bb = sum(part_bb), ctl->rr = sum(part_rr), tol2 = (rtol^2) bb; the loop
+// condition is set to "not converged, no breakdown, maxit > 0"; x is zeroed when b = 0.
+void pcg_graph_init(const double* part_bb, const double* part_rr, PcgCtl* ctl,
+                    cudaGraphConditionalHandle cond, int maxit, double* x, int n, cudaStream_t s);
+// beta of the device loop: 0 on the first pass (p = z), else rule 0 / rule 1
+void pcg_graph_beta(const double* part_rz, const double* part_zq, int rule, PcgCtl* ctl,
+                    cudaStream_t s);
+// end of a pass: rr, iters, converged; clears the loop condition when done
+void pcg_graph_check(const double* partials, PcgCtl* ctl, cudaGraphConditionalHandle cond,
+                     int maxit, cudaStream_t s);
+// ctl->rr_true = sum(partials)
+void pcg_store_true(const double* partials, PcgCtl* ctl, cudaStream_t s);
 
 }  // namespace saamg

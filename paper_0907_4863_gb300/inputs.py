@@ -119,3 +119,84 @@ def taper_workload(nx, ny, nz, mode: int = LINEAR) -> Workload:
     """Circular pipe narrowing linearly from radius 0.45 to 0.30 along z."""
     return Workload(f"taper_{nx}x{ny}x{nz}", cell_centred_grid(nx, ny, nz),
                     Domain(0.45, 0.45, taper=0.30 / 0.45), mode)
+
+
+def gaussian_bunch_torch(grid: Grid, centre, sigma, seed: int, jitter: float = 0.02, device="cuda"):
+    """The same Gaussian bunch built with torch on the device (for large serving workloads)."""
+    import torch
+    j = uniform(0x5EED0000 + seed, 3, -jitter, jitter) if jitter > 0 else [0.0, 0.0, 0.0]
+    c = [centre[d] + j[d] for d in range(3)]
+    ax = [grid.origin[d] + torch.arange(grid.n[d], dtype=torch.float64, device=device) * grid.h[d]
+          for d in range(3)]
+    g = [torch.exp(-0.5 * ((ax[d] - c[d]) / sigma[d]) ** 2) for d in range(3)]
+    return (g[2][:, None, None] * g[1][None, :, None] * g[0][None, None, :]).reshape(-1).contiguous()
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float       # seconds after the start of the stream
+    geometry: int        # index into the geometry table
+    step: int            # PIC time step of this geometry (the bunch drifts +0.005 in z per step)
+    seed: int
+
+
+def serving_geometries(count: int = 20, seed: int = 7, sizes=(32, 48, 64, 96, 128, 160, 192, 256)):
+    """`count` geometries: kind cycles cylinder / elliptic pipe / taper, grid drawn from `sizes`."""
+    out = []
+    s = seed & _M64
+    for g in range(count):
+        s, z = splitmix64(s)
+        n = sizes[z % len(sizes)]
+        kind = g % 3
+        if kind == 0:
+            w = cylinder_workload(n, LINEAR)
+        elif kind == 1:
+            w = pipe_workload(n, LINEAR)
+        else:
+            w = taper_workload(n, n, n, LINEAR)
+        w.name = f"g{g}_{w.name}"
+        out.append(w)
+    return out
+
+
+def serving_requests(count: int = 10000, mean_gap_s: float = 0.002, ngeom: int = 20, seed: int = 99):
+    """Poisson arrivals (exponential gaps) over `ngeom` geometries; each geometry's requests are
+    consecutive time steps of one simulation."""
+    import math
+    out = []
+    s = seed & _M64
+    t = 0.0
+    steps = [0] * ngeom
+    for r in range(count):
+        s, z1 = splitmix64(s)
+        s, z2 = splitmix64(s)
+        u = ((z1 >> 11) + 1) * (1.0 / ((1 << 53) + 1))
+        t += -mean_gap_s * math.log(u)
+        g = z2 % ngeom
+        out.append(Request(r, t, g, steps[g], seed=1000 * g + steps[g]))
+        steps[g] += 1
+    return out
+
+
+def batched_instances(count: int = 64, seed: int = 1234, lo: int = 48, hi: int = 160):
+    """`count` instances with n_x, n_y, n_z drawn independently from U{lo..hi} (h_i = 1/n_i);
+    geometry cycles cylinder / elliptic pipe / taper 0.45 -> 0.30."""
+    out = []
+    s = seed & _M64
+    for k in range(count):
+        n = []
+        for _ in range(3):
+            s, z = splitmix64(s)
+            n.append(lo + z % (hi - lo + 1))
+        grid = cell_centred_grid(*n)
+        kind = k % 3
+        if kind == 0:
+            dom = Domain(0.45, 0.45)
+        elif kind == 1:
+            dom = Domain(0.45, 0.30)
+        else:
+            dom = Domain(0.45, 0.45, taper=0.30 / 0.45)
+        out.append(Workload(f"b{k}_{n[0]}x{n[1]}x{n[2]}_k{kind}", grid, dom, LINEAR,
+                            centre=(0.0, 0.0, 0.0)))
+    return out

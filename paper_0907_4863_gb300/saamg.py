@@ -11,7 +11,7 @@ import os
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(PKG, "libsaamg.so")
 
-OK, NOT_CONVERGED = 0, 1
+OK, NOT_CONVERGED, NOT_READY = 0, 1, 2
 EINVAL, ENOMEM, ECUDA, NUMERICAL, DEVICE_TIMEOUT, UNIMPLEMENTED = -1, -2, -3, -4, -5, -6
 BC_CONSTANT, BC_LINEAR, BC_QUADRATIC = 0, 1, 2
 Z_ROBIN, Z_DIRICHLET = 0, 1
@@ -67,6 +67,18 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
 _lib = None
 _hooks = None
+# Handles dropped by the garbage collector.  The collector can run inside an allocator
+# callback, i.e. while the library is executing a call on this thread; freeing there would
+# re-enter the library.  __del__ therefore only queues the handle; the queue is emptied at
+# the start of the next call made through this module.
+_deferred = []
+
+
+def _flush_deferred():
+    while _deferred:
+        h = _deferred.pop()
+        if _lib is not None:
+            _lib.saamg_free(h)
 
 _p = C.c_void_p
 _i = C.c_int
@@ -95,6 +107,13 @@ def lib():
         "saamg_solve_host": [_p, _p, _p, C.c_double, _p, C.POINTER(SolveInfo)],
         "saamg_mis2_aggregate": [_i, _p, _p, _p, C.c_uint32, _p, _p, C.POINTER(_i), _p],
         "saamg_mis2_aggregate_noalloc": [_i, _p, _p, _p, C.c_uint32, _p, _p, C.POINTER(_i), _p],
+        "saamg_solve_async": [_p, _p, _p, C.c_double, _p],
+        "saamg_solve_test": [_p],
+        "saamg_solve_wait": [_p, C.POINTER(SolveInfo)],
+        "saamg_solve_batched": [_p, _p, _p, _i, C.c_double, _p, _p],
+        "saamg_set_cheb_degree": [_p, _i],
+        "saamg_autotune_cheb_degree": [_p, _p, _i, _i, C.c_double, _p, C.POINTER(_i),
+                                       C.POINTER(C.c_double)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -119,6 +138,17 @@ def last_error():
     return lib().saamg_last_error().decode()
 
 
+def _entry(fn):
+    """Decorator: release queued handles before entering the library."""
+    import functools
+
+    @functools.wraps(fn)
+    def wrapped(*a, **k):
+        _flush_deferred()
+        return fn(*a, **k)
+    return wrapped
+
+
 def _check(status, allow_not_converged=False):
     if status == OK or (allow_not_converged and status == NOT_CONVERGED):
         return status
@@ -136,9 +166,17 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
 
+# Every callback object ever installed stays referenced here: buffers allocated under a hook
+# keep calling that hook's free function when they are released, so a callback must never be
+# collected while the library may still hold memory it allocated.
+_all_hooks = []
+
+
 def use_torch_allocator():
-    """Route the library's device allocations to torch's caching allocator."""
+    """Route the library's device allocations to torch's caching allocator (idempotent)."""
     global _hooks
+    if _hooks is not None and _hooks[2] == "torch":
+        return
     import torch
 
     def _alloc(nbytes, stream, ctx):
@@ -151,11 +189,14 @@ def use_torch_allocator():
     def _free(ptr, stream, ctx):
         torch.cuda.caching_allocator_delete(ptr)
 
-    _hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
-    _check(lib().saamg_set_allocator(_hooks[0], _hooks[1], None))
+    hooks = (ALLOC_FN(_alloc), FREE_FN(_free), "torch")
+    _all_hooks.append(hooks)
+    _check(lib().saamg_set_allocator(hooks[0], hooks[1], None))
+    _hooks = hooks
 
 
 def use_cuda_malloc():
+    """Back to cudaMalloc / cudaFree for new allocations."""
     global _hooks
     _check(lib().saamg_set_allocator(ALLOC_FN(), FREE_FN(), None))
     _hooks = None
@@ -184,14 +225,14 @@ class Operator:
 
     def free(self):
         if self.handle:
+            _flush_deferred()
             lib().saamg_free(self.handle)
             self.handle = None
 
     def __del__(self):
-        try:
-            self.free()
-        except Exception:
-            pass
+        if getattr(self, "handle", None):
+            _deferred.append(self.handle)
+            self.handle = None
 
 
 class Hierarchy:
@@ -208,16 +249,17 @@ class Hierarchy:
 
     def free(self):
         if self.handle:
+            _flush_deferred()
             lib().saamg_free(self.handle)
             self.handle = None
 
     def __del__(self):
-        try:
-            self.free()
-        except Exception:
-            pass
+        if getattr(self, "handle", None):
+            _deferred.append(self.handle)
+            self.handle = None
 
 
+@_entry
 def build_operator(domain: Domain, grid: Grid, mode: int, stream=None) -> Operator:
     h = C.c_void_p()
     _check(lib().saamg_build_operator(C.byref(domain), C.byref(grid), int(mode), _stream(stream),
@@ -225,10 +267,12 @@ def build_operator(domain: Domain, grid: Grid, mode: int, stream=None) -> Operat
     return Operator(h, tuple(grid.n))
 
 
+@_entry
 def operator_size(op: Operator):
     return op.size()
 
 
+@_entry
 def operator_copy(op: Operator, stream=None):
     """Host copies: node_of_row, scale, rowptr, col, val, is_regular (numpy)."""
     import numpy as np
@@ -243,10 +287,12 @@ def operator_copy(op: Operator, stream=None):
     return out
 
 
+@_entry
 def operator_apply(op: Operator, x, y, stream=None):
     _check(lib().saamg_operator_apply(op.handle, _ptr(x), _ptr(y), _stream(stream)))
 
 
+@_entry
 def setup(op: Operator, params: Params = None, stream=None) -> Hierarchy:
     h = C.c_void_p()
     _check(lib().saamg_setup(op.handle, C.byref(params) if params is not None else None,
@@ -254,10 +300,12 @@ def setup(op: Operator, params: Params = None, stream=None) -> Hierarchy:
     return Hierarchy(h, op)
 
 
+@_entry
 def hierarchy_get_info(h: Hierarchy):
     return h.info()
 
 
+@_entry
 def hierarchy_copy_level(h: Hierarchy, l: int, stream=None):
     """Host copies of level l: A (rowptr, col, val), agg, root, P and R (numpy)."""
     import numpy as np
@@ -282,10 +330,12 @@ def hierarchy_copy_level(h: Hierarchy, l: int, stream=None):
     return out
 
 
+@_entry
 def vcycle(h: Hierarchy, r, z, stream=None):
     _check(lib().saamg_vcycle(h.handle, _ptr(r), _ptr(z), _stream(stream)))
 
 
+@_entry
 def solve(h: Hierarchy, rho, phi, rtol=1e-8, stream=None):
     """rho, phi: float64 CUDA tensors over the whole box; phi = initial guess in, solution out."""
     info = SolveInfo()
@@ -297,6 +347,7 @@ def solve(h: Hierarchy, rho, phi, rtol=1e-8, stream=None):
     return d
 
 
+@_entry
 def solve_host(h: Hierarchy, rho, phi, rtol=1e-8, stream=None):
     """Host (numpy float64) box arrays; the copies to and from the device are in the call."""
     info = SolveInfo()
@@ -309,6 +360,59 @@ def solve_host(h: Hierarchy, rho, phi, rtol=1e-8, stream=None):
     return d
 
 
+@_entry
+def solve_async(h: Hierarchy, rho, phi, rtol=1e-8, stream=None):
+    """Enqueue the whole PCG solve as one device-loop graph on the stream; returns at once."""
+    _check(lib().saamg_solve_async(h.handle, _ptr(rho), _ptr(phi), float(rtol), _stream(stream)))
+
+
+@_entry
+def solve_test(h: Hierarchy) -> bool:
+    st = lib().saamg_solve_test(h.handle)
+    if st == NOT_READY:
+        return False
+    _check(st)
+    return True
+
+
+@_entry
+def solve_wait(h: Hierarchy):
+    info = SolveInfo()
+    st = lib().saamg_solve_wait(h.handle, C.byref(info))
+    _check(st, allow_not_converged=True)
+    d = info.as_dict()
+    d["status"] = st
+    return d
+
+
+@_entry
+def solve_batched(hs, rhos, phis, rtol=1e-8, stream=None):
+    """Solves rhos[j] -> phis[j] on hierarchies hs[j] in one call; returns the infos."""
+    n = len(hs)
+    H = (C.c_void_p * n)(*[h.handle for h in hs])
+    R = (C.c_void_p * n)(*[r.data_ptr() for r in rhos])
+    X = (C.c_void_p * n)(*[x.data_ptr() for x in phis])
+    infos = (SolveInfo * n)()
+    st = lib().saamg_solve_batched(H, R, X, n, float(rtol), _stream(stream), infos)
+    _check(st, allow_not_converged=True)
+    return [dict(infos[j].as_dict()) for j in range(n)]
+
+
+@_entry
+def set_cheb_degree(h: Hierarchy, degree: int):
+    _check(lib().saamg_set_cheb_degree(h.handle, int(degree)))
+
+
+@_entry
+def autotune_cheb_degree(h: Hierarchy, rho, lo=2, hi=4, rtol=1e-8, stream=None):
+    best = C.c_int(0)
+    ms = C.c_double(0)
+    _check(lib().saamg_autotune_cheb_degree(h.handle, _ptr(rho), int(lo), int(hi), float(rtol),
+                                            _stream(stream), C.byref(best), C.byref(ms)))
+    return best.value, ms.value
+
+
+@_entry
 def mis2_aggregate(rowptr, col, ids, seed, root, agg, stream=None):
     """Device CSR (int32 tensors), ids (int32/uint32 tensor or None) -> root (uint8), agg (int32)."""
     nagg = C.c_int(0)
@@ -319,6 +423,7 @@ def mis2_aggregate(rowptr, col, ids, seed, root, agg, stream=None):
     return nagg.value
 
 
+@_entry
 def mis2_aggregate_noalloc(rowptr, col, ids, seed, root, agg, stream=None):
     """Same as mis2_aggregate, for callers that cannot allocate device memory during the call:
     the library uses its own static scratch (graphs of at most 262,144 nodes; calls must not

@@ -1,0 +1,125 @@
+"""Device-loop (graph) solves, batched solves and the Chebyshev-degree autotuner."""
+import numpy as np
+import pytest
+
+from paper_0907_4863_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    from paper_0907_4863_gb300 import build
+    build.build()
+    from paper_0907_4863_gb300 import saamg
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    saamg.use_torch_allocator()
+    return saamg
+
+
+def _setup(S, w, **prm):
+    op = S.build_operator(S.make_domain(w.domain), S.make_grid(w.grid), w.mode)
+    return S.setup(op, S.params_default(**prm))
+
+
+def _rho(w, seed):
+    import torch
+    return torch.from_numpy(I.gaussian_bunch(w.grid, w.centre, w.sigma, seed)).cuda()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2], ids=["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("w", [I.pipe_workload(40, I.LINEAR), I.taper_workload(30, 27, 45, I.QUADRATIC)],
+                         ids=lambda w: w.name)
+def test_device_loop_equals_host_loop(S, w, prec):
+    import torch
+    prm = dict(max_coarse=100, precision=prec, beta_rule=1 if prec else 0)
+    h = _setup(S, w, **prm)
+    rho = _rho(w, 1)
+    a = torch.zeros_like(rho)
+    ia = S.solve(h, rho, a)
+    b = torch.full_like(rho, 0.0)
+    S.solve_async(h, rho, b)
+    ib = S.solve_wait(h)
+    assert ib["status"] == 0 and ib["iters"] == ia["iters"]
+    assert ib["relres"] == pytest.approx(ia["relres"], rel=0, abs=0)
+    assert ib["relres_true"] == pytest.approx(ia["relres_true"], rel=1e-12)
+    assert torch.equal(a, b)
+    # again, the captured graph is reused
+    c = torch.zeros_like(rho)
+    S.solve_async(h, rho, c)
+    while not S.solve_test(h):
+        pass
+    assert S.solve_wait(h)["iters"] == ia["iters"] and torch.equal(a, c)
+
+
+def test_device_loop_edge_cases(S):
+    import torch
+    w = I.pipe_workload(24, I.LINEAR)
+    h = _setup(S, w, max_coarse=100)
+    phi = torch.full((w.grid.nbox,), 2.0, dtype=torch.float64, device="cuda")
+    S.solve_async(h, torch.zeros_like(phi), phi)
+    info = S.solve_wait(h)
+    assert info["status"] == 0 and info["iters"] == 0 and torch.all(phi == 0)
+    rho = _rho(w, 0)
+    bad = rho.clone()
+    m = w.grid.n[0] // 2
+    bad[m + w.grid.n[0] * (m + w.grid.n[1] * m)] = float("nan")
+    S.solve_async(h, bad, torch.zeros_like(rho))
+    with pytest.raises(S.SaamgError) as e:
+        S.solve_wait(h)
+    assert e.value.status == S.NUMERICAL
+    h2 = _setup(S, w, max_coarse=100, maxit=3)
+    S.solve_async(h2, rho, torch.zeros_like(rho))
+    info = S.solve_wait(h2)
+    assert info["status"] == S.NOT_CONVERGED and info["iters"] == 3
+    # warm start through the device loop
+    x = torch.zeros_like(rho)
+    S.solve_async(h, rho, x)
+    cold = S.solve_wait(h)["iters"]
+    S.solve_async(h, rho, x)
+    assert S.solve_wait(h)["iters"] == 0
+
+
+def test_batched_results_equal_solo_results(S):
+    """Uneven instances (sizes, geometries, modes, precisions) and several rhs per instance:
+    every result in the batch equals the same solve run alone, bit for bit."""
+    import torch
+    ws = [(I.pipe_workload(36, I.LINEAR), dict(max_coarse=150)),
+          (I.Workload("cyl48x40x64", I.cell_centred_grid(48, 40, 64), I.Domain(0.45, 0.45), I.CONSTANT),
+           dict(max_coarse=200, precision=1, beta_rule=1)),
+          (I.taper_workload(28, 33, 52, I.QUADRATIC), dict(max_coarse=100, precision=2, beta_rule=1)),
+          (I.pipe_workload(20, I.QUADRATIC), dict(max_coarse=50))]
+    hs, rhos, phis, solo = [], [], [], []
+    for w, prm in ws:
+        h = _setup(S, w, **prm)
+        for seed in range(3):
+            rho = _rho(w, seed)
+            phi = torch.zeros_like(rho)
+            S.solve(h, rho, phi)
+            solo.append(phi)
+            hs.append(h)
+            rhos.append(rho)
+            phis.append(torch.full_like(rho, 7.0) * 0.0)
+    infos = S.solve_batched(hs, rhos, phis, rtol=1e-8)
+    assert all(i["converged"] == 1 for i in infos)
+    for a, b in zip(solo, phis):
+        assert torch.equal(a, b)
+
+
+def test_autotune_picks_a_degree_and_keeps_accuracy(S):
+    import torch
+    w = I.pipe_workload(48, I.LINEAR)
+    h = _setup(S, w, max_coarse=200, precision=1, beta_rule=1)
+    rho = _rho(w, 2)
+    best, ms = S.autotune_cheb_degree(h, rho, 2, 4)
+    assert 2 <= best <= 4 and ms > 0
+    phi = torch.zeros_like(rho)
+    info = S.solve(h, rho, phi)
+    assert info["converged"] == 1 and info["relres_true"] <= 1.5e-8
+    S.set_cheb_degree(h, 3)
+    info3 = S.solve(h, rho, torch.zeros_like(rho))
+    assert info3["converged"] == 1
+    with pytest.raises(S.SaamgError):
+        S.set_cheb_degree(h, 0)
