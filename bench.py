@@ -193,7 +193,8 @@ def run_ours(args):
     # --- roofline of the dominant kernel (live, CUDA events on the launching stream).  Each
     # solve-phase class is one kernel template; the sparse products of the setup are several
     # different kernels, reported as a class time only.
-    solve_classes = ("stencil_smooth", "stencil_apply", "coarse_csr", "transfer")
+    solve_classes = ("stencil_smooth", "stencil_apply", "stencil_resid", "stencil_first",
+                     "coarse_csr", "transfer")
     dom_name = max(solve_classes, key=lambda k: ktime[k][0])
     roof = roofline(dom_name, ktime[dom_name], prec, args.n)
 
@@ -270,22 +271,23 @@ def roofline(name, rec, prec, n=256):
         return None
     avg_s = total_ms / launches / 1e3
     rows_per_launch = rows / launches
-    if prec == 0 and name in ("stencil_smooth", "stencil_apply"):
+    if prec == 0 and name in ("stencil_smooth", "stencil_apply", "stencil_resid"):
         # FP64 issue-bound: 19 flops per row for a Chebyshev step fused with the residual
         # (13 for A x, 1 for b - A x, 4 for the direction update, 1 for x + d); 13 for A x
-        flops = (19 if name == "stencil_smooth" else 13) * rows_per_launch
+        flops = {"stencil_smooth": 19, "stencil_apply": 15, "stencil_resid": 14}[name] * rows_per_launch
         ach = flops / avg_s / 1e12
         return {"bound": "alu", "kernel": name, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
                 "traffic": TRAFFIC_BYTES.get((name, prec, n)),
-                "algorithmic_bytes_per_launch": (40 if name == "stencil_smooth" else 16) * rows_per_launch,
+                "algorithmic_bytes_per_launch": {"stencil_smooth": 40, "stencil_apply": 16,
+                                                 "stencil_resid": 24}[name] * rows_per_launch,
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
                 "avg_launch_us": avg_s * 1e6, "launches": launches}
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
     w = 8 if prec == 0 else 4
-    per_row = {"stencil_smooth": 5 * w, "stencil_apply": 2 * w}.get(name, 2 * w)
+    per_row = {"stencil_smooth": 5 * w, "stencil_apply": 2 * w, "stencil_resid": 3 * w}.get(name, 2 * w)
     ach = per_row * rows_per_launch / avg_s / 1e9
     return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": hbm, "unit": "GB/s",
             "frac": ach / hbm, "traffic": None,

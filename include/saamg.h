@@ -162,6 +162,18 @@ saamg_status saamg_operator_apply(const saamg_operator *op, const double *x, dou
 saamg_status saamg_setup(const saamg_operator *op, const saamg_params *params, void *stream,
                          saamg_hierarchy **out);
 
+/* Setup that reuses the aggregation hierarchy of `prev` (Sec. 5.2, "Reusing the aggregation
+ * hierarchy"; Table 6): for a new operator whose matrix has the same pattern as the one
+ * prev was built on (same unknowns; e.g. another boundary mode or other grid spacings on
+ * the same lattice of unknowns), the aggregates and the number of levels of prev are kept
+ * and only lambda_hat, the smoothed prolongators, the Galerkin operators and the coarse LU
+ * are rebuilt from the new values.  Aggregation depends on the pattern only, so the result
+ * equals a fresh saamg_setup on op.  params NULL = prev's parameters (max_coarse and
+ * max_levels are ignored: prev fixes the levels).  prev stays valid and independent.
+ * EINVAL when the patterns differ. */
+saamg_status saamg_setup_reuse(const saamg_operator *op, const saamg_hierarchy *prev,
+                               const saamg_params *params, void *stream, saamg_hierarchy **out);
+
 saamg_status saamg_hierarchy_get_info(const saamg_hierarchy *h, saamg_hierarchy_info *info);
 
 /* Copies level l to HOST buffers (any may be NULL): A_l as CSR (rowptr[n_l+1], col, val),
@@ -253,12 +265,13 @@ saamg_status saamg_mis2_aggregate_noalloc(int n, const int *rowptr, const int *c
 /* Kernel classes for saamg_kernel_timing_read. */
 typedef enum {
   SAAMG_KT_STENCIL_SMOOTH = 0, /* level-0 Chebyshev step fused with the residual (full step) */
-  SAAMG_KT_STENCIL_APPLY = 1,  /* other level-0 stencil passes: A x, residual, A p with p'Ap,
-                                  first smoothing steps */
+  SAAMG_KT_STENCIL_APPLY = 1,  /* level-0 A x, and A p with p'Ap in PCG */
   SAAMG_KT_COARSE = 2,         /* CSR smoother / residual on levels >= 1 */
   SAAMG_KT_TRANSFER = 3,       /* restriction R r and prolongation x += P v */
   SAAMG_KT_SPGEMM = 4,         /* sparse products of the setup */
-  SAAMG_KT_COUNT = 5
+  SAAMG_KT_STENCIL_RESID = 5,  /* level-0 residual b - A x */
+  SAAMG_KT_STENCIL_FIRST = 6,  /* first Chebyshev steps on level 0 (from zero, or c1 = 0) */
+  SAAMG_KT_COUNT = 7
 } saamg_kernel_class;
 
 /* Number of kernels this library has launched in the calling process. */

@@ -253,8 +253,37 @@ static void alloc_level_vectors(saamg_hierarchy* h, Level& L, bool is0, cudaStre
   }
 }
 
+__global__ void pattern_diff_k(int n, const int* __restrict__ rp1, const int* __restrict__ c1,
+                               const int* __restrict__ rp2, const int* __restrict__ c2,
+                               int* __restrict__ diff) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (rp1[i] != rp2[i] || rp1[i + 1] != rp2[i + 1]) {
+      *diff = 1;
+      continue;
+    }
+    for (int p = rp1[i]; p < rp1[i + 1]; ++p)
+      if (c1[p] != c2[p]) *diff = 1;
+  }
+}
+
+static bool same_pattern(const DevCsr& a, const DevCsr& b, cudaStream_t s) {
+  if (a.n != b.n || a.nnz != b.nnz) return false;
+  if (a.n == 0) return true;
+  Buf<int> diff;
+  diff.alloc(1, s);
+  SAAMG_CUDA(cudaMemsetAsync(diff.p, 0, sizeof(int), s));
+  pattern_diff_k<<<std::min((a.n + 255) / 256, 152 * 8), 256, 0, s>>>(a.n, a.rowptr.p, a.col.p,
+                                                                      b.rowptr.p, b.col.p, diff.p);
+  SAAMG_LAUNCH();
+  int h = 0;
+  d2h_sync(&h, diff.p, sizeof(int), s);
+  return h == 0;
+}
+
+// prev != NULL: the aggregates of every level are copied from prev (whose level-0 pattern
+// must equal op's) instead of being recomputed; everything numeric is rebuilt.
 static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaStream_t s,
-                       saamg_hierarchy* h) {
+                       saamg_hierarchy* h, const saamg_hierarchy* prev = nullptr) {
   auto t0 = std::chrono::steady_clock::now();
   PhaseTimer pt(s);
   h->op = op;
@@ -272,23 +301,37 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
   }
   int l = 0;
   AggScratchBufs agg_scratch;
-  agg_scratch.alloc(od.n > 0 ? od.n : 1, s);
+  if (!prev) agg_scratch.alloc(od.n > 0 ? od.n : 1, s);
   for (;;) {
     Level& L = *h->lev[l];
     const DevCsr& A = level_matrix(h, l);
-    if (L.n <= prm.max_coarse || l == prm.max_levels - 1 || l == SAAMG_MAX_LEVELS - 1) break;
-    const unsigned seed = 0x9E3779B9u * (unsigned)(l + 1);
-    L.root.alloc(L.n, s);
-    L.agg.alloc(L.n, s);
     const unsigned* ids = (l == 0) ? od.ids.p : nullptr;
-    pt.mark("L" + std::to_string(l) + ".pre");
-    int nagg = mis2_aggregate(L.n, A.rowptr.p, A.col.p, A.nnz, ids, seed, L.root.p, L.agg.p,
-                              agg_scratch.view(), s);
-    pt.mark("L" + std::to_string(l) + ".mis2agg");
-    if (10LL * nagg > 9LL * L.n) {  // coarsening stalled
-      L.root.release();
-      L.agg.release();
-      break;
+    int nagg = 0;
+    if (prev) {
+      // reuse: the previous hierarchy decides the levels and the aggregates
+      if (l + 1 >= (int)prev->lev.size()) break;
+      const Level& PL = *prev->lev[l];
+      if (PL.n != L.n) fail(SAAMG_EINVAL, "level sizes differ from the reused hierarchy");
+      L.root.alloc(L.n, s);
+      L.agg.alloc(L.n, s);
+      SAAMG_CUDA(cudaMemcpyAsync(L.root.p, PL.root.p, L.n, cudaMemcpyDeviceToDevice, s));
+      SAAMG_CUDA(cudaMemcpyAsync(L.agg.p, PL.agg.p, sizeof(int) * L.n, cudaMemcpyDeviceToDevice, s));
+      nagg = prev->lev[l + 1]->n;
+      pt.mark("L" + std::to_string(l) + ".reuse");
+    } else {
+      if (L.n <= prm.max_coarse || l == prm.max_levels - 1 || l == SAAMG_MAX_LEVELS - 1) break;
+      const unsigned seed = 0x9E3779B9u * (unsigned)(l + 1);
+      L.root.alloc(L.n, s);
+      L.agg.alloc(L.n, s);
+      pt.mark("L" + std::to_string(l) + ".pre");
+      nagg = mis2_aggregate(L.n, A.rowptr.p, A.col.p, A.nnz, ids, seed, L.root.p, L.agg.p,
+                            agg_scratch.view(), s);
+      pt.mark("L" + std::to_string(l) + ".mis2agg");
+      if (10LL * nagg > 9LL * L.n) {  // coarsening stalled
+        L.root.release();
+        L.agg.release();
+        break;
+      }
     }
     const StencilDev<double> S0 = od.view<double>();
     L.lambda = power_lambda(A, L.invd.p, ids, prm.power_iters, s, l == 0 ? &S0 : nullptr);
@@ -928,6 +971,27 @@ saamg_status saamg_setup(const saamg_operator* op, const saamg_params* params, v
     if (prm.beta_rule != 0 && prm.beta_rule != 1) fail(SAAMG_EINVAL, "beta_rule must be 0 or 1");
     auto h = std::make_unique<saamg_hierarchy>();
     setup_impl(op, prm, (cudaStream_t)stream, h.get());
+    SAAMG_CUDA(cudaMallocHost(&h->result, sizeof(PcgCtl)));
+    *out = h.release();
+  });
+}
+
+saamg_status saamg_setup_reuse(const saamg_operator* op, const saamg_hierarchy* prev,
+                               const saamg_params* params, void* stream, saamg_hierarchy** out) {
+  return guard("saamg_setup_reuse", [&] {
+    if (!op || op->magic != kOpMagic || !prev || prev->magic != kHierMagic || !out)
+      fail(SAAMG_EINVAL, "NULL or invalid argument");
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!same_pattern(op->d.A, prev->op->d.A, s))
+      fail(SAAMG_EINVAL, "the operator's pattern differs from the one the hierarchy was built on");
+    saamg_params prm = prev->prm;
+    if (params) prm = *params;
+    if (prm.cheb_degree < 1 || prm.cheb_degree > 16) fail(SAAMG_EINVAL, "cheb_degree must be in 1..16");
+    if (prm.precision < SAAMG_PREC_FP64 || prm.precision > SAAMG_PREC_FP32_BF16)
+      fail(SAAMG_EINVAL, "unknown precision");
+    auto h = std::make_unique<saamg_hierarchy>();
+    setup_impl(op, prm, s, h.get(), prev);
     SAAMG_CUDA(cudaMallocHost(&h->result, sizeof(PcgCtl)));
     *out = h.release();
   });

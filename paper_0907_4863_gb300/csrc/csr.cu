@@ -34,7 +34,19 @@ __global__ void __launch_bounds__(256) csr_k(int n, const int* __restrict__ rowp
     TV acc = TV(0);
     if (MODE != CSR_CHEB0 && active) {
       const int p0 = rowptr[row], p1 = rowptr[row + 1];
-      for (int p = p0 + gl; p < p1; p += G) acc += (TV)ld(val, p) * x[col[p]];
+      int p = p0 + gl;
+      // four independent (column, value) loads and gathers in flight per lane
+      for (; p + 3 * G < p1; p += 4 * G) {
+        const int k0 = col[p], k1 = col[p + G], k2 = col[p + 2 * G], k3 = col[p + 3 * G];
+        const TV a0 = (TV)ld(val, p), a1 = (TV)ld(val, p + G), a2 = (TV)ld(val, p + 2 * G),
+                 a3 = (TV)ld(val, p + 3 * G);
+        const TV x0 = x[k0], x1 = x[k1], x2 = x[k2], x3 = x[k3];
+        acc += a0 * x0;
+        acc += a1 * x1;
+        acc += a2 * x2;
+        acc += a3 * x3;
+      }
+      for (; p < p1; p += G) acc += (TV)ld(val, p) * x[col[p]];
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
@@ -158,14 +170,15 @@ void csr_apply(int mode, int n, const int* rowptr, const int* col, const TM* val
     else
       launch_g<TV, TM, 8>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
   } else {
+    // FP32: groups sized so that a lane holds about four entries of its row
     if (avg_nnz <= 6.0)
+      launch_g<TV, TM, 2>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
+    else if (avg_nnz <= 20.0)
       launch_g<TV, TM, 4>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
-    else if (avg_nnz <= 16.0)
+    else if (avg_nnz <= 64.0)
       launch_g<TV, TM, 8>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
-    else if (avg_nnz <= 48.0)
-      launch_g<TV, TM, 16>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
     else
-      launch_g<TV, TM, 32>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
+      launch_g<TV, TM, 16>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
   }
 }
 

@@ -18,22 +18,17 @@ __device__ __forceinline__ double to_d(T v) {
   return (double)v;
 }
 
+// One row of chunk c for this lane (x, b and the metadata are read-only; y and d are written).
 template <class T, int MODE>
-__global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __restrict__ x,
-                                                 T* __restrict__ y, const T* __restrict__ b,
-                                                 T* __restrict__ d, T c1, T c2,
-                                                 double* __restrict__ partials) {
-  const int lane = threadIdx.x & 31;
-  const int wpb = blockDim.x >> 5;
-  const int nw = gridDim.x * wpb;
-  const T c2invd0 = c2 * S.invd0;
-  double dacc = 0.0;
-  for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < S.nchunks; c += nw) {
+__device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int lane,
+                                            const T* __restrict__ x, T* __restrict__ y,
+                                            const T* __restrict__ b, T* __restrict__ d, T c1,
+                                            T c2, T c2invd0, double& dacc) {
     const int2 ch = S.chunks[c];
     const int L = ch.x;
     const LineInfo me = S.lines[L];
     const int i = me.lo + ch.y + lane;
-    if (i > me.hi) continue;
+    if (i > me.hi) return;
     const int row = me.start + ch.y + lane;
     const bool reg = (i >= me.rlo) && (i <= me.rhi);
     T invd;
@@ -49,9 +44,8 @@ __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __res
       T dv = (reg ? c2invd0 : c2 * invd) * b[row];
       d[row] = dv;
       y[row] = dv;
-      continue;
+      return;
     }
-    const int j = L % S.ny, k = L / S.ny;
     const T xc = x[row];
     // SPMV modes accumulate A x; RESID / CHEB accumulate r = b - A x directly (FP64 issue
     // slots bound this kernel in double precision, so every add is folded into an FMA)
@@ -76,6 +70,7 @@ __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __res
         acc = fma(S.cz, sz, acc);
       }
     } else {
+      const int j = L % S.ny, k = L / S.ny;  // only boundary rows need the line's (j, k)
       acc = tb[0] * xc;
       if (i - 1 >= me.lo) acc = fma(tb[1], x[row - 1], acc);
       if (i + 1 <= me.hi) acc = fma(tb[2], x[row + 1], acc);
@@ -112,6 +107,25 @@ __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __res
       d[row] = dv;
       y[row] = xc + dv;
     }
+}
+
+// K chunks per warp iteration: the unrolled copies let the read-only loads of the next chunk
+// be issued before the stores of the current one (more bytes in flight per warp).
+template <class T, int MODE, int K>
+__global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __restrict__ x,
+                                                 T* __restrict__ y, const T* __restrict__ b,
+                                                 T* __restrict__ d, T c1, T c2,
+                                                 double* __restrict__ partials) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int nw = gridDim.x * wpb;
+  const T c2invd0 = c2 * S.invd0;
+  double dacc = 0.0;
+  for (int c0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * K; c0 < S.nchunks; c0 += nw * K) {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (c0 + k < S.nchunks)
+        stencil_row<T, MODE>(S, c0 + k, lane, x, y, b, d, c1, c2, c2invd0, dacc);
   }
   if (MODE == ST_SPMV_DOT || MODE == ST_DINV_DOT) {
     __shared__ double sh[32];
@@ -127,6 +141,13 @@ __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __res
   }
 }
 
+// chunks per warp iteration: FP32 is latency/HBM-bound and gains from more loads in flight;
+// FP64 is bound by FP64 issue and keeps one
+template <class T>
+constexpr int kChunks() {
+  return sizeof(T) == 4 ? 2 : 1;
+}
+
 }  // namespace
 
 template <class T>
@@ -138,37 +159,40 @@ void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* 
   }
   // the smoother class holds only the full Chebyshev step (fixed work per row); the
   // other modes of the same kernel are timed as "apply"
-  KernelTimer kt(mode == ST_CHEB        ? SAAMG_KT_STENCIL_SMOOTH
-                 : mode == ST_DINV_DOT ? -1
-                                       : SAAMG_KT_STENCIL_APPLY,
+  // one timing class per kind of pass (each has a fixed amount of work per row)
+  KernelTimer kt(mode == ST_CHEB                           ? SAAMG_KT_STENCIL_SMOOTH
+                 : (mode == ST_SPMV || mode == ST_SPMV_DOT) ? SAAMG_KT_STENCIL_APPLY
+                 : mode == ST_RESID                         ? SAAMG_KT_STENCIL_RESID
+                 : (mode == ST_CHEB0 || mode == ST_CHEB1)   ? SAAMG_KT_STENCIL_FIRST
+                                                            : -1,
                  S.n, s);
   // Reductions use the fixed grid so that partial sums are always taken the same way.
   int blocks = kRedBlocks;
   if (mode != ST_SPMV_DOT && mode != ST_DINV_DOT) {
-    long long need = ((long long)S.nchunks + 7) / 8;
+    long long need = ((long long)S.nchunks + 8 * kChunks<T>() - 1) / (8 * kChunks<T>());
     blocks = (int)(need < 152 * 16 ? need : 152 * 16);
   }
   switch (mode) {
     case ST_SPMV:
-      stencil_k<T, ST_SPMV><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      stencil_k<T, ST_SPMV, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
       break;
     case ST_SPMV_DOT:
-      stencil_k<T, ST_SPMV_DOT><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      stencil_k<T, ST_SPMV_DOT, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
       break;
     case ST_RESID:
-      stencil_k<T, ST_RESID><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      stencil_k<T, ST_RESID, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
       break;
     case ST_CHEB:
-      stencil_k<T, ST_CHEB><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      stencil_k<T, ST_CHEB, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
       break;
     case ST_CHEB0:
-      stencil_k<T, ST_CHEB0><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      stencil_k<T, ST_CHEB0, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
       break;
     case ST_CHEB1:
-      stencil_k<T, ST_CHEB1><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      stencil_k<T, ST_CHEB1, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
       break;
     case ST_DINV_DOT:
-      stencil_k<T, ST_DINV_DOT><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      stencil_k<T, ST_DINV_DOT, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
       break;
     default:
       fail(SAAMG_EINVAL, "bad stencil mode");

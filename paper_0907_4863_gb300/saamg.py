@@ -17,7 +17,9 @@ BC_CONSTANT, BC_LINEAR, BC_QUADRATIC = 0, 1, 2
 Z_ROBIN, Z_DIRICHLET = 0, 1
 PREC_FP64, PREC_FP32, PREC_FP32_BF16 = 0, 1, 2
 KT_STENCIL_SMOOTH, KT_STENCIL_APPLY, KT_COARSE, KT_TRANSFER, KT_SPGEMM = 0, 1, 2, 3, 4
-KT_NAMES = ["stencil_smooth", "stencil_apply", "coarse_csr", "transfer", "spgemm"]
+KT_STENCIL_RESID, KT_STENCIL_FIRST = 5, 6
+KT_NAMES = ["stencil_smooth", "stencil_apply", "coarse_csr", "transfer", "spgemm", "stencil_resid",
+            "stencil_first"]
 MAX_LEVELS = 16
 
 
@@ -100,6 +102,7 @@ def lib():
         "saamg_operator_copy": [_p, _p, _p, _p, _p, _p, _p, _p],
         "saamg_operator_apply": [_p, _p, _p, _p],
         "saamg_setup": [_p, C.POINTER(Params), _p, C.POINTER(_p)],
+        "saamg_setup_reuse": [_p, _p, C.POINTER(Params), _p, C.POINTER(_p)],
         "saamg_hierarchy_get_info": [_p, C.POINTER(HierarchyInfo)],
         "saamg_hierarchy_copy_level": [_p, _i] + [_p] * 12,
         "saamg_vcycle": [_p, _p, _p, _p],
@@ -297,6 +300,16 @@ def setup(op: Operator, params: Params = None, stream=None) -> Hierarchy:
     h = C.c_void_p()
     _check(lib().saamg_setup(op.handle, C.byref(params) if params is not None else None,
                              _stream(stream), C.byref(h)))
+    return Hierarchy(h, op)
+
+
+@_entry
+def setup_reuse(op: Operator, prev: Hierarchy, params: Params = None, stream=None) -> Hierarchy:
+    """Hierarchy for `op` that keeps prev's aggregates (same operator pattern required)."""
+    h = C.c_void_p()
+    _check(lib().saamg_setup_reuse(op.handle, prev.handle,
+                                   C.byref(params) if params is not None else None,
+                                   _stream(stream), C.byref(h)))
     return Hierarchy(h, op)
 
 

@@ -1,0 +1,108 @@
+"""Parity at the benchmark's full size (256^3 elliptic pipe, linear extrapolation, coarse
+<= 4096, rtol 1e-8 -- the configuration bench.py times), and properties at 512^3.
+
+At 256^3 the oracle is still affordable: its operator, its level-0 aggregation, one of its
+V-cycles and a complete solve are compared with the GPU path.  At 512^3 (5.7e7 unknowns) the
+checks are properties that hold at any size.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_0907_4863_gb300 import inputs as I
+from tests.oracle_cases import oracle_hierarchy, oracle_operator
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+SEED0 = 0x9E3779B9
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    from paper_0907_4863_gb300 import build
+    build.build()
+    from paper_0907_4863_gb300 import saamg
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    saamg.use_torch_allocator()
+    return saamg
+
+
+@pytest.fixture(scope="module")
+def world256(S):
+    w = I.pipe_workload(256, I.LINEAR)
+    o = oracle_operator(w)
+    g = S.build_operator(S.make_domain(w.domain), S.make_grid(w.grid), w.mode)
+    h = S.setup(g, S.params_default(max_coarse=4096))
+    return w, o, g, h
+
+
+def test_operator_256_bitwise(S, world256):
+    w, o, g, h = world256
+    c = S.operator_copy(g)
+    assert g.size() == (o.n, o.nnz) == (7119872, 49586872)
+    assert np.array_equal(c["node_of_row"], o.node_of_row)
+    assert np.array_equal(c["scale"], o.scale)
+    assert np.array_equal(c["rowptr"], o.rowptr)
+    assert np.array_equal(c["col"], o.col)
+    assert np.array_equal(c["val"], o.ahat)
+
+
+def test_level0_aggregates_256_bit_exact(S, world256):
+    w, o, g, h = world256
+    ids = o.node_of_row.astype(np.uint32)
+    root = O.mis2(o.rowptr, o.col, ids, SEED0)
+    agg, nagg = O.aggregate(o.rowptr, o.col, ids, SEED0, root)
+    lv = S.hierarchy_copy_level(h, 0)
+    assert h.info()["n"][1] == nagg
+    assert np.array_equal(lv["root"], root)
+    assert np.array_equal(lv["agg"], agg)
+
+
+def test_vcycle_and_solve_256_match_oracle(S, world256):
+    import torch
+    w, o, g, h = world256
+    oh = oracle_hierarchy(o, max_coarse=4096)
+    assert [oh.n(l) for l in range(oh.levels)] == h.info()["n"]
+    r = np.random.default_rng(9).standard_normal(o.n)
+    z = torch.empty(o.n, dtype=torch.float64, device="cuda")
+    S.vcycle(h, torch.from_numpy(r).cuda(), z)
+    ref = oh.vcycle(r)
+    assert np.max(np.abs(z.cpu().numpy() - ref)) < 1e-11 * np.max(np.abs(ref))
+    rho = I.gaussian_bunch(w.grid, w.centre, w.sigma, seed=0)
+    phi_ref, oinfo = oh.solve(rho, rtol=1e-8)
+    phi = torch.zeros(w.grid.nbox, dtype=torch.float64, device="cuda")
+    info = S.solve(h, torch.from_numpy(rho).cuda(), phi, rtol=1e-8)
+    got = phi.cpu().numpy()
+    assert info["converged"] == 1 and abs(info["iters"] - oinfo["iters"]) <= 1
+    assert np.max(np.abs(got - phi_ref)) <= 1e-10 * np.max(np.abs(phi_ref))
+    # true residual of the scaled system, recomputed with the oracle's operator
+    rows = o.node_of_row
+    xh = got[rows] / o.scale
+    bh = o.scale * (o.bfac * rho[rows])
+    res = bh - o.scipy() @ xh
+    assert np.linalg.norm(res) <= 1.01e-8 * np.linalg.norm(bh)
+
+
+def test_solve_512_properties(S):
+    """5.7e7 unknowns: convergence, the recomputed residual, the FP32 V-cycle reaching the same
+    accuracy, and the iteration count staying in the grid-independent range."""
+    import torch
+    w = I.pipe_workload(512, I.LINEAR)
+    g = S.build_operator(S.make_domain(w.domain), S.make_grid(w.grid), w.mode)
+    n, nnz = g.size()
+    assert 5.6e7 < n < 5.8e7
+    rho = I.gaussian_bunch_torch(w.grid, w.centre, w.sigma, 0)
+    its = {}
+    for prec in (0, 1):
+        h = S.setup(g, S.params_default(max_coarse=4096, precision=prec, beta_rule=1 if prec else 0))
+        info = h.info()
+        assert info["n"][-1] <= 4096
+        phi = torch.zeros_like(rho)
+        si = S.solve(h, rho, phi, rtol=1e-8)
+        assert si["converged"] == 1 and si["relres_true"] <= 1.5e-8
+        assert torch.all(torch.isfinite(phi))
+        its[prec] = si["iters"]
+        h.free()
+    assert its[0] <= 30 and abs(its[1] - its[0]) <= 3
