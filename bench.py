@@ -31,7 +31,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 f
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP64 level-0 Chebyshev step
 # on the 256^3 elliptic pipe (profiles/stencil_cheb_fp64_pipe256.md); None for other kernels or
 # sizes, and to be reset whenever that kernel changes
-TRAFFIC_BYTES = {("stencil_smooth", 0, 256): 283.02e6}
+TRAFFIC_BYTES = {("stencil_smooth", 0, 256): 285.69e6}
+# kernel timing classes of the solve phase (one kernel template each)
+SOLVE_CLASSES = ("stencil_smooth", "stencil_apply", "stencil_resid", "stencil_first",
+                 "coarse_csr", "transfer")
 
 
 def parse():
@@ -193,9 +196,7 @@ def run_ours(args):
     # --- roofline of the dominant kernel (live, CUDA events on the launching stream).  Each
     # solve-phase class is one kernel template; the sparse products of the setup are several
     # different kernels, reported as a class time only.
-    solve_classes = ("stencil_smooth", "stencil_apply", "stencil_resid", "stencil_first",
-                     "coarse_csr", "transfer")
-    dom_name = max(solve_classes, key=lambda k: ktime[k][0])
+    dom_name = max(SOLVE_CLASSES, key=lambda k: ktime[k][0])
     roof = roofline(dom_name, ktime[dom_name], prec, args.n)
 
     # --- end to end through the public API with host buffers (pinned), copies in the region
@@ -265,34 +266,47 @@ def run_ours(args):
 
 
 def roofline(name, rec, prec, n=256):
-    """Algorithmic work per launch / average launch duration for the dominant class."""
-    total_ms, launches, rows = rec
+    """Algorithmic work per launch / average launch duration of one timing class.
+
+    Stencil classes count rows; the sparse-matrix classes (coarse_csr, transfer) count
+    matrix entries.  FP64 passes are FP64-issue-bound on this part and are reported against
+    the derived FP64 peak; the FP32/BF16 passes against the measured HBM copy bandwidth.
+    """
+    total_ms, launches, units = rec
     if launches == 0 or total_ms <= 0:
         return None
     avg_s = total_ms / launches / 1e3
-    rows_per_launch = rows / launches
-    if prec == 0 and name in ("stencil_smooth", "stencil_apply", "stencil_resid"):
-        # FP64 issue-bound: 19 flops per row for a Chebyshev step fused with the residual
-        # (13 for A x, 1 for b - A x, 4 for the direction update, 1 for x + d); 13 for A x
-        flops = {"stencil_smooth": 19, "stencil_apply": 15, "stencil_resid": 14}[name] * rows_per_launch
-        ach = flops / avg_s / 1e12
-        return {"bound": "alu", "kernel": name, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": TRAFFIC_BYTES.get((name, prec, n)),
-                "algorithmic_bytes_per_launch": {"stencil_smooth": 40, "stencil_apply": 16,
-                                                 "stencil_resid": 24}[name] * rows_per_launch,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                "avg_launch_us": avg_s * 1e6, "launches": launches}
+    per = units / launches
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
     w = 8 if prec == 0 else 4
-    per_row = {"stencil_smooth": 5 * w, "stencil_apply": 2 * w, "stencil_resid": 3 * w}.get(name, 2 * w)
-    ach = per_row * rows_per_launch / avg_s / 1e9
-    return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": hbm, "unit": "GB/s",
-            "frac": ach / hbm, "traffic": None,
-            "peak_source": "measured" if peaks else "fallback",
-            "avg_launch_us": avg_s * 1e6, "launches": launches}
+    if name.startswith("stencil"):
+        # flops per row: 13 for A x (7 multiply-adds less one), +1 for b - A x, +4 for the
+        # Chebyshev update, +1 for x + d; bytes per row: the compulsory vector traffic
+        flops = {"stencil_smooth": 19, "stencil_apply": 15, "stencil_resid": 14,
+                 "stencil_first": 17}[name] * per
+        nbytes = {"stencil_smooth": 5, "stencil_apply": 2, "stencil_resid": 3,
+                  "stencil_first": 4}[name] * w * per
+    else:
+        # 2 flops per entry; bytes per entry: column index + value (FP32 / BF16 values in
+        # the mixed V-cycle; transfers keep FP32 values in both mixed modes)
+        flops = 2 * per
+        vbytes = 8 if prec == 0 else (2 if (prec == 2 and name == "coarse_csr") else 4)
+        nbytes = (4 + vbytes) * per
+    out = {"kernel": name, "avg_launch_us": avg_s * 1e6, "launches": launches,
+           "traffic": TRAFFIC_BYTES.get((name, prec, n)),
+           "algorithmic_bytes_per_launch": nbytes, "algorithmic_flops_per_launch": flops}
+    if prec == 0:
+        ach = flops / avg_s / 1e12
+        out.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS,
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"})
+    else:
+        ach = nbytes / avg_s / 1e9
+        out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm, "peak_source": "measured" if peaks else "fallback"})
+    return out
 
 
 def extra_legs(S, torch, w, dom, grid, rho, args):
@@ -331,12 +345,11 @@ def extra_legs(S, torch, w, dom, grid, rho, args):
             op2.free()
         torch.cuda.synchronize()
         full_ms = 1e3 * (time.perf_counter() - t0) / args.steps
-        dom_name = "stencil_smooth"
         out[f"{name}_vcycle"] = {
             "solve_only_solves_per_s": 1e3 / ms, "solve_ms": ms,
             "full_pipeline_solves_per_s": 1e3 / full_ms, "setup_ms": h.info()["setup_ms"],
             "iters": its[-1]["iters"], "relres_true": its[-1]["relres_true"],
-            "roofline_stencil_smooth": roofline(dom_name, kt[dom_name], prec, args.n),
+            "rooflines": {c: roofline(c, kt[c], prec, args.n) for c in SOLVE_CLASSES},
             "kernel_classes_ms_per_solve": {k: v[0] / args.steps for k, v in kt.items()},
         }
         h.free()

@@ -187,6 +187,176 @@ __global__ void agg_number_k(int n, const int* __restrict__ aggroot, const int* 
   if (i < n) agg[i] = aggroot[i] >= 0 ? rank[aggroot[i]] : -1;
 }
 
+// --- level 0 on the line structure ------------------------------------------
+// Lane per row of a chunk; the six neighbours are row + off[q] with box ids id + dq[q].
+struct Nb0 {
+  int row;
+  unsigned id, mask;
+  int off[6];
+};
+
+__device__ __forceinline__ bool grid_row(const GridGraph& g, int c, int lane, Nb0& r) {
+  const int2 ch = g.chunks[c];
+  const LineInfo me = g.lines[ch.x];
+  const int i = me.lo + ch.y + lane;
+  if (i > me.hi) return false;
+  const int4 nb = g.nbr[ch.x];
+  r.row = me.start + ch.y + lane;
+  r.id = (unsigned)i + g.nx * (unsigned)ch.x;
+  r.mask = g.nbmask[r.row];
+  r.off[0] = -1;
+  r.off[1] = 1;
+  r.off[2] = nb.x;
+  r.off[3] = nb.y;
+  r.off[4] = nb.z;
+  r.off[5] = nb.w;
+  return true;
+}
+
+__device__ __forceinline__ unsigned nb_id(const GridGraph& g, unsigned id, int q) {
+  switch (q) {
+    case 0: return id - 1u;
+    case 1: return id + 1u;
+    case 2: return id - g.nx;
+    case 3: return id + g.nx;
+    case 4: return id - g.nxy;
+    default: return id + g.nxy;
+  }
+}
+
+__device__ __forceinline__ unsigned long long prio_id(unsigned id, int row, uint32_t seed) {
+  return (((unsigned long long)fmix32(id ^ seed) << 32) | (unsigned long long)(uint32_t)row) + 1ull;
+}
+
+#define SAAMG_CHUNK_LOOP                                                                  \
+  const int lane = threadIdx.x & 31;                                                      \
+  const int nw = (gridDim.x * blockDim.x) >> 5;                                           \
+  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < g.nchunks; c += nw)
+
+__global__ void __launch_bounds__(256) mis0_max1_k(GridGraph g,
+                                                   const unsigned char* __restrict__ state,
+                                                   uint32_t seed,
+                                                   unsigned long long* __restrict__ m1) {
+  SAAMG_CHUNK_LOOP {
+    Nb0 r;
+    if (!grid_row(g, c, lane, r)) continue;
+    unsigned long long acc = state[r.row] == 0 ? prio_id(r.id, r.row, seed) : 0ull;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      if ((r.mask >> q) & 1u) {
+        const int u = r.row + r.off[q];
+        if (state[u] == 0) {
+          const unsigned long long k = prio_id(nb_id(g, r.id, q), u, seed);
+          acc = k > acc ? k : acc;
+        }
+      }
+    }
+    m1[r.row] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(256) mis0_max2_k(GridGraph g, unsigned char* __restrict__ state,
+                                                   uint32_t seed,
+                                                   const unsigned long long* __restrict__ m1) {
+  SAAMG_CHUNK_LOOP {
+    Nb0 r;
+    if (!grid_row(g, c, lane, r)) continue;
+    if (state[r.row] != 0) continue;
+    unsigned long long acc = m1[r.row];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      if ((r.mask >> q) & 1u) {
+        const unsigned long long k = m1[r.row + r.off[q]];
+        acc = k > acc ? k : acc;
+      }
+    }
+    if (acc == prio_id(r.id, r.row, seed)) state[r.row] = 1;
+  }
+}
+
+__global__ void __launch_bounds__(256) mis0_or1_k(GridGraph g,
+                                                  const unsigned char* __restrict__ state,
+                                                  unsigned char* __restrict__ o1) {
+  SAAMG_CHUNK_LOOP {
+    Nb0 r;
+    if (!grid_row(g, c, lane, r)) continue;
+    int any = state[r.row] == 1;
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      if ((r.mask >> q) & 1u) any |= state[r.row + r.off[q]] == 1;
+    o1[r.row] = (unsigned char)any;
+  }
+}
+
+__global__ void __launch_bounds__(256) mis0_or2_k(GridGraph g, unsigned char* __restrict__ state,
+                                                  const unsigned char* __restrict__ o1,
+                                                  int* __restrict__ undecided) {
+  int cnt = 0;
+  SAAMG_CHUNK_LOOP {
+    Nb0 r;
+    if (!grid_row(g, c, lane, r)) continue;
+    if (state[r.row] != 0) continue;
+    int any = o1[r.row];
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      if ((r.mask >> q) & 1u) any |= o1[r.row + r.off[q]];
+    if (any) state[r.row] = 2;
+    else ++cnt;
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(undecided, cnt);
+}
+
+__global__ void __launch_bounds__(256) agg0_phase1_k(GridGraph g,
+                                                     const unsigned char* __restrict__ root,
+                                                     int* __restrict__ root1) {
+  SAAMG_CHUNK_LOOP {
+    Nb0 r;
+    if (!grid_row(g, c, lane, r)) continue;
+    if (!root[r.row]) continue;
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      if ((r.mask >> q) & 1u) root1[r.row + r.off[q]] = r.row;
+    root1[r.row] = r.row;
+  }
+}
+
+// the roots of the neighbours' phase-1 aggregates compete by priority (root ids from `ids`)
+__global__ void __launch_bounds__(256) agg0_phase2_k(GridGraph g, const unsigned* __restrict__ ids,
+                                                     uint32_t seed,
+                                                     const int* __restrict__ root1,
+                                                     int* __restrict__ aggroot,
+                                                     int* __restrict__ err) {
+  SAAMG_CHUNK_LOOP {
+    Nb0 r;
+    if (!grid_row(g, c, lane, r)) continue;
+    const int own = root1[r.row];
+    if (own >= 0) {
+      aggroot[r.row] = own;
+      continue;
+    }
+    unsigned long long best = 0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      if ((r.mask >> q) & 1u) {
+        const int rt = root1[r.row + r.off[q]];
+        if (rt >= 0) {
+          const unsigned long long k = prio(ids, rt, seed);
+          best = k > best ? k : best;
+        }
+      }
+    }
+    if (best == 0) {
+      aggroot[r.row] = -1;
+      atomicOr(err, 1);
+    } else {
+      aggroot[r.row] = (int)(uint32_t)((best - 1ull) & 0xffffffffull);
+    }
+  }
+}
+
+#undef SAAMG_CHUNK_LOOP
+
 template <int G>
 int rounds(int n, const int* rowptr, const int* col, const unsigned* ids, uint32_t seed,
            unsigned char* state, unsigned long long* m1, unsigned char* o1, int* counter,
@@ -253,6 +423,44 @@ int mis2_aggregate(int n, const int* rowptr, const int* col, long long nnz, cons
     phase2<16>(n, rowptr, col, ids, seed, w.root1, w.aggroot, w.counter, s);
   else
     phase2<32>(n, rowptr, col, ids, seed, w.root1, w.aggroot, w.counter, s);
+  long long nagg = exclusive_scan_u8(root, w.rank, n, s);
+  agg_number_k<<<(n + 255) / 256, 256, 0, s>>>(n, w.aggroot, w.rank, agg);
+  SAAMG_LAUNCH();
+  int err = 0;
+  d2h_sync(&err, w.counter, sizeof(int), s);
+  if (err) fail(SAAMG_NUMERICAL, "aggregation left a node without an aggregate");
+  return (int)nagg;
+}
+
+int mis2_aggregate_grid(int n, const GridGraph& g, const unsigned* ids, uint32_t seed,
+                        unsigned char* root, int* agg, const AggScratch& w, cudaStream_t s) {
+  if (n <= 0) return 0;
+  const long long need = ((long long)g.nchunks + 7) / 8;
+  const int blocks = (int)(need < 152 * 16 ? (need > 0 ? need : 1) : 152 * 16);
+  SAAMG_CUDA(cudaMemsetAsync(w.state, 0, (size_t)n, s));
+  for (int done = 0;;) {
+    mis0_max1_k<<<blocks, 256, 0, s>>>(g, w.state, seed, w.m1);
+    SAAMG_LAUNCH();
+    mis0_max2_k<<<blocks, 256, 0, s>>>(g, w.state, seed, w.m1);
+    SAAMG_LAUNCH();
+    mis0_or1_k<<<blocks, 256, 0, s>>>(g, w.state, w.o1);
+    SAAMG_LAUNCH();
+    SAAMG_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(int), s));
+    mis0_or2_k<<<blocks, 256, 0, s>>>(g, w.state, w.o1, w.counter);
+    SAAMG_LAUNCH();
+    int left = 0;
+    d2h_sync(&left, w.counter, sizeof(int), s);
+    if (left == 0) break;
+    if (++done > n + 1) fail(SAAMG_NUMERICAL, "MIS-2 rounds did not terminate");
+  }
+  roots_from_state_k<<<(n + 255) / 256, 256, 0, s>>>(n, w.state, root);
+  SAAMG_LAUNCH();
+  fill_int(w.root1, -1, (size_t)n, s);
+  agg0_phase1_k<<<blocks, 256, 0, s>>>(g, root, w.root1);
+  SAAMG_LAUNCH();
+  SAAMG_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(int), s));
+  agg0_phase2_k<<<blocks, 256, 0, s>>>(g, ids, seed, w.root1, w.aggroot, w.counter);
+  SAAMG_LAUNCH();
   long long nagg = exclusive_scan_u8(root, w.rank, n, s);
   agg_number_k<<<(n + 255) / 256, 256, 0, s>>>(n, w.aggroot, w.rank, agg);
   SAAMG_LAUNCH();

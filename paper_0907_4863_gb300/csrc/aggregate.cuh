@@ -31,6 +31,23 @@ int mis2_aggregate(int n, const int* rowptr, const int* col, long long nnz, cons
                    uint32_t seed, unsigned char* root, int* agg, const AggScratch& w,
                    cudaStream_t s);
 
+// Level-0 graph: the 7-point star on the line structure, i.e. the pattern of the assembled
+// level-0 matrix (neighbour q of a row exists when bit q of nbmask is set; order -x, +x, -y,
+// +y, -z, +z).  Node ids are the box indices i + nx (j + ny k).
+struct GridGraph {
+  const LineInfo* lines;
+  const int4* nbr;      // row offsets to the -y, +y, -z, +z lines
+  const int2* chunks;   // (line, offset) of <= 32 consecutive rows
+  int nchunks;
+  const unsigned char* nbmask;
+  unsigned nx, nxy;     // id strides in y and z
+};
+
+// mis2_aggregate on the level-0 graph, walking the line structure instead of a CSR pattern;
+// the same rounds, priorities and phases, so the same roots and aggregates.
+int mis2_aggregate_grid(int n, const GridGraph& g, const unsigned* ids, uint32_t seed,
+                        unsigned char* root, int* agg, const AggScratch& w, cudaStream_t s);
+
 // The same aggregation with every temporary in caller-provided scratch (w and `tiles`,
 // scan_u8_tiles_needed(n) entries); allocates nothing.
 int mis2_aggregate_into(int n, const int* rowptr, const int* col, long long nnz,

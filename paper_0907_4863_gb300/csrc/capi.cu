@@ -18,6 +18,7 @@
 #include "galerkin.cuh"
 #include "operator.cuh"
 #include "pcg.cuh"
+#include "sell.cuh"
 
 namespace saamg {
 
@@ -162,7 +163,11 @@ struct Level {
   // V-cycle work vectors (FP64 and FP32 sets; only the one for the precision is allocated)
   Buf<double> x0, x1, b, d, r;
   Buf<float> fx0, fx1, fb, fd, fr;
-  Buf<float> P32, R32;          // FP32 values of P and R
+  // SELL-32 copy of A used by the V-cycle smoother (levels 1 .. L-2), with the values of
+  // the working precision (FP64, FP32 or BF16); P and R stay CSR (a warp-wide row group
+  // gathers neighbouring columns, which one-thread-per-row slices would scatter)
+  DevSell As;
+  Buf<float> P32, R32;          // FP32 values of P and R (mixed precision)
 };
 
 }  // namespace saamg
@@ -324,8 +329,15 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
       L.root.alloc(L.n, s);
       L.agg.alloc(L.n, s);
       pt.mark("L" + std::to_string(l) + ".pre");
-      nagg = mis2_aggregate(L.n, A.rowptr.p, A.col.p, A.nnz, ids, seed, L.root.p, L.agg.p,
-                            agg_scratch.view(), s);
+      if (l == 0) {
+        // level 0: the graph of the 7-point star, walked on the line structure
+        GridGraph gg{od.lines.p, od.nbr.p, od.chunks.p, od.nchunks, od.nbmask.p,
+                     (unsigned)od.g.nx, (unsigned)od.g.nx * (unsigned)od.g.ny};
+        nagg = mis2_aggregate_grid(L.n, gg, ids, seed, L.root.p, L.agg.p, agg_scratch.view(), s);
+      } else {
+        nagg = mis2_aggregate(L.n, A.rowptr.p, A.col.p, A.nnz, ids, seed, L.root.p, L.agg.p,
+                              agg_scratch.view(), s);
+      }
       pt.mark("L" + std::to_string(l) + ".mis2agg");
       if (10LL * nagg > 9LL * L.n) {  // coarsening stalled
         L.root.release();
@@ -368,22 +380,14 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
     Level& L = *h->lev[q];
     if (q < nl - 1) L.cheb = cheb_coefficients(L.lambda, prm.cheb_ratio, prm.cheb_safety, prm.cheb_degree);
     alloc_level_vectors(h, L, q == 0, s);
-    if (mixed(h)) {
-      if (q >= 1) {
-        if (prm.precision == SAAMG_PREC_FP32) {
-          L.A.val32.alloc(L.A.nnz, s);
-          to_float(L.A.val.p, L.A.val32.p, L.A.nnz, s);
-        } else {
-          L.A.val16.alloc(L.A.nnz, s);
-          to_bf16(L.A.val.p, L.A.val16.p, L.A.nnz, s);
-        }
-      }
-      if (q < nl - 1) {
-        L.P32.alloc(L.P.nnz, s);
-        to_float(L.P.val.p, L.P32.p, L.P.nnz, s);
-        L.R32.alloc(L.R.nnz, s);
-        to_float(L.R.val.p, L.R32.p, L.R.nnz, s);
-      }
+    const bool f64 = !mixed(h), f32 = prm.precision == SAAMG_PREC_FP32;
+    const bool bf16 = prm.precision == SAAMG_PREC_FP32_BF16;
+    if (q >= 1 && q < nl - 1) sell_from_csr(L.A, L.As, f64, f32, bf16, s);
+    if (!f64 && q < nl - 1) {
+      L.P32.alloc(L.P.nnz, s);
+      to_float(L.P.val.p, L.P32.p, L.P.nnz, s);
+      L.R32.alloc(L.R.nnz, s);
+      to_float(L.R.val.p, L.R32.p, L.R.nnz, s);
     }
   }
   const int n = od.n;
@@ -409,7 +413,7 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
     bytes += L->A.bytes() + L->P.bytes() + L->R.bytes() + L->invd.bytes() + L->invd32.bytes() +
              L->agg.bytes() + L->root.bytes() + L->x0.bytes() + L->x1.bytes() + L->b.bytes() +
              L->d.bytes() + L->r.bytes() + L->fx0.bytes() + L->fx1.bytes() + L->fb.bytes() +
-             L->fd.bytes() + L->fr.bytes() + L->P32.bytes() + L->R32.bytes();
+             L->fd.bytes() + L->fr.bytes() + L->As.bytes() + L->P32.bytes() + L->R32.bytes();
   }
   bytes += h->coarse.inv.bytes() + 6LL * n * 8 + (mixed(h) ? 8LL * n : 0);
   h->bytes = bytes;
@@ -460,8 +464,8 @@ template <>
 void level_csr<double>(saamg_hierarchy* h, int l, int mode, const double* x, double* y,
                        const double* b, double* d, double c1, double c2, cudaStream_t s) {
   Level& L = *h->lev[l];
-  csr_apply<double, double>(mode, L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, L.avg, x, y, b, d,
-                            L.invd.p, c1, c2, nullptr, s, SAAMG_KT_COARSE);
+  sell_apply<double, double>(mode, L.As, L.As.val.p, x, y, b, d, L.invd.p, c1, c2, s,
+                             SAAMG_KT_COARSE);
 }
 
 template <>
@@ -469,11 +473,11 @@ void level_csr<float>(saamg_hierarchy* h, int l, int mode, const float* x, float
                       const float* b, float* d, float c1, float c2, cudaStream_t s) {
   Level& L = *h->lev[l];
   if (h->prm.precision == SAAMG_PREC_FP32)
-    csr_apply<float, float>(mode, L.n, L.A.rowptr.p, L.A.col.p, L.A.val32.p, L.avg, x, y, b, d,
-                            L.invd32.p, c1, c2, nullptr, s, SAAMG_KT_COARSE);
+    sell_apply<float, float>(mode, L.As, L.As.val32.p, x, y, b, d, L.invd32.p, c1, c2, s,
+                             SAAMG_KT_COARSE);
   else
-    csr_apply<float, __nv_bfloat16>(mode, L.n, L.A.rowptr.p, L.A.col.p, L.A.val16.p, L.avg, x, y,
-                                    b, d, L.invd32.p, c1, c2, nullptr, s, SAAMG_KT_COARSE);
+    sell_apply<float, __nv_bfloat16>(mode, L.As, L.As.val16.p, x, y, b, d, L.invd32.p, c1, c2,
+                                     s, SAAMG_KT_COARSE);
 }
 
 template <class T>

@@ -129,6 +129,9 @@ struct __align__(32) LineInfo {
 template <class T>
 struct StencilDev {
   const LineInfo* lines;
+  // per line: row offset from an unknown (i, L) to its neighbour (i, L') in the -y, +y, -z,
+  // +z line (start' - lo') - (start - lo); 0 where that line does not exist or is empty
+  const int4* nbr;
   const int2* chunks;  // (line, offset of the first of <= 32 consecutive unknowns)
   int nchunks;
   int n;               // unknowns
@@ -171,7 +174,8 @@ long long exclusive_scan_u8_into(const unsigned char* in, int* out, int n, long 
                                  cudaStream_t s);
 void fill_int(int* p, int v, size_t n, cudaStream_t s);
 void fill_double(double* p, double v, size_t n, cudaStream_t s);
-void sum_partials(const double* partials, int count, double* out, cudaStream_t s);
+void sum_partials(const double* partials, int count, double* out, cudaStream_t s,
+                  double* inv_sqrt = nullptr);
 // Copies `bytes` from device to host and waits.
 void d2h_sync(void* host, const void* dev, size_t bytes, cudaStream_t s);
 

@@ -2,6 +2,8 @@
 // restriction R r and prolongation x += P v (Algorithm 1), and D^-1 A x for the
 // power iteration.  G lanes cooperate on one row (G chosen from the mean row length),
 // partial row sums are combined with shuffles inside the G-lane group.
+#include <cmath>
+
 #include "csr.cuh"
 
 namespace saamg {
@@ -20,13 +22,15 @@ __global__ void __launch_bounds__(256) csr_k(int n, const int* __restrict__ rowp
                                              const TM* __restrict__ val, const TV* __restrict__ x,
                                              TV* __restrict__ y, const TV* __restrict__ b,
                                              TV* __restrict__ d, const TV* __restrict__ invd,
-                                             TV c1, TV c2, double* __restrict__ partials) {
+                                             TV c1, TV c2, double* __restrict__ partials,
+                                             const double* __restrict__ xscale) {
   const int lane = threadIdx.x & 31;
   const int gl = lane % G;
   constexpr int kRowsPerWarp = 32 / G;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   double dacc = 0.0;
+  if (MODE == CSR_SPMV_DINV_DOT) c2 = xscale ? (TV)*xscale : TV(1);
   // the trip count is uniform across the warp, so the group shuffles see all 32 lanes
   for (int wbase = warp * kRowsPerWarp; wbase < n; wbase += nwarps * kRowsPerWarp) {
     const int row = wbase + lane / G;
@@ -67,8 +71,8 @@ __global__ void __launch_bounds__(256) csr_k(int n, const int* __restrict__ rowp
         const TV dv = c2 * (invd[row] * b[row]);
         d[row] = dv;
         y[row] = dv;
-      } else {  // CSR_SPMV_DINV_DOT
-        const TV w = invd[row] * acc;
+      } else {  // CSR_SPMV_DINV_DOT: c2 carries the scale of x
+        const TV w = (c2 * invd[row]) * acc;
         y[row] = w;
         dacc += (double)w * (double)w;
       }
@@ -90,7 +94,7 @@ __global__ void __launch_bounds__(256) csr_k(int n, const int* __restrict__ rowp
 template <class TV, class TM, int G>
 void launch_g(int mode, int n, const int* rowptr, const int* col, const TM* val, const TV* x,
               TV* y, const TV* b, TV* d, const TV* invd, TV c1, TV c2, double* partials,
-              cudaStream_t s) {
+              cudaStream_t s, const double* xscale) {
   int blocks;
   if (mode == CSR_SPMV_DINV_DOT) {
     blocks = kRedBlocks;
@@ -101,7 +105,7 @@ void launch_g(int mode, int n, const int* rowptr, const int* col, const TM* val,
 #define SAAMG_CSR_CASE(M)                                                                  \
   case M:                                                                                  \
     csr_k<TV, TM, G, M><<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y, b, d, invd, c1, c2, \
-                                                partials);                                 \
+                                                partials, xscale);                         \
     break;
   switch (mode) {
     SAAMG_CSR_CASE(CSR_SPMV)
@@ -154,44 +158,53 @@ inline int grid_for(size_t n) {
 template <class TV, class TM>
 void csr_apply(int mode, int n, const int* rowptr, const int* col, const TM* val, double avg_nnz,
                const TV* x, TV* y, const TV* b, TV* d, const TV* invd, TV c1, TV c2,
-               double* partials, cudaStream_t s, int kclass) {
+               double* partials, cudaStream_t s, int kclass, const double* xscale) {
   if (n <= 0) {
     if (mode == CSR_SPMV_DINV_DOT) fill_double(partials, 0.0, kRedBlocks, s);
     return;
   }
-  KernelTimer kt(kclass, n, s);
+  // timing unit of the sparse-matrix classes: matrix entries
+  KernelTimer kt(kclass, std::llround(avg_nnz * n), s);
   // FP64 shuffle-adds are as costly as the row's multiply-adds on this part: few lanes per
   // row for double vectors; FP32 can afford wider groups for better coalescing.
   if (sizeof(TV) == 8) {
     if (avg_nnz <= 10.0)
-      launch_g<TV, TM, 2>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
+      launch_g<TV, TM, 2>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s,
+                              xscale);
     else if (avg_nnz <= 48.0)
-      launch_g<TV, TM, 4>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
+      launch_g<TV, TM, 4>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s,
+                              xscale);
     else
-      launch_g<TV, TM, 8>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
+      launch_g<TV, TM, 8>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s,
+                              xscale);
   } else {
     // FP32: groups sized so that a lane holds about four entries of its row
     if (avg_nnz <= 6.0)
-      launch_g<TV, TM, 2>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
+      launch_g<TV, TM, 2>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s,
+                              xscale);
     else if (avg_nnz <= 20.0)
-      launch_g<TV, TM, 4>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
+      launch_g<TV, TM, 4>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s,
+                              xscale);
     else if (avg_nnz <= 64.0)
-      launch_g<TV, TM, 8>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
+      launch_g<TV, TM, 8>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s,
+                              xscale);
     else
-      launch_g<TV, TM, 16>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s);
+      launch_g<TV, TM, 16>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s,
+                              xscale);
   }
 }
 
 template void csr_apply<double, double>(int, int, const int*, const int*, const double*, double,
                                         const double*, double*, const double*, double*,
-                                        const double*, double, double, double*, cudaStream_t, int);
+                                        const double*, double, double, double*, cudaStream_t, int,
+                                        const double*);
 template void csr_apply<float, float>(int, int, const int*, const int*, const float*, double,
                                       const float*, float*, const float*, float*, const float*,
-                                      float, float, double*, cudaStream_t, int);
+                                      float, float, double*, cudaStream_t, int, const double*);
 template void csr_apply<float, __nv_bfloat16>(int, int, const int*, const int*,
                                               const __nv_bfloat16*, double, const float*, float*,
                                               const float*, float*, const float*, float, float,
-                                              double*, cudaStream_t, int);
+                                              double*, cudaStream_t, int, const double*);
 
 void csr_diag_inverse(const DevCsr& A, double* invd, float* invd32, cudaStream_t s) {
   if (A.n == 0) return;

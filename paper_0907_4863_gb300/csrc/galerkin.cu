@@ -33,13 +33,6 @@ __global__ void power_init_k(int n, const unsigned* __restrict__ ids, double* __
   v[i] = 0.5 + (double)fmix32(id ^ 0xA5A5A5A5u) / 4294967296.0;
 }
 
-__global__ void power_normalize_k(int n, const double* __restrict__ w,
-                                  const double* __restrict__ nrm2, double* __restrict__ v) {
-  const double inv = 1.0 / sqrt(*nrm2);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    v[i] = w[i] * inv;
-}
-
 // --- sparse product --------------------------------------------------------
 struct CsrView {
   const int* rowptr;
@@ -291,52 +284,55 @@ __global__ void __launch_bounds__(128) spgemm_esc_k(const int* __restrict__ list
   }
 }
 
-// One thread per row for rows with at most 32 products: expand into a local list, stable
-// insertion sort by column (equal columns keep their product order), sum the runs.
+// One thread per row for rows whose X row has at most kMergeWays entries: a k-way merge of
+// the (sorted) Y rows that X's row selects.  Every output column is produced once, in
+// ascending order, and its products are summed in X's entry order -- the accumulation
+// order of the plain row-by-row product.  The lists' cursors stay in registers.
+constexpr int kMergeWays = 8;
+
 template <bool NUMERIC>
-__global__ void __launch_bounds__(128) spgemm_row_k(const int* __restrict__ list, int nlist,
-                                                    CsrView X, CsrView Y,
-                                                    const int* __restrict__ crowptr,
-                                                    int* __restrict__ count,
-                                                    int* __restrict__ ccol,
-                                                    double* __restrict__ cval) {
-  int c[32];
-  double v[32];
+__global__ void __launch_bounds__(128) spgemm_merge_k(const int* __restrict__ list, int nlist,
+                                                      CsrView X, CsrView Y,
+                                                      const int* __restrict__ crowptr,
+                                                      int* __restrict__ count,
+                                                      int* __restrict__ ccol,
+                                                      double* __restrict__ cval) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nlist; t += gridDim.x * blockDim.x) {
     const int i = list[t];
-    int np = 0;
-    for (int p = X.rowptr[i]; p < X.rowptr[i + 1]; ++p) {
-      const int k = X.col[p];
-      const double xv = NUMERIC ? X.val[p] : 0.0;
-      for (int q = Y.rowptr[k]; q < Y.rowptr[k + 1]; ++q) {
-        c[np] = Y.col[q];
-        if (NUMERIC) v[np] = xv * Y.val[q];
-        ++np;
+    const int p0 = X.rowptr[i], nxr = X.rowptr[i + 1] - p0;
+    int cur[kMergeWays], end[kMergeWays], head[kMergeWays];
+    double xv[kMergeWays];
+#pragma unroll
+    for (int w = 0; w < kMergeWays; ++w) {
+      cur[w] = 0;
+      end[w] = 0;
+      xv[w] = 0.0;
+      if (w < nxr) {
+        const int k = X.col[p0 + w];
+        cur[w] = Y.rowptr[k];
+        end[w] = Y.rowptr[k + 1];
+        if (NUMERIC) xv[w] = X.val[p0 + w];
       }
+      head[w] = cur[w] < end[w] ? Y.col[cur[w]] : INT_MAX;
     }
-    for (int a = 1; a < np; ++a) {
-      const int ca = c[a];
-      const double va = NUMERIC ? v[a] : 0.0;
-      int j = a - 1;
-      while (j >= 0 && c[j] > ca) {
-        c[j + 1] = c[j];
-        if (NUMERIC) v[j + 1] = v[j];
-        --j;
-      }
-      c[j + 1] = ca;
-      if (NUMERIC) v[j + 1] = va;
-    }
-    int out = 0;
     const int base = NUMERIC ? crowptr[i] : 0;
-    for (int a = 0; a < np;) {
-      const int ca = c[a];
+    int out = 0;
+    for (;;) {
+      int m = head[0];
+#pragma unroll
+      for (int w = 1; w < kMergeWays; ++w) m = min(m, head[w]);
+      if (m == INT_MAX) break;
       double sum = 0.0;
-      while (a < np && c[a] == ca) {
-        if (NUMERIC) sum += v[a];
-        ++a;
+#pragma unroll
+      for (int w = 0; w < kMergeWays; ++w) {
+        if (head[w] == m) {
+          if (NUMERIC) sum += xv[w] * Y.val[cur[w]];
+          ++cur[w];
+          head[w] = cur[w] < end[w] ? Y.col[cur[w]] : INT_MAX;
+        }
       }
       if (NUMERIC) {
-        ccol[base + out] = ca;
+        ccol[base + out] = m;
         cval[base + out] = sum;
       }
       ++out;
@@ -345,7 +341,8 @@ __global__ void __launch_bounds__(128) spgemm_row_k(const int* __restrict__ list
   }
 }
 
-// Row classes.  0: <= 32 products (thread per row); 1: <= 64 products (warp ESC);
+// Row classes.  0: X row of <= kMergeWays entries (thread per row, merge); 1: <= 64 products
+// (warp ESC);
 // 2 + (log2(table) - kHashMinLog): hash table of 2^log2 slots, log2 in [kHashMinLog, kHashMaxLog].
 constexpr int kHashMinLog = 6;
 constexpr int kHashMaxLog = 12;
@@ -364,7 +361,8 @@ __global__ void row_products_k(int n, CsrView X, CsrView Y, int* __restrict__ np
 
 // Class of every row (symbolic: table sized from min(products, m); numeric: from the exact
 // count); block-aggregated histogram.
-__global__ void classify_rows_k(int n, const int* __restrict__ nprod, const int* __restrict__ cnt,
+__global__ void classify_rows_k(int n, const int* __restrict__ xrowptr,
+                                const int* __restrict__ nprod, const int* __restrict__ cnt,
                                 int m, int* __restrict__ cls, int* __restrict__ hist) {
   __shared__ int sh[kClasses];
   if (threadIdx.x < kClasses) sh[threadIdx.x] = 0;
@@ -373,7 +371,7 @@ __global__ void classify_rows_k(int n, const int* __restrict__ nprod, const int*
   if (i < n) {
     const int np = nprod[i];
     int c;
-    if (np <= 32) {
+    if (xrowptr[i + 1] - xrowptr[i] <= kMergeWays) {
       c = 0;
     } else if (np <= 64) {
       c = 1;
@@ -483,24 +481,26 @@ double power_lambda(const DevCsr& A, const double* invd, const unsigned* ids, in
                     cudaStream_t s, const StencilDev<double>* S) {
   int n = A.n;
   if (n == 0) return 1.0;
+  // v_{k+1} = D^-1 A v_k / |D^-1 A v_k|: the pass that forms D^-1 A v_{k+1} applies the
+  // division by the previous norm to its output (one multiply per row, no separate sweep)
   Buf<double> v, w, part, nrm2;
   v.alloc(n, s);
   w.alloc(n, s);
   part.alloc(kRedBlocks, s);
-  nrm2.alloc(1, s);
+  nrm2.alloc(2, s);  // |w|^2 and 1 / |w|
   power_init_k<<<blocks_for(n), 256, 0, s>>>(n, ids, v.p);
   SAAMG_LAUNCH();
   double avg = (double)A.nnz / n;
   for (int it = 0; it <= iters; ++it) {
+    const double* xscale = it > 0 ? nrm2.p + 1 : nullptr;
     if (S)
-      stencil_apply<double>(*S, ST_DINV_DOT, v.p, w.p, nullptr, nullptr, 0.0, 0.0, part.p, s);
+      stencil_apply<double>(*S, ST_DINV_DOT, v.p, w.p, nullptr, nullptr, 0.0, 0.0, part.p, s,
+                            xscale);
     else
       csr_apply<double, double>(CSR_SPMV_DINV_DOT, n, A.rowptr.p, A.col.p, A.val.p, avg, v.p,
-                                w.p, nullptr, nullptr, invd, 0.0, 0.0, part.p, s);
-    sum_partials(part.p, kRedBlocks, nrm2.p, s);
-    if (it == iters) break;
-    power_normalize_k<<<std::min(blocks_for(n), 4096), 256, 0, s>>>(n, w.p, nrm2.p, v.p);
-    SAAMG_LAUNCH();
+                                w.p, nullptr, nullptr, invd, 0.0, 0.0, part.p, s, -1, xscale);
+    sum_partials(part.p, kRedBlocks, nrm2.p, s, nrm2.p + 1);
+    v.swap(w);
   }
   double h = 0;
   d2h_sync(&h, nrm2.p, sizeof(double), s);
@@ -521,10 +521,10 @@ void tentative(const int* agg, int n, int nagg, DevCsr& T, cudaStream_t s) {
 namespace {
 
 // Bins rows into per-class lists; returns the per-class counts and list offsets.
-void bin_rows(int n, const int* nprod, const int* cnt, int m, int* cls, int* list, int* ctl,
-              int hist[kClasses], int start[kClasses + 1], cudaStream_t s) {
+void bin_rows(int n, const int* xrowptr, const int* nprod, const int* cnt, int m, int* cls,
+              int* list, int* ctl, int hist[kClasses], int start[kClasses + 1], cudaStream_t s) {
   SAAMG_CUDA(cudaMemsetAsync(ctl, 0, sizeof(int) * 2 * kClasses, s));
-  classify_rows_k<<<blocks_for(n), 256, 0, s>>>(n, nprod, cnt, m, cls, ctl);
+  classify_rows_k<<<blocks_for(n), 256, 0, s>>>(n, xrowptr, nprod, cnt, m, cls, ctl);
   SAAMG_LAUNCH();
   d2h_sync(hist, ctl, sizeof(int) * kClasses, s);
   start[0] = 0;
@@ -543,7 +543,7 @@ void run_class(int c, const int* list, int nl, CsrView X, CsrView Y, const int* 
   const int threads = 32 * kSpgemmWarps;
   if (c == 0) {
     const int blocks = std::max(1, std::min((nl + 127) / 128, 152 * 16));
-    spgemm_row_k<NUMERIC><<<blocks, 128, 0, s>>>(list, nl, X, Y, crowptr, count, ccol, cval);
+    spgemm_merge_k<NUMERIC><<<blocks, 128, 0, s>>>(list, nl, X, Y, crowptr, count, ccol, cval);
     SAAMG_LAUNCH();
     return;
   }
@@ -601,7 +601,7 @@ void spgemm(const DevCsr& X, const DevCsr& Y, DevCsr& C, cudaStream_t s) {
   SAAMG_LAUNCH();
   int hist[kClasses], start[kClasses + 1];
   // symbolic: distinct columns per row
-  bin_rows(n, nprod.p, nullptr, Y.m, cls.p, list.p, ctl.p, hist, start, s);
+  bin_rows(n, X.rowptr.p, nprod.p, nullptr, Y.m, cls.p, list.p, ctl.p, hist, start, s);
   for (int c = 0; c < kClasses; ++c)
     run_class<false>(c, list.p + start[c], hist[c], view(X), view(Y), nullptr, cnt.p, overflow,
                      nullptr, nullptr, s);
@@ -615,7 +615,7 @@ void spgemm(const DevCsr& X, const DevCsr& Y, DevCsr& C, cudaStream_t s) {
   C.col.alloc(nnz, s);
   C.val.alloc(nnz, s);
   // numeric: tables sized from the exact counts
-  bin_rows(n, nprod.p, cnt.p, Y.m, cls.p, list.p, ctl.p, hist, start, s);
+  bin_rows(n, X.rowptr.p, nprod.p, cnt.p, Y.m, cls.p, list.p, ctl.p, hist, start, s);
   for (int c = 0; c < kClasses; ++c)
     run_class<true>(c, list.p + start[c], hist[c], view(X), view(Y), C.rowptr.p, nullptr, nullptr,
                     C.col.p, C.val.p, s);

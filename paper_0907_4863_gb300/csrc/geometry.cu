@@ -185,6 +185,26 @@ __global__ void set_start_and_chunks_k(LineInfo* lines, const int* start, const 
   for (int off = 0, c = c0; off < cnt; off += 32, ++c) chunks[c] = make_int2(L, off);
 }
 
+// Thread per line: row offsets to the four neighbouring lines (0 where a line is missing).
+__global__ void line_deltas_k(const LineInfo* __restrict__ lines, int nlines, int ny,
+                              int4* __restrict__ nbr) {
+  int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= nlines) return;
+  const int nz = nlines / ny, j = L % ny, k = L / ny;
+  const LineInfo me = lines[L];
+  const int base = me.start - me.lo;
+  auto delta = [&](int Ln) {
+    const LineInfo l = lines[Ln];
+    return l.hi >= l.lo ? (l.start - l.lo) - base : 0;
+  };
+  int4 r;
+  r.x = j > 0 ? delta(L - 1) : 0;
+  r.y = j < ny - 1 ? delta(L + 1) : 0;
+  r.z = k > 0 ? delta(L - ny) : 0;
+  r.w = k < nz - 1 ? delta(L + ny) : 0;
+  nbr[L] = r;
+}
+
 // Regular interior row: all six couplings -c_dir, diagonal 2(cx+cy+cz), scaled.
 __global__ void regular_consts_k(GeomParams g, double* out) {
   double dd[3], om, opl;
@@ -269,6 +289,7 @@ __global__ void assemble_scaled_k(GeomParams g, const LineInfo* __restrict__ lin
                                   double* __restrict__ coef, const double* __restrict__ scale,
                                   const int* __restrict__ rowptr, int* __restrict__ col,
                                   double* __restrict__ val, unsigned char* __restrict__ regular,
+                                  unsigned char* __restrict__ nbmask,
                                   const double* __restrict__ rc) {
   int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
@@ -313,6 +334,9 @@ __global__ void assemble_scaled_k(GeomParams g, const LineInfo* __restrict__ lin
   for (int q = 0; q < 7; ++q) cr[q] = sc[q];
   cr[7] = 1.0 / sc[0];
   regular[row] = reg ? 1 : 0;
+  unsigned char mk = 0;
+  for (int q = 0; q < 6; ++q) mk |= (unsigned char)((nb[q] >= 0) << q);
+  nbmask[row] = mk;
 }
 
 // Thread per line: longest run of regular rows -> [rlo, rhi]; table rows = the rest.
@@ -445,6 +469,9 @@ void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op) 
   set_start_and_chunks_k<<<(nlines + 255) / 256, 256, 0, s>>>(op.lines.p, start.p, chstart.p,
                                                                count.p, nlines, op.chunks.p);
   SAAMG_LAUNCH();
+  op.nbr.alloc(nlines, s);
+  line_deltas_k<<<(nlines + 255) / 256, 256, 0, s>>>(op.lines.p, nlines, g.ny, op.nbr.p);
+  SAAMG_LAUNCH();
 
   Buf<double> rc;
   rc.alloc(5, s);
@@ -461,6 +488,7 @@ void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op) 
   op.scale.alloc(op.n, s);
   op.ids.alloc(op.n, s);
   op.regular.alloc(op.n, s);
+  op.nbmask.alloc(op.n, s);
   Buf<double> coef;
   coef.alloc((size_t)op.n * 8, s);
   Buf<int> rowlen;
@@ -482,7 +510,7 @@ void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op) 
   if (op.n > 0) {
     assemble_scaled_k<<<warp_blocks(nchunks), 256, 0, s>>>(
         g, op.lines.p, op.chunks.p, op.nchunks, coef.p, op.scale.p, op.A.rowptr.p, op.A.col.p,
-        op.A.val.p, op.regular.p, rc.p);
+        op.A.val.p, op.regular.p, op.nbmask.p, rc.p);
     SAAMG_LAUNCH();
   }
   Buf<int> ntab, tstart;
@@ -508,6 +536,7 @@ template <>
 StencilDev<double> OperatorData::view<double>() const {
   StencilDev<double> v;
   v.lines = lines.p;
+  v.nbr = nbr.p;
   v.chunks = chunks.p;
   v.nchunks = nchunks;
   v.n = n;
@@ -527,6 +556,7 @@ template <>
 StencilDev<float> OperatorData::view<float>() const {
   StencilDev<float> v;
   v.lines = lines.p;
+  v.nbr = nbr.p;
   v.chunks = chunks.p;
   v.nchunks = nchunks;
   v.n = n;

@@ -22,6 +22,7 @@ struct OperatorData {
   long long nnz = 0;    // nonzeros of the explicit CSR
   int nlines = 0;       // ny * nz
   Buf<LineInfo> lines;
+  Buf<int4> nbr;        // per line: row offsets to the -y, +y, -z, +z neighbour lines
   Buf<int2> chunks;
   int nchunks = 0;
   Buf<double> table;    // 8 doubles per table row
@@ -31,10 +32,11 @@ struct OperatorData {
   Buf<double> scale;    // s_i = a_ii^-1/2 (unscaled diagonal)
   Buf<unsigned> ids;    // box index of each unknown
   Buf<unsigned char> regular;
+  Buf<unsigned char> nbmask;  // bit q: neighbour q (-x,+x,-y,+y,-z,+z) is an unknown
   DevCsr A;             // explicit scaled CSR (used by the AMG setup)
   size_t bytes() const {
-    return lines.bytes() + chunks.bytes() + table.bytes() + table32.bytes() + scale.bytes() +
-           ids.bytes() + regular.bytes() + A.bytes();
+    return lines.bytes() + nbr.bytes() + chunks.bytes() + table.bytes() + table32.bytes() + scale.bytes() +
+           ids.bytes() + regular.bytes() + nbmask.bytes() + A.bytes();
   }
   template <class T>
   StencilDev<T> view() const;
@@ -60,11 +62,11 @@ enum StencilMode {
   ST_RESID = 2,     // y = b - A x
   ST_CHEB = 3,      // r = b - A x; d = c1 d + c2 D^-1 r; y = x + d
   ST_CHEB0 = 4,     // d = c2 D^-1 b; y = d   (Chebyshev step 0 from x = 0)
-  ST_DINV_DOT = 5,  // y = D^-1 A x, partials of y.y (power iteration)
+  ST_DINV_DOT = 5,  // y = s D^-1 A x, partials of y.y (power iteration; s = *xscale or 1)
   ST_CHEB1 = 6      // ST_CHEB with c1 = 0 (first step from a nonzero x): d is not read
 };
 template <class T>
 void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* b, T* d, T c1,
-                   T c2, double* partials, cudaStream_t s);
+                   T c2, double* partials, cudaStream_t s, const double* xscale = nullptr);
 
 }  // namespace saamg

@@ -121,7 +121,9 @@ __global__ void fill_double_k(double* p, double v, size_t n) {
 }
 
 // Sums `count` partials in index order (one block, fixed tree), deterministic.
-__global__ void sum_partials_k(const double* __restrict__ part, int count, double* out) {
+// With `inv_sqrt`, also writes 1 / sqrt(sum) (the power iteration's normalisation).
+__global__ void sum_partials_k(const double* __restrict__ part, int count, double* out,
+                               double* inv_sqrt) {
   __shared__ double sh[kRedThreads];
   double acc = 0.0;
   for (int i = threadIdx.x; i < count; i += blockDim.x) acc += part[i];
@@ -131,7 +133,10 @@ __global__ void sum_partials_k(const double* __restrict__ part, int count, doubl
     if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = sh[0];
+  if (threadIdx.x == 0) {
+    *out = sh[0];
+    if (inv_sqrt) *inv_sqrt = 1.0 / sqrt(sh[0]);
+  }
 }
 
 }  // namespace
@@ -175,8 +180,9 @@ void fill_double(double* p, double v, size_t n, cudaStream_t s) {
   SAAMG_LAUNCH();
 }
 
-void sum_partials(const double* partials, int count, double* out, cudaStream_t s) {
-  sum_partials_k<<<1, kRedThreads, 0, s>>>(partials, count, out);
+void sum_partials(const double* partials, int count, double* out, cudaStream_t s,
+                  double* inv_sqrt) {
+  sum_partials_k<<<1, kRedThreads, 0, s>>>(partials, count, out, inv_sqrt);
   SAAMG_LAUNCH();
 }
 

@@ -1,0 +1,204 @@
+// SELL-32-sigma kernels: layout construction from CSR and the V-cycle operations on it
+// (Chebyshev step fused with the residual, residual, y = A x, y += A x).
+#include "sell.cuh"
+
+namespace saamg {
+
+namespace {
+
+constexpr int kSellCheb1 = 6;  // CSR_CHEB with c1 = 0: d is not read
+
+__device__ __forceinline__ double ld(const double* p, int i) { return p[i]; }
+__device__ __forceinline__ float ld(const float* p, int i) { return p[i]; }
+__device__ __forceinline__ float ld(const __nv_bfloat16* p, int i) {
+  return __bfloat162float(p[i]);
+}
+
+// Block per window: stable rank of each row by decreasing length, from the window's
+// lengths in shared memory.
+__global__ void __launch_bounds__(kSellWindow) sell_rank_k(int n, const int* __restrict__ rowptr,
+                                                           int* __restrict__ perm) {
+  __shared__ int len[kSellWindow];
+  const int t = threadIdx.x;
+  const int base = blockIdx.x * kSellWindow;
+  const int row = base + t;
+  const int L = row < n ? rowptr[row + 1] - rowptr[row] : -1;
+  len[t] = L;
+  __syncthreads();
+  if (row >= n) return;
+  int r = 0;
+  for (int j = 0; j < kSellWindow; ++j) {
+    const int lj = len[j];
+    r += (lj > L) | ((lj == L) & (j < t));
+  }
+  perm[base + r] = row;
+}
+
+// Entries of each slice: 32 x the length of its first (longest) row; windows hold whole
+// slices, so a slice never mixes two windows.
+__global__ void sell_width_k(int nslices, const int* __restrict__ rowptr,
+                             const int* __restrict__ perm, int* __restrict__ size) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s > nslices) return;
+  if (s == nslices) {
+    size[s] = 0;
+    return;
+  }
+  const int r = perm[32 * s];
+  size[s] = 32 * (rowptr[r + 1] - rowptr[r]);
+}
+
+__global__ void sell_fill_k(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                            const double* __restrict__ val, const int* __restrict__ perm,
+                            const int* __restrict__ soff, int* __restrict__ scol,
+                            double* __restrict__ sval, float* __restrict__ sval32,
+                            __nv_bfloat16* __restrict__ sval16) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int r = perm[p], s = p >> 5, lane = p & 31;
+  const int w = (soff[s + 1] - soff[s]) >> 5;
+  const int p0 = rowptr[r], len = rowptr[r + 1] - p0;
+  const int padc = len > 0 ? col[p0 + len - 1] : 0;
+  for (int k = 0; k < w; ++k) {
+    const int e = soff[s] + 32 * k + lane;
+    const bool real = k < len;
+    const double v = real ? val[p0 + k] : 0.0;
+    scol[e] = real ? col[p0 + k] : padc;
+    if (sval) sval[e] = v;
+    if (sval32) sval32[e] = (float)v;
+    if (sval16) sval16[e] = __double2bfloat16(v);
+  }
+}
+
+template <class TV, class TM, int MODE>
+__global__ void __launch_bounds__(256) sell_k(int n, int nslices, const int* __restrict__ perm,
+                                              const int* __restrict__ soff,
+                                              const int* __restrict__ col,
+                                              const TM* __restrict__ val, const TV* __restrict__ x,
+                                              TV* __restrict__ y, const TV* __restrict__ b,
+                                              TV* __restrict__ d, const TV* __restrict__ invd,
+                                              TV c1, TV c2) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < nslices; s += nw) {
+    const int p = 32 * s + lane;
+    if (p >= n) continue;  // no warp-collective operation follows
+    const int row = perm[p];
+    TV acc = TV(0);
+    if (MODE != CSR_CHEB0) {
+      const int e0 = soff[s] + lane, w = (soff[s + 1] - soff[s]) >> 5;
+      int k = 0;
+      // four independent (column, value, x) loads in flight per lane
+      for (; k + 4 <= w; k += 4) {
+        const int e = e0 + 32 * k;
+        const int k0 = col[e], k1 = col[e + 32], k2 = col[e + 64], k3 = col[e + 96];
+        const TV a0 = (TV)ld(val, e), a1 = (TV)ld(val, e + 32), a2 = (TV)ld(val, e + 64),
+                 a3 = (TV)ld(val, e + 96);
+        const TV x0 = x[k0], x1 = x[k1], x2 = x[k2], x3 = x[k3];
+        acc = fma(a0, x0, acc);
+        acc = fma(a1, x1, acc);
+        acc = fma(a2, x2, acc);
+        acc = fma(a3, x3, acc);
+      }
+      for (; k < w; ++k) {
+        const int e = e0 + 32 * k;
+        acc = fma((TV)ld(val, e), x[col[e]], acc);
+      }
+    }
+    if (MODE == CSR_SPMV) {
+      y[row] = acc;
+    } else if (MODE == CSR_RESID) {
+      y[row] = b[row] - acc;
+    } else if (MODE == CSR_ADD) {
+      y[row] = y[row] + acc;
+    } else if (MODE == CSR_CHEB) {
+      const TV dv = fma(c1, d[row], c2 * (invd[row] * (b[row] - acc)));
+      d[row] = dv;
+      y[row] = x[row] + dv;
+    } else if (MODE == kSellCheb1) {
+      const TV dv = c2 * (invd[row] * (b[row] - acc));
+      d[row] = dv;
+      y[row] = x[row] + dv;
+    } else {  // CSR_CHEB0
+      const TV dv = c2 * (invd[row] * b[row]);
+      d[row] = dv;
+      y[row] = dv;
+    }
+  }
+}
+
+}  // namespace
+
+void sell_from_csr(const DevCsr& A, DevSell& S, bool f64, bool f32, bool bf16, cudaStream_t s) {
+  S.n = A.n;
+  S.m = A.m;
+  S.nnz = A.nnz;
+  S.nslices = (A.n + 31) / 32;
+  S.perm.alloc(A.n, s);
+  S.soff.alloc(S.nslices + 1, s);
+  if (A.n == 0) {
+    fill_int(S.soff.p, 0, 1, s);
+    S.nent = 0;
+    S.col.alloc(0, s);
+    return;
+  }
+  const int nwin = (A.n + kSellWindow - 1) / kSellWindow;
+  sell_rank_k<<<nwin, kSellWindow, 0, s>>>(A.n, A.rowptr.p, S.perm.p);
+  SAAMG_LAUNCH();
+  Buf<int> size;
+  size.alloc(S.nslices + 1, s);
+  sell_width_k<<<(S.nslices + 1 + 255) / 256, 256, 0, s>>>(S.nslices, A.rowptr.p, S.perm.p,
+                                                           size.p);
+  SAAMG_LAUNCH();
+  const long long nent = exclusive_scan(size.p, S.soff.p, S.nslices + 1, s);
+  if (nent > 0x7fffffffLL) fail(SAAMG_EINVAL, "SELL layout above 2^31 entries");
+  S.nent = nent;
+  S.col.alloc(nent, s);
+  if (f64) S.val.alloc(nent, s);
+  if (f32) S.val32.alloc(nent, s);
+  if (bf16) S.val16.alloc(nent, s);
+  sell_fill_k<<<(A.n + 255) / 256, 256, 0, s>>>(A.n, A.rowptr.p, A.col.p, A.val.p, S.perm.p,
+                                                S.soff.p, S.col.p, f64 ? S.val.p : nullptr,
+                                                f32 ? S.val32.p : nullptr,
+                                                bf16 ? S.val16.p : nullptr);
+  SAAMG_LAUNCH();
+}
+
+template <class TV, class TM>
+void sell_apply(int mode, const DevSell& S, const TM* val, const TV* x, TV* y, const TV* b,
+                TV* d, const TV* invd, TV c1, TV c2, cudaStream_t s, int kclass) {
+  if (S.n <= 0) return;
+  KernelTimer kt(kclass, S.nnz, s);  // timing unit of the SELL classes: matrix entries
+  if (mode == CSR_CHEB && c1 == TV(0)) mode = kSellCheb1;
+  const long long need = ((long long)S.nslices + 7) / 8;
+  const int blocks = (int)(need < 152 * 16 ? need : 152 * 16);
+#define SAAMG_SELL_CASE(M)                                                                    \
+  case M:                                                                                     \
+    sell_k<TV, TM, M><<<blocks, 256, 0, s>>>(S.n, S.nslices, S.perm.p, S.soff.p, S.col.p, val, \
+                                             x, y, b, d, invd, c1, c2);                        \
+    break;
+  switch (mode) {
+    SAAMG_SELL_CASE(CSR_SPMV)
+    SAAMG_SELL_CASE(CSR_RESID)
+    SAAMG_SELL_CASE(CSR_CHEB)
+    SAAMG_SELL_CASE(CSR_CHEB0)
+    SAAMG_SELL_CASE(CSR_ADD)
+    SAAMG_SELL_CASE(kSellCheb1)
+    default:
+      fail(SAAMG_EINVAL, "bad SELL mode");
+  }
+#undef SAAMG_SELL_CASE
+  SAAMG_LAUNCH();
+}
+
+template void sell_apply<double, double>(int, const DevSell&, const double*, const double*,
+                                         double*, const double*, double*, const double*, double,
+                                         double, cudaStream_t, int);
+template void sell_apply<float, float>(int, const DevSell&, const float*, const float*, float*,
+                                       const float*, float*, const float*, float, float,
+                                       cudaStream_t, int);
+template void sell_apply<float, __nv_bfloat16>(int, const DevSell&, const __nv_bfloat16*,
+                                               const float*, float*, const float*, float*,
+                                               const float*, float, float, cudaStream_t, int);
+
+}  // namespace saamg

@@ -2,11 +2,11 @@
 // Sec. 2, scaled by D^-1/2 on both sides, applied on compact vectors.
 //
 // One warp per chunk of <= 32 consecutive unknowns of one x-line.  The x-neighbours are
-// the adjacent compact rows; the y- and z-neighbours of lane i are the rows start' +
-// (i - lo') of the neighbouring lines, so every warp load is a contiguous run.  Rows
-// inside the line's regular run use the four interior coefficients held in registers;
-// the remaining rows (near-boundary rows and their neighbours, about 5-8 % of all
-// rows) read their 7 coefficients and 1/diag from the table.
+// the adjacent compact rows; the y- and z-neighbours of a row are at a fixed offset per
+// pair of lines (row + (start' - lo') - (start - lo)), so every warp load is a contiguous
+// run.  Rows inside the line's regular run use the four interior coefficients held in
+// registers; the remaining rows (near-boundary rows and their neighbours, about 5-8 % of
+// all rows) read their 7 coefficients and 1/diag from the table.
 #include "operator.cuh"
 
 namespace saamg {
@@ -18,7 +18,40 @@ __device__ __forceinline__ double to_d(T v) {
   return (double)v;
 }
 
+// Bit test for a nonzero coefficient with integer instructions only (the FP64 pipe is the
+// bottleneck of the double-precision kernel).
+__device__ __forceinline__ bool nonzero(double v) {
+  return (static_cast<unsigned long long>(__double_as_longlong(v)) << 1) != 0ull;
+}
+__device__ __forceinline__ bool nonzero(float v) { return (__float_as_uint(v) << 1) != 0u; }
+
+// The 8 table entries of one row (64 B in double, 32 B in float, aligned to their size).
+__device__ __forceinline__ void load8(const double* p, double v[8]) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 t = q[k];
+    v[2 * k] = t.x;
+    v[2 * k + 1] = t.y;
+  }
+}
+__device__ __forceinline__ void load8(const float* p, float v[8]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float4 t = q[k];
+    v[4 * k] = t.x;
+    v[4 * k + 1] = t.y;
+    v[4 * k + 2] = t.z;
+    v[4 * k + 3] = t.w;
+  }
+}
+
 // One row of chunk c for this lane (x, b and the metadata are read-only; y and d are written).
+// Every row runs the same seven-term arithmetic: a regular row takes the interior
+// coefficients and the line's neighbour offsets; a table row (only its selection below
+// diverges, and it holds no floating-point work) takes its own coefficients, and a missing
+// neighbour (coefficient 0) points at the row itself.
 template <class T, int MODE>
 __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int lane,
                                             const T* __restrict__ x, T* __restrict__ y,
@@ -27,73 +60,65 @@ __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int l
     const int2 ch = S.chunks[c];
     const int L = ch.x;
     const LineInfo me = S.lines[L];
+    const int4 nb = S.nbr[L];
     const int i = me.lo + ch.y + lane;
     if (i > me.hi) return;
     const int row = me.start + ch.y + lane;
-    const bool reg = (i >= me.rlo) && (i <= me.rhi);
-    T invd;
-    const T* tb = nullptr;
-    if (reg) {
-      invd = S.invd0;
-    } else {
+    T a0 = S.c0, axm = S.cx, axp = S.cx, aym = S.cy, ayp = S.cy, azm = S.cz, azp = S.cz;
+    T c2i = c2invd0;
+    int oxm = -1, oxp = 1, oym = nb.x, oyp = nb.y, ozm = nb.z, ozp = nb.w;
+    if (i < me.rlo || i > me.rhi) {
       const int t = me.tstart + (i < me.rlo ? i - me.lo : (me.rlo - me.lo) + (i - me.rhi - 1));
-      tb = S.table + 8 * (size_t)t;
-      invd = tb[7];
+      T tb[8];
+      load8(S.table + 8 * (size_t)t, tb);
+      a0 = tb[0];
+      axm = tb[1];
+      axp = tb[2];
+      aym = tb[3];
+      ayp = tb[4];
+      azm = tb[5];
+      azp = tb[6];
+      c2i = c2 * tb[7];
+      oxm = nonzero(axm) ? oxm : 0;
+      oxp = nonzero(axp) ? oxp : 0;
+      oym = nonzero(aym) ? oym : 0;
+      oyp = nonzero(ayp) ? oyp : 0;
+      ozm = nonzero(azm) ? ozm : 0;
+      ozp = nonzero(azp) ? ozp : 0;
     }
     if (MODE == ST_CHEB0) {
-      T dv = (reg ? c2invd0 : c2 * invd) * b[row];
+      const T dv = c2i * b[row];
       d[row] = dv;
       y[row] = dv;
       return;
     }
-    const T xc = x[row];
-    // SPMV modes accumulate A x; RESID / CHEB accumulate r = b - A x directly (FP64 issue
-    // slots bound this kernel in double precision, so every add is folded into an FMA)
+    const T* xr = x + row;
+    const T xc = xr[0];
+    const T vxm = xr[oxm], vxp = xr[oxp], vym = xr[oym], vyp = xr[oyp], vzm = xr[ozm],
+            vzp = xr[ozp];
+    // SPMV modes accumulate A x; RESID / CHEB accumulate r = b - A x directly (one FMA per
+    // term: FP64 issue slots bound this kernel in double precision)
     constexpr bool kResid = (MODE == ST_RESID || MODE == ST_CHEB || MODE == ST_CHEB1);
     T acc;
-    if (reg) {
-      // all six neighbours are unknowns
-      const LineInfo ym = S.lines[L - 1], yp = S.lines[L + 1];
-      const LineInfo zm = S.lines[L - S.ny], zp = S.lines[L + S.ny];
-      const T sx = x[row - 1] + x[row + 1];
-      const T sy = x[ym.start + (i - ym.lo)] + x[yp.start + (i - yp.lo)];
-      const T sz = x[zm.start + (i - zm.lo)] + x[zp.start + (i - zp.lo)];
-      if (kResid) {
-        acc = fma(-S.c0, xc, b[row]);
-        acc = fma(-S.cx, sx, acc);
-        acc = fma(-S.cy, sy, acc);
-        acc = fma(-S.cz, sz, acc);
-      } else {
-        acc = S.c0 * xc;
-        acc = fma(S.cx, sx, acc);
-        acc = fma(S.cy, sy, acc);
-        acc = fma(S.cz, sz, acc);
-      }
+    if (kResid) {
+      acc = fma(-a0, xc, b[row]);
+      acc = fma(-axm, vxm, acc);
+      acc = fma(-axp, vxp, acc);
+      acc = fma(-aym, vym, acc);
+      acc = fma(-ayp, vyp, acc);
+      acc = fma(-azm, vzm, acc);
+      acc = fma(-azp, vzp, acc);
     } else {
-      const int j = L % S.ny, k = L / S.ny;  // only boundary rows need the line's (j, k)
-      acc = tb[0] * xc;
-      if (i - 1 >= me.lo) acc = fma(tb[1], x[row - 1], acc);
-      if (i + 1 <= me.hi) acc = fma(tb[2], x[row + 1], acc);
-      if (j > 0) {
-        const LineInfo l = S.lines[L - 1];
-        if (i >= l.lo && i <= l.hi) acc = fma(tb[3], x[l.start + (i - l.lo)], acc);
-      }
-      if (j < S.ny - 1) {
-        const LineInfo l = S.lines[L + 1];
-        if (i >= l.lo && i <= l.hi) acc = fma(tb[4], x[l.start + (i - l.lo)], acc);
-      }
-      if (k > 0) {
-        const LineInfo l = S.lines[L - S.ny];
-        if (i >= l.lo && i <= l.hi) acc = fma(tb[5], x[l.start + (i - l.lo)], acc);
-      }
-      if (k < S.nz - 1) {
-        const LineInfo l = S.lines[L + S.ny];
-        if (i >= l.lo && i <= l.hi) acc = fma(tb[6], x[l.start + (i - l.lo)], acc);
-      }
-      if (kResid) acc = b[row] - acc;
+      acc = a0 * xc;
+      acc = fma(axm, vxm, acc);
+      acc = fma(axp, vxp, acc);
+      acc = fma(aym, vym, acc);
+      acc = fma(ayp, vyp, acc);
+      acc = fma(azm, vzm, acc);
+      acc = fma(azp, vzp, acc);
     }
-    if (MODE == ST_DINV_DOT) {
-      const T w = invd * acc;
+    if (MODE == ST_DINV_DOT) {  // c2 carries the scale of x: w = c2 D^-1 A x
+      const T w = c2i * acc;
       y[row] = w;
       dacc = fma(to_d(w), to_d(w), dacc);
     } else if (MODE == ST_SPMV || MODE == ST_SPMV_DOT) {
@@ -102,7 +127,6 @@ __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int l
     } else if (MODE == ST_RESID) {
       y[row] = acc;
     } else {  // ST_CHEB / ST_CHEB1: d = c1 d + c2 D^-1 r; x_out = x + d
-      const T c2i = reg ? c2invd0 : c2 * invd;
       const T dv = (MODE == ST_CHEB1) ? acc * c2i : fma(c1, d[row], acc * c2i);
       d[row] = dv;
       y[row] = xc + dv;
@@ -115,10 +139,12 @@ template <class T, int MODE, int K>
 __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __restrict__ x,
                                                  T* __restrict__ y, const T* __restrict__ b,
                                                  T* __restrict__ d, T c1, T c2,
-                                                 double* __restrict__ partials) {
+                                                 double* __restrict__ partials,
+                                                 const double* __restrict__ xscale) {
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   const int nw = gridDim.x * wpb;
+  if (MODE == ST_DINV_DOT) c2 = xscale ? (T)*xscale : T(1);
   const T c2invd0 = c2 * S.invd0;
   double dacc = 0.0;
   for (int c0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * K; c0 < S.nchunks; c0 += nw * K) {
@@ -152,7 +178,7 @@ constexpr int kChunks() {
 
 template <class T>
 void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* b, T* d, T c1,
-                   T c2, double* partials, cudaStream_t s) {
+                   T c2, double* partials, cudaStream_t s, const double* xscale) {
   if (S.nchunks == 0) {
     if (mode == ST_SPMV_DOT || mode == ST_DINV_DOT) fill_double(partials, 0.0, kRedBlocks, s);
     return;
@@ -174,25 +200,25 @@ void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* 
   }
   switch (mode) {
     case ST_SPMV:
-      stencil_k<T, ST_SPMV, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      stencil_k<T, ST_SPMV, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials, xscale);
       break;
     case ST_SPMV_DOT:
-      stencil_k<T, ST_SPMV_DOT, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      stencil_k<T, ST_SPMV_DOT, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials, xscale);
       break;
     case ST_RESID:
-      stencil_k<T, ST_RESID, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      stencil_k<T, ST_RESID, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials, xscale);
       break;
     case ST_CHEB:
-      stencil_k<T, ST_CHEB, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      stencil_k<T, ST_CHEB, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials, xscale);
       break;
     case ST_CHEB0:
-      stencil_k<T, ST_CHEB0, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      stencil_k<T, ST_CHEB0, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials, xscale);
       break;
     case ST_CHEB1:
-      stencil_k<T, ST_CHEB1, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      stencil_k<T, ST_CHEB1, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials, xscale);
       break;
     case ST_DINV_DOT:
-      stencil_k<T, ST_DINV_DOT, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials);
+      stencil_k<T, ST_DINV_DOT, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials, xscale);
       break;
     default:
       fail(SAAMG_EINVAL, "bad stencil mode");
@@ -202,8 +228,9 @@ void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* 
 
 template void stencil_apply<double>(const StencilDev<double>&, int, const double*, double*,
                                     const double*, double*, double, double, double*,
-                                    cudaStream_t);
+                                    cudaStream_t, const double*);
 template void stencil_apply<float>(const StencilDev<float>&, int, const float*, float*,
-                                   const float*, float*, float, float, double*, cudaStream_t);
+                                   const float*, float*, float, float, double*, cudaStream_t,
+                                   const double*);
 
 }  // namespace saamg
