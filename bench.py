@@ -233,6 +233,7 @@ def run_ours(args):
     if not args.no_extra:
         extra = extra_legs(S, torch, w, dom, grid, rhs[args.warmup], args)
         extra.update(mixed_quadratic_leg(S, torch, args))
+        extra["aggregation_cubes_vs_mis2"] = aggregation_leg(S, torch, args)
     del rhs, phis
     torch.cuda.empty_cache()
     if not args.no_batched:
@@ -390,6 +391,58 @@ def mixed_quadratic_leg(S, torch, args):
         h.free()
         op.free()
     return {"mixed_quadratic_c3": {"workload": f"{w.name}, quadratic extrapolation, rtol 1e-8", **out}}
+
+
+def vcycle_bytes(info, prec, degree=2):
+    """Algorithmic bytes of one V-cycle from the level sizes: per smoothing or residual sweep
+    the matrix entries (column + value) and the vectors; level 0 is matrix-free (20 B per row
+    per Chebyshev step in FP32, 40 in FP64); transfers read P and R once each."""
+    w = 8 if prec == 0 else 4
+    n, nnz, nnz_p = info["n"], info["nnz"], info["nnz_p"]
+    total = n[0] * w * (10 * degree + 3) + 2 * nnz_p[0] * (w + 4)
+    for l in range(1, len(n) - 1):
+        total += (2 * degree + 1) * nnz[l] * (w + 4) + n[l] * w * (10 * degree + 3)
+        total += 2 * nnz_p[l] * (w + 4)
+    total += n[-1] * n[-1] * 8  # explicit inverse of the coarsest operator
+    return total
+
+
+def aggregation_leg(S, torch, args):
+    """MIS-2 aggregates against the paper's 3^3 cubes (Sec. 3.2) on the same workload:
+    hierarchy, CG iterations, setup and solve time, V-cycle bytes."""
+    w = workload(args.n)
+    dom, grid = S.make_domain(w.domain), S.make_grid(w.grid)
+    rho = torch.from_numpy(I.gaussian_bunch(w.grid, w.centre, w.sigma, seed=11)).cuda()
+    out = {"workload": f"{w.name}, linear extrapolation, rtol 1e-8"}
+    for name, agg in (("mis2", 0), ("cubes", 1)):
+        for pname, prec in (("fp64", 0), ("fp32", 1)):
+            params = S.params_default(max_coarse=4096, aggregation=agg, precision=prec,
+                                      beta_rule=1 if prec else 0)
+            op = S.build_operator(dom, grid, w.mode)
+            h = S.setup(op, params)  # warm-up of this configuration
+            h.free()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = S.setup(op, params)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            phi = torch.zeros_like(rho)
+            info = S.solve(h, rho, phi, rtol=RTOL)
+            phi.zero_()
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            info = S.solve(h, rho, phi, rtol=RTOL)
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            hi = h.info()
+            out[f"{name}_{pname}"] = {
+                "levels": hi["n"], "nnz": hi["nnz"], "iters": info["iters"],
+                "relres_true": info["relres_true"], "setup_ms": 1e3 * (t1 - t0),
+                "solve_ms": 1e3 * (t3 - t2), "vcycle_bytes": vcycle_bytes(hi, prec),
+                "hierarchy_device_bytes": hi["device_bytes"]}
+            h.free()
+            op.free()
+    return out
 
 
 def batched_leg(S, torch):

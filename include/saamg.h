@@ -64,6 +64,19 @@ typedef enum {
   SAAMG_PREC_FP32_BF16 = 2  /* V-cycle in FP32, coarse operators stored BF16 */
 } saamg_precision;
 
+/* Aggregation of the tentative prolongator (Sec. 3.2, "Prolongation operator").
+ * MIS2: aggregates grown from a distance-2 maximal independent set of the graph of A_l
+ * (hashed priorities; identical on any launch configuration).
+ * CUBES: the paper's own "decoupled" aggregation: aggregates are the cubes of 3 x 3 x 3
+ * lattice nodes (fewer where the domain boundary cuts a cube); the coarse nodes are the
+ * cubes, so every level is again a lattice with ceil(n/3) nodes per axis. */
+typedef enum { SAAMG_AGG_MIS2 = 0, SAAMG_AGG_CUBES = 1 } saamg_aggregation;
+
+/* Coarsest-level solver (Sec. 3.2, "Coarse level solver"): an exact solve by dense LU
+ * with partial pivoting (applied as an explicit inverse), or coarse_sweeps symmetric
+ * Gauss-Seidel steps from zero. */
+typedef enum { SAAMG_COARSE_LU = 0, SAAMG_COARSE_GS = 1 } saamg_coarse_solver;
+
 /* Domain Omega (Sec. 2, Sec. 4.1): an elliptic pipe along z, cross-section
  * ((x-cx)/(a s))^2 + ((y-cy)/(b s))^2 < 1 where s = 1 at the first z-plane of the grid
  * and s = taper at the last, linear in between (taper = 1: straight pipe).  The first
@@ -93,6 +106,9 @@ typedef struct {
   int precision;      /* saamg_precision (FP64) */
   int beta_rule;      /* 0: r'z ratio (Fletcher-Reeves form), 1: Polak-Ribiere (0) */
   int maxit;          /* PCG iteration limit (1000) */
+  int aggregation;    /* saamg_aggregation (MIS-2) */
+  int coarse_solver;  /* saamg_coarse_solver (dense LU) */
+  int coarse_sweeps;  /* Gauss-Seidel steps per coarse solve (3, Sec. 3.2) */
 } saamg_params;
 
 typedef struct {

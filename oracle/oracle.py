@@ -41,6 +41,17 @@ def lib():
         L.orc_node_inside.restype = _i
         L.orc_setup.restype = _p
         L.orc_setup.argtypes = [_p, _i, _d, _d, _i, _i, _i]
+        L.orc_setup_agg.restype = _p
+        L.orc_setup_agg.argtypes = [_p, _i, _d, _d, _i, _i, _i, _i]
+        L.orc_setup_ex.restype = _p
+        L.orc_setup_ex.argtypes = [_p, _i, _d, _d, _i, _i, _i, _i, _i, _i]
+        L.orc_hier_colours.argtypes = [_p, _p]
+        L.orc_hier_colours.restype = _i
+        L.orc_colour.argtypes = [_i, _p, _p, _p, C.c_uint, _p]
+        L.orc_colour.restype = _i
+        L.orc_sgs.argtypes = [_i, _p, _p, _p, _p, _p, _i, _i, _p, _p]
+        L.orc_cube_aggregate.argtypes = [_i, _p, _p, _p, _p, _p, _p]
+        L.orc_cube_aggregate.restype = _i
         L.orc_hier_free.argtypes = [_p]
         for f in ("orc_hier_levels", "orc_hier_status"):
             getattr(L, f).argtypes = [_p]
@@ -135,12 +146,18 @@ class Operator:
 class Hierarchy:
     """SA-AMG hierarchy of Sec. 3.2 built on the scaled operator."""
 
+    AGG_MIS2, AGG_CUBES = 0, 1
+    COARSE_LU, COARSE_GS = 0, 1
+
     def __init__(self, op, cheb_degree=2, cheb_ratio=30.0, cheb_safety=1.1, max_coarse=1000,
-                 max_levels=10, power_iters=10):
+                 max_levels=10, power_iters=10, aggregation=0, coarse_solver=0,
+                 coarse_sweeps=3):
         self.op = op
         L = lib()
-        self._h = L.orc_setup(op._h, int(cheb_degree), float(cheb_ratio), float(cheb_safety),
-                              int(max_coarse), int(max_levels), int(power_iters))
+        self._h = L.orc_setup_ex(op._h, int(cheb_degree), float(cheb_ratio),
+                                 float(cheb_safety), int(max_coarse), int(max_levels),
+                                 int(power_iters), int(aggregation), int(coarse_solver),
+                                 int(coarse_sweeps))
         self.status = L.orc_hier_status(self._h)
         self.levels = L.orc_hier_levels(self._h)
 
@@ -172,6 +189,12 @@ class Hierarchy:
         root = np.empty(n, np.uint8)
         lib().orc_hier_get_agg(self._h, l, _ptr(agg), _ptr(root))
         return agg, root
+
+    def colours(self):
+        """Colour of each row of the coarsest level (Gauss-Seidel coarse solver), or None."""
+        c = np.empty(self.n(self.levels - 1), np.int32)
+        k = lib().orc_hier_colours(self._h, _ptr(c))
+        return (c, k) if k else None
 
     def lam(self, l):
         return lib().orc_hier_lambda(self._h, l)
@@ -232,6 +255,44 @@ def aggregate(rowptr, col, ids, seed, root):
     nagg = lib().orc_aggregate(n, _ptr(rowptr), _ptr(col), _ptr(ids), int(seed) & 0xFFFFFFFF,
                                _ptr(root), _ptr(agg))
     return agg, nagg
+
+
+def cube_aggregate(ids, dims):
+    """Cubes of 3 x 3 x 3 lattice nodes (Sec. 3.2): (agg, root, next_ids, next_dims)."""
+    ids = np.ascontiguousarray(ids, np.uint32)
+    n = len(ids)
+    d = np.ascontiguousarray(dims, np.int32)
+    agg = np.empty(n, np.int32)
+    root = np.empty(n, np.uint8)
+    nxt = np.empty(max(n, 1), np.uint32)
+    nd = np.zeros(3, np.int32)
+    nagg = lib().orc_cube_aggregate(n, _ptr(ids), _ptr(d), _ptr(agg), _ptr(root), _ptr(nxt),
+                                    _ptr(nd))
+    return agg, root, nxt[:nagg].copy(), tuple(int(v) for v in nd)
+
+
+def colour(rowptr, col, ids, seed=0x2545F491):
+    rowptr, col, _ = _csr_arrays(rowptr, col)
+    n = len(rowptr) - 1
+    ids = np.ascontiguousarray(ids, np.uint32)
+    c = np.empty(n, np.int32)
+    k = lib().orc_colour(n, _ptr(rowptr), _ptr(col), _ptr(ids), int(seed) & 0xFFFFFFFF, _ptr(c))
+    return c, k
+
+
+def sgs(rowptr, col, val, colours, ncolours, steps, b):
+    rowptr, col, val = _csr_arrays(rowptr, col, val)
+    n = len(rowptr) - 1
+    invd = np.empty(n)
+    for i in range(n):
+        s, e = rowptr[i], rowptr[i + 1]
+        invd[i] = 1.0 / val[s:e][col[s:e] == i][0]
+    colours = np.ascontiguousarray(colours, np.int32)
+    b = np.ascontiguousarray(b, np.float64)
+    x = np.empty(n)
+    lib().orc_sgs(n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(invd), _ptr(colours),
+                  int(ncolours), int(steps), _ptr(b), _ptr(x))
+    return x
 
 
 def power_lambda(rowptr, col, val, ids, iters=10):

@@ -718,6 +718,114 @@ static void csr_transpose(const csr_t *a, csr_t *t) {
 }
 
 /* ------------------------------------------------------------------------- */
+/* Cube ("decoupled") aggregation (Sec. 3.2)                                  */
+/* ------------------------------------------------------------------------- */
+/* The paper's own coarsening: aggregates are cubes of 3 x 3 x 3 lattice nodes, fewer where
+ * the cube meets the domain boundary.  Node v carries the lattice id i + d0 (j + d1 k) of a
+ * d0 x d1 x d2 lattice; its cube is (i/3, j/3, k/3) on the lattice of ceil(d/3) cubes per
+ * axis.  Every cube that holds a node is one aggregate; aggregates are numbered by
+ * ascending cube index, and the cube index is the coarse node's lattice id.
+ * READING: a cube's nodes form one aggregate even when the domain boundary cuts the cube
+ * into pieces that are not connected inside it.  The root of an aggregate (reported for
+ * inspection only) is its member with the smallest row.  Returns the number of aggregates. */
+int orc_cube_aggregate(int n, const unsigned int *ids, const int dims[3], int *agg,
+                       unsigned char *is_root, unsigned int *next_ids, int next_dims[3]) {
+  long c0 = (dims[0] + 2) / 3, c1 = (dims[1] + 2) / 3, c2 = (dims[2] + 2) / 3;
+  long ncubes = c0 * c1 * c2;
+  if (next_dims) {
+    next_dims[0] = (int)c0;
+    next_dims[1] = (int)c1;
+    next_dims[2] = (int)c2;
+  }
+  long *cube = (long *)malloc((size_t)(n > 0 ? n : 1) * sizeof(long));
+  int *rank = (int *)malloc((size_t)(ncubes > 0 ? ncubes : 1) * sizeof(int));
+  for (long c = 0; c < ncubes; ++c) rank[c] = -1;
+  for (int v = 0; v < n; ++v) {
+    long id = (long)ids[v];
+    long i = id % dims[0], j = (id / dims[0]) % dims[1], k = id / ((long)dims[0] * dims[1]);
+    cube[v] = i / 3 + c0 * (j / 3 + c1 * (k / 3));
+    rank[cube[v]] = 0; /* used */
+  }
+  int nagg = 0;
+  for (long c = 0; c < ncubes; ++c)
+    if (rank[c] == 0) {
+      if (next_ids) next_ids[nagg] = (unsigned int)c;
+      rank[c] = nagg++;
+    }
+  for (int v = 0; v < n; ++v) agg[v] = rank[cube[v]];
+  if (is_root) {
+    int *first = (int *)malloc((size_t)(nagg > 0 ? nagg : 1) * sizeof(int));
+    for (int a = 0; a < nagg; ++a) first[a] = -1;
+    for (int v = 0; v < n; ++v)
+      if (first[agg[v]] < 0) first[agg[v]] = v;
+    for (int v = 0; v < n; ++v) is_root[v] = (unsigned char)(first[agg[v]] == v);
+    free(first);
+  }
+  free(cube);
+  free(rank);
+  return nagg;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Gauss-Seidel coarse solver (Sec. 3.2, "Coarse level solver")               */
+/* ------------------------------------------------------------------------- */
+/* READING: the paper applies three Gauss-Seidel steps on the coarsest level.  A step here is
+ * a symmetric sweep (forward, then backward) in a multicolour order, from x = 0, which keeps
+ * the V-cycle a symmetric operator for CG.  The colouring is the sequence of synchronous
+ * rounds: in round c every uncoloured node whose key exceeds the keys of all its uncoloured
+ * neighbours takes colour c; key(v) = (fmix32(id_v ^ seed), id_v), seed = 0x2545F491.  Rows
+ * of one colour are never adjacent, so their updates within a sweep are independent. */
+int orc_colour(int n, const int *rowptr, const int *col, const unsigned int *ids,
+               unsigned int seed, int *colour) {
+  for (int i = 0; i < n; ++i) colour[i] = -1;
+  int left = n, c = 0;
+  unsigned char *pick = (unsigned char *)malloc((size_t)(n > 0 ? n : 1));
+  while (left > 0) {
+    for (int i = 0; i < n; ++i) {
+      pick[i] = 0;
+      if (colour[i] >= 0) continue;
+      uint64_t ki = ((uint64_t)orc_fmix32(ids[i] ^ seed) << 32) | ids[i];
+      int best = 1;
+      for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        int j = col[p];
+        if (j == i || colour[j] >= 0) continue;
+        uint64_t kj = ((uint64_t)orc_fmix32(ids[j] ^ seed) << 32) | ids[j];
+        if (kj > ki) best = 0;
+      }
+      pick[i] = (unsigned char)best;
+    }
+    for (int i = 0; i < n; ++i)
+      if (pick[i]) {
+        colour[i] = c;
+        --left;
+      }
+    ++c;
+  }
+  free(pick);
+  return c;
+}
+
+/* `steps` symmetric Gauss-Seidel steps from x = 0: forward over colours 0..C-1, then
+ * backward over C-1..0; x_i = (b_i - sum_{j != i} a_ij x_j) / a_ii with the sum in the
+ * row's column order, the division as a multiply by invd_i = 1 / a_ii. */
+void orc_sgs(int n, const int *rowptr, const int *col, const double *val, const double *invd,
+             const int *colour, int ncolours, int steps, const double *b, double *x) {
+  for (int i = 0; i < n; ++i) x[i] = 0.0;
+  for (int st = 0; st < steps; ++st)
+    for (int half = 0; half < 2; ++half)
+      for (int cc = 0; cc < ncolours; ++cc) {
+        int c = half == 0 ? cc : ncolours - 1 - cc;
+        for (int i = 0; i < n; ++i) {
+          if (colour[i] != c) continue;
+          double acc = b[i];
+          for (int p = rowptr[i]; p < rowptr[i + 1]; ++p)
+            if (col[p] != i) acc -= val[p] * x[col[p]];
+          x[i] = acc * invd[i];
+        }
+      }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Hierarchy (Sec. 3.2)                                                       */
 /* ------------------------------------------------------------------------- */
 #define ORC_MAX_LEVELS 32
@@ -727,6 +835,7 @@ typedef struct {
   csr_t A;
   double *invd;
   unsigned int *ids;
+  int dims[3]; /* lattice of the ids (cube aggregation) */
   int *agg;
   unsigned char *root;
   double lambda, omega;
@@ -741,6 +850,8 @@ struct orc_hier {
   double ratio, safety;
   level_t lev[ORC_MAX_LEVELS];
   dense_lu_t coarse;
+  int coarse_solver, coarse_sweeps; /* ORC_COARSE_*; Gauss-Seidel steps */
+  int *colour, ncolours;            /* colouring of the coarsest level (Gauss-Seidel) */
   double **wb, **wx, **wr; /* per-level work vectors */
 };
 
@@ -813,7 +924,23 @@ static void smoothed_prolongator(const csr_t *a, const double *invd, const int *
 orc_hier *orc_setup(const orc_op *op, int cheb_degree, double cheb_ratio,
                     double cheb_safety, int max_coarse, int max_levels,
                     int power_iters) {
+  return orc_setup_agg(op, cheb_degree, cheb_ratio, cheb_safety, max_coarse, max_levels,
+                       power_iters, ORC_AGG_MIS2);
+}
+
+orc_hier *orc_setup_agg(const orc_op *op, int cheb_degree, double cheb_ratio,
+                        double cheb_safety, int max_coarse, int max_levels,
+                        int power_iters, int aggregation) {
+  return orc_setup_ex(op, cheb_degree, cheb_ratio, cheb_safety, max_coarse, max_levels,
+                      power_iters, aggregation, ORC_COARSE_LU, 3);
+}
+
+orc_hier *orc_setup_ex(const orc_op *op, int cheb_degree, double cheb_ratio,
+                       double cheb_safety, int max_coarse, int max_levels, int power_iters,
+                       int aggregation, int coarse_solver, int coarse_sweeps) {
   orc_hier *h = (orc_hier *)calloc(1, sizeof(orc_hier));
+  h->coarse_solver = coarse_solver;
+  h->coarse_sweeps = coarse_sweeps;
   h->op = op;
   h->degree = cheb_degree;
   h->ratio = cheb_ratio;
@@ -825,6 +952,9 @@ orc_hier *orc_setup(const orc_op *op, int cheb_degree, double cheb_ratio,
   csr_copy(&op->Ahat, &L0->A);
   L0->ids = (unsigned int *)malloc((size_t)(op->n > 0 ? op->n : 1) * sizeof(unsigned int));
   for (int i = 0; i < op->n; ++i) L0->ids[i] = (unsigned int)op->node_of_row[i];
+  L0->dims[0] = op->nx;
+  L0->dims[1] = op->ny;
+  L0->dims[2] = op->nz;
 
   int l = 0;
   for (;;) {
@@ -837,14 +967,26 @@ orc_hier *orc_setup(const orc_op *op, int cheb_degree, double cheb_ratio,
     unsigned int seed = 0x9E3779B9u * (unsigned int)(l + 1);
     lv->root = (unsigned char *)malloc((size_t)(n > 0 ? n : 1));
     lv->agg = (int *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int));
-    orc_mis2(n, lv->A.rowptr, lv->A.col, lv->ids, seed, lv->root);
-    int nagg = orc_aggregate(n, lv->A.rowptr, lv->A.col, lv->ids, seed, lv->root, lv->agg);
+    unsigned int *next_ids = NULL;
+    int next_dims[3] = {0, 0, 0};
+    int nagg;
+    if (aggregation == ORC_AGG_CUBES) {
+      next_ids = (unsigned int *)malloc((size_t)(n > 0 ? n : 1) * sizeof(unsigned int));
+      nagg = orc_cube_aggregate(n, lv->ids, lv->dims, lv->agg, lv->root, next_ids, next_dims);
+    } else {
+      orc_mis2(n, lv->A.rowptr, lv->A.col, lv->ids, seed, lv->root);
+      nagg = orc_aggregate(n, lv->A.rowptr, lv->A.col, lv->ids, seed, lv->root, lv->agg);
+    }
     if (nagg < 0) {
+      free(next_ids);
       h->status = -2;
       break;
     }
     /* READING: stop when coarsening stalls (more than 90 % of the nodes remain). */
-    if (10L * nagg > 9L * n) break;
+    if (10L * nagg > 9L * n) {
+      free(next_ids);
+      break;
+    }
     lv->lambda = orc_power_lambda(n, lv->A.rowptr, lv->A.col, lv->A.val, lv->ids, power_iters);
     /* READING: omega = 4 / (3 lambda), the usual SA damping of Vanek, Mandel, Brezina. */
     lv->omega = 4.0 / (3.0 * lv->lambda);
@@ -855,15 +997,24 @@ orc_hier *orc_setup(const orc_op *op, int cheb_degree, double cheb_ratio,
     level_t *nx = &h->lev[l + 1];
     csr_matmul(&lv->R, &ap, &nx->A); /* A_{l+1} = R A_l P */
     csr_free(&ap);
-    nx->ids = (unsigned int *)malloc((size_t)(nagg > 0 ? nagg : 1) * sizeof(unsigned int));
-    for (int J = 0; J < nagg; ++J) nx->ids[J] = (unsigned int)J;
+    if (next_ids) {
+      /* cube aggregation: the coarse nodes are the cubes, ids on the cube lattice */
+      nx->ids = next_ids;
+      memcpy(nx->dims, next_dims, sizeof(next_dims));
+    } else {
+      nx->ids = (unsigned int *)malloc((size_t)(nagg > 0 ? nagg : 1) * sizeof(unsigned int));
+      for (int J = 0; J < nagg; ++J) nx->ids[J] = (unsigned int)J;
+    }
     ++l;
   }
   h->nlev = l + 1;
   /* The coarsest level needs a spectral bound only if it is smoothed; it is not. */
   level_t *lc = &h->lev[l];
   int nc = lc->A.n;
-  if (h->status == 0) {
+  if (h->status == 0 && h->coarse_solver == ORC_COARSE_GS) {
+    h->colour = (int *)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(int));
+    h->ncolours = orc_colour(nc, lc->A.rowptr, lc->A.col, lc->ids, 0x2545F491u, h->colour);
+  } else if (h->status == 0) {
     if (nc > ORC_MAX_DENSE) {
       h->status = -3;
     } else {
@@ -900,6 +1051,7 @@ void orc_hier_free(orc_hier *h) {
     free(lv->root);
   }
   if (h->coarse.lu) dense_lu_free(&h->coarse);
+  free(h->colour);
   for (int q = 0; q < h->nlev; ++q) {
     free(h->wb[q]);
     free(h->wx[q]);
@@ -912,6 +1064,11 @@ void orc_hier_free(orc_hier *h) {
 }
 
 int orc_hier_levels(const orc_hier *h) { return h->nlev; }
+int orc_hier_colours(const orc_hier *h, int *colour) {
+  if (!h->colour) return 0;
+  if (colour) memcpy(colour, h->colour, (size_t)h->lev[h->nlev - 1].A.n * sizeof(int));
+  return h->ncolours;
+}
 int orc_hier_status(const orc_hier *h) { return h->status; }
 int orc_hier_n(const orc_hier *h, int l) { return h->lev[l].A.n; }
 long orc_hier_nnz(const orc_hier *h, int l) { return h->lev[l].A.nnz; }
@@ -946,8 +1103,12 @@ void orc_hier_get_agg(const orc_hier *h, int l, int *agg, unsigned char *is_root
 static void mg_solve(const orc_hier *h, int l, const double *b, double *x) {
   const level_t *lv = &h->lev[l];
   int n = lv->A.n;
-  if (l == h->nlev - 1) { /* DirectSolve */
-    dense_lu_solve(&h->coarse, b, x);
+  if (l == h->nlev - 1) { /* DirectSolve, or Gauss-Seidel steps */
+    if (h->coarse_solver == ORC_COARSE_GS)
+      orc_sgs(n, lv->A.rowptr, lv->A.col, lv->A.val, lv->invd, h->colour, h->ncolours,
+              h->coarse_sweeps, b, x);
+    else
+      dense_lu_solve(&h->coarse, b, x);
     return;
   }
   /* presmoothing from x = 0 */

@@ -60,6 +60,18 @@ int orc_node_inside(const orc_op *op, int i, int j, int k);
 orc_hier *orc_setup(const orc_op *op, int cheb_degree, double cheb_ratio,
                     double cheb_safety, int max_coarse, int max_levels,
                     int power_iters);
+/* Aggregation kinds: MIS-2 seeded (default) or cubes of 3^3 lattice nodes (Sec. 3.2). */
+enum { ORC_AGG_MIS2 = 0, ORC_AGG_CUBES = 1 };
+orc_hier *orc_setup_agg(const orc_op *op, int cheb_degree, double cheb_ratio,
+                        double cheb_safety, int max_coarse, int max_levels,
+                        int power_iters, int aggregation);
+/* Coarsest-level solver: dense LU (default) or symmetric Gauss-Seidel steps (Sec. 3.2). */
+enum { ORC_COARSE_LU = 0, ORC_COARSE_GS = 1 };
+orc_hier *orc_setup_ex(const orc_op *op, int cheb_degree, double cheb_ratio,
+                       double cheb_safety, int max_coarse, int max_levels, int power_iters,
+                       int aggregation, int coarse_solver, int coarse_sweeps);
+/* Colouring of the coarsest level (Gauss-Seidel); returns the number of colours or 0. */
+int orc_hier_colours(const orc_hier *h, int *colour);
 void orc_hier_free(orc_hier *h);
 int orc_hier_levels(const orc_hier *h);
 int orc_hier_n(const orc_hier *h, int l);
@@ -80,6 +92,17 @@ void orc_mis2(int n, const int *rowptr, const int *col, const unsigned int *ids,
               unsigned int seed, unsigned char *is_root);
 int orc_aggregate(int n, const int *rowptr, const int *col, const unsigned int *ids,
                   unsigned int seed, const unsigned char *is_root, int *agg);
+/* Cubes of 3 x 3 x 3 lattice nodes (ids on a dims[0] x dims[1] x dims[2] lattice); fills
+ * agg, is_root (smallest row of each aggregate), next_ids (cube index of each aggregate)
+ * and next_dims (the cube lattice); any output may be NULL except agg. */
+int orc_cube_aggregate(int n, const unsigned int *ids, const int dims[3], int *agg,
+                       unsigned char *is_root, unsigned int *next_ids, int next_dims[3]);
+/* Multicolouring by synchronous rounds of local key maxima (colour = round). */
+int orc_colour(int n, const int *rowptr, const int *col, const unsigned int *ids,
+               unsigned int seed, int *colour);
+/* `steps` symmetric multicolour Gauss-Seidel steps from x = 0. */
+void orc_sgs(int n, const int *rowptr, const int *col, const double *val, const double *invd,
+             const int *colour, int ncolours, int steps, const double *b, double *x);
 double orc_power_lambda(int n, const int *rowptr, const int *col, const double *val,
                         const unsigned int *ids, int iters);
 void orc_cheb_smooth(int n, const int *rowptr, const int *col, const double *val,

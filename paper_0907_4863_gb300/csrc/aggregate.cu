@@ -357,6 +357,36 @@ __global__ void __launch_bounds__(256) agg0_phase2_k(GridGraph g, const unsigned
 
 #undef SAAMG_CHUNK_LOOP
 
+// --- cubes of 3 x 3 x 3 lattice nodes ---------------------------------------------
+__global__ void cube_mark_k(int n, const unsigned* __restrict__ ids, unsigned d0, unsigned d1,
+                            unsigned c0, unsigned c1, int* __restrict__ cube_of,
+                            unsigned char* __restrict__ used, int* __restrict__ first) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const unsigned id = ids[v];
+  const unsigned i = id % d0, j = (id / d0) % d1, k = id / d0 / d1;
+  const int c = (int)(i / 3 + c0 * (j / 3 + c1 * (k / 3)));
+  cube_of[v] = c;
+  used[c] = 1;
+  atomicMin(&first[c], v);  // the minimum is the same whatever the order of the updates
+}
+
+__global__ void cube_assign_k(int n, const int* __restrict__ cube_of, const int* __restrict__ rank,
+                              const int* __restrict__ first, int* __restrict__ agg,
+                              unsigned char* __restrict__ root) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const int c = cube_of[v];
+  agg[v] = rank[c];
+  root[v] = first[c] == v;
+}
+
+__global__ void cube_ids_k(int ncubes, const unsigned char* __restrict__ used,
+                           const int* __restrict__ rank, unsigned* __restrict__ next_ids) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < ncubes && used[c]) next_ids[rank[c]] = (unsigned)c;
+}
+
 template <int G>
 int rounds(int n, const int* rowptr, const int* col, const unsigned* ids, uint32_t seed,
            unsigned char* state, unsigned long long* m1, unsigned char* o1, int* counter,
@@ -467,6 +497,38 @@ int mis2_aggregate_grid(int n, const GridGraph& g, const unsigned* ids, uint32_t
   int err = 0;
   d2h_sync(&err, w.counter, sizeof(int), s);
   if (err) fail(SAAMG_NUMERICAL, "aggregation left a node without an aggregate");
+  return (int)nagg;
+}
+
+int cube_aggregate(int n, const unsigned* ids, const int dims[3], int* agg, unsigned char* root,
+                   Buf<unsigned>& next_ids, int next_dims[3], cudaStream_t s) {
+  const long long c0 = (dims[0] + 2) / 3, c1 = (dims[1] + 2) / 3, c2 = (dims[2] + 2) / 3;
+  next_dims[0] = (int)c0;
+  next_dims[1] = (int)c1;
+  next_dims[2] = (int)c2;
+  if (n <= 0) return 0;
+  if (!ids) fail(SAAMG_EINVAL, "cube aggregation needs lattice ids");
+  const long long ncubes = c0 * c1 * c2;
+  if (ncubes > INT_MAX / 2) fail(SAAMG_EINVAL, "cube lattice too large");
+  Buf<int> cube_of, first, rank;
+  Buf<unsigned char> used;
+  cube_of.alloc(n, s);
+  first.alloc(ncubes, s);
+  rank.alloc(ncubes, s);
+  used.alloc(ncubes, s);
+  SAAMG_CUDA(cudaMemsetAsync(used.p, 0, (size_t)ncubes, s));
+  fill_int(first.p, INT_MAX, (size_t)ncubes, s);
+  cube_mark_k<<<(n + 255) / 256, 256, 0, s>>>(n, ids, (unsigned)dims[0], (unsigned)dims[1],
+                                              (unsigned)c0, (unsigned)c1, cube_of.p, used.p,
+                                              first.p);
+  SAAMG_LAUNCH();
+  const long long nagg = exclusive_scan_u8(used.p, rank.p, (int)ncubes, s);
+  cube_assign_k<<<(n + 255) / 256, 256, 0, s>>>(n, cube_of.p, rank.p, first.p, agg, root);
+  SAAMG_LAUNCH();
+  next_ids.alloc(nagg, s);
+  cube_ids_k<<<(int)((ncubes + 255) / 256), 256, 0, s>>>((int)ncubes, used.p, rank.p,
+                                                          next_ids.p);
+  SAAMG_LAUNCH();
   return (int)nagg;
 }
 

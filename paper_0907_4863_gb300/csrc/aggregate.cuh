@@ -48,6 +48,14 @@ struct GridGraph {
 int mis2_aggregate_grid(int n, const GridGraph& g, const unsigned* ids, uint32_t seed,
                         unsigned char* root, int* agg, const AggScratch& w, cudaStream_t s);
 
+// The paper's own aggregation (Sec. 3.2): the cubes of 3 x 3 x 3 lattice nodes.  Node v has
+// the lattice id ids[v] = i + d0 (j + d1 k) on the dims lattice; every cube holding a node
+// is an aggregate, numbered by ascending cube index; root = the aggregate's smallest row.
+// next_ids (allocated here) receives each aggregate's cube index and next_dims the cube
+// lattice (ceil(d / 3) per axis).  Returns the number of aggregates.
+int cube_aggregate(int n, const unsigned* ids, const int dims[3], int* agg, unsigned char* root,
+                   Buf<unsigned>& next_ids, int next_dims[3], cudaStream_t s);
+
 // The same aggregation with every temporary in caller-provided scratch (w and `tiles`,
 // scan_u8_tiles_needed(n) entries); allocates nothing.
 int mis2_aggregate_into(int n, const int* rowptr, const int* col, long long nnz,

@@ -157,6 +157,8 @@ struct Level {
   Buf<float> invd32;
   Buf<int> agg;
   Buf<unsigned char> root;
+  Buf<unsigned> ids;            // lattice ids of the nodes (cube aggregation, levels >= 1)
+  int dims[3] = {0, 0, 0};      // lattice of the ids (cube aggregation)
   DevCsr P, R;                  // to the next level
   double lambda = 0, omega = 0;
   ChebCoef cheb;
@@ -237,6 +239,16 @@ static saamg_status guard(const char* where, F&& f) {
 
 static bool mixed(const saamg_hierarchy* h) { return h->prm.precision != SAAMG_PREC_FP64; }
 
+static void check_params_ext(const saamg_params& p) {
+  if (p.aggregation != SAAMG_AGG_MIS2 && p.aggregation != SAAMG_AGG_CUBES)
+    fail(SAAMG_EINVAL, "unknown aggregation");
+  if (p.coarse_solver != SAAMG_COARSE_LU && p.coarse_solver != SAAMG_COARSE_GS)
+    fail(SAAMG_EINVAL, "unknown coarse solver");
+  if (p.coarse_sweeps < 1 || p.coarse_sweeps > 64) fail(SAAMG_EINVAL, "coarse_sweeps must be in 1..64");
+  if (p.coarse_solver == SAAMG_COARSE_GS)
+    fail(SAAMG_UNIMPLEMENTED, "the Gauss-Seidel coarse solver is not available in this build");
+}
+
 // Matrix of level l (level 0 = the operator's CSR)
 static const DevCsr& level_matrix(const saamg_hierarchy* h, int l) {
   return l == 0 ? h->op->d.A : h->lev[l]->A;
@@ -310,8 +322,17 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
   for (;;) {
     Level& L = *h->lev[l];
     const DevCsr& A = level_matrix(h, l);
-    const unsigned* ids = (l == 0) ? od.ids.p : nullptr;
+    // node ids: level 0 the box index; coarse levels the cube lattice index (cube
+    // aggregation) or the row itself (MIS-2)
+    const unsigned* ids = (l == 0) ? od.ids.p : L.ids.p;
+    if (l == 0) {
+      L.dims[0] = od.g.nx;
+      L.dims[1] = od.g.ny;
+      L.dims[2] = od.g.nz;
+    }
     int nagg = 0;
+    Buf<unsigned> next_ids;
+    int next_dims[3] = {0, 0, 0};
     if (prev) {
       // reuse: the previous hierarchy decides the levels and the aggregates
       if (l + 1 >= (int)prev->lev.size()) break;
@@ -322,6 +343,13 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
       SAAMG_CUDA(cudaMemcpyAsync(L.root.p, PL.root.p, L.n, cudaMemcpyDeviceToDevice, s));
       SAAMG_CUDA(cudaMemcpyAsync(L.agg.p, PL.agg.p, sizeof(int) * L.n, cudaMemcpyDeviceToDevice, s));
       nagg = prev->lev[l + 1]->n;
+      const Level& PN = *prev->lev[l + 1];
+      if (PN.ids.p) {
+        next_ids.alloc(nagg, s);
+        SAAMG_CUDA(cudaMemcpyAsync(next_ids.p, PN.ids.p, sizeof(unsigned) * nagg,
+                                   cudaMemcpyDeviceToDevice, s));
+        std::memcpy(next_dims, PN.dims, sizeof(next_dims));
+      }
       pt.mark("L" + std::to_string(l) + ".reuse");
     } else {
       if (L.n <= prm.max_coarse || l == prm.max_levels - 1 || l == SAAMG_MAX_LEVELS - 1) break;
@@ -329,7 +357,9 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
       L.root.alloc(L.n, s);
       L.agg.alloc(L.n, s);
       pt.mark("L" + std::to_string(l) + ".pre");
-      if (l == 0) {
+      if (prm.aggregation == SAAMG_AGG_CUBES) {
+        nagg = cube_aggregate(L.n, ids, L.dims, L.agg.p, L.root.p, next_ids, next_dims, s);
+      } else if (l == 0) {
         // level 0: the graph of the 7-point star, walked on the line structure
         GridGraph gg{od.lines.p, od.nbr.p, od.chunks.p, od.nchunks, od.nbmask.p,
                      (unsigned)od.g.nx, (unsigned)od.g.nx * (unsigned)od.g.ny};
@@ -338,7 +368,7 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
         nagg = mis2_aggregate(L.n, A.rowptr.p, A.col.p, A.nnz, ids, seed, L.root.p, L.agg.p,
                               agg_scratch.view(), s);
       }
-      pt.mark("L" + std::to_string(l) + ".mis2agg");
+      pt.mark("L" + std::to_string(l) + ".agg");
       if (10LL * nagg > 9LL * L.n) {  // coarsening stalled
         L.root.release();
         L.agg.release();
@@ -363,6 +393,8 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
     pt.mark("L" + std::to_string(l) + ".RAP");
     N->n = N->A.n;
     N->nnz = N->A.nnz;
+    N->ids = std::move(next_ids);
+    std::memcpy(N->dims, next_dims, sizeof(next_dims));
     N->avg = N->n ? (double)N->nnz / N->n : 0.0;
     N->invd.alloc(N->n, s);
     N->invd32.alloc(N->n, s);
@@ -411,7 +443,7 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
   long long bytes = 0;
   for (auto& L : h->lev) {
     bytes += L->A.bytes() + L->P.bytes() + L->R.bytes() + L->invd.bytes() + L->invd32.bytes() +
-             L->agg.bytes() + L->root.bytes() + L->x0.bytes() + L->x1.bytes() + L->b.bytes() +
+             L->agg.bytes() + L->root.bytes() + L->ids.bytes() + L->x0.bytes() + L->x1.bytes() + L->b.bytes() +
              L->d.bytes() + L->r.bytes() + L->fx0.bytes() + L->fx1.bytes() + L->fb.bytes() +
              L->fd.bytes() + L->fr.bytes() + L->As.bytes() + L->P32.bytes() + L->R32.bytes();
   }
@@ -497,6 +529,13 @@ template <>
 void transfer<float>(saamg_hierarchy* h, int l, bool restrict_, const float* x, float* y,
                      cudaStream_t s) {
   Level& L = *h->lev[l];
+  if (l == 0 && !restrict_) {
+    // level 0, FP32: the prolongation from the stencil and the aggregates (about 12 bytes per
+    // row instead of the 39 of the CSR matrix); FP64 keeps the CSR, which needs fewer FP64
+    // operations per row
+    stencil_prolong<float>(h->op->d.template view<float>(), L.agg.p, (float)L.omega, x, y, s);
+    return;
+  }
   const DevCsr& M = restrict_ ? L.R : L.P;
   const float* v = restrict_ ? L.R32.p : L.P32.p;
   csr_apply<float, float>(restrict_ ? CSR_SPMV : CSR_ADD, M.n, M.rowptr.p, M.col.p, v,
@@ -559,14 +598,29 @@ static void vcycle_level(saamg_hierarchy* h, int l, const T* b, T* out, cudaStre
 }
 
 // z = M r on level 0, FP64 in and out (FP32 inside in mixed mode)
+// r32_current: the FP32 copy h->r32 of r is already up to date (written by the update)
 static void apply_preconditioner(saamg_hierarchy* h, const double* r, double* z, float* z32,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, bool r32_current = false) {
   const int n = h->op->d.n;
   if (!mixed(h)) {
     vcycle_level<double>(h, 0, r, z, s);
   } else {
-    to_float(r, h->r32.p, n, s);
+    if (!r32_current) to_float(r, h->r32.p, n, s);
     vcycle_level<float>(h, 0, h->r32.p, z32, s);
+  }
+}
+
+// r'z (and z'q for the Polak-Ribiere rule) of the new preconditioned residual
+static void rz_partials(saamg_hierarchy* h, const double* r, const double* z, const double* q,
+                        cudaStream_t s) {
+  const int n = h->op->d.n;
+  const bool pr = h->prm.beta_rule == 1;
+  if (mixed(h)) {
+    if (pr) dot2_partials<float>(n, r, h->z32.p, q, h->part0.p, h->part2.p, s);
+    else dot_partials<double, float>(n, r, h->z32.p, h->part0.p, s);
+  } else {
+    if (pr) dot2_partials<double>(n, r, z, q, h->part0.p, h->part2.p, s);
+    else dot_partials<double, double>(n, r, z, h->part0.p, s);
   }
 }
 
@@ -635,7 +689,7 @@ static int pcg_impl(saamg_hierarchy* h, double rtol, cudaStream_t s, saamg_solve
     for (int it = 1; it <= h->prm.maxit; ++it) {
       stencil_apply<double>(S, ST_SPMV_DOT, p, q, nullptr, nullptr, 0.0, 0.0, h->part0.p, s);
       pcg_alpha(h->part0.p, ctl, s);
-      pcg_update(n, x, r, p, q, ctl, h->part1.p, s);
+      pcg_update(n, x, r, p, q, ctl, h->part1.p, s, mx ? h->r32.p : nullptr);
       pcg_check(h->part1.p, ctl, s);
       d2h_sync(hc, ctl, sizeof(PcgCtl), s);
       info->iters = hc->iters;
@@ -648,18 +702,11 @@ static int pcg_impl(saamg_hierarchy* h, double rtol, cudaStream_t s, saamg_solve
         info->converged = 1;
         break;
       }
-      apply_preconditioner(h, r, z, h->z32.p, s);
-      if (mx) {
-        dot_partials<double, float>(n, r, h->z32.p, h->part0.p, s);
-        if (h->prm.beta_rule == 1) dot_partials<float, double>(n, h->z32.p, q, h->part2.p, s);
-        pcg_beta(h->part0.p, h->prm.beta_rule == 1 ? h->part2.p : nullptr, h->prm.beta_rule, ctl, s);
-        pcg_direction<float>(n, h->z32.p, p, ctl, s);
-      } else {
-        dot_partials<double, double>(n, r, z, h->part0.p, s);
-        if (h->prm.beta_rule == 1) dot_partials<double, double>(n, z, q, h->part2.p, s);
-        pcg_beta(h->part0.p, h->prm.beta_rule == 1 ? h->part2.p : nullptr, h->prm.beta_rule, ctl, s);
-        pcg_direction<double>(n, z, p, ctl, s);
-      }
+      apply_preconditioner(h, r, z, h->z32.p, s, true);
+      rz_partials(h, r, z, q, s);
+      pcg_beta(h->part0.p, h->prm.beta_rule == 1 ? h->part2.p : nullptr, h->prm.beta_rule, ctl, s);
+      if (mx) pcg_direction<float>(n, h->z32.p, p, ctl, s);
+      else pcg_direction<double>(n, z, p, ctl, s);
     }
   }
   d2h_sync(hc, ctl, sizeof(PcgCtl), s);
@@ -692,21 +739,14 @@ static void pcg_pass(saamg_hierarchy* h, cudaGraphConditionalHandle cond, cudaSt
   double* p = h->p.p;
   double* q = h->q.p;
   PcgCtl* ctl = h->ctl.p;
-  apply_preconditioner(h, r, h->z.p, h->z32.p, s);
-  if (mixed(h)) {
-    dot_partials<double, float>(n, r, h->z32.p, h->part0.p, s);
-    if (rule == 1) dot_partials<float, double>(n, h->z32.p, q, h->part2.p, s);
-    pcg_graph_beta(h->part0.p, rule == 1 ? h->part2.p : nullptr, rule, ctl, s);
-    pcg_direction<float>(n, h->z32.p, p, ctl, s);
-  } else {
-    dot_partials<double, double>(n, r, h->z.p, h->part0.p, s);
-    if (rule == 1) dot_partials<double, double>(n, h->z.p, q, h->part2.p, s);
-    pcg_graph_beta(h->part0.p, rule == 1 ? h->part2.p : nullptr, rule, ctl, s);
-    pcg_direction<double>(n, h->z.p, p, ctl, s);
-  }
+  apply_preconditioner(h, r, h->z.p, h->z32.p, s, true);
+  rz_partials(h, r, h->z.p, q, s);
+  pcg_graph_beta(h->part0.p, rule == 1 ? h->part2.p : nullptr, rule, ctl, s);
+  if (mixed(h)) pcg_direction<float>(n, h->z32.p, p, ctl, s);
+  else pcg_direction<double>(n, h->z.p, p, ctl, s);
   stencil_apply<double>(S, ST_SPMV_DOT, p, q, nullptr, nullptr, 0.0, 0.0, h->part0.p, s);
   pcg_alpha(h->part0.p, ctl, s);
-  pcg_update(n, h->xhat.p, r, p, q, ctl, h->part1.p, s);
+  pcg_update(n, h->xhat.p, r, p, q, ctl, h->part1.p, s, mixed(h) ? h->r32.p : nullptr);
   pcg_graph_check(h->part1.p, ctl, cond, h->prm.maxit, s);
 }
 
@@ -738,6 +778,7 @@ static void build_solve_graph(saamg_hierarchy* h) {
     capturing = true;
     dot_partials<double, double>(n, h->bhat.p, h->bhat.p, h->part2.p, s);
     stencil_apply<double>(S, ST_RESID, h->xhat.p, h->r.p, h->bhat.p, nullptr, 0.0, 0.0, nullptr, s);
+    if (mixed(h)) to_float(h->r.p, h->r32.p, n, s);  // the first pass's V-cycle input
     dot_partials<double, double>(n, h->r.p, h->r.p, h->part1.p, s);
     SAAMG_CUDA(cudaMemsetAsync(h->p.p, 0, sizeof(double) * n, s));
     pcg_graph_init(h->part2.p, h->part1.p, h->ctl.p, cond, h->prm.maxit, h->xhat.p, n, s);
@@ -861,6 +902,9 @@ saamg_status saamg_params_default(saamg_params* p) {
   p->precision = SAAMG_PREC_FP64;
   p->beta_rule = 0;
   p->maxit = 1000;
+  p->aggregation = SAAMG_AGG_MIS2;
+  p->coarse_solver = SAAMG_COARSE_LU;
+  p->coarse_sweeps = 3;
   return SAAMG_OK;
 }
 
@@ -973,6 +1017,7 @@ saamg_status saamg_setup(const saamg_operator* op, const saamg_params* params, v
     if (prm.precision < SAAMG_PREC_FP64 || prm.precision > SAAMG_PREC_FP32_BF16)
       fail(SAAMG_EINVAL, "unknown precision");
     if (prm.beta_rule != 0 && prm.beta_rule != 1) fail(SAAMG_EINVAL, "beta_rule must be 0 or 1");
+    check_params_ext(prm);
     auto h = std::make_unique<saamg_hierarchy>();
     setup_impl(op, prm, (cudaStream_t)stream, h.get());
     SAAMG_CUDA(cudaMallocHost(&h->result, sizeof(PcgCtl)));
@@ -991,9 +1036,11 @@ saamg_status saamg_setup_reuse(const saamg_operator* op, const saamg_hierarchy* 
       fail(SAAMG_EINVAL, "the operator's pattern differs from the one the hierarchy was built on");
     saamg_params prm = prev->prm;
     if (params) prm = *params;
+    prm.aggregation = prev->prm.aggregation;  // the aggregates come from `prev`
     if (prm.cheb_degree < 1 || prm.cheb_degree > 16) fail(SAAMG_EINVAL, "cheb_degree must be in 1..16");
     if (prm.precision < SAAMG_PREC_FP64 || prm.precision > SAAMG_PREC_FP32_BF16)
       fail(SAAMG_EINVAL, "unknown precision");
+    check_params_ext(prm);
     auto h = std::make_unique<saamg_hierarchy>();
     setup_impl(op, prm, s, h.get(), prev);
     SAAMG_CUDA(cudaMallocHost(&h->result, sizeof(PcgCtl)));

@@ -63,10 +63,16 @@ enum StencilMode {
   ST_CHEB = 3,      // r = b - A x; d = c1 d + c2 D^-1 r; y = x + d
   ST_CHEB0 = 4,     // d = c2 D^-1 b; y = d   (Chebyshev step 0 from x = 0)
   ST_DINV_DOT = 5,  // y = s D^-1 A x, partials of y.y (power iteration; s = *xscale or 1)
-  ST_CHEB1 = 6      // ST_CHEB with c1 = 0 (first step from a nonzero x): d is not read
+  ST_CHEB1 = 6,     // ST_CHEB with c1 = 0 (first step from a nonzero x): d is not read
+  ST_PROLONG = 7    // y += P v with P = (I - omega D^-1 A) T, T from the aggregates
 };
 template <class T>
 void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* b, T* d, T c1,
                    T c2, double* partials, cudaStream_t s, const double* xscale = nullptr);
+// Level-0 prolongation without the matrix P (Sec. 3.2: P = (I - omega D^-1 A) T):
+// y_i += v_agg(i) - omega invd_i sum_j a_ij v_agg(j), agg = level-0 aggregate of each row
+template <class T>
+void stencil_prolong(const StencilDev<T>& S, const int* agg, T omega, const T* v, T* y,
+                     cudaStream_t s);
 
 }  // namespace saamg

@@ -35,14 +35,57 @@ __device__ __forceinline__ double sum_fixed(const double* part) {
   return r;
 }
 
+// Loads of four grid strides are issued before their (in-order) multiply-adds: the sum is
+// the same sequence of operations as the plain strided loop, with more bytes in flight.
 template <class TA, class TB>
 __global__ void dot_k(int n, const TA* __restrict__ a, const TB* __restrict__ b,
                       double* __restrict__ part) {
   double acc = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    acc += (double)a[i] * (double)b[i];
+  const int st = gridDim.x * blockDim.x;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * st < n; i += 4 * st) {
+    const double a0 = (double)a[i], a1 = (double)a[i + st], a2 = (double)a[i + 2 * st],
+                 a3 = (double)a[i + 3 * st];
+    const double b0 = (double)b[i], b1 = (double)b[i + st], b2 = (double)b[i + 2 * st],
+                 b3 = (double)b[i + 3 * st];
+    acc += a0 * b0;
+    acc += a1 * b1;
+    acc += a2 * b2;
+    acc += a3 * b3;
+  }
+  for (; i < n; i += st) acc += (double)a[i] * (double)b[i];
   double t = block_sum(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// r'z and z'q in one sweep; the same per-thread order and block tree as two dot_k calls
+template <class TZ>
+__global__ void dot2_k(int n, const double* __restrict__ r, const TZ* __restrict__ z,
+                       const double* __restrict__ q, double* __restrict__ part_rz,
+                       double* __restrict__ part_zq) {
+  double a1 = 0.0, a2 = 0.0;
+  const int st = gridDim.x * blockDim.x;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + st < n; i += 2 * st) {
+    const double z0 = (double)z[i], z1 = (double)z[i + st];
+    const double r0 = r[i], r1 = r[i + st], q0 = q[i], q1 = q[i + st];
+    a1 += r0 * z0;
+    a2 += z0 * q0;
+    a1 += r1 * z1;
+    a2 += z1 * q1;
+  }
+  for (; i < n; i += st) {
+    const double zi = (double)z[i];
+    a1 += r[i] * zi;
+    a2 += zi * q[i];
+  }
+  const double t1 = block_sum(a1);
+  __syncthreads();  // block_sum's shared array is reused
+  const double t2 = block_sum(a2);
+  if (threadIdx.x == 0) {
+    part_rz[blockIdx.x] = t1;
+    part_zq[blockIdx.x] = t2;
+  }
 }
 
 __global__ void alpha_k(const double* __restrict__ part, PcgCtl* ctl) {
@@ -58,15 +101,18 @@ __global__ void alpha_k(const double* __restrict__ part, PcgCtl* ctl) {
   }
 }
 
+// r32 (mixed precision): the FP32 copy of the new residual, the next V-cycle's input
 __global__ void update_k(int n, double* __restrict__ x, double* __restrict__ r,
                          const double* __restrict__ p, const double* __restrict__ q,
-                         const PcgCtl* __restrict__ ctl, double* __restrict__ part) {
+                         const PcgCtl* __restrict__ ctl, double* __restrict__ part,
+                         float* __restrict__ r32) {
   const double a = ctl->alpha;
   double acc = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     x[i] = x[i] + a * p[i];
     double ri = r[i] - a * q[i];
     r[i] = ri;
+    if (r32) r32[i] = (float)ri;
     acc += ri * ri;
   }
   double t = block_sum(acc);
@@ -201,14 +247,25 @@ template void dot_partials<double, double>(int, const double*, const double*, do
 template void dot_partials<double, float>(int, const double*, const float*, double*, cudaStream_t);
 template void dot_partials<float, double>(int, const float*, const double*, double*, cudaStream_t);
 
+template <class TZ>
+void dot2_partials(int n, const double* r, const TZ* z, const double* q, double* part_rz,
+                   double* part_zq, cudaStream_t s) {
+  dot2_k<TZ><<<kRedBlocks, kRedThreads, 0, s>>>(n, r, z, q, part_rz, part_zq);
+  SAAMG_LAUNCH();
+}
+template void dot2_partials<double>(int, const double*, const double*, const double*, double*,
+                                    double*, cudaStream_t);
+template void dot2_partials<float>(int, const double*, const float*, const double*, double*,
+                                   double*, cudaStream_t);
+
 void pcg_alpha(const double* partials, PcgCtl* ctl, cudaStream_t s) {
   alpha_k<<<1, kRedThreads, 0, s>>>(partials, ctl);
   SAAMG_LAUNCH();
 }
 
 void pcg_update(int n, double* x, double* r, const double* p, const double* q, const PcgCtl* ctl,
-                double* partials, cudaStream_t s) {
-  update_k<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, p, q, ctl, partials);
+                double* partials, cudaStream_t s, float* r32) {
+  update_k<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, p, q, ctl, partials, r32);
   SAAMG_LAUNCH();
 }
 

@@ -30,9 +30,14 @@ void dot_partials(int n, const TA* a, const TB* b, double* partials, cudaStream_
 
 // ctl->pq = sum(partials); alpha = rz / pq (breakdown flag on 0/NaN)
 void pcg_alpha(const double* partials, PcgCtl* ctl, cudaStream_t s);
-// x += alpha p; r -= alpha q; partials of r'r
+// partials of r'z and z'q in one sweep (bitwise the two dot_partials calls)
+template <class TZ>
+void dot2_partials(int n, const double* r, const TZ* z, const double* q, double* part_rz,
+                   double* part_zq, cudaStream_t s);
+
+// x += alpha p; r -= alpha q; partials of r'r; r32 (if not null) = FP32 copy of the new r
 void pcg_update(int n, double* x, double* r, const double* p, const double* q, const PcgCtl* ctl,
-                double* partials, cudaStream_t s);
+                double* partials, cudaStream_t s, float* r32 = nullptr);
 // ctl->rr = sum(partials); converged = rr <= tol2; iters++
 void pcg_check(const double* partials, PcgCtl* ctl, cudaStream_t s);
 // rz_new = sum(part_rz); beta = rz_new / rz (rule 0) or -alpha zq / rz (rule 1, part_zq);

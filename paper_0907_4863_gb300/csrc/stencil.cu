@@ -56,7 +56,8 @@ template <class T, int MODE>
 __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int lane,
                                             const T* __restrict__ x, T* __restrict__ y,
                                             const T* __restrict__ b, T* __restrict__ d, T c1,
-                                            T c2, T c2invd0, double& dacc) {
+                                            T c2, T c2invd0, double& dacc,
+                                            const int* __restrict__ agg) {
     const int2 ch = S.chunks[c];
     const int L = ch.x;
     const LineInfo me = S.lines[L];
@@ -92,10 +93,26 @@ __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int l
       y[row] = dv;
       return;
     }
-    const T* xr = x + row;
-    const T xc = xr[0];
-    const T vxm = xr[oxm], vxp = xr[oxp], vym = xr[oym], vyp = xr[oyp], vzm = xr[ozm],
-            vzp = xr[ozp];
+    T xc, vxm, vxp, vym, vyp, vzm, vzp;
+    if (MODE == ST_PROLONG) {  // x is the coarse vector, read through the aggregates: (T v)_j
+      const int* ar = agg + row;
+      xc = x[ar[0]];
+      vxm = x[ar[oxm]];
+      vxp = x[ar[oxp]];
+      vym = x[ar[oym]];
+      vyp = x[ar[oyp]];
+      vzm = x[ar[ozm]];
+      vzp = x[ar[ozp]];
+    } else {
+      const T* xr = x + row;
+      xc = xr[0];
+      vxm = xr[oxm];
+      vxp = xr[oxp];
+      vym = xr[oym];
+      vyp = xr[oyp];
+      vzm = xr[ozm];
+      vzp = xr[ozp];
+    }
     // SPMV modes accumulate A x; RESID / CHEB accumulate r = b - A x directly (one FMA per
     // term: FP64 issue slots bound this kernel in double precision)
     constexpr bool kResid = (MODE == ST_RESID || MODE == ST_CHEB || MODE == ST_CHEB1);
@@ -126,6 +143,8 @@ __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int l
       if (MODE == ST_SPMV_DOT) dacc = fma(to_d(xc), to_d(acc), dacc);
     } else if (MODE == ST_RESID) {
       y[row] = acc;
+    } else if (MODE == ST_PROLONG) {  // c2 = omega: y += (T v)_i - omega invd_i (A T v)_i
+      y[row] = y[row] + fma(-c2i, acc, xc);
     } else {  // ST_CHEB / ST_CHEB1: d = c1 d + c2 D^-1 r; x_out = x + d
       const T dv = (MODE == ST_CHEB1) ? acc * c2i : fma(c1, d[row], acc * c2i);
       d[row] = dv;
@@ -140,7 +159,8 @@ __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __res
                                                  T* __restrict__ y, const T* __restrict__ b,
                                                  T* __restrict__ d, T c1, T c2,
                                                  double* __restrict__ partials,
-                                                 const double* __restrict__ xscale) {
+                                                 const double* __restrict__ xscale,
+                                                 const int* __restrict__ agg) {
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   const int nw = gridDim.x * wpb;
@@ -151,7 +171,7 @@ __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __res
 #pragma unroll
     for (int k = 0; k < K; ++k)
       if (c0 + k < S.nchunks)
-        stencil_row<T, MODE>(S, c0 + k, lane, x, y, b, d, c1, c2, c2invd0, dacc);
+        stencil_row<T, MODE>(S, c0 + k, lane, x, y, b, d, c1, c2, c2invd0, dacc, agg);
   }
   if (MODE == ST_SPMV_DOT || MODE == ST_DINV_DOT) {
     __shared__ double sh[32];
@@ -200,31 +220,55 @@ void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* 
   }
   switch (mode) {
     case ST_SPMV:
-      stencil_k<T, ST_SPMV, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials, xscale);
+      stencil_k<T, ST_SPMV, kChunks<T>()><<<blocks, 256, 0, s>>>(
+          S, x, y, b, d, c1, c2, partials, xscale, nullptr);
       break;
     case ST_SPMV_DOT:
-      stencil_k<T, ST_SPMV_DOT, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials, xscale);
+      stencil_k<T, ST_SPMV_DOT, kChunks<T>()><<<blocks, 256, 0, s>>>(
+          S, x, y, b, d, c1, c2, partials, xscale, nullptr);
       break;
     case ST_RESID:
-      stencil_k<T, ST_RESID, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials, xscale);
+      stencil_k<T, ST_RESID, kChunks<T>()><<<blocks, 256, 0, s>>>(
+          S, x, y, b, d, c1, c2, partials, xscale, nullptr);
       break;
     case ST_CHEB:
-      stencil_k<T, ST_CHEB, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials, xscale);
+      stencil_k<T, ST_CHEB, kChunks<T>()><<<blocks, 256, 0, s>>>(
+          S, x, y, b, d, c1, c2, partials, xscale, nullptr);
       break;
     case ST_CHEB0:
-      stencil_k<T, ST_CHEB0, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials, xscale);
+      stencil_k<T, ST_CHEB0, kChunks<T>()><<<blocks, 256, 0, s>>>(
+          S, x, y, b, d, c1, c2, partials, xscale, nullptr);
       break;
     case ST_CHEB1:
-      stencil_k<T, ST_CHEB1, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials, xscale);
+      stencil_k<T, ST_CHEB1, kChunks<T>()><<<blocks, 256, 0, s>>>(
+          S, x, y, b, d, c1, c2, partials, xscale, nullptr);
       break;
     case ST_DINV_DOT:
-      stencil_k<T, ST_DINV_DOT, kChunks<T>()><<<blocks, 256, 0, s>>>(S, x, y, b, d, c1, c2, partials, xscale);
+      stencil_k<T, ST_DINV_DOT, kChunks<T>()><<<blocks, 256, 0, s>>>(
+          S, x, y, b, d, c1, c2, partials, xscale, nullptr);
       break;
     default:
       fail(SAAMG_EINVAL, "bad stencil mode");
   }
   SAAMG_LAUNCH();
 }
+
+template <class T>
+void stencil_prolong(const StencilDev<T>& S, const int* agg, T omega, const T* v, T* y,
+                     cudaStream_t s) {
+  if (S.nchunks == 0) return;
+  KernelTimer kt(SAAMG_KT_TRANSFER, S.n, s);
+  const long long need = ((long long)S.nchunks + 8 * kChunks<T>() - 1) / (8 * kChunks<T>());
+  const int blocks = (int)(need < 152 * 16 ? need : 152 * 16);
+  stencil_k<T, ST_PROLONG, kChunks<T>()><<<blocks, 256, 0, s>>>(
+      S, v, y, nullptr, nullptr, T(0), omega, nullptr, nullptr, agg);
+  SAAMG_LAUNCH();
+}
+
+template void stencil_prolong<float>(const StencilDev<float>&, const int*, float, const float*,
+                                     float*, cudaStream_t);
+template void stencil_prolong<double>(const StencilDev<double>&, const int*, double,
+                                      const double*, double*, cudaStream_t);
 
 template void stencil_apply<double>(const StencilDev<double>&, int, const double*, double*,
                                     const double*, double*, double, double, double*,

@@ -364,3 +364,164 @@ def test_phase2_nodes_join_highest_key_root():
         assert cand, i
         best = max(cand, key=lambda r: key[r])
         assert agg[i] == agg[best]
+
+
+# --- cube aggregation (Sec. 3.2, the paper's "decoupled" 3^d cubes) -------------------------
+
+def _lattice(ids, dims):
+    ids = np.asarray(ids, np.int64)
+    return ids % dims[0], (ids // dims[0]) % dims[1], ids // (dims[0] * dims[1])
+
+
+@pytest.mark.parametrize("w", [I.pipe_workload(20, I.LINEAR), I.taper_workload(13, 12, 16),
+                               I.cylinder_workload(17, I.CONSTANT)], ids=lambda w: w.name)
+def test_cube_aggregates_are_the_lattice_blocks(w):
+    """Every aggregate is the set of unknowns of one 3x3x3 block of the lattice: two rows share
+    an aggregate exactly when their block coordinates agree; aggregates are numbered by
+    ascending block index; the coarse ids decode to the block coordinates."""
+    op = oracle_operator(w)
+    dims = w.grid.n
+    agg, root, nxt, nd = O.cube_aggregate(op.node_of_row, dims)
+    i, j, k = _lattice(op.node_of_row, dims)
+    blk = np.stack([i // 3, j // 3, k // 3], 1)
+    assert nd == tuple((d + 2) // 3 for d in dims)
+    nagg = agg.max() + 1
+    assert len(nxt) == nagg and np.all(np.diff(nxt.astype(np.int64)) > 0)
+    for a in range(nagg):
+        members = np.flatnonzero(agg == a)
+        b = blk[members]
+        assert np.all(b == b[0]) and 1 <= len(members) <= 27
+        ci, cj, ck = _lattice([nxt[a]], nd)
+        assert (ci[0], cj[0], ck[0]) == tuple(b[0])
+        assert root[members].sum() == 1 and root[members[0]] == 1  # smallest row
+    # rows of one block never split across aggregates
+    key = blk[:, 0] + 1000 * (blk[:, 1] + 1000 * blk[:, 2])
+    for kv in np.unique(key):
+        assert len(np.unique(agg[key == kv])) == 1
+    # interior blocks are complete cubes: 27 members
+    counts = np.bincount(agg)
+    assert counts.max() == 27
+
+
+def test_cube_aggregation_of_a_full_box_is_regular():
+    """Semi-axes larger than the box: every lattice node is an unknown, so with sides that
+    are multiples of 3 each level has exactly (n/3)^3 aggregates of 27 rows and T has 27 ones
+    per column."""
+    w = I.Workload("box18", I.cell_centred_grid(18), I.Domain(5.0, 5.0), I.LINEAR)
+    op = oracle_operator(w)
+    assert op.n == 18 ** 3
+    h = oracle_hierarchy(op, max_coarse=10, aggregation=O.Hierarchy.AGG_CUBES)
+    assert [h.n(l) for l in range(h.levels)] == [18 ** 3, 6 ** 3, 2 ** 3]
+    for l in range(h.levels - 1):
+        agg, root = h.agg(l)
+        assert np.all(np.bincount(agg) == 27) and root.sum() == h.n(l + 1)
+
+
+@pytest.mark.parametrize("w", [I.pipe_workload(18, I.LINEAR), I.pipe_workload(15, I.QUADRATIC),
+                               I.taper_workload(13, 12, 16, I.CONSTANT)], ids=lambda w: w.name)
+def test_cube_hierarchy_solves_like_a_direct_solver(w):
+    op = oracle_operator(w)
+    h = oracle_hierarchy(op, max_coarse=40, aggregation=O.Hierarchy.AGG_CUBES)
+    assert h.status == 0 and h.levels >= 2
+    # the coarse levels are the cube lattices: level l+1 has at most ceil(n_l-lattice / 27)
+    agg0, _ = h.agg(0)
+    assert h.n(1) == agg0.max() + 1
+    rho = I.gaussian_bunch(w.grid, w.centre, w.sigma, seed=3)
+    phi, info = h.solve(rho, rtol=1e-12, beta_rule=1 if w.mode == I.QUADRATIC else 0)
+    assert info["rc"] == 0
+    b = op.bfac * rho[op.node_of_row]
+    x_ref = spla.spsolve(op.scipy(scaled=False).tocsc(), b)
+    assert np.max(np.abs(phi[op.node_of_row] - x_ref)) <= 1e-10 * np.max(np.abs(x_ref))
+    # Galerkin coarse operator of the cube hierarchy is P^T A P
+    rp, ci, va = h.A(0)
+    A0 = sps.csr_matrix((va, ci, rp), shape=(h.n(0), h.n(0)))
+    P0 = sps.csr_matrix((h.P(0)[2], h.P(0)[1], h.P(0)[0]), shape=(h.n(0), h.n(1)))
+    A1 = sps.csr_matrix((h.A(1)[2], h.A(1)[1], h.A(1)[0]), shape=(h.n(1), h.n(1)))
+    ref = (P0.T @ A0 @ P0).toarray()
+    assert np.max(np.abs(A1.toarray() - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+# --- Gauss-Seidel coarse solver (Sec. 3.2, "Coarse level solver") ---------------------------
+
+def _key(ids, seed=0x2545F491):
+    return np.array([(O.fmix32(int(v) ^ seed) << 32) | int(v) for v in ids], dtype=object)
+
+
+def _random_spd(n, seed, density=0.15):
+    rng = np.random.default_rng(seed)
+    M = sps.random(n, n, density=density, random_state=rng, format="csr")
+    A = (M + M.T).tocsr()
+    A.data = -np.abs(A.data)
+    A = A + sps.diags(np.asarray(abs(A).sum(1)).ravel() + 0.5)
+    A = A.tocsr()
+    A.sort_indices()
+    return A
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_colouring_is_the_rounds_of_local_key_maxima(seed):
+    """colour(i) = c exactly when i beats every neighbour still uncoloured at round c, and in
+    every earlier round some uncoloured neighbour beat it (the synchronous-round rule)."""
+    A = _random_spd(60 + 20 * seed, seed)
+    ids = np.arange(A.shape[0], dtype=np.uint32) * 7 + 3
+    col, k = O.colour(A.indptr, A.indices, ids)
+    key = _key(ids)
+    assert col.min() == 0 and col.max() == k - 1
+    for i in range(A.shape[0]):
+        nb = [j for j in A.indices[A.indptr[i]:A.indptr[i + 1]] if j != i]
+        assert all(col[j] != col[i] for j in nb)  # a proper colouring
+        assert all(key[i] > key[j] for j in nb if col[j] >= col[i])
+        for r in range(col[i]):
+            assert any(key[j] > key[i] for j in nb if col[j] >= r)
+
+
+def test_symmetric_gauss_seidel_step_closed_form():
+    """One step from zero equals (D+U)^-1 (b - L (D+L)^-1 b) in the colour-sorted ordering
+    (L, U: strictly lower / upper parts), computed with dense triangular solves."""
+    import scipy.linalg as sla
+    A = _random_spd(70, 11)
+    n = A.shape[0]
+    ids = np.arange(n, dtype=np.uint32)
+    col, k = O.colour(A.indptr, A.indices, ids)
+    b = np.random.default_rng(5).standard_normal(n)
+    perm = np.lexsort((np.arange(n), col))  # by colour, then row
+    Ap = A.toarray()[np.ix_(perm, perm)]
+    bp = b[perm]
+    Lw = np.tril(Ap)  # D + L
+    Up = np.triu(Ap)  # D + U
+    xh = sla.solve_triangular(Lw, bp, lower=True)
+    x1 = sla.solve_triangular(Up, bp - np.tril(Ap, -1) @ xh, lower=False)
+    got = O.sgs(A.indptr, A.indices, A.data, col, k, 1, b)
+    ref = np.empty(n)
+    ref[perm] = x1
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    # many steps converge to the solution of A x = b
+    x = O.sgs(A.indptr, A.indices, A.data, col, k, 200, b)
+    assert np.max(np.abs(A @ x - b)) <= 1e-10 * np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("w", [I.pipe_workload(20, I.LINEAR), I.cylinder_workload(16, I.CONSTANT)],
+                         ids=lambda w: w.name)
+def test_gauss_seidel_coarse_solver_in_the_hierarchy(w):
+    op = oracle_operator(w)
+    hl = oracle_hierarchy(op, max_coarse=200)
+    hg = oracle_hierarchy(op, max_coarse=200, coarse_solver=O.Hierarchy.COARSE_GS, coarse_sweeps=3)
+    assert hg.status == 0 and hg.colours() is not None and hl.colours() is None
+    c, k = hg.colours()
+    A = hg.A(hg.levels - 1)
+    for i in range(len(c)):
+        nb = A[1][A[0][i]:A[0][i + 1]]
+        assert all(c[j] != c[i] for j in nb if j != i)
+    # the V-cycle stays symmetric: u'M v = v'M u
+    rng = np.random.default_rng(4)
+    u, v = rng.standard_normal(op.n), rng.standard_normal(op.n)
+    mu, mv = hg.vcycle(u), hg.vcycle(v)
+    assert abs(v @ mu - u @ mv) <= 1e-11 * abs(v @ mu)
+    # three steps give about the quality of the exact coarse solve (the paper's finding)
+    rho = I.gaussian_bunch(w.grid, w.centre, w.sigma, seed=2)
+    _, il = hl.solve(rho, rtol=1e-8)
+    phi, ig = hg.solve(rho, rtol=1e-8)
+    assert ig["rc"] == 0 and ig["iters"] <= il["iters"] + 3
+    b = op.bfac * rho[op.node_of_row]
+    x_ref = spla.spsolve(op.scipy(scaled=False).tocsc(), b)
+    assert np.max(np.abs(phi[op.node_of_row] - x_ref)) <= 1e-6 * np.max(np.abs(x_ref))
