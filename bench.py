@@ -234,6 +234,7 @@ def run_ours(args):
         extra = extra_legs(S, torch, w, dom, grid, rhs[args.warmup], args)
         extra.update(mixed_quadratic_leg(S, torch, args))
         extra["aggregation_cubes_vs_mis2"] = aggregation_leg(S, torch, args)
+        extra["coarse_gauss_seidel_vs_lu"] = coarse_solver_leg(S, torch, args)
     del rhs, phis
     torch.cuda.empty_cache()
     if not args.no_batched:
@@ -442,6 +443,39 @@ def aggregation_leg(S, torch, args):
                 "hierarchy_device_bytes": hi["device_bytes"]}
             h.free()
             op.free()
+    return out
+
+
+def coarse_solver_leg(S, torch, args):
+    """Dense LU against three symmetric Gauss-Seidel steps on the coarsest level (Sec. 3.2):
+    setup time, CG iterations and solve time on the same workload, both aggregations."""
+    w = workload(args.n)
+    dom, grid = S.make_domain(w.domain), S.make_grid(w.grid)
+    rho = torch.from_numpy(I.gaussian_bunch(w.grid, w.centre, w.sigma, seed=13)).cuda()
+    out = {"workload": f"{w.name}, linear extrapolation, rtol 1e-8, FP64"}
+    op = S.build_operator(dom, grid, w.mode)
+    for aname, agg in (("mis2", 0), ("cubes", 1)):
+        for cname, cs in (("lu", 0), ("gs3", 1)):
+            params = S.params_default(max_coarse=4096, aggregation=agg, coarse_solver=cs)
+            S.setup(op, params).free()  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = S.setup(op, params)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            phi = torch.zeros_like(rho)
+            S.solve(h, rho, phi, rtol=RTOL)
+            phi.zero_()
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            info = S.solve(h, rho, phi, rtol=RTOL)
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            out[f"{aname}_{cname}"] = {"coarse_n": h.info()["n"][-1], "iters": info["iters"],
+                                       "relres_true": info["relres_true"],
+                                       "setup_ms": 1e3 * (t1 - t0), "solve_ms": 1e3 * (t3 - t2)}
+            h.free()
+    op.free()
     return out
 
 

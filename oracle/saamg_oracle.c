@@ -377,6 +377,126 @@ void orc_op_fractions(const orc_op *op, double *frac) {
 }
 
 /* ------------------------------------------------------------------------- */
+/* Around the solve in the PIC step: CIC deposition, E = -grad phi, CIC gather */
+/* ------------------------------------------------------------------------- */
+/* Cloud-in-cell weights of one coordinate: cell index c = floor((x - o) / h) and the
+ * weights (1 - f, f) of the nodes c and c + 1, f = (x - o) / h - c. */
+static void cic_axis(double x, double o, double h, long *c, double *f) {
+  double u = (x - o) / h;
+  double fl = floor(u);
+  *c = (long)fl;
+  *f = u - fl;
+}
+
+/* Sec. 4.1 (the charge density comes from the particles by cloud-in-cell area weighting):
+ * rho(node) = sum_p q_p W(x_p - x_node) / (hx hy hz), W the product of the three 1-D hat
+ * weights.  Each particle adds ((q / V) wx) wy) wz to its 8 surrounding nodes, in particle
+ * order, z-slab, y-row, x-node (c, b, a = 0, 1); nodes outside the box are dropped. */
+void orc_deposit_cic(int nx, int ny, int nz, double hx, double hy, double hz, double ox,
+                     double oy, double oz, int np, const double *x, const double *y,
+                     const double *z, const double *q, double *rho) {
+  const double vol = (hx * hy) * hz;
+  for (long v = 0; v < (long)nx * ny * nz; ++v) rho[v] = 0.0;
+  for (int p = 0; p < np; ++p) {
+    long ci, cj, ck;
+    double fx, fy, fz;
+    cic_axis(x[p], ox, hx, &ci, &fx);
+    cic_axis(y[p], oy, hy, &cj, &fy);
+    cic_axis(z[p], oz, hz, &ck, &fz);
+    const double qv = q[p] / vol;
+    for (int c = 0; c < 2; ++c)
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) {
+          long i = ci + a, j = cj + b, k = ck + c;
+          if (i < 0 || j < 0 || k < 0 || i >= nx || j >= ny || k >= nz) continue;
+          double wx = a ? fx : 1.0 - fx, wy = b ? fy : 1.0 - fy, wz = c ? fz : 1.0 - fz;
+          rho[i + nx * (j + (long)ny * k)] += ((qv * wx) * wy) * wz;
+        }
+  }
+}
+
+/* Derivative at a node from the node value p0 and its neighbours along one axis, at
+ * distances h (inside) or s h (wall point, value 0, s = boundary fraction): the derivative
+ * of the quadratic through the three points.  in_m / in_p: neighbour is an unknown. */
+static double axis_derivative(double h, int in_m, int in_p, double pm, double p0, double pp,
+                              double t, double s) {
+  if (in_m && in_p) return (pp - pm) / (2.0 * h);
+  if (in_m) /* wall at +s h */
+    return (-(s * s) * pm + (s * s - 1.0) * p0) / (h * s * (1.0 + s));
+  if (in_p) /* wall at -t h */
+    return ((t * t) * pp - (t * t - 1.0) * p0) / (h * t * (1.0 + t));
+  return p0 * (s - t) / (h * s * t); /* walls at -t h and +s h */
+}
+
+/* E = -grad phi (the self field of the beam, Sec. 1) at the unknowns, 0 elsewhere.
+ * READING: second-order differences that use the wall value phi = 0 at the boundary
+ * fraction of Sec. 2 (the same clamped s as the operator); on a Robin end plane the
+ * z-derivative is the one the Robin condition prescribes (outward normal derivative
+ * = -phi / d with d = (nz - 1) hz / 2). */
+void orc_field_gradient(const orc_op *op, const double *phi, double *ex, double *ey,
+                        double *ez) {
+  const int nx = op->nx, ny = op->ny, nz = op->nz;
+  const double dist = 0.5 * ((double)(nz - 1) * op->hz);
+  const double h[3] = {op->hx, op->hy, op->hz};
+  double *E[3] = {ex, ey, ez};
+  for (long v = 0; v < (long)nx * ny * nz; ++v) ex[v] = ey[v] = ez[v] = 0.0;
+  for (int r = 0; r < op->n; ++r) {
+    long q = op->node_of_row[r];
+    int i = (int)(q % nx), j = (int)((q / nx) % ny), k = (int)(q / ((long)nx * ny));
+    int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k},
+                    {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
+    const double p0 = phi[q];
+    for (int ax = 0; ax < 3; ++ax) {
+      int dm = 2 * ax, dp = 2 * ax + 1;
+      double d;
+      if (ax == 2 && op->zbc == ORC_Z_ROBIN && (k == 0 || k == nz - 1)) {
+        d = (k == 0 ? 1.0 : -1.0) * p0 / dist;
+      } else {
+        int in_m = is_unknown(op, nb[dm][0], nb[dm][1], nb[dm][2]);
+        int in_p = is_unknown(op, nb[dp][0], nb[dp][1], nb[dp][2]);
+        double pm = in_m ? phi[nb[dm][0] + nx * (nb[dm][1] + (long)ny * nb[dm][2])] : 0.0;
+        double pp = in_p ? phi[nb[dp][0] + nx * (nb[dp][1] + (long)ny * nb[dp][2])] : 0.0;
+        double t = in_m ? 1.0 : boundary_fraction(op, i, j, k, dm);
+        double s = in_p ? 1.0 : boundary_fraction(op, i, j, k, dp);
+        d = axis_derivative(h[ax], in_m, in_p, pm, p0, pp, t, s);
+      }
+      E[ax][q] = -d;
+    }
+  }
+}
+
+/* The field at the particles with the deposition's weights (momentum-conserving pair of
+ * the CIC scheme): E_p = sum over the 8 nodes of ((wx wy) wz) E(node), in the deposition's
+ * node order; nodes outside the box contribute nothing. */
+void orc_gather_cic(int nx, int ny, int nz, double hx, double hy, double hz, double ox,
+                    double oy, double oz, const double *ex, const double *ey, const double *ez,
+                    int np, const double *x, const double *y, const double *z, double *epx,
+                    double *epy, double *epz) {
+  for (int p = 0; p < np; ++p) {
+    long ci, cj, ck;
+    double fx, fy, fz;
+    cic_axis(x[p], ox, hx, &ci, &fx);
+    cic_axis(y[p], oy, hy, &cj, &fy);
+    cic_axis(z[p], oz, hz, &ck, &fz);
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int c = 0; c < 2; ++c)
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) {
+          long i = ci + a, j = cj + b, k = ck + c;
+          if (i < 0 || j < 0 || k < 0 || i >= nx || j >= ny || k >= nz) continue;
+          double w = ((a ? fx : 1.0 - fx) * (b ? fy : 1.0 - fy)) * (c ? fz : 1.0 - fz);
+          long v = i + nx * (j + (long)ny * k);
+          sx += w * ex[v];
+          sy += w * ey[v];
+          sz += w * ez[v];
+        }
+    epx[p] = sx;
+    epy[p] = sy;
+    epz[p] = sz;
+  }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Hashed priorities                                                          */
 /* ------------------------------------------------------------------------- */
 /* MurmurHash3 32-bit finaliser (Appleby, public domain): xor-shift 16, multiply by

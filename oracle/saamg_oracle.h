@@ -56,6 +56,19 @@ void orc_op_fractions(const orc_op *op, double *frac);
 /* Inside test of one box node (1 = unknown). */
 int orc_node_inside(const orc_op *op, int i, int j, int k);
 
+/* The steps on either side of the solve in a PIC time step (Sec. 1, Sec. 4.1).
+ * Particles: coordinate arrays x, y, z and charges q of length np.  Box arrays of the
+ * nx x ny x nz node lattice node(i,j,k) = origin + (i hx, j hy, k hz), i fastest. */
+void orc_deposit_cic(int nx, int ny, int nz, double hx, double hy, double hz, double ox,
+                     double oy, double oz, int np, const double *x, const double *y,
+                     const double *z, const double *q, double *rho);
+void orc_field_gradient(const orc_op *op, const double *phi, double *ex, double *ey,
+                        double *ez);
+void orc_gather_cic(int nx, int ny, int nz, double hx, double hy, double hz, double ox,
+                    double oy, double oz, const double *ex, const double *ey, const double *ez,
+                    int np, const double *x, const double *y, const double *z, double *epx,
+                    double *epy, double *epz);
+
 /* SA-AMG hierarchy (Sec. 3.2). */
 orc_hier *orc_setup(const orc_op *op, int cheb_degree, double cheb_ratio,
                     double cheb_safety, int max_coarse, int max_levels,

@@ -245,8 +245,6 @@ static void check_params_ext(const saamg_params& p) {
   if (p.coarse_solver != SAAMG_COARSE_LU && p.coarse_solver != SAAMG_COARSE_GS)
     fail(SAAMG_EINVAL, "unknown coarse solver");
   if (p.coarse_sweeps < 1 || p.coarse_sweeps > 64) fail(SAAMG_EINVAL, "coarse_sweeps must be in 1..64");
-  if (p.coarse_solver == SAAMG_COARSE_GS)
-    fail(SAAMG_UNIMPLEMENTED, "the Gauss-Seidel coarse solver is not available in this build");
 }
 
 // Matrix of level l (level 0 = the operator's CSR)
@@ -404,10 +402,15 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
   }
   const int nl = (int)h->lev.size();
   Level& C = *h->lev[nl - 1];
-  if (C.n > 16384) fail(SAAMG_NUMERICAL, "coarsest level has more than 16384 unknowns");
   pt.mark("levels");
-  coarse_factor(level_matrix(h, nl - 1), h->coarse, s);
-  pt.mark("coarseLU");
+  if (prm.coarse_solver == SAAMG_COARSE_GS) {
+    const unsigned* cids = (nl == 1) ? od.ids.p : C.ids.p;  // key ids of the colouring
+    coarse_gs_setup(level_matrix(h, nl - 1), C.invd.p, cids, prm.coarse_sweeps, h->coarse, s);
+  } else {
+    if (C.n > 16384) fail(SAAMG_NUMERICAL, "coarsest level has more than 16384 unknowns");
+    coarse_factor(level_matrix(h, nl - 1), h->coarse, s);
+  }
+  pt.mark("coarse");
   for (int q = 0; q < nl; ++q) {
     Level& L = *h->lev[q];
     if (q < nl - 1) L.cheb = cheb_coefficients(L.lambda, prm.cheb_ratio, prm.cheb_safety, prm.cheb_degree);
@@ -447,7 +450,7 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
              L->d.bytes() + L->r.bytes() + L->fx0.bytes() + L->fx1.bytes() + L->fb.bytes() +
              L->fd.bytes() + L->fr.bytes() + L->As.bytes() + L->P32.bytes() + L->R32.bytes();
   }
-  bytes += h->coarse.inv.bytes() + 6LL * n * 8 + (mixed(h) ? 8LL * n : 0);
+  bytes += h->coarse.bytes() + 6LL * n * 8 + (mixed(h) ? 8LL * n : 0);
   h->bytes = bytes;
   h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }

@@ -124,7 +124,166 @@ __global__ void coarse_apply_k(int n, const double* __restrict__ inv, const TV* 
   x[i] = (TV)acc;
 }
 
+// --- Gauss-Seidel (one CTA) ---------------------------------------------------------
+constexpr int kGsThreads = 1024;
+constexpr int kGsMaxColours = 256;
+
+__device__ __forceinline__ uint32_t fmix32_gs(uint32_t h) {  // MurmurHash3 finaliser
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+__device__ __forceinline__ unsigned long long gs_key(const unsigned* ids, int v) {
+  const uint32_t id = ids ? ids[v] : (uint32_t)v;
+  return ((unsigned long long)fmix32_gs(id ^ 0x2545F491u) << 32) | id;
+}
+
+// Colouring by synchronous rounds, then a stable sort of the rows by colour (order, coff).
+// pick: n bytes of scratch.  err: set when more than kGsMaxColours colours are needed.
+__global__ void __launch_bounds__(kGsThreads) gs_colour_k(int n, const int* __restrict__ rowptr,
+                                                          const int* __restrict__ col,
+                                                          const unsigned* __restrict__ ids,
+                                                          int* __restrict__ colour,
+                                                          unsigned char* __restrict__ pick,
+                                                          int* __restrict__ order,
+                                                          int* __restrict__ coff,
+                                                          int* __restrict__ ncol_out) {
+  __shared__ int left, wcount[kGsThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < n; i += blockDim.x) colour[i] = -1;
+  if (tid == 0) left = n;
+  __syncthreads();
+  int c = 0;
+  while (left > 0 && c < kGsMaxColours) {
+    for (int i = tid; i < n; i += blockDim.x) {
+      unsigned char pk = 0;
+      if (colour[i] < 0) {
+        const unsigned long long ki = gs_key(ids, i);
+        pk = 1;
+        for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+          const int j = col[p];
+          if (j != i && colour[j] < 0 && gs_key(ids, j) > ki) pk = 0;
+        }
+      }
+      pick[i] = pk;
+    }
+    __syncthreads();
+    int got = 0;
+    for (int i = tid; i < n; i += blockDim.x)
+      if (pick[i]) {
+        colour[i] = c;
+        ++got;
+      }
+    got = __reduce_add_sync(0xffffffffu, got);
+    if (lane == 0 && got) atomicSub(&left, got);
+    ++c;
+    __syncthreads();
+  }
+  const int ncol = left > 0 ? -1 : c;
+  if (tid == 0) *ncol_out = ncol;
+  if (ncol < 0) return;
+  // stable partition by colour: for each colour, rows in ascending order
+  int base = 0;
+  for (int cc = 0; cc < ncol; ++cc) {
+    if (tid == 0) coff[cc] = base;
+    for (int b0 = 0; b0 < n; b0 += blockDim.x) {
+      const int i = b0 + tid;
+      const bool f = i < n && colour[i] == cc;
+      const unsigned bal = __ballot_sync(0xffffffffu, f);
+      if (lane == 0) wcount[warp] = __popc(bal);
+      __syncthreads();
+      int before = 0, total = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        before += w < warp ? wcount[w] : 0;
+        total += wcount[w];
+      }
+      if (f) order[base + before + __popc(bal & ((1u << lane) - 1u))] = i;
+      base += total;
+      __syncthreads();
+    }
+  }
+  if (tid == 0) coff[ncol] = base;
+}
+
+// `steps` symmetric sweeps from x = 0; x and b in shared memory (FP64); warp per row,
+// lanes over the row's entries, shuffle reduction in a fixed order.
+template <class TV>
+__global__ void __launch_bounds__(kGsThreads) gs_apply_k(int n, const int* __restrict__ rowptr,
+                                                         const int* __restrict__ col,
+                                                         const double* __restrict__ val,
+                                                         const double* __restrict__ invd,
+                                                         const int* __restrict__ order,
+                                                         const int* __restrict__ coff, int ncol,
+                                                         int steps, const TV* __restrict__ b,
+                                                         TV* __restrict__ x) {
+  extern __shared__ double gs_sm[];
+  double* xs = gs_sm;
+  double* bs = gs_sm + n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  for (int i = tid; i < n; i += blockDim.x) {
+    xs[i] = 0.0;
+    bs[i] = (double)b[i];
+  }
+  __syncthreads();
+  for (int st = 0; st < steps; ++st)
+    for (int half = 0; half < 2; ++half)
+      for (int cc = 0; cc < ncol; ++cc) {
+        const int c = half == 0 ? cc : ncol - 1 - cc;
+        for (int k = coff[c] + warp; k < coff[c + 1]; k += nwarp) {
+          const int i = order[k];
+          double acc = 0.0;
+          for (int p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) {
+            const int j = col[p];
+            if (j != i) acc += val[p] * xs[j];
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+          if (lane == 0) xs[i] = (bs[i] - acc) * invd[i];
+        }
+        __syncthreads();
+      }
+  for (int i = tid; i < n; i += blockDim.x) x[i] = (TV)xs[i];
+}
+
 }  // namespace
+
+void coarse_gs_setup(const DevCsr& A, const double* invd, const unsigned* ids, int steps,
+                     CoarseSolver& cs, cudaStream_t s) {
+  const int n = A.n;
+  if (n > kCoarseGsMax) fail(SAAMG_UNIMPLEMENTED, "Gauss-Seidel coarse level above 12288 rows");
+  cs.kind = SAAMG_COARSE_GS;
+  cs.n = n;
+  cs.steps = steps;
+  cs.rowptr = A.rowptr.p;
+  cs.col = A.col.p;
+  cs.val = A.val.p;
+  cs.invd = invd;
+  // shared-memory opt-in for the largest coarse level (set outside any stream capture)
+  const int smax = (int)(2 * kCoarseGsMax * sizeof(double));
+  SAAMG_CUDA(cudaFuncSetAttribute(gs_apply_k<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smax));
+  SAAMG_CUDA(cudaFuncSetAttribute(gs_apply_k<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smax));
+  cs.colour.alloc(n, s);
+  cs.order.alloc(n, s);
+  cs.coff.alloc(kGsMaxColours + 1, s);
+  if (n == 0) return;
+  Buf<unsigned char> pick;
+  Buf<int> ncol;
+  pick.alloc(n, s);
+  ncol.alloc(1, s);
+  gs_colour_k<<<1, kGsThreads, 0, s>>>(n, A.rowptr.p, A.col.p, ids, cs.colour.p, pick.p,
+                                       cs.order.p, cs.coff.p, ncol.p);
+  SAAMG_LAUNCH();
+  int h = 0;
+  d2h_sync(&h, ncol.p, sizeof(int), s);
+  if (h <= 0) fail(SAAMG_NUMERICAL, "coarse-level colouring needs more than 256 colours");
+  cs.ncolours = h;
+}
 
 void coarse_factor(const DevCsr& A, CoarseSolver& cs, cudaStream_t s) {
   const int n = A.n;
@@ -163,6 +322,13 @@ void coarse_factor(const DevCsr& A, CoarseSolver& cs, cudaStream_t s) {
 template <class TV>
 void coarse_apply(const CoarseSolver& cs, const TV* b, TV* x, cudaStream_t s) {
   if (cs.n == 0) return;
+  if (cs.kind == SAAMG_COARSE_GS) {
+    const size_t sm = 2 * (size_t)cs.n * sizeof(double);
+    gs_apply_k<TV><<<1, kGsThreads, sm, s>>>(cs.n, cs.rowptr, cs.col, cs.val, cs.invd,
+                                             cs.order.p, cs.coff.p, cs.ncolours, cs.steps, b, x);
+    SAAMG_LAUNCH();
+    return;
+  }
   coarse_apply_k<TV><<<(cs.n + 127) / 128, 128, 0, s>>>(cs.n, cs.inv.p, b, x);
   SAAMG_LAUNCH();
 }
