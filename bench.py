@@ -235,6 +235,7 @@ def run_ours(args):
         extra.update(mixed_quadratic_leg(S, torch, args))
         extra["aggregation_cubes_vs_mis2"] = aggregation_leg(S, torch, args)
         extra["coarse_gauss_seidel_vs_lu"] = coarse_solver_leg(S, torch, args)
+        extra["pic_transfers"] = pic_leg(S, torch, args)
     del rhs, phis
     torch.cuda.empty_cache()
     if not args.no_batched:
@@ -477,6 +478,44 @@ def coarse_solver_leg(S, torch, args):
             h.free()
     op.free()
     return out
+
+
+def pic_leg(S, torch, args, nparticles=10_000_000, reps=5):
+    """The steps around the solve in a PIC time step (Sec. 1, Sec. 4.1) at the bench grid:
+    CIC deposition of a Gaussian bunch of macro-particles, E = -grad phi, CIC gather.
+    Times from CUDA events on the launching stream, inputs resident."""
+    w = workload(args.n)
+    G = S.make_grid(w.grid)
+    op = S.build_operator(S.make_domain(w.domain), G, w.mode)
+    x, y, z, q = (torch.from_numpy(a).cuda() for a in
+                  I.bunch_particles(w.grid, nparticles, w.centre, w.sigma, seed=21))
+    nbox = w.grid.nbox
+    rho = torch.empty(nbox, dtype=torch.float64, device="cuda")
+    e = [torch.empty(nbox, dtype=torch.float64, device="cuda") for _ in range(3)]
+    ep = [torch.empty(nparticles, dtype=torch.float64, device="cuda") for _ in range(3)]
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_dep = timed(lambda: S.deposit_cic(G, x, y, z, q, rho))
+    phi = rho  # any box field: the gradient's cost does not depend on the values
+    t_grad = timed(lambda: S.field_gradient(op, phi, *e))
+    t_gat = timed(lambda: S.gather_cic(G, *e, x, y, z, *ep))
+    op.free()
+    return {"grid": list(w.grid.n), "particles": nparticles,
+            "deposit_ms": t_dep, "deposit_particles_per_s": nparticles / (t_dep / 1e3),
+            "gradient_ms": t_grad,
+            "gradient_gbs": (nbox * 8 * 4) / (t_grad / 1e3) / 1e9,  # phi read, 3 fields written
+            "gather_ms": t_gat, "gather_particles_per_s": nparticles / (t_gat / 1e3),
+            "gather_gbs": (nparticles * 48) / (t_gat / 1e3) / 1e9}  # x, y, z in; 3 fields out
 
 
 def batched_leg(S, torch):

@@ -278,6 +278,36 @@ saamg_status saamg_mis2_aggregate_noalloc(int n, const int *rowptr, const int *c
                                           const uint32_t *ids, uint32_t seed, unsigned char *root,
                                           int *agg, int *n_agg, void *stream);
 
+/* --- Around the solve in a PIC time step (Sec. 1, Sec. 4.1) --------------------------
+ * Box arrays follow saamg_solve's layout (i fastest, nx*ny*nz FP64, device memory).
+ * Particles are structure-of-arrays: x, y, z, q, np entries each, device memory. */
+
+/* Cloud-in-cell deposition (Sec. 4.1, the charge density from the particles):
+ * rho(node) = sum_p q_p W(x_p - x_node) / (hx hy hz), W the product of the 1-D hat
+ * functions of width h; each particle reaches the 8 nodes of its cell, nodes outside the
+ * box are dropped.  rho is overwritten.  Deterministic: every contribution is rounded once
+ * to a 64-bit fixed-point value scaled from sum |q|, so the result does not depend on the
+ * order of the atomic additions (relative accuracy about np * 2^-61 of sum|q| / V).
+ * rho is NaN everywhere when a charge is not finite.  EINVAL on NULL arrays with np > 0. */
+saamg_status saamg_deposit_cic(const saamg_grid *grid, int np, const double *x, const double *y,
+                               const double *z, const double *q, double *rho, void *stream);
+
+/* E = -grad phi (Sec. 1, the self field from the potential) on the box: at the unknowns of
+ * op, second-order differences that take phi = 0 at the wall point of an outside neighbour
+ * (boundary fraction of Sec. 2, the operator's clamped s; the derivative of the quadratic
+ * through the three points), and on a Robin end plane the z-derivative of the Robin
+ * condition (-phi/d outward); 0 at all other box nodes.  phi: box, e.g. saamg_solve's
+ * output; ex, ey, ez: box, overwritten. */
+saamg_status saamg_field_gradient(const saamg_operator *op, const double *phi, double *ex,
+                                  double *ey, double *ez, void *stream);
+
+/* The nodal field at the particles with the deposition's weights (the CIC pair that
+ * conserves momentum): epx[p] = sum over the 8 nodes of W * ex(node), likewise y, z. */
+saamg_status saamg_gather_cic(const saamg_grid *grid, const double *ex, const double *ey,
+                              const double *ez, int np, const double *x, const double *y,
+                              const double *z, double *epx, double *epy, double *epz,
+                              void *stream);
+
 /* Kernel classes for saamg_kernel_timing_read. */
 typedef enum {
   SAAMG_KT_STENCIL_SMOOTH = 0, /* level-0 Chebyshev step fused with the residual (full step) */
@@ -287,7 +317,8 @@ typedef enum {
   SAAMG_KT_SPGEMM = 4,         /* sparse products of the setup */
   SAAMG_KT_STENCIL_RESID = 5,  /* level-0 residual b - A x */
   SAAMG_KT_STENCIL_FIRST = 6,  /* first Chebyshev steps on level 0 (from zero, or c1 = 0) */
-  SAAMG_KT_COUNT = 7
+  SAAMG_KT_PIC = 7,            /* CIC deposition and gather (rows = particles) */
+  SAAMG_KT_COUNT = 8
 } saamg_kernel_class;
 
 /* Number of kernels this library has launched in the calling process. */

@@ -67,6 +67,10 @@ def lib():
         for f in ("orc_hier_lambda", "orc_hier_omega"):
             getattr(L, f).argtypes = [_p, _i]
             getattr(L, f).restype = _d
+        L.orc_deposit_cic.argtypes = [_i, _i, _i, _d, _d, _d, _d, _d, _d, _i, _p, _p, _p, _p, _p]
+        L.orc_field_gradient.argtypes = [_p, _p, _p, _p, _p]
+        L.orc_gather_cic.argtypes = [_i, _i, _i, _d, _d, _d, _d, _d, _d, _p, _p, _p, _i, _p, _p,
+                                     _p, _p, _p, _p]
         L.orc_fmix32.argtypes = [C.c_uint]
         L.orc_fmix32.restype = C.c_uint
         L.orc_mis2.argtypes = [_i, _p, _p, _p, C.c_uint, _p]
@@ -231,6 +235,36 @@ class Hierarchy:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.orc_hier_free(self._h)
             self._h = None
+
+
+def deposit_cic(grid, x, y, z, q):
+    """Cloud-in-cell charge density on the box (Sec. 4.1)."""
+    (nx, ny, nz), h, o = grid.n, grid.h, grid.origin
+    x, y, z, q = (np.ascontiguousarray(a, np.float64) for a in (x, y, z, q))
+    rho = np.empty(nx * ny * nz)
+    lib().orc_deposit_cic(nx, ny, nz, h[0], h[1], h[2], o[0], o[1], o[2], len(x), _ptr(x),
+                          _ptr(y), _ptr(z), _ptr(q), _ptr(rho))
+    return rho
+
+
+def field_gradient(op, phi):
+    """E = -grad phi on the box (zero outside the unknowns)."""
+    phi = np.ascontiguousarray(phi, np.float64).ravel()
+    e = [np.empty_like(phi) for _ in range(3)]
+    lib().orc_field_gradient(op._h, _ptr(phi), _ptr(e[0]), _ptr(e[1]), _ptr(e[2]))
+    return e
+
+
+def gather_cic(grid, e, x, y, z):
+    """E at the particles with the CIC weights of the deposition."""
+    (nx, ny, nz), h, o = grid.n, grid.h, grid.origin
+    e = [np.ascontiguousarray(a, np.float64) for a in e]
+    x, y, z = (np.ascontiguousarray(a, np.float64) for a in (x, y, z))
+    out = [np.empty(len(x)) for _ in range(3)]
+    lib().orc_gather_cic(nx, ny, nz, h[0], h[1], h[2], o[0], o[1], o[2], _ptr(e[0]), _ptr(e[1]),
+                         _ptr(e[2]), len(x), _ptr(x), _ptr(y), _ptr(z), _ptr(out[0]),
+                         _ptr(out[1]), _ptr(out[2]))
+    return out
 
 
 def fmix32(x):

@@ -18,6 +18,7 @@
 #include "galerkin.cuh"
 #include "operator.cuh"
 #include "pcg.cuh"
+#include "pic.cuh"
 #include "sell.cuh"
 
 namespace saamg {
@@ -1002,6 +1003,44 @@ saamg_status saamg_operator_apply(const saamg_operator* op, const double* x, dou
     if (op->d.n > 0 && (!x || !y)) fail(SAAMG_EINVAL, "NULL vector");
     stencil_apply<double>(op->d.view<double>(), ST_SPMV, x, y, nullptr, nullptr, 0.0, 0.0, nullptr,
                           (cudaStream_t)stream);
+  });
+}
+
+static void check_grid(const saamg_grid* g) {
+  if (!g) fail(SAAMG_EINVAL, "NULL grid");
+  for (int d = 0; d < 3; ++d)
+    if (g->n[d] < 1 || !(g->h[d] > 0.0) || !std::isfinite(g->origin[d]))
+      fail(SAAMG_EINVAL, "bad grid");
+  if ((double)g->n[0] * g->n[1] * g->n[2] > 4.0e9) fail(SAAMG_EINVAL, "grid too large");
+}
+
+saamg_status saamg_deposit_cic(const saamg_grid* grid, int np, const double* x, const double* y,
+                               const double* z, const double* q, double* rho, void* stream) {
+  return guard("saamg_deposit_cic", [&] {
+    check_grid(grid);
+    if (np < 0 || !rho || (np > 0 && (!x || !y || !z || !q))) fail(SAAMG_EINVAL, "bad arrays");
+    deposit_cic(*grid, np, x, y, z, q, rho, (cudaStream_t)stream);
+  });
+}
+
+saamg_status saamg_field_gradient(const saamg_operator* op, const double* phi, double* ex,
+                                  double* ey, double* ez, void* stream) {
+  return guard("saamg_field_gradient", [&] {
+    if (!op || op->magic != kOpMagic) fail(SAAMG_EINVAL, "not an operator handle");
+    if (!phi || !ex || !ey || !ez) fail(SAAMG_EINVAL, "NULL array");
+    field_gradient(op->d, phi, ex, ey, ez, (cudaStream_t)stream);
+  });
+}
+
+saamg_status saamg_gather_cic(const saamg_grid* grid, const double* ex, const double* ey,
+                              const double* ez, int np, const double* x, const double* y,
+                              const double* z, double* epx, double* epy, double* epz,
+                              void* stream) {
+  return guard("saamg_gather_cic", [&] {
+    check_grid(grid);
+    if (np < 0 || (np > 0 && (!ex || !ey || !ez || !x || !y || !z || !epx || !epy || !epz)))
+      fail(SAAMG_EINVAL, "bad arrays");
+    gather_cic(*grid, ex, ey, ez, np, x, y, z, epx, epy, epz, (cudaStream_t)stream);
   });
 }
 

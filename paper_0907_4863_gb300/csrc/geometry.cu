@@ -572,6 +572,75 @@ StencilDev<float> OperatorData::view<float>() const {
   return v;
 }
 
+namespace {
+
+// Derivative of the quadratic through the node value p0 and its neighbours along one axis,
+// at distances h (unknown neighbour) or s h (wall point, value 0); written with the same
+// operations, in the same order, as the CPU reference (this unit is compiled without FMA
+// contraction, so the results agree bit for bit).
+__device__ double axis_derivative(double h, bool in_m, bool in_p, double pm, double p0,
+                                  double pp, double t, double s) {
+  if (in_m && in_p) return (pp - pm) / (2.0 * h);
+  if (in_m) return (-(s * s) * pm + (s * s - 1.0) * p0) / (h * s * (1.0 + s));
+  if (in_p) return ((t * t) * pp - (t * t - 1.0) * p0) / (h * t * (1.0 + t));
+  return p0 * (s - t) / (h * s * t);
+}
+
+// E = -grad phi at the unknowns (warp per chunk, lane per unknown).  Neighbours inside
+// Omega_h use their phi; an outside neighbour is replaced by the wall point at the boundary
+// fraction with phi = 0; on a Robin end plane the z-derivative is the Robin condition's.
+__global__ void field_gradient_k(GeomParams g, const LineInfo* __restrict__ lines,
+                                 const int2* __restrict__ chunks, int nchunks,
+                                 const double* __restrict__ phi, double* __restrict__ ex,
+                                 double* __restrict__ ey, double* __restrict__ ez) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= nchunks) return;
+  const int2 ch = chunks[c];
+  const int L = ch.x;
+  const LineInfo me = lines[L];
+  const int i = me.lo + ch.y + lane;
+  if (i > me.hi) return;
+  const int j = L % g.ny, k = L / g.ny;
+  const size_t sy = (size_t)g.nx, sz = (size_t)g.nx * g.ny;
+  const size_t q = (size_t)i + sy * (size_t)j + sz * (size_t)k;
+  const double p0 = phi[q];
+  const double dist = 0.5 * ((double)(g.nz - 1) * g.h[2]);
+  const size_t stride[3] = {1, sy, sz};
+  double* E[3] = {ex, ey, ez};
+  for (int ax = 0; ax < 3; ++ax) {
+    double d;
+    if (ax == 2 && g.zbc == SAAMG_Z_ROBIN && (k == 0 || k == g.nz - 1)) {
+      d = (k == 0 ? 1.0 : -1.0) * p0 / dist;
+    } else {
+      const int im = i - (ax == 0), jm = j - (ax == 1), km = k - (ax == 2);
+      const int ip = i + (ax == 0), jp = j + (ax == 1), kp = k + (ax == 2);
+      const bool in_m = node_inside(g, im, jm, km);
+      const bool in_p = node_inside(g, ip, jp, kp);
+      const double pm = in_m ? phi[q - stride[ax]] : 0.0;
+      const double pp = in_p ? phi[q + stride[ax]] : 0.0;
+      const double t = in_m ? 1.0 : boundary_fraction(g, i, j, k, 2 * ax);
+      const double s = in_p ? 1.0 : boundary_fraction(g, i, j, k, 2 * ax + 1);
+      d = axis_derivative(g.h[ax], in_m, in_p, pm, p0, pp, t, s);
+    }
+    E[ax][q] = -d;
+  }
+}
+
+}  // namespace
+
+void field_gradient(const OperatorData& op, const double* phi, double* ex, double* ey,
+                    double* ez, cudaStream_t s) {
+  const size_t nbox = (size_t)op.g.nx * op.g.ny * op.g.nz;
+  SAAMG_CUDA(cudaMemsetAsync(ex, 0, nbox * sizeof(double), s));
+  SAAMG_CUDA(cudaMemsetAsync(ey, 0, nbox * sizeof(double), s));
+  SAAMG_CUDA(cudaMemsetAsync(ez, 0, nbox * sizeof(double), s));
+  if (op.n == 0) return;
+  field_gradient_k<<<warp_blocks(op.nchunks), 256, 0, s>>>(op.g, op.lines.p, op.chunks.p,
+                                                            op.nchunks, phi, ex, ey, ez);
+  SAAMG_LAUNCH();
+}
+
 void gather_rhs(const OperatorData& op, const double* rho, const double* phi0, double* bhat,
                 double* xhat, cudaStream_t s) {
   if (op.n == 0) return;

@@ -55,6 +55,10 @@ void gather_rhs(const OperatorData& op, const double* rho, const double* phi0, d
 // xhat (compact) -> phi (box) = s_i * xhat at unknowns, 0 elsewhere
 void scatter_solution(const OperatorData& op, const double* xhat, double* phi, cudaStream_t s);
 
+// E = -grad phi on the box (phi and E box arrays; E is 0 outside the unknowns)
+void field_gradient(const OperatorData& op, const double* phi, double* ex, double* ey,
+                    double* ez, cudaStream_t s);
+
 // stencil.cu -- matrix-free level-0 kernels.  MODE selects the fused operation.
 enum StencilMode {
   ST_SPMV = 0,      // y = A x

@@ -121,6 +121,23 @@ def taper_workload(nx, ny, nz, mode: int = LINEAR) -> Workload:
                     Domain(0.45, 0.45, taper=0.30 / 0.45), mode)
 
 
+def bunch_particles(grid: Grid, n: int, centre, sigma, seed: int, total_charge: float = 1.0):
+    """Synthetic macro-particles of a Gaussian bunch: positions ~ N(centre, sigma) per axis
+    (numpy PCG64, seed), kept when all 8 surrounding lattice nodes lie in the box; equal
+    charges summing to total_charge.  Returns x, y, z, q (float64 arrays)."""
+    rng = np.random.default_rng(seed)
+    lo = np.array(grid.origin)
+    hi = lo + (np.array(grid.n) - 1) * np.array(grid.h)
+    out = []
+    while sum(len(a) for a in out) < n:
+        p = rng.normal(np.array(centre), np.array(sigma), size=(n, 3))
+        p = p[np.all((p >= lo) & (p < hi), axis=1)]
+        out.append(p)
+    p = np.concatenate(out)[:n]
+    q = np.full(n, total_charge / n)
+    return p[:, 0].copy(), p[:, 1].copy(), p[:, 2].copy(), q
+
+
 def gaussian_bunch_torch(grid: Grid, centre, sigma, seed: int, jitter: float = 0.02, device="cuda"):
     """The same Gaussian bunch built with torch on the device (for large serving workloads)."""
     import torch

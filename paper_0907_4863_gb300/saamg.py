@@ -19,7 +19,7 @@ PREC_FP64, PREC_FP32, PREC_FP32_BF16 = 0, 1, 2
 KT_STENCIL_SMOOTH, KT_STENCIL_APPLY, KT_COARSE, KT_TRANSFER, KT_SPGEMM = 0, 1, 2, 3, 4
 KT_STENCIL_RESID, KT_STENCIL_FIRST = 5, 6
 KT_NAMES = ["stencil_smooth", "stencil_apply", "coarse_csr", "transfer", "spgemm", "stencil_resid",
-            "stencil_first"]
+            "stencil_first", "pic"]
 MAX_LEVELS = 16
 
 
@@ -118,6 +118,9 @@ def lib():
         "saamg_set_cheb_degree": [_p, _i],
         "saamg_autotune_cheb_degree": [_p, _p, _i, _i, C.c_double, _p, C.POINTER(_i),
                                        C.POINTER(C.c_double)],
+        "saamg_deposit_cic": [C.POINTER(Grid), _i, _p, _p, _p, _p, _p, _p],
+        "saamg_field_gradient": [_p, _p, _p, _p, _p, _p],
+        "saamg_gather_cic": [C.POINTER(Grid), _p, _p, _p, _i, _p, _p, _p, _p, _p, _p, _p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -294,6 +297,28 @@ def operator_copy(op: Operator, stream=None):
 @_entry
 def operator_apply(op: Operator, x, y, stream=None):
     _check(lib().saamg_operator_apply(op.handle, _ptr(x), _ptr(y), _stream(stream)))
+
+
+@_entry
+def deposit_cic(grid: Grid, x, y, z, q, rho, stream=None):
+    """rho (box) = cloud-in-cell density of the particles (device arrays)."""
+    _check(lib().saamg_deposit_cic(C.byref(grid), int(len(x)), _ptr(x), _ptr(y), _ptr(z),
+                                   _ptr(q), _ptr(rho), _stream(stream)))
+
+
+@_entry
+def field_gradient(op: Operator, phi, ex, ey, ez, stream=None):
+    """E = -grad phi on the box (device arrays)."""
+    _check(lib().saamg_field_gradient(op.handle, _ptr(phi), _ptr(ex), _ptr(ey), _ptr(ez),
+                                      _stream(stream)))
+
+
+@_entry
+def gather_cic(grid: Grid, ex, ey, ez, x, y, z, epx, epy, epz, stream=None):
+    """E at the particles with the deposition's weights (device arrays)."""
+    _check(lib().saamg_gather_cic(C.byref(grid), _ptr(ex), _ptr(ey), _ptr(ez), int(len(x)),
+                                  _ptr(x), _ptr(y), _ptr(z), _ptr(epx), _ptr(epy), _ptr(epz),
+                                  _stream(stream)))
 
 
 @_entry
