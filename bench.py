@@ -283,14 +283,18 @@ def roofline(name, rec, prec, n=256):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
+    if name == "stencil_apply":
+        prec = 0  # the CG product A p is FP64 in every precision mode
     w = 8 if prec == 0 else 4
     if name.startswith("stencil"):
         # flops per row: 13 for A x (7 multiply-adds less one), +1 for b - A x, +4 for the
         # Chebyshev update, +1 for x + d; bytes per row: the compulsory vector traffic
+        # stencil_first alternates the step from x = 0 (2 flops; b in, d and x out) and the
+        # step with c1 = 0 (17 flops; b, x in, d, x out): their mean
         flops = {"stencil_smooth": 19, "stencil_apply": 15, "stencil_resid": 14,
-                 "stencil_first": 17}[name] * per
+                 "stencil_first": 9.5}[name] * per
         nbytes = {"stencil_smooth": 5, "stencil_apply": 2, "stencil_resid": 3,
-                  "stencil_first": 4}[name] * w * per
+                  "stencil_first": 3.5}[name] * w * per
     else:
         # 2 flops per entry; bytes per entry: column index + value (FP32 / BF16 values in
         # the mixed V-cycle; transfers keep FP32 values in both mixed modes)

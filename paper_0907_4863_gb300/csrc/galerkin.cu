@@ -124,10 +124,14 @@ __global__ void __launch_bounds__(128) spgemm_hash_symbolic_k(const int* __restr
 }
 
 // Hash path, numeric.  1) insert every column (lane-parallel); 2) compact the distinct
-// columns and give each its rank in ascending order; 3) accumulate the products one X
-// entry at a time (lanes over the distinct columns of one Y row: no two lanes share a
-// slot), which fixes the summation order; 4) write the row in ascending column order.
-// Per warp: cap keys, cap ranks, cap/2 compacted keys (ints) and cap values (doubles).
+// columns and give each its rank in ascending order; 3) accumulate the products: the warp
+// splits into NG groups of 32/NG lanes, group g takes X's entries g, g + NG, ... in order and
+// its lanes the distinct columns of that entry's Y row, adding into the group's own copy of
+// the value table (no two lanes of a group share a slot, no two groups share a copy), which
+// fixes the summation order; 4) the copies are added in group order and the row is written
+// in ascending column order.  Per warp: cap keys, cap ranks, cap/2 compacted keys (ints)
+// and NG x cap values (doubles).
+template <int NG>
 __global__ void __launch_bounds__(128) spgemm_hash_numeric_k(const int* __restrict__ list,
                                                              int nlist, int logcap, CsrView X,
                                                              CsrView Y,
@@ -135,12 +139,16 @@ __global__ void __launch_bounds__(128) spgemm_hash_numeric_k(const int* __restri
                                                              int* __restrict__ ccol,
                                                              double* __restrict__ cval) {
   extern __shared__ double smem_d[];
+  constexpr int GL = 32 / NG;
   const int lane = threadIdx.x & 31;
+  const int grp = lane / GL, gl = lane % GL;
   const int wib = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
   const int cap = 1 << logcap;
-  double* vals = smem_d + (size_t)wib * cap;
-  int* ibase = reinterpret_cast<int*>(smem_d + (size_t)wpb * cap) + (size_t)wib * (cap * 5 / 2);
+  // copy g starts at g (cap + 1): the same slot of two groups falls in different banks
+  const int cstride = cap + (NG > 1 ? 1 : 0);
+  double* vals = smem_d + (size_t)wib * cstride * NG;
+  int* ibase = reinterpret_cast<int*>(smem_d + (size_t)wpb * cstride * NG) + (size_t)wib * (cap * 5 / 2);
   int* keys = ibase;
   int* rank = ibase + cap;
   int* uniq = ibase + 2 * cap;
@@ -148,10 +156,8 @@ __global__ void __launch_bounds__(128) spgemm_hash_numeric_k(const int* __restri
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int t = gw; t < nlist; t += nw) {
     const int i = list[t];
-    for (int q = lane; q < cap; q += 32) {
-      keys[q] = -1;
-      vals[q] = 0.0;
-    }
+    for (int q = lane; q < cap; q += 32) keys[q] = -1;
+    for (int q = lane; q < cstride * NG; q += 32) vals[q] = 0.0;
     __syncwarp();
     const int p0 = X.rowptr[i], p1 = X.rowptr[i + 1];
     for (int pb = p0; pb < p1; pb += 32) {
@@ -179,12 +185,16 @@ __global__ void __launch_bounds__(128) spgemm_hash_numeric_k(const int* __restri
       rank[q] = r;
     }
     __syncwarp();
-    for (int p = p0; p < p1; ++p) {
-      const int k = X.col[p];
-      const double xv = X.val[p];
-      for (int q = Y.rowptr[k] + lane; q < Y.rowptr[k + 1]; q += 32) {
-        const int slot = hash_find(keys, logcap, Y.col[q]);
-        if (slot >= 0) vals[slot] += xv * Y.val[q];
+    double* mine = vals + (size_t)grp * cstride;
+    for (int pb = p0; pb < p1; pb += NG) {
+      const int p = pb + grp;
+      if (p < p1) {
+        const int k = X.col[p];
+        const double xv = X.val[p];
+        for (int q = Y.rowptr[k] + gl; q < Y.rowptr[k + 1]; q += GL) {
+          const int slot = hash_find(keys, logcap, Y.col[q]);
+          if (slot >= 0) mine[slot] += xv * Y.val[q];
+        }
       }
       __syncwarp();
     }
@@ -192,8 +202,11 @@ __global__ void __launch_bounds__(128) spgemm_hash_numeric_k(const int* __restri
     for (int q = lane; q < cap; q += 32) {
       const int key = keys[q];
       if (key < 0) continue;
+      double v = vals[q];
+#pragma unroll
+      for (int g = 1; g < NG; ++g) v += vals[(size_t)g * cstride + q];
       ccol[base + rank[q]] = key;
-      cval[base + rank[q]] = vals[q];
+      cval[base + rank[q]] = v;
     }
     __syncwarp();
   }
@@ -536,8 +549,9 @@ void bin_rows(int n, const int* xrowptr, const int* nprod, const int* cnt, int m
 }
 
 template <bool NUMERIC>
-void run_class(int c, const int* list, int nl, CsrView X, CsrView Y, const int* crowptr, int* count,
-               int* overflow, int* ccol, double* cval, cudaStream_t s) {
+void run_class(int c, const int* list, int nl, CsrView X, CsrView Y, double yavg,
+               const int* crowptr, int* count, int* overflow, int* ccol, double* cval,
+               cudaStream_t s) {
   if (nl == 0) return;
   KernelTimer kt(SAAMG_KT_SPGEMM, nl, s);
   const int threads = 32 * kSpgemmWarps;
@@ -563,14 +577,24 @@ void run_class(int c, const int* list, int nl, CsrView X, CsrView Y, const int* 
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     spgemm_hash_symbolic_k<<<blocks, threads, sm, s>>>(list, nl, lg, X, Y, count, overflow);
   } else {
-    // 18 bytes per slot and warp: the 4096-slot table runs 2 warps per block (147 KB)
-    const int wpb = cap >= 4096 ? 2 : kSpgemmWarps;
-    const size_t sm = (size_t)wpb * cap * (sizeof(double) + sizeof(int) * 5 / 2);
-    if (sm > 48 * 1024)
-      SAAMG_CUDA(cudaFuncSetAttribute(spgemm_hash_numeric_k,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    // lane groups sized to Y's rows (one group covers a typical row in one pass)
+    const int ng = yavg <= 7.0 ? 4 : (yavg <= 14.0 ? 2 : 1);
+    // 8 NG + 10 bytes per slot and warp; as many warps per block as fit in 200 KB
+    const size_t per_warp = (size_t)(cap + (ng > 1 ? 1 : 0)) * sizeof(double) * ng +
+                            (size_t)cap * sizeof(int) * 5 / 2;
+    const int wpb =
+        (int)std::max<size_t>(1, std::min<size_t>(kSpgemmWarps, (size_t)(200 << 10) / per_warp));
+    const size_t sm = (size_t)wpb * per_warp;
     const int nb = std::max(1, std::min((nl + wpb - 1) / wpb, 152 * 16));
-    spgemm_hash_numeric_k<<<nb, 32 * wpb, sm, s>>>(list, nl, lg, X, Y, crowptr, ccol, cval);
+    auto launch = [&](auto kernel) {
+      if (sm > 48 * 1024)
+        SAAMG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sm));
+      kernel<<<nb, 32 * wpb, sm, s>>>(list, nl, lg, X, Y, crowptr, ccol, cval);
+    };
+    if (ng == 4) launch(spgemm_hash_numeric_k<4>);
+    else if (ng == 2) launch(spgemm_hash_numeric_k<2>);
+    else launch(spgemm_hash_numeric_k<1>);
   }
   SAAMG_LAUNCH();
 }
@@ -589,6 +613,7 @@ void spgemm(const DevCsr& X, const DevCsr& Y, DevCsr& C, cudaStream_t s) {
     C.val.alloc(0, s);
     return;
   }
+  const double yavg = Y.n > 0 ? (double)Y.nnz / Y.n : 0.0;
   Buf<int> nprod, cls, list, cnt, ctl;
   nprod.alloc(n, s);
   cls.alloc(n, s);
@@ -603,7 +628,7 @@ void spgemm(const DevCsr& X, const DevCsr& Y, DevCsr& C, cudaStream_t s) {
   // symbolic: distinct columns per row
   bin_rows(n, X.rowptr.p, nprod.p, nullptr, Y.m, cls.p, list.p, ctl.p, hist, start, s);
   for (int c = 0; c < kClasses; ++c)
-    run_class<false>(c, list.p + start[c], hist[c], view(X), view(Y), nullptr, cnt.p, overflow,
+    run_class<false>(c, list.p + start[c], hist[c], view(X), view(Y), yavg, nullptr, cnt.p, overflow,
                      nullptr, nullptr, s);
   int nover = 0;
   d2h_sync(&nover, overflow, sizeof(int), s);
@@ -617,7 +642,7 @@ void spgemm(const DevCsr& X, const DevCsr& Y, DevCsr& C, cudaStream_t s) {
   // numeric: tables sized from the exact counts
   bin_rows(n, X.rowptr.p, nprod.p, cnt.p, Y.m, cls.p, list.p, ctl.p, hist, start, s);
   for (int c = 0; c < kClasses; ++c)
-    run_class<true>(c, list.p + start[c], hist[c], view(X), view(Y), C.rowptr.p, nullptr, nullptr,
+    run_class<true>(c, list.p + start[c], hist[c], view(X), view(Y), yavg, C.rowptr.p, nullptr, nullptr,
                     C.col.p, C.val.p, s);
 }
 

@@ -529,6 +529,7 @@ void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op) 
                                                        op.table.p, op.table32.p);
     SAAMG_LAUNCH();
   }
+
   SAAMG_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -586,6 +587,8 @@ __device__ double axis_derivative(double h, bool in_m, bool in_p, double pm, dou
   return p0 * (s - t) / (h * s * t);
 }
 
+__device__ __forceinline__ bool line_has(const LineInfo& l, int i) { return i >= l.lo && i <= l.hi; }
+
 // E = -grad phi at the unknowns (warp per chunk, lane per unknown).  Neighbours inside
 // Omega_h use their phi; an outside neighbour is replaced by the wall point at the boundary
 // fraction with phi = 0; on a Robin end plane the z-derivative is the Robin condition's.
@@ -613,10 +616,18 @@ __global__ void field_gradient_k(GeomParams g, const LineInfo* __restrict__ line
     if (ax == 2 && g.zbc == SAAMG_Z_ROBIN && (k == 0 || k == g.nz - 1)) {
       d = (k == 0 ? 1.0 : -1.0) * p0 / dist;
     } else {
-      const int im = i - (ax == 0), jm = j - (ax == 1), km = k - (ax == 2);
-      const int ip = i + (ax == 0), jp = j + (ax == 1), kp = k + (ax == 2);
-      const bool in_m = node_inside(g, im, jm, km);
-      const bool in_p = node_inside(g, ip, jp, kp);
+      // membership from the line records (the classification node_inside produced)
+      bool in_m, in_p;
+      if (ax == 0) {
+        in_m = i - 1 >= me.lo;
+        in_p = i + 1 <= me.hi;
+      } else {
+        const int lstride = ax == 1 ? 1 : g.ny;
+        const bool has_m = ax == 1 ? j > 0 : k > 0;
+        const bool has_p = ax == 1 ? j < g.ny - 1 : k < g.nz - 1;
+        in_m = has_m && line_has(lines[L - lstride], i);
+        in_p = has_p && line_has(lines[L + lstride], i);
+      }
       const double pm = in_m ? phi[q - stride[ax]] : 0.0;
       const double pp = in_p ? phi[q + stride[ax]] : 0.0;
       const double t = in_m ? 1.0 : boundary_fraction(g, i, j, k, 2 * ax);
