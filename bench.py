@@ -34,7 +34,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 f
 TRAFFIC_BYTES = {("stencil_smooth", 0, 256): 285.69e6}
 # kernel timing classes of the solve phase (one kernel template each)
 SOLVE_CLASSES = ("stencil_smooth", "stencil_apply", "stencil_resid", "stencil_first",
-                 "coarse_csr", "transfer")
+                 "coarse_csr", "transfer", "prolong0")
 
 
 def parse():
@@ -286,7 +286,11 @@ def roofline(name, rec, prec, n=256):
     if name == "stencil_apply":
         prec = 0  # the CG product A p is FP64 in every precision mode
     w = 8 if prec == 0 else 4
-    if name.startswith("stencil"):
+    if name == "prolong0":
+        # matrix-free level-0 prolongation (FP32 V-cycle): per row the aggregate index and
+        # x in / x out; 2 flops per coupling of the 7-point star plus the update
+        flops, nbytes = 16 * per, (4 + 2 * w) * per
+    elif name.startswith("stencil"):
         # flops per row: 13 for A x (7 multiply-adds less one), +1 for b - A x, +4 for the
         # Chebyshev update, +1 for x + d; bytes per row: the compulsory vector traffic
         # stencil_first alternates the step from x = 0 (2 flops; b in, d and x out) and the
@@ -304,7 +308,10 @@ def roofline(name, rec, prec, n=256):
     out = {"kernel": name, "avg_launch_us": avg_s * 1e6, "launches": launches,
            "traffic": TRAFFIC_BYTES.get((name, prec, n)),
            "algorithmic_bytes_per_launch": nbytes, "algorithmic_flops_per_launch": flops}
-    if prec == 0:
+    # FP64 stencil passes are bound by FP64 issue; the FP64 sparse passes move 12 B per
+    # 2 flops, past the FP64 ridge of this part (1.26 TFLOP/s / 6.66 TB/s = 0.19 flop/B):
+    # HBM is their tighter roofline, as for every FP32 / BF16 pass
+    if prec == 0 and (name.startswith("stencil") or name == "prolong0"):
         ach = flops / avg_s / 1e12
         out.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": ach / FP64_PEAK_TFLOPS,

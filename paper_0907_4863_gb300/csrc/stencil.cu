@@ -257,7 +257,7 @@ template <class T>
 void stencil_prolong(const StencilDev<T>& S, const int* agg, T omega, const T* v, T* y,
                      cudaStream_t s) {
   if (S.nchunks == 0) return;
-  KernelTimer kt(SAAMG_KT_TRANSFER, S.n, s);
+  KernelTimer kt(SAAMG_KT_PROLONG0, S.n, s);
   const long long need = ((long long)S.nchunks + 8 * kChunks<T>() - 1) / (8 * kChunks<T>());
   const int blocks = (int)(need < 152 * 16 ? need : 152 * 16);
   stencil_k<T, ST_PROLONG, kChunks<T>()><<<blocks, 256, 0, s>>>(

@@ -36,8 +36,12 @@ def test_fp32_stencil_and_sparse_classes_are_reported_against_hbm(bench):
     assert r["algorithmic_bytes_per_launch"] == pytest.approx(6e6)
     r = bench.roofline("transfer", (1.0, 10, 10_000_000), 2)  # transfers keep FP32 values
     assert r["algorithmic_bytes_per_launch"] == pytest.approx(8e6)
+    # FP64 sparse passes sit past the FP64 ridge: reported against HBM, 12 B per entry
     r = bench.roofline("coarse_csr", (1.0, 10, 10_000_000), 0)
-    assert r["bound"] == "alu" and r["algorithmic_flops_per_launch"] == pytest.approx(2e6)
+    assert r["bound"] == "hbm" and r["algorithmic_bytes_per_launch"] == pytest.approx(12e6)
+    assert r["algorithmic_flops_per_launch"] == pytest.approx(2e6)
+    # the CG product is FP64 in every precision mode
+    assert bench.roofline("stencil_apply", (1.0, 10, 10_000_000), 1)["bound"] == "alu"
 
 
 def test_empty_class_has_no_roofline(bench):
