@@ -34,7 +34,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 f
 TRAFFIC_BYTES = {("stencil_smooth", 0, 256): 285.69e6}
 # kernel timing classes of the solve phase (one kernel template each)
 SOLVE_CLASSES = ("stencil_smooth", "stencil_apply", "stencil_resid", "stencil_first",
-                 "coarse_csr", "transfer", "prolong0")
+                 "coarse_csr", "coarse_deep", "transfer", "transfer_deep", "prolong0")
 
 
 def parse():
@@ -57,6 +57,22 @@ def parse():
 def workload(n):
     w = I.pipe_workload(n, I.LINEAR)
     return w
+
+
+def max_over_ranks(x, world, device):
+    """The slowest rank's value (replicas: the job ends with its last rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, seconds):
+    """Solves per second of the whole job: every replica completes `steps` solves."""
+    return world * steps / seconds
 
 
 def dist_env():
@@ -180,18 +196,13 @@ def run_ours(args):
     clk = clocks.stop()
     S.kernel_timing(False)
     ktime = {S.KT_NAMES[c]: S.kernel_timing_read(c) for c in range(len(S.KT_NAMES))}
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     timed = infos[args.warmup:]
     iters = [i["iters"] for i, _ in timed]
     relres = max(i["relres_true"] for i, _ in timed)
     assert all(i["converged"] == 1 for i, _ in timed), "a timed solve did not converge"
     hinfo = timed[-1][1]
-    value = world * args.steps / (ms / 1e3)
+    value = whole_job_rate(world, args.steps, ms / 1e3)
 
     # --- roofline of the dominant kernel (live, CUDA events on the launching stream).  Each
     # solve-phase class is one kernel template; the sparse products of the setup are several
@@ -220,13 +231,8 @@ def run_ours(args):
     for k in range(args.steps):
         e2e_step(k)
     barrier()
-    t_e2e = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": world * args.steps / t_e2e, "unit": UNIT,
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+    e2e = {"value": whole_job_rate(world, args.steps, t_e2e), "unit": UNIT,
            "h2d_bytes_per_step": 2 * nbox * 8, "d2h_bytes_per_step": nbox * 8}
 
     extra = {}
@@ -236,6 +242,7 @@ def run_ours(args):
         extra["aggregation_cubes_vs_mis2"] = aggregation_leg(S, torch, args)
         extra["coarse_gauss_seidel_vs_lu"] = coarse_solver_leg(S, torch, args)
         extra["pic_transfers"] = pic_leg(S, torch, args)
+        extra["grid_sizes"] = sizes_leg(S, torch)
     del rhs, phis
     torch.cuda.empty_cache()
     if not args.no_batched:
@@ -303,7 +310,7 @@ def roofline(name, rec, prec, n=256):
         # 2 flops per entry; bytes per entry: column index + value (FP32 / BF16 values in
         # the mixed V-cycle; transfers keep FP32 values in both mixed modes)
         flops = 2 * per
-        vbytes = 8 if prec == 0 else (2 if (prec == 2 and name == "coarse_csr") else 4)
+        vbytes = 8 if prec == 0 else (2 if (prec == 2 and name.startswith("coarse")) else 4)
         nbytes = (4 + vbytes) * per
     out = {"kernel": name, "avg_launch_us": avg_s * 1e6, "launches": launches,
            "traffic": TRAFFIC_BYTES.get((name, prec, n)),
@@ -527,6 +534,40 @@ def pic_leg(S, torch, args, nparticles=10_000_000, reps=5):
             "gradient_gbs": (nbox * 8 * 4) / (t_grad / 1e3) / 1e9,  # phi read, 3 fields written
             "gather_ms": t_gat, "gather_particles_per_s": nparticles / (t_gat / 1e3),
             "gather_gbs": (nparticles * 48) / (t_gat / 1e3) / 1e9}  # x, y, z in; 3 fields out
+
+
+def sizes_leg(S, torch, sizes=(128, 256, 512)):
+    """The elliptic-pipe workload at 128^3, 256^3 and 512^3 (linear, rtol 1e-8, coarse <= 4096):
+    hierarchy, CG iterations (grid independence, Sec. 5), setup / solve / full-pipeline time,
+    FP64 and the FP32 V-cycle.  One warm-up pass, then one timed pass per size."""
+    out = {}
+    for n in sizes:
+        w = workload(n)
+        dom, grid = S.make_domain(w.domain), S.make_grid(w.grid)
+        rho = I.gaussian_bunch_torch(w.grid, w.centre, w.sigma, 31)
+        for pname, prec in (("fp64", 0), ("fp32", 1)):
+            params = S.params_default(max_coarse=4096, precision=prec, beta_rule=1 if prec else 0)
+            for rep in range(2):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                op = S.build_operator(dom, grid, w.mode)
+                h = S.setup(op, params)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                phi = torch.zeros_like(rho)
+                info = S.solve(h, rho, phi, rtol=RTOL)
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                hi = h.info()
+                h.free()
+                op.free()
+            out[f"{n}^3_{pname}"] = {
+                "unknowns": hi["n"][0], "levels": hi["n"], "iters": info["iters"],
+                "relres_true": info["relres_true"], "build_setup_ms": 1e3 * (t1 - t0),
+                "solve_ms": 1e3 * (t2 - t1), "full_pipeline_solves_per_s": 1.0 / (t2 - t0)}
+        del rho
+        torch.cuda.empty_cache()
+    return out
 
 
 def batched_leg(S, torch):

@@ -312,14 +312,16 @@ saamg_status saamg_gather_cic(const saamg_grid *grid, const double *ex, const do
 typedef enum {
   SAAMG_KT_STENCIL_SMOOTH = 0, /* level-0 Chebyshev step fused with the residual (full step) */
   SAAMG_KT_STENCIL_APPLY = 1,  /* level-0 A x, and A p with p'Ap in PCG */
-  SAAMG_KT_COARSE = 2,         /* smoother / residual on levels >= 1 (rows = matrix entries) */
-  SAAMG_KT_TRANSFER = 3,       /* CSR restriction R r and prolongation x += P v (entries) */
+  SAAMG_KT_COARSE = 2,         /* smoother / residual on level 1 (rows = matrix entries) */
+  SAAMG_KT_TRANSFER = 3,       /* CSR restriction / prolongation between levels 0 and 1 (entries) */
   SAAMG_KT_SPGEMM = 4,         /* sparse products of the setup */
   SAAMG_KT_STENCIL_RESID = 5,  /* level-0 residual b - A x */
   SAAMG_KT_STENCIL_FIRST = 6,  /* first Chebyshev steps on level 0 (from zero, or c1 = 0) */
   SAAMG_KT_PIC = 7,            /* CIC deposition and gather (rows = particles) */
   SAAMG_KT_PROLONG0 = 8,       /* matrix-free level-0 prolongation of the FP32 V-cycle */
-  SAAMG_KT_COUNT = 9
+  SAAMG_KT_COARSE_DEEP = 9,    /* SAAMG_KT_COARSE on levels >= 2 */
+  SAAMG_KT_TRANSFER_DEEP = 10, /* SAAMG_KT_TRANSFER between levels >= 1 */
+  SAAMG_KT_COUNT = 11
 } saamg_kernel_class;
 
 /* Number of kernels this library has launched in the calling process. */

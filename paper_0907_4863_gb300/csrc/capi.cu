@@ -501,7 +501,7 @@ void level_csr<double>(saamg_hierarchy* h, int l, int mode, const double* x, dou
                        const double* b, double* d, double c1, double c2, cudaStream_t s) {
   Level& L = *h->lev[l];
   sell_apply<double, double>(mode, L.As, L.As.val.p, x, y, b, d, L.invd.p, c1, c2, s,
-                             SAAMG_KT_COARSE);
+                             l == 1 ? SAAMG_KT_COARSE : SAAMG_KT_COARSE_DEEP);
 }
 
 template <>
@@ -510,10 +510,10 @@ void level_csr<float>(saamg_hierarchy* h, int l, int mode, const float* x, float
   Level& L = *h->lev[l];
   if (h->prm.precision == SAAMG_PREC_FP32)
     sell_apply<float, float>(mode, L.As, L.As.val32.p, x, y, b, d, L.invd32.p, c1, c2, s,
-                             SAAMG_KT_COARSE);
+                             l == 1 ? SAAMG_KT_COARSE : SAAMG_KT_COARSE_DEEP);
   else
     sell_apply<float, __nv_bfloat16>(mode, L.As, L.As.val16.p, x, y, b, d, L.invd32.p, c1, c2,
-                                     s, SAAMG_KT_COARSE);
+                                     s, l == 1 ? SAAMG_KT_COARSE : SAAMG_KT_COARSE_DEEP);
 }
 
 template <class T>
@@ -526,7 +526,7 @@ void transfer<double>(saamg_hierarchy* h, int l, bool restrict_, const double* x
   const DevCsr& M = restrict_ ? L.R : L.P;
   csr_apply<double, double>(restrict_ ? CSR_SPMV : CSR_ADD, M.n, M.rowptr.p, M.col.p, M.val.p,
                             M.n ? (double)M.nnz / M.n : 0.0, x, y, nullptr, nullptr, nullptr, 0.0,
-                            0.0, nullptr, s, SAAMG_KT_TRANSFER);
+                            0.0, nullptr, s, l == 0 ? SAAMG_KT_TRANSFER : SAAMG_KT_TRANSFER_DEEP);
 }
 
 template <>
@@ -544,7 +544,7 @@ void transfer<float>(saamg_hierarchy* h, int l, bool restrict_, const float* x, 
   const float* v = restrict_ ? L.R32.p : L.P32.p;
   csr_apply<float, float>(restrict_ ? CSR_SPMV : CSR_ADD, M.n, M.rowptr.p, M.col.p, v,
                           M.n ? (double)M.nnz / M.n : 0.0, x, y, nullptr, nullptr, nullptr, 0.0f,
-                          0.0f, nullptr, s, SAAMG_KT_TRANSFER);
+                          0.0f, nullptr, s, l == 0 ? SAAMG_KT_TRANSFER : SAAMG_KT_TRANSFER_DEEP);
 }
 
 template <class T>

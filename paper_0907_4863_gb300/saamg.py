@@ -19,7 +19,7 @@ PREC_FP64, PREC_FP32, PREC_FP32_BF16 = 0, 1, 2
 KT_STENCIL_SMOOTH, KT_STENCIL_APPLY, KT_COARSE, KT_TRANSFER, KT_SPGEMM = 0, 1, 2, 3, 4
 KT_STENCIL_RESID, KT_STENCIL_FIRST = 5, 6
 KT_NAMES = ["stencil_smooth", "stencil_apply", "coarse_csr", "transfer", "spgemm", "stencil_resid",
-            "stencil_first", "pic", "prolong0"]
+            "stencil_first", "pic", "prolong0", "coarse_deep", "transfer_deep"]
 MAX_LEVELS = 16
 
 

@@ -46,3 +46,38 @@ def test_fp32_stencil_and_sparse_classes_are_reported_against_hbm(bench):
 
 def test_empty_class_has_no_roofline(bench):
     assert bench.roofline("transfer", (0.0, 0, 0), 0) is None
+
+
+def _replica(rank, world, port, local_seconds, out):
+    import importlib.util
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    t = b.max_over_ranks(local_seconds[rank], world, "cpu")
+    out[rank] = (t, b.whole_job_rate(world, 5, t))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_replicas_report_the_slowest_rank_over_gloo():
+    """Two gloo ranks on the CPU: every rank gets the maximum of the local times, and the
+    whole-job rate counts the solves of all replicas over that time."""
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s_:
+        s_.bind(("127.0.0.1", 0))
+        port = s_.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    local = [0.8, 1.25]
+    ps = [ctx.Process(target=_replica, args=(r, 2, port, local, out)) for r in range(2)]
+    for p in ps:
+        p.start()
+    for p in ps:
+        p.join(120)
+        assert p.exitcode == 0
+    for r in range(2):
+        assert out[r][0] == 1.25 and out[r][1] == pytest.approx(2 * 5 / 1.25)
