@@ -1,7 +1,8 @@
 // Coarsest-level direct solver (Sec. 3.2, "Coarse level solver"; Algorithm 1,
-// DirectSolve).  The paper factors A_L with KLU; here A_L is small (<= max_coarse) and
-// is factored densely in FP64 with partial pivoting (largest |a_ik|, lowest row on ties),
-// then inverted once so that every V-cycle applies x = A_L^-1 b as one dense product.
+// DirectSolve).  The paper factors A_L with KLU; here A_L is small (<= max_coarse) and its
+// inverse is formed once, densely in FP64, by Gauss-Jordan elimination with the pivoting of
+// an LU with partial pivoting (largest |a_ik|, lowest row on ties), so that every V-cycle
+// applies x = A_L^-1 b as one dense product.
 // All dense arrays are column-major: a(i, j) at [j * n + i].
 #include "coarse.cuh"
 
@@ -16,100 +17,169 @@ __global__ void densify_k(int n, const int* __restrict__ rowptr, const int* __re
   for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) a[(size_t)col[p] * n + i] = val[p];
 }
 
-// Step k, one block: pivot search in column k, row swap k <-> p over all columns,
-// multipliers l_ik = a_ik / a_kk stored below the diagonal.
-__global__ void lu_pivot_k(int n, int k, double* __restrict__ a, int* __restrict__ perm,
-                           int* __restrict__ err) {
-  __shared__ double bv[1024];
-  __shared__ int bi[1024];
+// --- explicit inverse by Gauss-Jordan elimination ------------------------------------
+// Partial pivoting as in the LU: at step k the pivot is the row i >= k of largest |a_ik|
+// (lowest row on ties); rows k and p are exchanged and column k is eliminated from every
+// other row, which leaves (P A)^-1 in place; the columns are unscrambled at the end.
+// One launch per step: each block owns a range of columns, so all writes of a step stay in
+// the writer's own columns.  Column k is read from a copy (made in the previous step by the
+// owner of that column, together with its pivot row), so no block reads a column that
+// another block is writing.
+
+// Block argmax of |col[i]| over i in [lo, n), lowest index on ties.
+__device__ void block_argmax(const double* __restrict__ col, int lo, int n, double* sv, int* si,
+                             double& best_out, int& idx_out) {
   double best = -1.0;
-  int bidx = n;
-  for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-    double v = fabs(a[(size_t)k * n + i]);
-    if (v > best || (v == best && i < bidx)) {
+  int bi = n;
+  for (int i = lo + threadIdx.x; i < n; i += blockDim.x) {
+    const double v = fabs(col[i]);
+    if (v > best) {
       best = v;
-      bidx = i;
+      bi = i;
     }
   }
-  bv[threadIdx.x] = best;
-  bi[threadIdx.x] = bidx;
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) {
-      double v = bv[threadIdx.x + w];
-      int i = bi[threadIdx.x + w];
-      if (v > bv[threadIdx.x] || (v == bv[threadIdx.x] && i < bi[threadIdx.x])) {
-        bv[threadIdx.x] = v;
-        bi[threadIdx.x] = i;
+      const double v = sv[threadIdx.x + w];
+      const int i = si[threadIdx.x + w];
+      if (v > sv[threadIdx.x] || (v == sv[threadIdx.x] && i < si[threadIdx.x])) {
+        sv[threadIdx.x] = v;
+        si[threadIdx.x] = i;
       }
     }
     __syncthreads();
   }
-  const int p = bi[0];
-  if (!(bv[0] > 0.0)) {
-    if (threadIdx.x == 0) atomicOr(err, 1);
-    return;
+  best_out = sv[0];
+  idx_out = si[0];
+}
+
+constexpr int kGjThreads = 256;
+constexpr int kGjMaxCols = 64;  // columns per block
+
+// step 0: pivot of column 0 and its copy
+__global__ void __launch_bounds__(kGjThreads) gj_first_k(int n, const double* __restrict__ a,
+                                                         double* __restrict__ colk,
+                                                         int* __restrict__ pivrow,
+                                                         int* __restrict__ err) {
+  __shared__ double sv[kGjThreads];
+  __shared__ int si[kGjThreads];
+  double best;
+  int p;
+  block_argmax(a, 0, n, sv, si, best, p);
+  if (threadIdx.x == 0) {
+    // a zero or NaN column: flagged, and the pivot index stays a valid row
+    if (!(best > 0.0)) {
+      atomicOr(err, 1);
+      p = 0;
+    }
+    pivrow[0] = p;
   }
-  if (p != k) {
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      double t = a[(size_t)j * n + k];
-      a[(size_t)j * n + k] = a[(size_t)j * n + p];
-      a[(size_t)j * n + p] = t;
-    }
-    if (threadIdx.x == 0) {
-      int t = perm[k];
-      perm[k] = perm[p];
-      perm[p] = t;
-    }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) colk[i] = a[i];
+}
+
+__global__ void __launch_bounds__(kGjThreads) gj_step_k(int n, int k, int cpb,
+                                                        double* __restrict__ a,
+                                                        const double* __restrict__ colk,
+                                                        double* __restrict__ colk_next,
+                                                        int* __restrict__ pivrow,
+                                                        int* __restrict__ err) {
+  __shared__ double rk[kGjMaxCols], rp[kGjMaxCols];
+  __shared__ double sv[kGjThreads / 32];
+  __shared__ int si[kGjThreads / 32];
+  const int p = pivrow[k];
+  const double piv = colk[p];  // a_kk after the exchange
+  const double ip = 1.0 / piv;
+  const int c0 = blockIdx.x * cpb, c1 = min(n, c0 + cpb);
+  for (int t = threadIdx.x; t < c1 - c0; t += blockDim.x) {
+    const size_t o = (size_t)(c0 + t) * n;
+    rk[t] = a[o + k];
+    rp[t] = a[o + p];
   }
   __syncthreads();
-  const double piv = a[(size_t)k * n + k];
-  for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) a[(size_t)k * n + i] /= piv;
-}
-
-// Step k: trailing update a_ij -= l_ik a_kj for i, j > k.
-__global__ void lu_update_k(int n, int k, double* __restrict__ a) {
-  const int m = n - k - 1;
-  const int i = k + 1 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double lik = a[(size_t)k * n + i];
-  for (int j = k + 1 + blockIdx.y; j < n; j += gridDim.y) a[(size_t)j * n + i] -= lik * a[(size_t)j * n + k];
-  (void)m;
-}
-
-__global__ void perm_init_k(int n, int* perm) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) perm[i] = i;
-}
-
-// Warp per column c of A^-1: solve L U x = P e_c (forward then backward substitution,
-// column-oriented, lanes over rows).  Output column-major.
-__global__ void lu_inverse_k(int n, const double* __restrict__ lu, const int* __restrict__ perm,
-                             double* __restrict__ inv) {
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (c >= n) return;
-  double* x = inv + (size_t)c * n;
-  for (int i = lane; i < n; i += 32) x[i] = (perm[i] == c) ? 1.0 : 0.0;
-  __syncwarp();
-  for (int j = 0; j < n; ++j) {
-    const double xj = x[j];
-    __syncwarp();
-    if (xj != 0.0)
-      for (int i = j + 1 + lane; i < n; i += 32) x[i] -= lu[(size_t)j * n + i] * xj;
-    __syncwarp();
-  }
-  for (int j = n - 1; j >= 0; --j) {
-    double xj = 0.0;
-    if (lane == 0) {
-      xj = x[j] / lu[(size_t)j * n + j];
-      x[j] = xj;
+  // the owner of column k + 1 updates it first, copies it for the next step and finds its
+  // pivot on the way (largest |a_i,k+1| over i > k, lowest row on ties)
+  const int kn = k + 1;
+  const bool owner = kn < n && kn >= c0 && kn < c1;
+  double best = -1.0;
+  int bi = n;
+  for (int tt = 0; tt < c1 - c0; ++tt) {
+    const int t = owner ? (tt == 0 ? kn - c0 : (tt <= kn - c0 ? tt - 1 : tt)) : tt;
+    const int j = c0 + t;
+    const double r = rp[t] * ip;  // the new row k (row p before the exchange)
+    double* col = a + (size_t)j * n;
+    const bool next = j == kn;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double ci = i == k ? colk[p] : (i == p ? colk[k] : colk[i]);  // column k, exchanged
+      double v;
+      if (j == k) v = i == k ? ip : -ci * ip;
+      else if (i == k) v = r;
+      else v = (i == p ? rk[t] : col[i]) - ci * r;
+      col[i] = v;
+      if (next) {
+        colk_next[i] = v;
+        const double av = fabs(v);
+        if (i > k && av > best) {  // ascending i per thread: the first maximum is kept
+          best = av;
+          bi = i;
+        }
+      }
     }
-    xj = __shfl_sync(0xffffffffu, xj, 0);
-    __syncwarp();
-    if (xj != 0.0)
-      for (int i = lane; i < j; i += 32) x[i] -= lu[(size_t)j * n + i] * xj;
-    __syncwarp();
+  }
+  if (owner) {
+    // block argmax of (best, bi), lowest index on ties
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    if ((threadIdx.x & 31) == 0) {
+      sv[threadIdx.x >> 5] = best;
+      si[threadIdx.x >> 5] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double bb = sv[0];
+      int ii = si[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (sv[w] > bb || (sv[w] == bb && si[w] < ii)) {
+          bb = sv[w];
+          ii = si[w];
+        }
+      if (!(bb > 0.0)) {  // a zero or NaN column: flagged, the pivot stays a valid row
+        atomicOr(err, 1);
+        ii = kn;
+      }
+      pivrow[kn] = ii;
+    }
+  }
+}
+
+// inverse(:, j) = work(:, q_j), q: the exchanges undone in reverse order (one thread)
+__global__ void gj_perm_k(int n, const int* __restrict__ pivrow, int* __restrict__ q) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int j = 0; j < n; ++j) q[j] = j;
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = pivrow[k];
+    const int t = q[k];
+    q[k] = q[p];
+    q[p] = t;
+  }
+}
+
+__global__ void gj_gather_k(int n, const double* __restrict__ w, const int* __restrict__ q,
+                            double* __restrict__ inv) {
+  const size_t total = (size_t)n * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t j = e / n, i = e - j * n;
+    inv[e] = w[(size_t)q[j] * n + i];
   }
 }
 
@@ -290,33 +360,36 @@ void coarse_factor(const DevCsr& A, CoarseSolver& cs, cudaStream_t s) {
   cs.n = n;
   cs.inv.alloc((size_t)n * n, s);
   if (n == 0) return;
-  Buf<double> lu;
-  Buf<int> perm, err;
-  lu.alloc((size_t)n * n, s);
-  perm.alloc(n, s);
+  Buf<double> w, colk;
+  Buf<int> pivrow, q, err;
+  w.alloc((size_t)n * n, s);
+  colk.alloc(2 * (size_t)n, s);
+  pivrow.alloc(n, s);
+  q.alloc(n, s);
   err.alloc(1, s);
-  SAAMG_CUDA(cudaMemsetAsync(lu.p, 0, sizeof(double) * (size_t)n * n, s));
+  SAAMG_CUDA(cudaMemsetAsync(w.p, 0, sizeof(double) * (size_t)n * n, s));
   fill_int(err.p, 0, 1, s);
-  densify_k<<<(n + 255) / 256, 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, lu.p);
+  densify_k<<<(n + 255) / 256, 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, w.p);
   SAAMG_LAUNCH();
-  perm_init_k<<<(n + 255) / 256, 256, 0, s>>>(n, perm.p);
+  gj_first_k<<<1, kGjThreads, 0, s>>>(n, w.p, colk.p, pivrow.p, err.p);
   SAAMG_LAUNCH();
+  // about two blocks per SM, at most kGjMaxCols columns each
+  const int cpb = std::min(kGjMaxCols, std::max(1, (n + 303) / 304));
+  const int blocks = (n + cpb - 1) / cpb;
   for (int k = 0; k < n; ++k) {
-    lu_pivot_k<<<1, 1024, 0, s>>>(n, k, lu.p, perm.p, err.p);
+    gj_step_k<<<blocks, kGjThreads, 0, s>>>(n, k, cpb, w.p, colk.p + (size_t)(k & 1) * n,
+                                            colk.p + (size_t)((k + 1) & 1) * n, pivrow.p, err.p);
     SAAMG_LAUNCH();
-    int m = n - k - 1;
-    if (m > 0) {
-      dim3 grid((m + 127) / 128, m < 64 ? m : 64);
-      lu_update_k<<<grid, 128, 0, s>>>(n, k, lu.p);
-      SAAMG_LAUNCH();
-    }
   }
+  gj_perm_k<<<1, 32, 0, s>>>(n, pivrow.p, q.p);
+  SAAMG_LAUNCH();
+  const size_t total = (size_t)n * n;
+  gj_gather_k<<<(int)std::min<size_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(n, w.p, q.p,
+                                                                                  cs.inv.p);
+  SAAMG_LAUNCH();
   int herr = 0;
   d2h_sync(&herr, err.p, sizeof(int), s);
-  if (herr) fail(SAAMG_NUMERICAL, "zero pivot in the coarse LU");
-  lu_inverse_k<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, lu.p, perm.p, cs.inv.p);
-  SAAMG_LAUNCH();
-  SAAMG_CUDA(cudaStreamSynchronize(s));
+  if (herr) fail(SAAMG_NUMERICAL, "zero pivot in the coarse factorisation");
 }
 
 template <class TV>
