@@ -418,7 +418,18 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
     alloc_level_vectors(h, L, q == 0, s);
     const bool f64 = !mixed(h), f32 = prm.precision == SAAMG_PREC_FP32;
     const bool bf16 = prm.precision == SAAMG_PREC_FP32_BF16;
-    if (q >= 1 && q < nl - 1) sell_from_csr(L.A, L.As, f64, f32, bf16, s);
+    // SELL for the large smoothed levels; a small level runs on CSR with wide row groups
+    if (q >= 1 && q < nl - 1 && L.n >= kSellMinRows) {
+      sell_from_csr(L.A, L.As, f64, f32, bf16, s);
+    } else if (q >= 1 && q < nl - 1) {
+      if (f32) {
+        L.A.val32.alloc(L.A.nnz, s);
+        to_float(L.A.val.p, L.A.val32.p, L.A.nnz, s);
+      } else if (bf16) {
+        L.A.val16.alloc(L.A.nnz, s);
+        to_bf16(L.A.val.p, L.A.val16.p, L.A.nnz, s);
+      }
+    }
     if (!f64 && q < nl - 1) {
       L.P32.alloc(L.P.nnz, s);
       to_float(L.P.val.p, L.P32.p, L.P.nnz, s);
@@ -500,20 +511,33 @@ template <>
 void level_csr<double>(saamg_hierarchy* h, int l, int mode, const double* x, double* y,
                        const double* b, double* d, double c1, double c2, cudaStream_t s) {
   Level& L = *h->lev[l];
-  sell_apply<double, double>(mode, L.As, L.As.val.p, x, y, b, d, L.invd.p, c1, c2, s,
-                             l == 1 ? SAAMG_KT_COARSE : SAAMG_KT_COARSE_DEEP);
+  const int kc = l == 1 ? SAAMG_KT_COARSE : SAAMG_KT_COARSE_DEEP;
+  if (L.As.n > 0)
+    sell_apply<double, double>(mode, L.As, L.As.val.p, x, y, b, d, L.invd.p, c1, c2, s, kc);
+  else
+    csr_apply<double, double>(mode, L.n, L.A.rowptr.p, L.A.col.p, L.A.val.p, L.avg, x, y, b, d,
+                              L.invd.p, c1, c2, nullptr, s, kc);
 }
 
 template <>
 void level_csr<float>(saamg_hierarchy* h, int l, int mode, const float* x, float* y,
                       const float* b, float* d, float c1, float c2, cudaStream_t s) {
   Level& L = *h->lev[l];
-  if (h->prm.precision == SAAMG_PREC_FP32)
-    sell_apply<float, float>(mode, L.As, L.As.val32.p, x, y, b, d, L.invd32.p, c1, c2, s,
-                             l == 1 ? SAAMG_KT_COARSE : SAAMG_KT_COARSE_DEEP);
-  else
-    sell_apply<float, __nv_bfloat16>(mode, L.As, L.As.val16.p, x, y, b, d, L.invd32.p, c1, c2,
-                                     s, l == 1 ? SAAMG_KT_COARSE : SAAMG_KT_COARSE_DEEP);
+  const int kc = l == 1 ? SAAMG_KT_COARSE : SAAMG_KT_COARSE_DEEP;
+  const bool fp32 = h->prm.precision == SAAMG_PREC_FP32;
+  if (L.As.n > 0) {
+    if (fp32)
+      sell_apply<float, float>(mode, L.As, L.As.val32.p, x, y, b, d, L.invd32.p, c1, c2, s, kc);
+    else
+      sell_apply<float, __nv_bfloat16>(mode, L.As, L.As.val16.p, x, y, b, d, L.invd32.p, c1, c2,
+                                       s, kc);
+  } else if (fp32) {
+    csr_apply<float, float>(mode, L.n, L.A.rowptr.p, L.A.col.p, L.A.val32.p, L.avg, x, y, b, d,
+                            L.invd32.p, c1, c2, nullptr, s, kc);
+  } else {
+    csr_apply<float, __nv_bfloat16>(mode, L.n, L.A.rowptr.p, L.A.col.p, L.A.val16.p, L.avg, x,
+                                    y, b, d, L.invd32.p, c1, c2, nullptr, s, kc);
+  }
 }
 
 template <class T>

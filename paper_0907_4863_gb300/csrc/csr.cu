@@ -165,32 +165,34 @@ void csr_apply(int mode, int n, const int* rowptr, const int* col, const TM* val
   }
   // timing unit of the sparse-matrix classes: matrix entries
   KernelTimer kt(kclass, std::llround(avg_nnz * n), s);
-  // FP64 shuffle-adds are as costly as the row's multiply-adds on this part: few lanes per
-  // row for double vectors; FP32 can afford wider groups for better coalescing.
-  if (sizeof(TV) == 8) {
-    if (avg_nnz <= 10.0)
-      launch_g<TV, TM, 2>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s,
-                              xscale);
-    else if (avg_nnz <= 48.0)
-      launch_g<TV, TM, 4>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s,
-                              xscale);
-    else
-      launch_g<TV, TM, 8>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s,
-                              xscale);
-  } else {
-    // FP32: groups sized so that a lane holds about four entries of its row
-    if (avg_nnz <= 6.0)
-      launch_g<TV, TM, 2>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s,
-                              xscale);
-    else if (avg_nnz <= 20.0)
-      launch_g<TV, TM, 4>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s,
-                              xscale);
-    else if (avg_nnz <= 64.0)
-      launch_g<TV, TM, 8>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s,
-                              xscale);
-    else
+  // Lanes per row: FP64 shuffle-adds cost as much as the row's multiply-adds on this part, so
+  // double vectors use few lanes (FP32 can afford wider groups for better coalescing) -- but
+  // a small level (few rows, long rows: the deep levels of the hierarchy) needs wider groups
+  // to fill the GPU at all: enough lanes for ~150 k threads, never more than the row length.
+  int g = sizeof(TV) == 8 ? (avg_nnz <= 10.0 ? 2 : (avg_nnz <= 48.0 ? 4 : 8))
+                          : (avg_nnz <= 6.0 ? 2 : (avg_nnz <= 20.0 ? 4 : (avg_nnz <= 64.0 ? 8 : 16)));
+  int gpar = 1;
+  while (gpar < 32 && (long long)n * gpar < 150000) gpar <<= 1;
+  int glen = 1;
+  while (glen < 32 && glen < avg_nnz) glen <<= 1;
+  g = std::max(g, std::min(gpar, glen));
+  switch (g) {
+    case 2:
+      launch_g<TV, TM, 2>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s, xscale);
+      break;
+    case 4:
+      launch_g<TV, TM, 4>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s, xscale);
+      break;
+    case 8:
+      launch_g<TV, TM, 8>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s, xscale);
+      break;
+    case 16:
       launch_g<TV, TM, 16>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s,
-                              xscale);
+                           xscale);
+      break;
+    default:
+      launch_g<TV, TM, 32>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s,
+                           xscale);
   }
 }
 

@@ -16,6 +16,9 @@
 namespace saamg {
 
 constexpr int kSellWindow = 512;
+// smallest level stored as SELL: below it one thread per row leaves most of the GPU idle and
+// the CSR kernel with wide row groups is faster
+constexpr int kSellMinRows = 100000;
 
 struct DevSell {
   int n = 0, m = 0, nslices = 0;
