@@ -372,6 +372,7 @@ def extra_legs(S, torch, w, dom, grid, rho, args):
             "iters": its[-1]["iters"], "relres_true": its[-1]["relres_true"],
             "rooflines": {c: roofline(c, kt[c], prec, args.n) for c in SOLVE_CLASSES},
             "kernel_classes_ms_per_solve": {k: v[0] / args.steps for k, v in kt.items()},
+            "solve_hbm": solve_hbm(h.info(), prec, its[-1]["iters"], ms),
         }
         h.free()
         op.free()
@@ -425,6 +426,19 @@ def vcycle_bytes(info, prec, degree=2):
         total += 2 * nnz_p[l] * (w + 4)
     total += n[-1] * n[-1] * 8  # explicit inverse of the coarsest operator
     return total
+
+
+def solve_hbm(info, prec, iters, solve_ms, degree=2):
+    """The whole solve against the HBM roofline: algorithmic bytes per PCG iteration (the
+    FP64 CG vectors, 88 B per unknown: A p, the x / r update, p = z + beta p; plus one V-cycle)
+    times the iterations, over the measured solve time."""
+    per_iter = 88 * info["n"][0] + vcycle_bytes(info, prec, degree)
+    gbs = per_iter * iters / (solve_ms * 1e-3) / 1e9
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(path)) if os.path.exists(path) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    return {"bytes_per_iteration": per_iter, "achieved_gbs": gbs, "peak_gbs": hbm,
+            "frac": gbs / hbm, "peak_source": "measured" if peaks else "fallback"}
 
 
 def aggregation_leg(S, torch, args):

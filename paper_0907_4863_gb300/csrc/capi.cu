@@ -1,6 +1,7 @@
 // C ABI of libsaamg: handles, the setup of the SA-AMG hierarchy (Sec. 3.2), the V-cycle
 // (Algorithm 1) and the PCG driver (Sec. 3.1).  Host code here only orchestrates; every
 // arithmetic step runs in the kernels of the other translation units.
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -201,6 +202,9 @@ struct saamg_hierarchy {
   HostScratch host;
   Buf<double> scratch;
   long long bytes = 0;
+  // identity for cached batch graphs: a new value at creation and whenever the V-cycle
+  // changes (a cached graph never outlives the kernels and pointers it was captured with)
+  unsigned long long version = 0;
   // device-loop solve: the whole PCG as one graph (conditional while node)
   cudaGraph_t graph = nullptr;      // owns the conditional handle: lives as long as gexec
   cudaGraphExec_t gexec = nullptr;
@@ -779,23 +783,73 @@ static void pcg_pass(saamg_hierarchy* h, cudaGraphConditionalHandle cond, cudaSt
 }
 
 // Capture needs a stream that can be captured (not the legacy default stream): the graph is
-// recorded on a private stream (nothing executes during capture) and launched on the
-// caller's stream.
-static cudaStream_t capture_stream() {
+// recorded on private streams (nothing executes during capture) and launched on the caller's
+// stream.  Stream 0 records the graph, stream 1 the body of a conditional node, the others
+// the parallel branches of a batch.
+static std::mutex g_capture_mu;  // one capture at a time on the private streams
+
+static cudaStream_t capture_stream(int k) {
   static std::mutex mu;
-  static cudaStream_t cs = nullptr;
+  static std::vector<cudaStream_t> cs;
   std::lock_guard<std::mutex> lock(mu);
-  if (!cs) SAAMG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  return cs;
+  while ((int)cs.size() <= k) {
+    cudaStream_t st;
+    SAAMG_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    cs.push_back(st);
+  }
+  return cs[k];
 }
 
-static void build_solve_graph(saamg_hierarchy* h) {
-  static std::mutex capture_mu;  // one capture at a time on the shared capture stream
-  std::lock_guard<std::mutex> lock(capture_mu);
-  cudaStream_t s = capture_stream();
+static unsigned long long next_version() {
+  static std::atomic<unsigned long long> v{0};
+  return ++v;
+}
+
+// One whole PCG solve into the graph that stream s is capturing: prologue (||b||, r = b - A x,
+// the loop condition), a conditional while node whose body (captured on body_s) is one PCG
+// pass, and the epilogue (true residual).  cond belongs to the graph being captured.
+static void capture_pcg(saamg_hierarchy* h, cudaGraphConditionalHandle cond, cudaStream_t s,
+                        cudaStream_t body_s) {
   const OperatorData& od = h->op->d;
   const int n = od.n;
   const StencilDev<double> S = od.view<double>();
+  dot_partials<double, double>(n, h->bhat.p, h->bhat.p, h->part2.p, s);
+  stencil_apply<double>(S, ST_RESID, h->xhat.p, h->r.p, h->bhat.p, nullptr, 0.0, 0.0, nullptr, s);
+  if (mixed(h)) to_float(h->r.p, h->r32.p, n, s);  // the first pass's V-cycle input
+  dot_partials<double, double>(n, h->r.p, h->r.p, h->part1.p, s);
+  SAAMG_CUDA(cudaMemsetAsync(h->p.p, 0, sizeof(double) * n, s));
+  pcg_graph_init(h->part2.p, h->part1.p, h->ctl.p, cond, h->prm.maxit, h->xhat.p, n, s);
+  cudaStreamCaptureStatus st;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  SAAMG_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, &deps, nullptr, &nd));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  SAAMG_CUDA(cudaGraphAddNode(&cnode, cg, deps, nullptr, nd, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  SAAMG_CUDA(cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  stencil_apply<double>(S, ST_RESID, h->xhat.p, h->q.p, h->bhat.p, nullptr, 0.0, 0.0, nullptr, s);
+  dot_partials<double, double>(n, h->q.p, h->q.p, h->part0.p, s);
+  pcg_store_true(h->part0.p, h->ctl.p, s);
+  SAAMG_CUDA(cudaStreamBeginCaptureToGraph(body_s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  try {
+    pcg_pass(h, cond, body_s);
+  } catch (...) {
+    cudaGraph_t junk = nullptr;
+    cudaStreamEndCapture(body_s, &junk);
+    throw;
+  }
+  SAAMG_CUDA(cudaStreamEndCapture(body_s, &body));
+}
+
+static void build_solve_graph(saamg_hierarchy* h) {
+  std::lock_guard<std::mutex> lock(g_capture_mu);
+  cudaStream_t s = capture_stream(0);
   cudaGraph_t g = nullptr;
   SAAMG_CUDA(cudaGraphCreate(&g, 0));
   bool capturing = false;
@@ -804,36 +858,9 @@ static void build_solve_graph(saamg_hierarchy* h) {
     SAAMG_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault));
     SAAMG_CUDA(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     capturing = true;
-    dot_partials<double, double>(n, h->bhat.p, h->bhat.p, h->part2.p, s);
-    stencil_apply<double>(S, ST_RESID, h->xhat.p, h->r.p, h->bhat.p, nullptr, 0.0, 0.0, nullptr, s);
-    if (mixed(h)) to_float(h->r.p, h->r32.p, n, s);  // the first pass's V-cycle input
-    dot_partials<double, double>(n, h->r.p, h->r.p, h->part1.p, s);
-    SAAMG_CUDA(cudaMemsetAsync(h->p.p, 0, sizeof(double) * n, s));
-    pcg_graph_init(h->part2.p, h->part1.p, h->ctl.p, cond, h->prm.maxit, h->xhat.p, n, s);
-    cudaStreamCaptureStatus st;
-    cudaGraph_t cg = nullptr;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t nd = 0;
-    SAAMG_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, &deps, nullptr, &nd));
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = cond;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t cnode;
-    SAAMG_CUDA(cudaGraphAddNode(&cnode, cg, deps, nullptr, nd, &cp));
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    SAAMG_CUDA(cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
-    stencil_apply<double>(S, ST_RESID, h->xhat.p, h->q.p, h->bhat.p, nullptr, 0.0, 0.0, nullptr, s);
-    dot_partials<double, double>(n, h->q.p, h->q.p, h->part0.p, s);
-    pcg_store_true(h->part0.p, h->ctl.p, s);
+    capture_pcg(h, cond, s, capture_stream(1));
     capturing = false;
     SAAMG_CUDA(cudaStreamEndCapture(s, &g));
-    SAAMG_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    capturing = true;
-    pcg_pass(h, cond, s);
-    capturing = false;
-    SAAMG_CUDA(cudaStreamEndCapture(s, &body));
     SAAMG_CUDA(cudaGraphInstantiate(&h->gexec, g, 0));
     h->graph = g;
   } catch (...) {
@@ -910,6 +937,7 @@ static void recompute_cheb(saamg_hierarchy* h, int degree) {
   }
   h->prm.cheb_degree = degree;
   drop_solve_graph(h);
+  h->version = next_version();
 }
 
 }  // namespace saamg
@@ -1086,6 +1114,7 @@ saamg_status saamg_setup(const saamg_operator* op, const saamg_params* params, v
     check_params_ext(prm);
     auto h = std::make_unique<saamg_hierarchy>();
     setup_impl(op, prm, (cudaStream_t)stream, h.get());
+    h->version = next_version();
     SAAMG_CUDA(cudaMallocHost(&h->result, sizeof(PcgCtl)));
     *out = h.release();
   });
@@ -1109,6 +1138,7 @@ saamg_status saamg_setup_reuse(const saamg_operator* op, const saamg_hierarchy* 
     check_params_ext(prm);
     auto h = std::make_unique<saamg_hierarchy>();
     setup_impl(op, prm, s, h.get(), prev);
+    h->version = next_version();
     SAAMG_CUDA(cudaMallocHost(&h->result, sizeof(PcgCtl)));
     *out = h.release();
   });
@@ -1262,6 +1292,116 @@ saamg_status saamg_solve_wait(saamg_hierarchy* h, saamg_solve_info* info) {
   return g != SAAMG_OK ? g : st;
 }
 
+// --- batched solves as one graph -----------------------------------------------------
+// The whole batch is captured once into one graph: one branch per group of hierarchies (the
+// solves of one hierarchy share its work vectors and run in order on their branch), every
+// solve inline as gather -> prologue -> conditional while (PCG pass) -> epilogue -> result
+// copy -> scatter.  A call whose hierarchies (by version), arrays and tolerance match a
+// cached graph is one graph launch.
+struct BatchGraph {
+  std::vector<const saamg_hierarchy*> hs;
+  std::vector<unsigned long long> versions;
+  std::vector<const double*> rho;
+  std::vector<double*> phi;
+  double rtol = 0.0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  PcgCtl* res = nullptr;  // pinned, one per solve
+  ~BatchGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (res) cudaFreeHost(res);
+  }
+  bool matches(saamg_hierarchy* const* h, const double* const* r, double* const* x, int count,
+               double tol) const {
+    if ((int)hs.size() != count || tol != rtol) return false;
+    for (int j = 0; j < count; ++j)
+      if (hs[j] != h[j] || versions[j] != h[j]->version || rho[j] != r[j] || phi[j] != x[j])
+        return false;
+    return true;
+  }
+};
+
+static std::mutex g_batch_mu;  // batched calls run one at a time
+static std::vector<std::unique_ptr<BatchGraph>> g_batch_cache;  // most recent last
+constexpr size_t kBatchCache = 2;
+
+static std::unique_ptr<BatchGraph> build_batch_graph(
+    saamg_hierarchy* const* hs, const double* const* rho, double* const* phi, int count,
+    double rtol, const std::vector<saamg_hierarchy*>& order,
+    std::map<saamg_hierarchy*, std::vector<int>>& groups) {
+  auto bg = std::make_unique<BatchGraph>();
+  for (int j = 0; j < count; ++j) {
+    bg->hs.push_back(hs[j]);
+    bg->versions.push_back(hs[j]->version);
+    bg->rho.push_back(rho[j]);
+    bg->phi.push_back(phi[j]);
+  }
+  bg->rtol = rtol;
+  SAAMG_CUDA(cudaMallocHost(&bg->res, sizeof(PcgCtl) * count));
+  std::lock_guard<std::mutex> lock(g_capture_mu);
+  cudaStream_t cs = capture_stream(0), body = capture_stream(1);
+  const int nbr = (int)std::min<size_t>(order.size(), 32);
+  std::vector<cudaEvent_t> evs;
+  cudaGraph_t g = nullptr;
+  SAAMG_CUDA(cudaGraphCreate(&g, 0));
+  bool capturing = false;
+  try {
+    std::vector<cudaGraphConditionalHandle> conds(count);
+    for (int j = 0; j < count; ++j)  // a handle that no conditional node uses fails instantiation
+      if (hs[j]->op->d.n > 0)
+        SAAMG_CUDA(cudaGraphConditionalHandleCreate(&conds[j], g, 0, cudaGraphCondAssignDefault));
+    SAAMG_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    capturing = true;
+    cudaEvent_t fork;
+    SAAMG_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    evs.push_back(fork);
+    SAAMG_CUDA(cudaEventRecord(fork, cs));
+    for (int k = 0; k < nbr; ++k) SAAMG_CUDA(cudaStreamWaitEvent(capture_stream(2 + k), fork, 0));
+    for (size_t gi = 0; gi < order.size(); ++gi) {
+      saamg_hierarchy* h = order[gi];
+      const OperatorData& od = h->op->d;
+      cudaStream_t ps = capture_stream(2 + (int)(gi % nbr));
+      for (int j : groups[h]) {
+        if (od.n == 0) {  // no unknowns: phi = 0, converged at once
+          bg->res[j] = PcgCtl{};
+          bg->res[j].converged = 1;
+          scatter_solution(od, h->xhat.p, phi[j], ps);
+          continue;
+        }
+        gather_rhs(od, rho[j], phi[j], h->bhat.p, h->xhat.p, ps);
+        set_rtol_k<<<1, 1, 0, ps>>>(h->ctl.p, rtol);
+        SAAMG_LAUNCH();
+        capture_pcg(h, conds[j], ps, body);
+        SAAMG_CUDA(cudaMemcpyAsync(&bg->res[j], h->ctl.p, sizeof(PcgCtl), cudaMemcpyDeviceToHost, ps));
+        scatter_solution(od, h->xhat.p, phi[j], ps);
+      }
+    }
+    for (int k = 0; k < nbr; ++k) {
+      cudaEvent_t e;
+      SAAMG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      evs.push_back(e);
+      SAAMG_CUDA(cudaEventRecord(e, capture_stream(2 + k)));
+      SAAMG_CUDA(cudaStreamWaitEvent(cs, e, 0));
+    }
+    capturing = false;
+    SAAMG_CUDA(cudaStreamEndCapture(cs, &g));
+    SAAMG_CUDA(cudaGraphInstantiate(&bg->exec, g, 0));
+    bg->graph = g;
+  } catch (...) {
+    if (capturing) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(cs, &junk);
+      if (junk && junk != g) cudaGraphDestroy(junk);
+    }
+    cudaGraphDestroy(g);
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
+    throw;
+  }
+  for (cudaEvent_t e : evs) cudaEventDestroy(e);
+  return bg;
+}
+
 saamg_status saamg_solve_batched(saamg_hierarchy* const* hs, const double* const* rho,
                                  double* const* phi, int count, double rtol, void* stream,
                                  saamg_solve_info* infos) {
@@ -1285,42 +1425,34 @@ saamg_status saamg_solve_batched(saamg_hierarchy* const* hs, const double* const
       if (!groups.count(hs[j])) order.push_back(hs[j]);
       groups[hs[j]].push_back(j);
     }
-    PcgCtl* res = nullptr;
-    SAAMG_CUDA(cudaMallocHost(&res, sizeof(PcgCtl) * count));
-    std::vector<cudaEvent_t> evs;
-    auto cleanup = [&] {
-      for (cudaEvent_t e : evs) cudaEventDestroy(e);
-      cudaFreeHost(res);
-    };
-    try {
-      const size_t nstreams = std::min<size_t>(order.size(), 32);
-      cudaEvent_t fork;
-      SAAMG_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-      evs.push_back(fork);
-      SAAMG_CUDA(cudaEventRecord(fork, s));
-      for (size_t k = 0; k < nstreams; ++k) SAAMG_CUDA(cudaStreamWaitEvent(pool_stream(k), fork, 0));
-      for (size_t gi = 0; gi < order.size(); ++gi) {
-        cudaStream_t ps = pool_stream(gi % nstreams);
-        for (int j : groups[order[gi]]) solve_async_impl(order[gi], rho[j], phi[j], rtol, ps, &res[j]);
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    BatchGraph* bg = nullptr;
+    for (size_t e = 0; e < g_batch_cache.size(); ++e)
+      if (g_batch_cache[e]->matches(hs, rho, phi, count, rtol)) {
+        // most recent last
+        std::unique_ptr<BatchGraph> hit = std::move(g_batch_cache[e]);
+        g_batch_cache.erase(g_batch_cache.begin() + e);
+        g_batch_cache.push_back(std::move(hit));
+        bg = g_batch_cache.back().get();
+        break;
       }
-      for (size_t k = 0; k < nstreams; ++k) {
-        cudaEvent_t e;
-        SAAMG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        evs.push_back(e);
-        SAAMG_CUDA(cudaEventRecord(e, pool_stream(k)));
-        SAAMG_CUDA(cudaStreamWaitEvent(s, e, 0));
-      }
-      SAAMG_CUDA(cudaStreamSynchronize(s));
-      for (int j = 0; j < count; ++j) {
-        saamg_status st = info_from_ctl(res[j], &infos[j]);
-        if (st < 0 && worst >= 0) worst = st;
-        else if (st == SAAMG_NOT_CONVERGED && worst == SAAMG_OK) worst = st;
-      }
-    } catch (...) {
-      cleanup();
-      throw;
+    if (!bg) {
+      auto built = build_batch_graph(hs, rho, phi, count, rtol, order, groups);
+      if (g_batch_cache.size() >= kBatchCache) g_batch_cache.erase(g_batch_cache.begin());
+      g_batch_cache.push_back(std::move(built));
+      bg = g_batch_cache.back().get();
     }
-    cleanup();
+    SAAMG_CUDA(cudaGraphLaunch(bg->exec, s));
+    for (saamg_hierarchy* h : order) {
+      if (!h->done) SAAMG_CUDA(cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming));
+      SAAMG_CUDA(cudaEventRecord(h->done, s));
+    }
+    SAAMG_CUDA(cudaStreamSynchronize(s));
+    for (int j = 0; j < count; ++j) {
+      saamg_status st = info_from_ctl(bg->res[j], &infos[j]);
+      if (st < 0 && worst >= 0) worst = st;
+      else if (st == SAAMG_NOT_CONVERGED && worst == SAAMG_OK) worst = st;
+    }
   });
   if (count > 0 && infos) {
     double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -183,15 +183,30 @@ __global__ void gj_gather_k(int n, const double* __restrict__ w, const int* __re
   }
 }
 
-// x_i = sum_c inv(i, c) b_c, FP64 accumulation.
+// x_i = sum_c inv(i, c) b_c, FP64 accumulation.  A block covers 32 consecutive rows (lane =
+// row, so every load of a column is one coalesced access) with kGemvWarps warps, warp w
+// summing the columns c = w mod kGemvWarps; the warps' partial sums are added in warp order.
+constexpr int kGemvWarps = 8;
+
 template <class TV>
-__global__ void coarse_apply_k(int n, const double* __restrict__ inv, const TV* __restrict__ b,
-                               TV* __restrict__ x) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__global__ void __launch_bounds__(32 * kGemvWarps) coarse_apply_k(int n,
+                                                                  const double* __restrict__ inv,
+                                                                  const TV* __restrict__ b,
+                                                                  TV* __restrict__ x) {
+  __shared__ double part[kGemvWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
   double acc = 0.0;
-  for (int c = 0; c < n; ++c) acc += inv[(size_t)c * n + i] * (double)b[c];
-  x[i] = (TV)acc;
+  if (i < n)
+    for (int c = w; c < n; c += kGemvWarps) acc += inv[(size_t)c * n + i] * (double)b[c];
+  part[w][lane] = acc;
+  __syncthreads();
+  if (w == 0 && i < n) {
+    double t = part[0][lane];
+#pragma unroll
+    for (int q = 1; q < kGemvWarps; ++q) t += part[q][lane];
+    x[i] = (TV)t;
+  }
 }
 
 // --- Gauss-Seidel (one CTA) ---------------------------------------------------------
@@ -402,7 +417,7 @@ void coarse_apply(const CoarseSolver& cs, const TV* b, TV* x, cudaStream_t s) {
     SAAMG_LAUNCH();
     return;
   }
-  coarse_apply_k<TV><<<(cs.n + 127) / 128, 128, 0, s>>>(cs.n, cs.inv.p, b, x);
+  coarse_apply_k<TV><<<(cs.n + 31) / 32, 32 * kGemvWarps, 0, s>>>(cs.n, cs.inv.p, b, x);
   SAAMG_LAUNCH();
 }
 

@@ -157,15 +157,17 @@ __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int l
 template <class T, int MODE, int K>
 __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __restrict__ x,
                                                  T* __restrict__ y, const T* __restrict__ b,
-                                                 T* __restrict__ d, T c1, T c2,
+                                                 T* __restrict__ d, T c1, T c2, T c2invd0,
                                                  double* __restrict__ partials,
                                                  const double* __restrict__ xscale,
                                                  const int* __restrict__ agg) {
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   const int nw = gridDim.x * wpb;
-  if (MODE == ST_DINV_DOT) c2 = xscale ? (T)*xscale : T(1);
-  const T c2invd0 = c2 * S.invd0;
+  if (MODE == ST_DINV_DOT) {
+    c2 = xscale ? (T)*xscale : T(1);
+    c2invd0 = c2 * S.invd0;
+  }
   double dacc = 0.0;
   for (int c0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * K; c0 < S.nchunks; c0 += nw * K) {
 #pragma unroll
@@ -218,34 +220,37 @@ void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* 
     long long need = ((long long)S.nchunks + 8 * kChunks<T>() - 1) / (8 * kChunks<T>());
     blocks = (int)(need < 152 * 16 ? need : 152 * 16);
   }
+  // c2 / diag of the regular rows, formed here: a kernel that forms it from c2 lets the
+  // compiler merge it with the table rows' c2 * (1/diag) into one multiply on every row
+  const T c2i0 = c2 * S.invd0;
   switch (mode) {
     case ST_SPMV:
       stencil_k<T, ST_SPMV, kChunks<T>()><<<blocks, 256, 0, s>>>(
-          S, x, y, b, d, c1, c2, partials, xscale, nullptr);
+          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
       break;
     case ST_SPMV_DOT:
       stencil_k<T, ST_SPMV_DOT, kChunks<T>()><<<blocks, 256, 0, s>>>(
-          S, x, y, b, d, c1, c2, partials, xscale, nullptr);
+          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
       break;
     case ST_RESID:
       stencil_k<T, ST_RESID, kChunks<T>()><<<blocks, 256, 0, s>>>(
-          S, x, y, b, d, c1, c2, partials, xscale, nullptr);
+          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
       break;
     case ST_CHEB:
       stencil_k<T, ST_CHEB, kChunks<T>()><<<blocks, 256, 0, s>>>(
-          S, x, y, b, d, c1, c2, partials, xscale, nullptr);
+          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
       break;
     case ST_CHEB0:
       stencil_k<T, ST_CHEB0, kChunks<T>()><<<blocks, 256, 0, s>>>(
-          S, x, y, b, d, c1, c2, partials, xscale, nullptr);
+          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
       break;
     case ST_CHEB1:
       stencil_k<T, ST_CHEB1, kChunks<T>()><<<blocks, 256, 0, s>>>(
-          S, x, y, b, d, c1, c2, partials, xscale, nullptr);
+          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
       break;
     case ST_DINV_DOT:
       stencil_k<T, ST_DINV_DOT, kChunks<T>()><<<blocks, 256, 0, s>>>(
-          S, x, y, b, d, c1, c2, partials, xscale, nullptr);
+          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
       break;
     default:
       fail(SAAMG_EINVAL, "bad stencil mode");
@@ -261,7 +266,7 @@ void stencil_prolong(const StencilDev<T>& S, const int* agg, T omega, const T* v
   const long long need = ((long long)S.nchunks + 8 * kChunks<T>() - 1) / (8 * kChunks<T>());
   const int blocks = (int)(need < 152 * 16 ? need : 152 * 16);
   stencil_k<T, ST_PROLONG, kChunks<T>()><<<blocks, 256, 0, s>>>(
-      S, v, y, nullptr, nullptr, T(0), omega, nullptr, nullptr, agg);
+      S, v, y, nullptr, nullptr, T(0), omega, T(omega * S.invd0), nullptr, nullptr, agg);
   SAAMG_LAUNCH();
 }
 

@@ -81,3 +81,15 @@ def test_replicas_report_the_slowest_rank_over_gloo():
         assert p.exitcode == 0
     for r in range(2):
         assert out[r][0] == 1.25 and out[r][1] == pytest.approx(2 * 5 / 1.25)
+
+
+def test_solve_hbm_counts_cg_vectors_and_one_vcycle_per_iteration(bench):
+    info = {"n": [1000, 100, 10], "nnz": [7000, 2000, 60], "nnz_p": [3000, 300, 0]}
+    # FP64, degree 2: level 0 1000*8*23 + 2*3000*12; level 1 5*2000*12 + 100*8*23 + 2*300*12;
+    # coarsest 10^2 * 8; CG vectors 88 * 1000
+    vc = 184000 + 72000 + 120000 + 18400 + 7200 + 800
+    assert bench.vcycle_bytes(info, 0) == vc
+    r = bench.solve_hbm(info, 0, iters=10, solve_ms=2.0)
+    assert r["bytes_per_iteration"] == 88000 + vc
+    assert r["achieved_gbs"] == pytest.approx((88000 + vc) * 10 / 2e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved_gbs"] / r["peak_gbs"])

@@ -108,6 +108,57 @@ def test_batched_results_equal_solo_results(S):
         assert torch.equal(a, b)
 
 
+def test_batched_graph_is_reused_and_rebuilt(S):
+    """A repeated batch (same hierarchies, arrays and tolerance) is one launch of the cached
+    graph and must see the arrays' new contents; a hierarchy changed since (a new Chebyshev
+    degree) or another tolerance gets a new graph.  Every result equals the solo solve."""
+    import torch
+    wa, wb = I.pipe_workload(32, I.LINEAR), I.taper_workload(26, 24, 40, I.QUADRATIC)
+    ha = _setup(S, wa, max_coarse=100)
+    hb = _setup(S, wb, max_coarse=100, precision=1, beta_rule=1)
+    hs = [ha, hb, ha]
+    rhos = [_rho(wa, 1), _rho(wb, 2), _rho(wa, 3)]
+    phis = [torch.zeros_like(r) for r in rhos]
+
+    def check(rtol):
+        for x in phis:
+            x.zero_()
+        infos = S.solve_batched(hs, rhos, phis, rtol=rtol)
+        for h, r, x, info in zip(hs, rhos, phis, infos):
+            ref = torch.zeros_like(r)
+            solo = S.solve(h, r, ref, rtol=rtol)
+            assert info["converged"] == 1 and info["iters"] == solo["iters"]
+            assert torch.equal(x, ref)
+        return infos
+
+    first = check(1e-8)
+    for r in rhos:
+        r.mul_(-0.5).add_(1e-3)  # same arrays, new contents
+    check(1e-8)
+    S.set_cheb_degree(ha, 3)
+    check(1e-8)
+    loose = check(1e-4)
+    assert all(a["iters"] < b["iters"] for a, b in zip(loose, first))
+
+
+def test_batched_with_a_domain_without_unknowns(S):
+    """A pipe thinner than the lattice spacing has no unknowns: its solve in a batch is
+    phi = 0 at once, the other solves are untouched."""
+    import torch
+    w0 = I.Workload("empty", I.cell_centred_grid(16), I.Domain(1e-3, 1e-3), I.LINEAR)
+    w1 = I.pipe_workload(24, I.LINEAR)
+    h0 = _setup(S, w0, max_coarse=100)
+    assert h0.info()["n"][0] == 0
+    h1 = _setup(S, w1, max_coarse=100)
+    r0, r1 = _rho(w0, 0), _rho(w1, 0)
+    x0 = torch.full_like(r0, 5.0)
+    x1 = torch.zeros_like(r1)
+    infos = S.solve_batched([h0, h1], [r0, r1], [x0, x1])
+    assert infos[0]["converged"] == 1 and infos[0]["iters"] == 0 and torch.all(x0 == 0)
+    ref = torch.zeros_like(r1)
+    assert infos[1]["iters"] == S.solve(h1, r1, ref)["iters"] and torch.equal(x1, ref)
+
+
 def test_autotune_picks_a_degree_and_keeps_accuracy(S):
     import torch
     w = I.pipe_workload(48, I.LINEAR)
