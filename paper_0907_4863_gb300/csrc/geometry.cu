@@ -205,7 +205,8 @@ __global__ void line_deltas_k(const LineInfo* __restrict__ lines, int nlines, in
   nbr[L] = r;
 }
 
-// Regular interior row: all six couplings -c_dir, diagonal 2(cx+cy+cz), scaled.
+// Regular interior row: all six couplings -c_dir, diagonal 2(cx+cy+cz), scaled; out[5], out[6]
+// hold the unscaled diagonal and its diag^-1/2 (the same operations as a general row's).
 __global__ void regular_consts_k(GeomParams g, double* out) {
   double dd[3], om, opl;
   for (int ax = 0; ax < 3; ++ax) direction_row(g.mode, g.cdir[ax], true, true, 1.0, 1.0, dd[ax], om, opl);
@@ -217,42 +218,35 @@ __global__ void regular_consts_k(GeomParams g, double* out) {
   out[2] = (-g.cdir[1]) * ss;
   out[3] = (-g.cdir[2]) * ss;
   out[4] = 1.0 / out[0];
+  out[5] = diag;  // unscaled interior diagonal
+  out[6] = s;     // its diag^-1/2
 }
 
-// Warp per chunk, lane per unknown: unscaled row (diag + 6 couplings), s_i, row length.
-__global__ void assemble_unscaled_k(GeomParams g, const LineInfo* __restrict__ lines,
-                                    const int2* __restrict__ chunks, int nchunks,
-                                    double* __restrict__ coef, double* __restrict__ scale,
-                                    int* __restrict__ rowlen, unsigned* __restrict__ ids) {
-  int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (c >= nchunks) return;
-  int2 ch = chunks[c];
-  int L = ch.x;
-  LineInfo me = lines[L];
-  int i = me.lo + ch.y + lane;
-  if (i > me.hi) return;
-  int row = me.start + ch.y + lane;
-  int j = L % g.ny, k = L / g.ny;
+// Unscaled row of unknown (i, L) at compact row `row`: diag + 6 couplings into cr[0..6],
+// cr[7] = 0; returns s_i = diag^-1/2 and the row length.
+__device__ double unscaled_row(const GeomParams& g, const LineInfo* __restrict__ lines, int L,
+                               int i, int row, const LineInfo& me, double* __restrict__ cr,
+                               int& len) {
+  const int j = L % g.ny, k = L / g.ny;
   int nb[6];
   neighbour_rows(g, lines, L, i, row, me, nb);
   double off[6] = {0, 0, 0, 0, 0, 0};
   double dd[3];
-  bool gamma2 = (g.zbc == SAAMG_Z_ROBIN) && (k == 0 || k == g.nz - 1);
+  const bool gamma2 = (g.zbc == SAAMG_Z_ROBIN) && (k == 0 || k == g.nz - 1);
   for (int ax = 0; ax < 3; ++ax) {
     const double cdir = g.cdir[ax];
-    int dm = 2 * ax, dp = 2 * ax + 1;
-    bool in_m = nb[dm] >= 0, in_p = nb[dp] >= 0;
+    const int dm = 2 * ax, dp = 2 * ax + 1;
+    const bool in_m = nb[dm] >= 0, in_p = nb[dp] >= 0;
     if (ax == 2 && gamma2) {
       // Robin plane, Eq. (11): virtual point u(x') = u(x'') - (2h/d) u(x)
-      bool inner_is_p = (k == 0);
-      bool in_inner = inner_is_p ? in_p : in_m;
+      const bool inner_is_p = (k == 0);
+      const bool in_inner = inner_is_p ? in_p : in_m;
       if (in_inner) {
         dd[2] = (2.0 + g.robin) * cdir;
         off[inner_is_p ? dp : dm] = -2.0 * cdir;
       } else {
         // inner neighbour outside the wall: replaced by its one-sided extrapolation
-        double t = boundary_fraction(g, i, j, k, inner_is_p ? dp : dm);
+        const double t = boundary_fraction(g, i, j, k, inner_is_p ? dp : dm);
         if (g.mode == SAAMG_BC_CONSTANT) dd[2] = (2.0 + g.robin) * cdir;
         else dd[2] = (g.robin + 2.0 / t) * cdir;
       }
@@ -268,22 +262,90 @@ __global__ void assemble_unscaled_k(GeomParams g, const LineInfo* __restrict__ l
     diag *= 0.5;
     for (int q = 0; q < 6; ++q) off[q] *= 0.5;
   }
-  double* cr = coef + 8 * (size_t)row;
   cr[0] = diag;
-  int len = 1;
+  len = 1;
   for (int q = 0; q < 6; ++q) {
     cr[1 + q] = off[q];
     len += nb[q] >= 0;
   }
   cr[7] = 0.0;
-  scale[row] = 1.0 / sqrt(diag);
-  rowlen[row] = len;
-  ids[row] = (unsigned)i + (unsigned)g.nx * (unsigned)L;
+  return 1.0 / sqrt(diag);
+}
+
+// A row is simple when all six neighbours are unknowns and it is not on a Robin plane: its
+// unscaled row is the interior one (diagonal rc[5], couplings -c_dir) and s_i = rc[6].
+__device__ __forceinline__ bool simple_row(const GeomParams& g, const int nb[6], int L) {
+  const int k = L / g.ny;
+  const bool gamma2 = (g.zbc == SAAMG_Z_ROBIN) && (k == 0 || k == g.nz - 1);
+  return !gamma2 && nb[0] >= 0 && nb[1] >= 0 && nb[2] >= 0 && nb[3] >= 0 && nb[4] >= 0 &&
+         nb[5] >= 0;
+}
+
+// Warp per chunk, lane per unknown: simple rows get s_i and their row length here; the
+// others (near the wall or on a Robin plane, a few per cent) are listed for
+// assemble_boundary_k, where every lane of a warp holds one of them (the boundary fractions,
+// divisions and square roots run on the FP64 pipe, which would otherwise idle the lanes of
+// the simple rows of the same warp).
+__global__ void assemble_unscaled_k(GeomParams g, const LineInfo* __restrict__ lines,
+                                    const int2* __restrict__ chunks, int nchunks,
+                                    double* __restrict__ scale, int* __restrict__ rowlen,
+                                    unsigned* __restrict__ ids, const double* __restrict__ rc,
+                                    int2* __restrict__ list, int* __restrict__ nlist) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= nchunks) return;  // warp-uniform
+  const int2 ch = chunks[c];
+  const int L = ch.x;
+  const LineInfo me = lines[L];
+  const int i = me.lo + ch.y + lane;
+  const bool active = i <= me.hi;
+  const int row = me.start + ch.y + lane;
+  bool simple = false;
+  if (active) {
+    int nb[6];
+    neighbour_rows(g, lines, L, i, row, me, nb);
+    simple = simple_row(g, nb, L);
+    if (simple) {
+      scale[row] = rc[6];
+      rowlen[row] = 7;
+    }
+    ids[row] = (unsigned)i + (unsigned)g.nx * (unsigned)L;
+  }
+  const unsigned need = __ballot_sync(0xffffffffu, active && !simple);
+  if (!need) return;
+  int base = 0;
+  if (lane == 0) base = atomicAdd(nlist, __popc(need));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (active && !simple) list[base + __popc(need & ((1u << lane) - 1u))] = make_int2(c, lane);
+}
+
+// Thread per listed row: the full unscaled row (boundary fractions, Eqs. (7)-(11)), s_i and
+// the row length.
+__global__ void assemble_boundary_k(GeomParams g, const LineInfo* __restrict__ lines,
+                                    const int2* __restrict__ chunks,
+                                    const int2* __restrict__ list, const int* __restrict__ nlist,
+                                    double* __restrict__ coef, double* __restrict__ scale,
+                                    int* __restrict__ rowlen) {
+  const int cnt = *nlist;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+    const int2 it = list[e];
+    const int2 ch = chunks[it.x];
+    const int L = ch.x;
+    const LineInfo me = lines[L];
+    const int i = me.lo + ch.y + it.y;
+    const int row = me.start + ch.y + it.y;
+    int len;
+    scale[row] = unscaled_row(g, lines, L, i, row, me, coef + 8 * (size_t)row, len);
+    rowlen[row] = len;
+  }
 }
 
 // Warp per chunk: scaled row ahat_ij = a_ij (s_i s_j), CSR fill in ascending column order
-// (-z, -y, -x, self, +x, +y, +z), the row kept in `coef` for the stencil table, and the
-// regular flag (all six neighbours present and the coefficients equal the interior ones).
+// (-z, -y, -x, self, +x, +y, +z), the regular flag (all six neighbours present and the
+// coefficients equal the interior ones) and, for the other rows, the scaled row and 1/diag in
+// `coef` for the stencil table.  A simple row whose neighbours all have the interior s_j
+// is regular: its scaled coefficients are the interior constants rc[0..3], the same products
+// in the same order, so it takes them without FP64 work.
 __global__ void assemble_scaled_k(GeomParams g, const LineInfo* __restrict__ lines,
                                   const int2* __restrict__ chunks, int nchunks,
                                   double* __restrict__ coef, const double* __restrict__ scale,
@@ -302,21 +364,49 @@ __global__ void assemble_scaled_k(GeomParams g, const LineInfo* __restrict__ lin
   int row = me.start + ch.y + lane;
   int nb[6];
   neighbour_rows(g, lines, L, i, row, me, nb);
-  double si = scale[row];
-  double* cr = coef + 8 * (size_t)row;
-  double sc[7];
-  sc[0] = cr[0] * (si * si);
-  bool reg = true;
-  for (int q = 0; q < 6; ++q) {
-    if (nb[q] >= 0) {
-      sc[1 + q] = cr[1 + q] * (si * scale[nb[q]]);
-    } else {
-      sc[1 + q] = 0.0;
-      reg = false;
-    }
+  const bool simple = simple_row(g, nb, L);
+  const long long sreg = __double_as_longlong(rc[6]);
+  bool fast = simple && __double_as_longlong(scale[row]) == sreg;
+  if (fast) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) fast = fast && __double_as_longlong(scale[nb[q]]) == sreg;
   }
-  reg = reg && sc[0] == rc[0] && sc[1] == rc[1] && sc[2] == rc[1] && sc[3] == rc[2] &&
-        sc[4] == rc[2] && sc[5] == rc[3] && sc[6] == rc[3];
+  double sc[7];
+  bool reg;
+  if (fast) {
+    sc[0] = rc[0];
+    sc[1] = sc[2] = rc[1];
+    sc[3] = sc[4] = rc[2];
+    sc[5] = sc[6] = rc[3];
+    reg = true;
+  } else {
+    double* cr = coef + 8 * (size_t)row;
+    double ur[7];
+    if (simple) {  // the interior unscaled row (not stored by the unscaled pass)
+      ur[0] = rc[5];
+      ur[1] = ur[2] = -g.cdir[0];
+      ur[3] = ur[4] = -g.cdir[1];
+      ur[5] = ur[6] = -g.cdir[2];
+    } else {
+      for (int q = 0; q < 7; ++q) ur[q] = cr[q];
+    }
+    double si = scale[row];
+    sc[0] = ur[0] * (si * si);
+    reg = true;
+    for (int q = 0; q < 6; ++q) {
+      if (nb[q] >= 0) {
+        sc[1 + q] = ur[1 + q] * (si * scale[nb[q]]);
+      } else {
+        sc[1 + q] = 0.0;
+        reg = false;
+      }
+    }
+    reg = reg && sc[0] == rc[0] && sc[1] == rc[1] && sc[2] == rc[1] && sc[3] == rc[2] &&
+          sc[4] == rc[2] && sc[5] == rc[3] && sc[6] == rc[3];
+    for (int q = 0; q < 7; ++q) cr[q] = sc[q];
+    // 1 / diag: rc[4] is 1.0 / rc[0], the same division
+    cr[7] = __double_as_longlong(sc[0]) == __double_as_longlong(rc[0]) ? rc[4] : 1.0 / sc[0];
+  }
   const int order[7] = {4, 2, 0, -1, 1, 3, 5};
   int p = rowptr[row];
   for (int o = 0; o < 7; ++o) {
@@ -331,8 +421,6 @@ __global__ void assemble_scaled_k(GeomParams g, const LineInfo* __restrict__ lin
       ++p;
     }
   }
-  for (int q = 0; q < 7; ++q) cr[q] = sc[q];
-  cr[7] = 1.0 / sc[0];
   regular[row] = reg ? 1 : 0;
   unsigned char mk = 0;
   for (int q = 0; q < 6; ++q) mk |= (unsigned char)((nb[q] >= 0) << q);
@@ -377,7 +465,9 @@ __global__ void set_tstart_k(LineInfo* lines, const int* tstart, int nlines) {
 // Warp per chunk: table rows copy their 7 scaled coefficients and 1/diag.
 __global__ void fill_table_k(const LineInfo* __restrict__ lines, const int2* __restrict__ chunks,
                              int nchunks, const double* __restrict__ coef,
-                             double* __restrict__ table, float* __restrict__ table32) {
+                             const unsigned char* __restrict__ regular,
+                             const double* __restrict__ rc, double* __restrict__ table,
+                             float* __restrict__ table32) {
   int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (c >= nchunks) return;
@@ -388,8 +478,11 @@ __global__ void fill_table_k(const LineInfo* __restrict__ lines, const int2* __r
   if (i >= me.rlo && i <= me.rhi) return;
   int row = me.start + ch.y + lane;
   int t = me.tstart + (i < me.rlo ? i - me.lo : (me.rlo - me.lo) + (i - me.rhi - 1));
+  // a regular row outside the line's longest regular run holds the interior constants
+  const bool reg = regular[row] != 0;
+  const double cst[8] = {rc[0], rc[1], rc[1], rc[2], rc[2], rc[3], rc[3], rc[4]};
   for (int q = 0; q < 8; ++q) {
-    double v = coef[8 * (size_t)row + q];
+    double v = reg ? cst[q] : coef[8 * (size_t)row + q];
     table[8 * (size_t)t + q] = v;
     table32[8 * (size_t)t + q] = (float)v;
   }
@@ -474,7 +567,7 @@ void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op) 
   SAAMG_LAUNCH();
 
   Buf<double> rc;
-  rc.alloc(5, s);
+  rc.alloc(8, s);
   regular_consts_k<<<1, 1, 0, s>>>(g, rc.p);
   SAAMG_LAUNCH();
   double hrc[5];
@@ -494,9 +587,17 @@ void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op) 
   Buf<int> rowlen;
   rowlen.alloc(op.n + 1, s);
   if (op.n > 0) {
+    Buf<int2> blist;
+    Buf<int> bcount;
+    blist.alloc(op.n, s);
+    bcount.alloc(1, s);
+    fill_int(bcount.p, 0, 1, s);
     assemble_unscaled_k<<<warp_blocks(nchunks), 256, 0, s>>>(g, op.lines.p, op.chunks.p,
-                                                              op.nchunks, coef.p, op.scale.p,
-                                                              rowlen.p, op.ids.p);
+                                                              op.nchunks, op.scale.p, rowlen.p,
+                                                              op.ids.p, rc.p, blist.p, bcount.p);
+    SAAMG_LAUNCH();
+    assemble_boundary_k<<<152 * 8, 256, 0, s>>>(g, op.lines.p, op.chunks.p, blist.p, bcount.p,
+                                                coef.p, op.scale.p, rowlen.p);
     SAAMG_LAUNCH();
   }
   fill_int(rowlen.p + op.n, 0, 1, s);
@@ -526,7 +627,8 @@ void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op) 
   op.table32.alloc((size_t)nt * 8, s);
   if (op.n > 0) {
     fill_table_k<<<warp_blocks(nchunks), 256, 0, s>>>(op.lines.p, op.chunks.p, op.nchunks, coef.p,
-                                                       op.table.p, op.table32.p);
+                                                       op.regular.p, rc.p, op.table.p,
+                                                       op.table32.p);
     SAAMG_LAUNCH();
   }
 
