@@ -302,6 +302,13 @@ static bool same_pattern(const DevCsr& a, const DevCsr& b, cudaStream_t s) {
 
 // prev != NULL: the aggregates of every level are copied from prev (whose level-0 pattern
 // must equal op's) instead of being recomputed; everything numeric is rebuilt.
+// SELL copy of a coarse level's operator with the value arrays of the V-cycle's precision.
+static void build_level_sell(saamg_hierarchy* h, Level& L, cudaStream_t s) {
+  const bool f64 = !mixed(h), f32 = h->prm.precision == SAAMG_PREC_FP32;
+  const bool bf16 = h->prm.precision == SAAMG_PREC_FP32_BF16;
+  sell_from_csr(L.A, L.As, f64, f32, bf16, s);
+}
+
 static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaStream_t s,
                        saamg_hierarchy* h, const saamg_hierarchy* prev = nullptr) {
   auto t0 = std::chrono::steady_clock::now();
@@ -379,13 +386,16 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
       }
     }
     const StencilDev<double> S0 = od.view<double>();
-    L.lambda = power_lambda(A, L.invd.p, ids, prm.power_iters, s, l == 0 ? &S0 : nullptr);
+    // a smoothed level >= 1 large enough for SELL gets its SELL copy now (it is not the
+    // coarsest: that one stops before its spectral bound), so that in the FP64 V-cycle the
+    // power iteration runs on it too
+    if (l >= 1 && L.n >= kSellMinRows && L.As.n == 0) build_level_sell(h, L, s);
+    L.lambda = power_lambda(A, L.invd.p, ids, prm.power_iters, s, l == 0 ? &S0 : nullptr,
+                            l >= 1 && L.As.n > 0 ? &L.As : nullptr);
     L.omega = 4.0 / (3.0 * L.lambda);
     pt.mark("L" + std::to_string(l) + ".lambda");
-    DevCsr T, AT, AP;
-    tentative(L.agg.p, L.n, nagg, T, s);
-    spgemm(A, T, AT, s);
-    smoothed_prolongator(AT, L.agg.p, L.invd.p, L.omega, L.P, s);
+    DevCsr AP;
+    prolongator(A, L.agg.p, nagg, L.invd.p, L.omega, L.P, s);
     pt.mark("L" + std::to_string(l) + ".P");
     transpose(L.P, L.R, s);
     pt.mark("L" + std::to_string(l) + ".R");
@@ -422,9 +432,10 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
     alloc_level_vectors(h, L, q == 0, s);
     const bool f64 = !mixed(h), f32 = prm.precision == SAAMG_PREC_FP32;
     const bool bf16 = prm.precision == SAAMG_PREC_FP32_BF16;
-    // SELL for the large smoothed levels; a small level runs on CSR with wide row groups
+    // SELL for the large smoothed levels (built before their spectral bound); a small level
+    // runs on CSR with wide row groups
     if (q >= 1 && q < nl - 1 && L.n >= kSellMinRows) {
-      sell_from_csr(L.A, L.As, f64, f32, bf16, s);
+      if (L.As.n == 0) build_level_sell(h, L, s);
     } else if (q >= 1 && q < nl - 1) {
       if (f32) {
         L.A.val32.alloc(L.A.nnz, s);

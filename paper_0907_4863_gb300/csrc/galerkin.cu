@@ -11,6 +11,7 @@
 
 #include "csr.cuh"
 #include "galerkin.cuh"
+#include "sell.cuh"
 #include "operator.cuh"
 
 namespace saamg {
@@ -67,6 +68,29 @@ __device__ __forceinline__ int hash_find(const int* keys, int logcap, int key) {
   return -1;
 }
 
+// Ascending bitonic sort of 64 values held two per lane (element lane in x0, lane + 32 in x1).
+template <class T>
+__device__ __forceinline__ void bitonic64(T& x0, T& x1, int lane) {
+#pragma unroll
+  for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j == 32) {  // partners in the same lane (k = 64: ascending everywhere)
+        const T lo = min(x0, x1), hi = max(x0, x1);
+        x0 = lo;
+        x1 = hi;
+        continue;
+      }
+      const T y0 = __shfl_xor_sync(0xffffffffu, x0, j);
+      const T y1 = __shfl_xor_sync(0xffffffffu, x1, j);
+      const bool lower = (lane & j) == 0;
+      const bool asc0 = (lane & k) == 0, asc1 = ((lane + 32) & k) == 0;
+      x0 = lower == asc0 ? min(x0, y0) : max(x0, y0);
+      x1 = lower == asc1 ? min(x1, y1) : max(x1, y1);
+    }
+  }
+}
+
 // Warp-wide exclusive prefix of v; *total gets the sum over the warp.
 __device__ __forceinline__ int warp_excl_scan(int v, int lane, int* total) {
   int inc = v;
@@ -102,10 +126,19 @@ __global__ void __launch_bounds__(128) spgemm_hash_symbolic_k(const int* __restr
       const int p = pb + lane;
       if (p < p1) {
         const int k = X.col[p];
-        for (int q = Y.rowptr[k]; q < Y.rowptr[k + 1]; ++q) {
-          const int r = hash_insert(keys, logcap, Y.col[q]);
-          cnt += r > 0;
-          full |= r < 0;
+        const int q1 = Y.rowptr[k + 1];
+        // four independent column loads in flight, then their inserts
+        for (int q = Y.rowptr[k]; q < q1; q += 4) {
+          int c[4];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) c[b] = q + b < q1 ? Y.col[q + b] : -1;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            if (c[b] < 0) continue;
+            const int r = hash_insert(keys, logcap, c[b]);
+            cnt += r > 0;
+            full |= r < 0;
+          }
         }
       }
     }
@@ -131,8 +164,9 @@ __global__ void __launch_bounds__(128) spgemm_hash_symbolic_k(const int* __restr
 // fixes the summation order; 4) the copies are added in group order and the row is written
 // in ascending column order.  Per warp: cap keys, cap ranks, cap/2 compacted keys (ints)
 // and NG x cap values (doubles).
+// (16 blocks of 128 threads per SM: the pass is latency-bound and wants every warp slot)
 template <int NG>
-__global__ void __launch_bounds__(128) spgemm_hash_numeric_k(const int* __restrict__ list,
+__global__ void __launch_bounds__(128, 16) spgemm_hash_numeric_k(const int* __restrict__ list,
                                                              int nlist, int logcap, CsrView X,
                                                              CsrView Y,
                                                              const int* __restrict__ crowptr,
@@ -164,7 +198,15 @@ __global__ void __launch_bounds__(128) spgemm_hash_numeric_k(const int* __restri
       const int p = pb + lane;
       if (p < p1) {
         const int k = X.col[p];
-        for (int q = Y.rowptr[k]; q < Y.rowptr[k + 1]; ++q) hash_insert(keys, logcap, Y.col[q]);
+        const int q1 = Y.rowptr[k + 1];
+        for (int q = Y.rowptr[k]; q < q1; q += 4) {
+          int c[4];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) c[b] = q + b < q1 ? Y.col[q + b] : -1;
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            if (c[b] >= 0) hash_insert(keys, logcap, c[b]);
+        }
       }
     }
     __syncwarp();
@@ -209,6 +251,124 @@ __global__ void __launch_bounds__(128) spgemm_hash_numeric_k(const int* __restri
       cval[base + rank[q]] = v;
     }
     __syncwarp();
+  }
+}
+
+// Block-per-row forms of the hash passes for classes of few rows (the long rows of the
+// smallest levels): the block's threads share one key table; in the numeric pass warp w
+// accumulates the w-th contiguous share of X's entries into its own NG value copies, and the
+// copies are added in (warp, group) order, so the sums are fixed for a given launch shape.
+__global__ void __launch_bounds__(256) spgemm_hash_symbolic_blk_k(const int* __restrict__ list,
+                                                                  int nlist, int logcap,
+                                                                  CsrView X, CsrView Y,
+                                                                  int* __restrict__ count,
+                                                                  int* __restrict__ overflow) {
+  extern __shared__ int smem_b[];
+  __shared__ int tot[2];
+  const int cap = 1 << logcap;
+  int* keys = smem_b;
+  for (int t = blockIdx.x; t < nlist; t += gridDim.x) {
+    const int i = list[t];
+    for (int q = threadIdx.x; q < cap; q += blockDim.x) keys[q] = -1;
+    if (threadIdx.x < 2) tot[threadIdx.x] = 0;
+    __syncthreads();
+    int cnt = 0, full = 0;
+    const int p1 = X.rowptr[i + 1];
+    for (int p = X.rowptr[i] + threadIdx.x; p < p1; p += blockDim.x) {
+      const int k = X.col[p];
+      for (int q = Y.rowptr[k]; q < Y.rowptr[k + 1]; ++q) {
+        const int r = hash_insert(keys, logcap, Y.col[q]);
+        cnt += r > 0;
+        full |= r < 0;
+      }
+    }
+    if (cnt) atomicAdd(&tot[0], cnt);
+    if (full) atomicOr(&tot[1], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const bool over = tot[1] || 2 * tot[0] > cap;
+      count[i] = over ? -1 : tot[0];
+      if (over) atomicAdd(overflow, 1);
+    }
+    __syncthreads();
+  }
+}
+
+template <int NG>
+__global__ void __launch_bounds__(256) spgemm_hash_numeric_blk_k(const int* __restrict__ list,
+                                                                 int nlist, int logcap, CsrView X,
+                                                                 CsrView Y,
+                                                                 const int* __restrict__ crowptr,
+                                                                 int* __restrict__ ccol,
+                                                                 double* __restrict__ cval) {
+  extern __shared__ double smem_bd[];
+  __shared__ int nus;
+  constexpr int GL = 32 / NG;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int grp = lane / GL, gl = lane % GL;
+  const int cap = 1 << logcap;
+  const int cstride = cap + 1;
+  double* vals = smem_bd;
+  int* keys = reinterpret_cast<int*>(vals + (size_t)cstride * NG * nwarps);
+  int* rank = keys + cap;
+  int* uniq = keys + 2 * cap;
+  double* mine = vals + (size_t)(warp * NG + grp) * cstride;
+  for (int t = blockIdx.x; t < nlist; t += gridDim.x) {
+    const int i = list[t];
+    for (int q = threadIdx.x; q < cap; q += blockDim.x) keys[q] = -1;
+    for (int q = threadIdx.x; q < cstride * NG * nwarps; q += blockDim.x) vals[q] = 0.0;
+    __syncthreads();
+    const int p0 = X.rowptr[i], p1 = X.rowptr[i + 1];
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+      const int k = X.col[p];
+      for (int q = Y.rowptr[k]; q < Y.rowptr[k + 1]; ++q) hash_insert(keys, logcap, Y.col[q]);
+    }
+    __syncthreads();
+    if (warp == 0) {  // compact the distinct columns
+      int nu = 0;
+      for (int q0 = 0; q0 < cap; q0 += 32) {
+        const int key = keys[q0 + lane];
+        const unsigned bm = __ballot_sync(0xffffffffu, key >= 0);
+        if (key >= 0) uniq[nu + __popc(bm & ((1u << lane) - 1u))] = key;
+        nu += __popc(bm);
+      }
+      if (lane == 0) nus = nu;
+    }
+    __syncthreads();
+    const int nu = nus;
+    for (int q = threadIdx.x; q < cap; q += blockDim.x) {
+      const int key = keys[q];
+      if (key < 0) continue;
+      int r = 0;
+      for (int u = 0; u < nu; ++u) r += uniq[u] < key;
+      rank[q] = r;
+    }
+    // warp w: entries [p0 + w * share, p0 + (w + 1) * share), its groups in turn
+    const int share = (p1 - p0 + nwarps - 1) / nwarps;
+    const int w0 = p0 + warp * share, w1 = min(p1, w0 + share);
+    for (int pb = w0; pb < w1; pb += NG) {
+      const int p = pb + grp;
+      if (p < w1) {
+        const int k = X.col[p];
+        const double xv = X.val[p];
+        for (int q = Y.rowptr[k] + gl; q < Y.rowptr[k + 1]; q += GL) {
+          const int slot = hash_find(keys, logcap, Y.col[q]);
+          if (slot >= 0) mine[slot] += xv * Y.val[q];
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    const int base = crowptr[i];
+    for (int q = threadIdx.x; q < cap; q += blockDim.x) {
+      const int key = keys[q];
+      if (key < 0) continue;
+      double v = vals[q];
+      for (int c = 1; c < NG * nwarps; ++c) v += vals[(size_t)c * cstride + q];
+      ccol[base + rank[q]] = key;
+      cval[base + rank[q]] = v;
+    }
+    __syncthreads();
   }
 }
 
@@ -372,6 +532,22 @@ __global__ void row_products_k(int n, CsrView X, CsrView Y, int* __restrict__ np
   nprod[i] = (int)(t < 0x7fffffffLL ? t : 0x7fffffffLL);
 }
 
+// Warp per row, for a few long X rows (the small coarse levels).
+__global__ void row_products_warp_k(int n, CsrView X, CsrView Y, int* __restrict__ nprod) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+    long long t = 0;
+    for (int p = X.rowptr[i] + lane; p < X.rowptr[i + 1]; p += 32) {
+      const int k = X.col[p];
+      t += Y.rowptr[k + 1] - Y.rowptr[k];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) nprod[i] = (int)(t < 0x7fffffffLL ? t : 0x7fffffffLL);
+  }
+}
+
 // Class of every row (symbolic: table sized from min(products, m); numeric: from the exact
 // count); block-aggregated histogram.
 __global__ void classify_rows_k(int n, const int* __restrict__ xrowptr,
@@ -445,6 +621,152 @@ __global__ void tentative_k(int n, const int* __restrict__ agg, int* __restrict_
   if (i == n) rowptr[n] = n;
 }
 
+// --- A T and the smoothed prolongator ------------------------------------------
+// Row i of A T (T(j, agg(j)) = 1) holds the distinct aggregates agg(j) of A's row i, each with
+// the sum of the row's a_ij over it.  A group of G lanes takes one row, G entries at a time:
+// equal aggregates inside a chunk are found by a match and summed by their lowest lane in
+// lane (= entry) order, and the chunk sums are merged into the row's list, kept in scratch
+// arrays laid out like A (a row never has more aggregates than entries), in order of first
+// appearance.  A row of at most G entries is therefore summed strictly in entry order.
+template <int G>
+__global__ void __launch_bounds__(256) at_lists_k(int n, const int* __restrict__ rowptr,
+                                                  const int* __restrict__ col,
+                                                  const double* __restrict__ val,
+                                                  const int* __restrict__ agg,
+                                                  int* __restrict__ lcol,
+                                                  double* __restrict__ lval,
+                                                  int* __restrict__ cnt, bool sortable) {
+  constexpr int RPW = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / G, gl = lane % G;
+  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (sub * G);
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int wb = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW; wb < n; wb += nw * RPW) {
+    const int i = wb + sub;
+    const bool act = i < n;
+    const int p0 = act ? rowptr[i] : 0;
+    const int len = act ? rowptr[i + 1] - p0 : 0;
+    int maxlen = len;
+#pragma unroll
+    for (int o = G; o < 32; o <<= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
+    if (G == 32 && sortable && len <= 64) {
+      // the row's (aggregate, entry) pairs sorted in registers: equal aggregates become
+      // neighbours in entry order and the list comes out in ascending order
+      __shared__ unsigned skey[8][64];
+      __shared__ double sval[8][64];
+      const int w = threadIdx.x >> 5;
+      unsigned x0 = 0xffffffffu, x1 = 0xffffffffu;
+      if (lane < len) {
+        x0 = ((unsigned)agg[col[p0 + lane]] << 6) | (unsigned)lane;
+        sval[w][lane] = val[p0 + lane];
+      }
+      if (lane + 32 < len) {
+        x1 = ((unsigned)agg[col[p0 + lane + 32]] << 6) | (unsigned)(lane + 32);
+        sval[w][lane + 32] = val[p0 + lane + 32];
+      }
+      bitonic64(x0, x1, lane);
+      skey[w][lane] = x0;
+      skey[w][lane + 32] = x1;
+      __syncwarp();
+      int m = 0;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int sp = lane + 32 * r;
+        const unsigned x = r ? x1 : x0;
+        const bool head = sp < len && (sp == 0 || (skey[w][sp - 1] >> 6) != (x >> 6));
+        const unsigned hm = __ballot_sync(0xffffffffu, head);
+        if (head) {
+          const unsigned kk = x >> 6;
+          double sum = sval[w][x & 63u];
+          for (int t = sp + 1; t < len && (skey[w][t] >> 6) == kk; ++t) sum += sval[w][skey[w][t] & 63u];
+          const int pos = m + __popc(hm & ((1u << lane) - 1u));
+          lcol[p0 + pos] = (int)kk;
+          lval[p0 + pos] = sum;
+        }
+        m += __popc(hm);
+      }
+      if (lane == 0) cnt[i] = m;
+      __syncwarp();
+      continue;
+    }
+    int m = 0;  // the group's list length
+    for (int cb = 0; cb < maxlen; cb += G) {
+      const bool ok = cb + gl < len;
+      const int p = p0 + cb + gl;
+      const int key = ok ? agg[col[p]] : -1;
+      const double v = ok ? val[p] : 0.0;
+      // the lanes of this group holding the same aggregate
+      const unsigned long long k64 = ((unsigned long long)(unsigned)sub << 32) | (unsigned)key;
+      const unsigned mt = __match_any_sync(0xffffffffu, k64);
+      int cmax = __popc(mt);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+      double sum = 0.0;
+      unsigned rem = mt;
+      for (int t = 0; t < cmax; ++t) {
+        const int src = rem ? __ffs(rem) - 1 : lane;
+        const double sv = __shfl_sync(0xffffffffu, v, src);
+        if (rem) {
+          sum = t == 0 ? sv : sum + sv;
+          rem &= rem - 1u;
+        }
+      }
+      const bool lead = ok && lane == __ffs(mt) - 1;
+      int pos = -1;
+      if (lead)
+        for (int u = 0; u < m; ++u)
+          if (lcol[p0 + u] == key) {
+            pos = u;
+            break;
+          }
+      const bool fresh = lead && pos < 0;
+      const unsigned fm = __ballot_sync(0xffffffffu, fresh) & gmask;
+      if (fresh) {
+        pos = m + __popc(fm & ((1u << lane) - 1u));
+        lcol[p0 + pos] = key;
+        lval[p0 + pos] = sum;
+      } else if (lead) {
+        lval[p0 + pos] += sum;
+      }
+      m += __popc(fm);
+      __syncwarp();
+    }
+    if (act && gl == 0) cnt[i] = m;
+  }
+}
+
+// P's row i from the list: P_iJ = [J == agg(i)] - (omega invd_i) (A T)_iJ, columns ascending
+// (each entry's rank among the row's aggregates gives its place).
+template <int G>
+__global__ void __launch_bounds__(256) at_prolong_k(int n, const int* __restrict__ arowptr,
+                                                    const int* __restrict__ lcol,
+                                                    const double* __restrict__ lval,
+                                                    const int* __restrict__ prowptr,
+                                                    const int* __restrict__ agg,
+                                                    const double* __restrict__ invd,
+                                                    double omega, int* __restrict__ pcol,
+                                                    double* __restrict__ pval) {
+  constexpr int RPW = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / G, gl = lane % G;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int wb = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW; wb < n; wb += nw * RPW) {
+    const int i = wb + sub;
+    if (i >= n) continue;  // no collective operation below
+    const int a0 = arowptr[i], b0 = prowptr[i], m = prowptr[i + 1] - b0;
+    const double w = omega * invd[i];
+    const int a = agg[i];
+    for (int u = gl; u < m; u += G) {
+      const int key = lcol[a0 + u];
+      int r = 0;
+      for (int q = 0; q < m; ++q) r += lcol[a0 + q] < key;
+      const double tij = key == a ? 1.0 : 0.0;
+      pcol[b0 + r] = key;
+      pval[b0 + r] = tij - w * lval[a0 + u];
+    }
+  }
+}
+
 __global__ void col_count_k(long long nnz, const int* __restrict__ col, int* __restrict__ cnt) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nnz;
        p += (long long)gridDim.x * blockDim.x)
@@ -482,16 +804,45 @@ __global__ void rank_rows_k(int n, const int* __restrict__ rowptr, const int* __
   }
 }
 
+// Block per row for the long rows of small levels: the row's columns are staged in shared
+// memory and every entry counts the smaller ones there.
+constexpr int kRankStage = 8192;
+__global__ void __launch_bounds__(256) rank_rows_block_k(int n, const int* __restrict__ rowptr,
+                                                         const int* __restrict__ tcol,
+                                                         const double* __restrict__ tval,
+                                                         int* __restrict__ col,
+                                                         double* __restrict__ val) {
+  __shared__ int sc[kRankStage];
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const int p0 = rowptr[i], len = rowptr[i + 1] - p0;
+    const bool staged = len <= kRankStage;
+    if (staged)
+      for (int u = threadIdx.x; u < len; u += blockDim.x) sc[u] = tcol[p0 + u];
+    __syncthreads();
+    const int* cs = staged ? sc : tcol + p0;
+    for (int u = threadIdx.x; u < len; u += blockDim.x) {
+      const int c = cs[u];
+      int rank = 0;
+      for (int q = 0; q < len; ++q) rank += cs[q] < c;
+      col[p0 + rank] = c;
+      val[p0 + rank] = tval[p0 + u];
+    }
+    __syncthreads();
+  }
+}
+
 inline int blocks_for(long long n, int t = 256) { return (int)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1); }
 
 constexpr int kSpgemmWarps = 4;
+// a hash class of at most this many rows runs a block per row
+constexpr int kFewRows = 2048;
 
 CsrView view(const DevCsr& a) { return CsrView{a.rowptr.p, a.col.p, a.val.p}; }
 
 }  // namespace
 
 double power_lambda(const DevCsr& A, const double* invd, const unsigned* ids, int iters,
-                    cudaStream_t s, const StencilDev<double>* S) {
+                    cudaStream_t s, const StencilDev<double>* S, const DevSell* As) {
   int n = A.n;
   if (n == 0) return 1.0;
   // v_{k+1} = D^-1 A v_k / |D^-1 A v_k|: the pass that forms D^-1 A v_{k+1} applies the
@@ -509,6 +860,9 @@ double power_lambda(const DevCsr& A, const double* invd, const unsigned* ids, in
     if (S)
       stencil_apply<double>(*S, ST_DINV_DOT, v.p, w.p, nullptr, nullptr, 0.0, 0.0, part.p, s,
                             xscale);
+    else if (As && As->val.p)
+      sell_apply<double, double>(CSR_SPMV_DINV_DOT, *As, As->val.p, v.p, w.p, nullptr, nullptr,
+                                 invd, 0.0, 0.0, s, -1, part.p, xscale);
     else
       csr_apply<double, double>(CSR_SPMV_DINV_DOT, n, A.rowptr.p, A.col.p, A.val.p, avg, v.p,
                                 w.p, nullptr, nullptr, invd, 0.0, 0.0, part.p, s, -1, xscale);
@@ -570,6 +924,36 @@ void run_class(int c, const int* list, int nl, CsrView X, CsrView Y, double yavg
   }
   const int lg = kHashMinLog + (c - 2);
   const int cap = 1 << lg;
+  if (nl <= kFewRows) {  // few rows: a block per row
+    const int nb = std::min(nl, 152 * 4);
+    if (!NUMERIC) {
+      const size_t sm = (size_t)cap * sizeof(int);
+      if (sm > 48 * 1024)
+        SAAMG_CUDA(cudaFuncSetAttribute(spgemm_hash_symbolic_blk_k,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      spgemm_hash_symbolic_blk_k<<<nb, 256, sm, s>>>(list, nl, lg, X, Y, count, overflow);
+    } else {
+      const int ng = yavg <= 7.0 ? 4 : (yavg <= 14.0 ? 2 : 1);
+      // 8 warps when their value copies fit 160 KB, else fewer
+      int wpb = 8;
+      auto bytes = [&](int w) {
+        return (size_t)(cap + 1) * sizeof(double) * ng * w + (size_t)cap * sizeof(int) * 5 / 2;
+      };
+      while (wpb > 1 && bytes(wpb) > (160u << 10)) wpb >>= 1;
+      const size_t sm = bytes(wpb);
+      auto launch = [&](auto kernel) {
+        if (sm > 48 * 1024)
+          SAAMG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sm));
+        kernel<<<nb, 32 * wpb, sm, s>>>(list, nl, lg, X, Y, crowptr, ccol, cval);
+      };
+      if (ng == 4) launch(spgemm_hash_numeric_blk_k<4>);
+      else if (ng == 2) launch(spgemm_hash_numeric_blk_k<2>);
+      else launch(spgemm_hash_numeric_blk_k<1>);
+    }
+    SAAMG_LAUNCH();
+    return;
+  }
   if (!NUMERIC) {
     const size_t sm = (size_t)kSpgemmWarps * cap * sizeof(int);
     if (sm > 48 * 1024)
@@ -622,7 +1006,11 @@ void spgemm(const DevCsr& X, const DevCsr& Y, DevCsr& C, cudaStream_t s) {
   ctl.alloc(2 * kClasses + 1, s);
   int* overflow = ctl.p + 2 * kClasses;
   SAAMG_CUDA(cudaMemsetAsync(overflow, 0, sizeof(int), s));
-  row_products_k<<<blocks_for(n), 256, 0, s>>>(n, view(X), view(Y), nprod.p);
+  if (n < 32768 && (double)X.nnz > 32.0 * n) {
+    row_products_warp_k<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, view(X), view(Y), nprod.p);
+  } else {
+    row_products_k<<<blocks_for(n), 256, 0, s>>>(n, view(X), view(Y), nprod.p);
+  }
   SAAMG_LAUNCH();
   int hist[kClasses], start[kClasses + 1];
   // symbolic: distinct columns per row
@@ -644,6 +1032,56 @@ void spgemm(const DevCsr& X, const DevCsr& Y, DevCsr& C, cudaStream_t s) {
   for (int c = 0; c < kClasses; ++c)
     run_class<true>(c, list.p + start[c], hist[c], view(X), view(Y), yavg, C.rowptr.p, nullptr, nullptr,
                     C.col.p, C.val.p, s);
+}
+
+void smoothed_prolongator(DevCsr& AT, const int* agg, const double* invd, double omega,
+                          DevCsr& P, cudaStream_t s);
+
+void prolongator(const DevCsr& A, const int* agg, int nagg, const double* invd, double omega,
+                 DevCsr& P, cudaStream_t s) {
+  const int n = A.n;
+  const double avg = n > 0 ? (double)A.nnz / n : 0.0;
+  if (avg <= 8.0) {  // short rows (level 0): T and the register k-way merge product
+    DevCsr T, AT;
+    tentative(agg, n, nagg, T, s);
+    spgemm(A, T, AT, s);
+    smoothed_prolongator(AT, agg, invd, omega, P, s);
+    return;
+  }
+  P.n = n;
+  P.m = nagg;
+  P.rowptr.alloc(n + 1, s);
+  Buf<int> lcol, cnt;
+  Buf<double> lval;
+  lcol.alloc(A.nnz, s);
+  lval.alloc(A.nnz, s);
+  cnt.alloc(n + 1, s);
+  const int G = avg <= 16.0 ? 16 : 32;
+  const bool sortable = nagg < (1 << 25);  // (aggregate << 6 | entry) stays below 0xffffffff
+  const int blocks = (int)std::min<long long>(((long long)n * G + 255) / 256, 152 * 32);
+  {
+    KernelTimer kt(SAAMG_KT_SPGEMM, n, s);
+    if (G == 16)
+      at_lists_k<16><<<blocks, 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, agg, lcol.p, lval.p,
+                                            cnt.p, sortable);
+    else
+      at_lists_k<32><<<blocks, 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, agg, lcol.p, lval.p,
+                                            cnt.p, sortable);
+    SAAMG_LAUNCH();
+  }
+  fill_int(cnt.p + n, 0, 1, s);
+  const long long nnz = exclusive_scan(cnt.p, P.rowptr.p, n + 1, s);
+  P.nnz = nnz;
+  P.col.alloc(nnz, s);
+  P.val.alloc(nnz, s);
+  KernelTimer kt(SAAMG_KT_SPGEMM, n, s);
+  if (G == 16)
+    at_prolong_k<16><<<blocks, 256, 0, s>>>(n, A.rowptr.p, lcol.p, lval.p, P.rowptr.p, agg, invd,
+                                            omega, P.col.p, P.val.p);
+  else
+    at_prolong_k<32><<<blocks, 256, 0, s>>>(n, A.rowptr.p, lcol.p, lval.p, P.rowptr.p, agg, invd,
+                                            omega, P.col.p, P.val.p);
+  SAAMG_LAUNCH();
 }
 
 void smoothed_prolongator(DevCsr& AT, const int* agg, const double* invd, double omega,
@@ -680,7 +1118,11 @@ void transpose(const DevCsr& P, DevCsr& R, cudaStream_t s) {
                                                      tcol.p, tval.p);
     SAAMG_LAUNCH();
   }
-  if (R.n > 0) {
+  if (R.n > 0 && R.n < 65536 && P.nnz > 64LL * R.n) {  // few long rows
+    rank_rows_block_k<<<std::min(R.n, 152 * 8), 256, 0, s>>>(R.n, R.rowptr.p, tcol.p, tval.p,
+                                                            R.col.p, R.val.p);
+    SAAMG_LAUNCH();
+  } else if (R.n > 0) {
     long long warps = R.n;
     int blocks = (int)std::min<long long>((warps * 32 + 255) / 256, 152 * 32);
     rank_rows_k<<<blocks, 256, 0, s>>>(R.n, R.rowptr.p, tcol.p, tval.p, R.col.p, R.val.p);

@@ -77,12 +77,15 @@ __global__ void __launch_bounds__(256) sell_k(int n, int nslices, const int* __r
                                               const TM* __restrict__ val, const TV* __restrict__ x,
                                               TV* __restrict__ y, const TV* __restrict__ b,
                                               TV* __restrict__ d, const TV* __restrict__ invd,
-                                              TV c1, TV c2) {
+                                              TV c1, TV c2, double* __restrict__ partials,
+                                              const double* __restrict__ xscale) {
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
+  double dacc = 0.0;
+  if (MODE == CSR_SPMV_DINV_DOT) c2 = xscale ? (TV)*xscale : TV(1);
   for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < nslices; s += nw) {
     const int p = 32 * s + lane;
-    if (p >= n) continue;  // no warp-collective operation follows
+    if (p >= n) continue;  // no warp-collective operation inside the loop
     const int row = perm[p];
     TV acc = TV(0);
     if (MODE != CSR_CHEB0) {
@@ -119,10 +122,25 @@ __global__ void __launch_bounds__(256) sell_k(int n, int nslices, const int* __r
       const TV dv = c2 * (invd[row] * (b[row] - acc));
       d[row] = dv;
       y[row] = x[row] + dv;
-    } else {  // CSR_CHEB0
+    } else if (MODE == CSR_CHEB0) {
       const TV dv = c2 * (invd[row] * b[row]);
       d[row] = dv;
       y[row] = dv;
+    } else {  // CSR_SPMV_DINV_DOT: c2 carries the scale of x
+      const TV w = (c2 * invd[row]) * acc;
+      y[row] = w;
+      dacc += (double)w * (double)w;
+    }
+  }
+  if (MODE == CSR_SPMV_DINV_DOT) {  // fixed grid of kRedBlocks: the same partial sums every run
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+    if (lane == 0) sh[threadIdx.x >> 5] = dacc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+      partials[blockIdx.x] = t;
     }
   }
 }
@@ -166,16 +184,21 @@ void sell_from_csr(const DevCsr& A, DevSell& S, bool f64, bool f32, bool bf16, c
 
 template <class TV, class TM>
 void sell_apply(int mode, const DevSell& S, const TM* val, const TV* x, TV* y, const TV* b,
-                TV* d, const TV* invd, TV c1, TV c2, cudaStream_t s, int kclass) {
-  if (S.n <= 0) return;
+                TV* d, const TV* invd, TV c1, TV c2, cudaStream_t s, int kclass,
+                double* partials, const double* xscale) {
+  if (S.n <= 0) {
+    if (mode == CSR_SPMV_DINV_DOT) fill_double(partials, 0.0, kRedBlocks, s);
+    return;
+  }
   KernelTimer kt(kclass, S.nnz, s);  // timing unit of the SELL classes: matrix entries
   if (mode == CSR_CHEB && c1 == TV(0)) mode = kSellCheb1;
   const long long need = ((long long)S.nslices + 7) / 8;
-  const int blocks = (int)(need < 152 * 16 ? need : 152 * 16);
+  const int blocks =
+      mode == CSR_SPMV_DINV_DOT ? kRedBlocks : (int)(need < 152 * 16 ? need : 152 * 16);
 #define SAAMG_SELL_CASE(M)                                                                    \
   case M:                                                                                     \
     sell_k<TV, TM, M><<<blocks, 256, 0, s>>>(S.n, S.nslices, S.perm.p, S.soff.p, S.col.p, val, \
-                                             x, y, b, d, invd, c1, c2);                        \
+                                             x, y, b, d, invd, c1, c2, partials, xscale);      \
     break;
   switch (mode) {
     SAAMG_SELL_CASE(CSR_SPMV)
@@ -184,6 +207,7 @@ void sell_apply(int mode, const DevSell& S, const TM* val, const TV* x, TV* y, c
     SAAMG_SELL_CASE(CSR_CHEB0)
     SAAMG_SELL_CASE(CSR_ADD)
     SAAMG_SELL_CASE(kSellCheb1)
+    SAAMG_SELL_CASE(CSR_SPMV_DINV_DOT)
     default:
       fail(SAAMG_EINVAL, "bad SELL mode");
   }
@@ -193,12 +217,13 @@ void sell_apply(int mode, const DevSell& S, const TM* val, const TV* x, TV* y, c
 
 template void sell_apply<double, double>(int, const DevSell&, const double*, const double*,
                                          double*, const double*, double*, const double*, double,
-                                         double, cudaStream_t, int);
+                                         double, cudaStream_t, int, double*, const double*);
 template void sell_apply<float, float>(int, const DevSell&, const float*, const float*, float*,
                                        const float*, float*, const float*, float, float,
-                                       cudaStream_t, int);
+                                       cudaStream_t, int, double*, const double*);
 template void sell_apply<float, __nv_bfloat16>(int, const DevSell&, const __nv_bfloat16*,
                                                const float*, float*, const float*, float*,
-                                               const float*, float, float, cudaStream_t, int);
+                                               const float*, float, float, cudaStream_t, int,
+                                               double*, const double*);
 
 }  // namespace saamg

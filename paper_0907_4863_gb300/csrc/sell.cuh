@@ -39,9 +39,11 @@ struct DevSell {
 // S = A in SELL form with the value arrays requested (FP64 / FP32 / BF16 copies of A.val).
 void sell_from_csr(const DevCsr& A, DevSell& S, bool f64, bool f32, bool bf16, cudaStream_t s);
 
-// The CSR modes of csr_apply (CSR_CHEB with c1 == 0 does not read d).
+// The CSR modes of csr_apply (CSR_CHEB with c1 == 0 does not read d; CSR_SPMV_DINV_DOT
+// writes kRedBlocks partial sums of y.y and takes the scale of x from *xscale, 1 if NULL).
 template <class TV, class TM>
 void sell_apply(int mode, const DevSell& S, const TM* val, const TV* x, TV* y, const TV* b,
-                TV* d, const TV* invd, TV c1, TV c2, cudaStream_t s, int kclass);
+                TV* d, const TV* invd, TV c1, TV c2, cudaStream_t s, int kclass,
+                double* partials = nullptr, const double* xscale = nullptr);
 
 }  // namespace saamg
