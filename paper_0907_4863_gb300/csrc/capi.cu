@@ -45,7 +45,34 @@ static AllocHook g_alloc;
 
 AllocHook current_allocator() { return g_alloc; }
 
-void* dev_alloc(const AllocHook& h, size_t bytes, cudaStream_t s) {
+namespace {
+
+struct CachedBlock {
+  void* p;
+  cudaStream_t s;
+  AllocHook hook;
+};
+
+constexpr size_t kPoolMaxBlock = 64ull << 20;
+constexpr size_t kPoolMaxBytes = 1ull << 30;
+
+std::mutex g_pool_mu;
+std::multimap<size_t, CachedBlock> g_pool;  // rounded size -> free block
+size_t g_pool_bytes = 0;
+
+bool same_hook(const AllocHook& a, const AllocHook& b) {
+  return a.alloc == b.alloc && a.free == b.free && a.ctx == b.ctx;
+}
+
+// size classes: multiples of 512 B up to 64 KB, then eight steps per power of two
+size_t pool_class(size_t bytes) {
+  if (bytes <= (64u << 10)) return (bytes + 511) & ~size_t(511);
+  size_t top = size_t(1) << (63 - __builtin_clzll(bytes - 1));
+  const size_t step = top >> 3;
+  return (bytes + step - 1) / step * step;
+}
+
+void* raw_alloc(const AllocHook& h, size_t bytes, cudaStream_t s) {
   void* p = nullptr;
   if (h.alloc) {
     p = h.alloc(bytes, (void*)s, h.ctx);
@@ -61,14 +88,63 @@ void* dev_alloc(const AllocHook& h, size_t bytes, cudaStream_t s) {
   return p;
 }
 
-void dev_free(const AllocHook& h, void* p, cudaStream_t s) {
-  if (!p) return;
+void raw_free(const AllocHook& h, void* p, cudaStream_t s) {
   if (h.free) {
     h.free(p, (void*)s, h.ctx);
     return;
   }
   // cudaFree synchronises the device: pending work that reads p finishes first
   cudaFree(p);
+}
+
+// Returns every cached block to its hook (the caller holds no lock).
+void pool_drain() {
+  std::multimap<size_t, CachedBlock> blocks;
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    blocks.swap(g_pool);
+    g_pool_bytes = 0;
+  }
+  for (auto& kv : blocks) raw_free(kv.second.hook, kv.second.p, kv.second.s);
+}
+
+}  // namespace
+
+void* dev_alloc(const AllocHook& h, size_t bytes, cudaStream_t s) {
+  const size_t c = pool_class(bytes);
+  if (c <= kPoolMaxBlock) {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    auto range = g_pool.equal_range(c);
+    for (auto it = range.first; it != range.second; ++it) {
+      if (it->second.s == s && same_hook(it->second.hook, h)) {
+        void* p = it->second.p;
+        g_pool.erase(it);
+        g_pool_bytes -= c;
+        return p;
+      }
+    }
+  }
+  try {
+    return raw_alloc(h, c, s);
+  } catch (const Error& e) {
+    if (e.status != SAAMG_ENOMEM) throw;
+    pool_drain();  // give the cached blocks back and try once more
+    return raw_alloc(h, c, s);
+  }
+}
+
+void dev_free(const AllocHook& h, void* p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  const size_t c = pool_class(bytes);
+  if (c <= kPoolMaxBlock) {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (g_pool_bytes + c <= kPoolMaxBytes && same_hook(h, g_alloc)) {
+      g_pool.emplace(c, CachedBlock{p, s, h});
+      g_pool_bytes += c;
+      return;
+    }
+  }
+  raw_free(h, p, s);
 }
 
 HostScratch::~HostScratch() {
@@ -926,20 +1002,6 @@ static saamg_status info_from_ctl(const PcgCtl& c, saamg_solve_info* info) {
   return info->converged ? SAAMG_OK : SAAMG_NOT_CONVERGED;
 }
 
-// Streams for batched solves (created once, non-blocking).
-static std::mutex g_pool_mu;
-static std::vector<cudaStream_t> g_pool;
-
-static cudaStream_t pool_stream(size_t k) {
-  std::lock_guard<std::mutex> lock(g_pool_mu);
-  while (g_pool.size() <= k) {
-    cudaStream_t st;
-    SAAMG_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    g_pool.push_back(st);
-  }
-  return g_pool[k];
-}
-
 static void recompute_cheb(saamg_hierarchy* h, int degree) {
   const int nl = (int)h->lev.size();
   for (int q = 0; q + 1 < nl; ++q) {
@@ -979,6 +1041,10 @@ saamg_status saamg_set_allocator(saamg_alloc_fn alloc, saamg_free_fn free_fn, vo
   if ((alloc == nullptr) != (free_fn == nullptr)) {
     g_last_error = "saamg_set_allocator: alloc and free must both be set or both be NULL";
     return SAAMG_EINVAL;
+  }
+  try {
+    pool_drain();  // cached blocks belong to the allocator being replaced
+  } catch (...) {
   }
   g_alloc.alloc = alloc;
   g_alloc.free = free_fn;

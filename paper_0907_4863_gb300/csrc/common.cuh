@@ -56,8 +56,12 @@ struct AllocHook {
   void* ctx = nullptr;
 };
 AllocHook current_allocator();
+// Blocks come from the hook (cudaMalloc without one).  Blocks of up to 64 MB that the library
+// frees are kept, up to 1 GB in all, and handed out again for the same stream and hook (stream
+// order makes that reuse safe without a synchronisation); they go back to the hook when the
+// allocator changes.  `bytes` of dev_free is the size given to dev_alloc.
 void* dev_alloc(const AllocHook& h, size_t bytes, cudaStream_t s);
-void dev_free(const AllocHook& h, void* p, cudaStream_t s);
+void dev_free(const AllocHook& h, void* p, size_t bytes, cudaStream_t s);
 
 // Owning device array (move-only).  Memory comes from the hook captured at allocation.
 template <class T>
@@ -95,7 +99,7 @@ struct Buf {
   void release() noexcept {
     if (p) {
       try {
-        dev_free(hook, p, stream);
+        dev_free(hook, p, (n > 0 ? n : 1) * sizeof(T), stream);
       } catch (...) {
       }
     }
