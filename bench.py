@@ -208,7 +208,8 @@ def run_ours(args):
     # solve-phase class is one kernel template; the sparse products of the setup are several
     # different kernels, reported as a class time only.
     dom_name = max(SOLVE_CLASSES, key=lambda k: ktime[k][0])
-    roof = roofline(dom_name, ktime[dom_name], prec, args.n)
+    ib1 = level1_index_bytes(hinfo)
+    roof = roofline(dom_name, ktime[dom_name], prec, args.n, ib1)
 
     # --- end to end through the public API with host buffers (pinned), copies in the region
     nbox = w.grid.nbox
@@ -275,7 +276,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def roofline(name, rec, prec, n=256):
+def roofline(name, rec, prec, n=256, index_bytes=4):
     """Algorithmic work per launch / average launch duration of one timing class.
 
     Stencil classes count rows; the sparse-matrix classes (coarse_csr, transfer) count
@@ -308,10 +309,12 @@ def roofline(name, rec, prec, n=256):
                   "stencil_first": 3.5}[name] * w * per
     else:
         # 2 flops per entry; bytes per entry: column index + value (FP32 / BF16 values in
-        # the mixed V-cycle; transfers keep FP32 values in both mixed modes)
+        # the mixed V-cycle; transfers keep FP32 values in both mixed modes).  The level-1
+        # smoother (coarse_csr) stores 16-bit column offsets when they fit (index_bytes 2).
         flops = 2 * per
         vbytes = 8 if prec == 0 else (2 if (prec == 2 and name.startswith("coarse")) else 4)
-        nbytes = (4 + vbytes) * per
+        ibytes = index_bytes if name == "coarse_csr" else 4
+        nbytes = (ibytes + vbytes) * per
     out = {"kernel": name, "avg_launch_us": avg_s * 1e6, "launches": launches,
            "traffic": TRAFFIC_BYTES.get((name, prec, n)),
            "algorithmic_bytes_per_launch": nbytes, "algorithmic_flops_per_launch": flops}
@@ -328,6 +331,12 @@ def roofline(name, rec, prec, n=256):
         out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                     "frac": ach / hbm, "peak_source": "measured" if peaks else "fallback"})
     return out
+
+
+def level1_index_bytes(info):
+    """Column bytes per stored entry of the level-1 smoother (SELL: 2 or 4; CSR: 4)."""
+    ib = info.get("sell_index_bytes", [])
+    return ib[1] if len(ib) > 1 and ib[1] else 4
 
 
 def extra_legs(S, torch, w, dom, grid, rho, args):
@@ -370,7 +379,8 @@ def extra_legs(S, torch, w, dom, grid, rho, args):
             "solve_only_solves_per_s": 1e3 / ms, "solve_ms": ms,
             "full_pipeline_solves_per_s": 1e3 / full_ms, "setup_ms": h.info()["setup_ms"],
             "iters": its[-1]["iters"], "relres_true": its[-1]["relres_true"],
-            "rooflines": {c: roofline(c, kt[c], prec, args.n) for c in SOLVE_CLASSES},
+            "rooflines": {c: roofline(c, kt[c], prec, args.n, level1_index_bytes(h.info()))
+                          for c in SOLVE_CLASSES},
             "kernel_classes_ms_per_solve": {k: v[0] / args.steps for k, v in kt.items()},
             "solve_hbm": solve_hbm(h.info(), prec, its[-1]["iters"], ms),
         }

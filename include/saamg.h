@@ -127,6 +127,9 @@ typedef struct {
   double lambda[SAAMG_MAX_LEVELS];  /* power-iteration estimate of lambda_max(D^-1 A_l) */
   long long device_bytes;           /* device memory held by the hierarchy */
   double setup_ms;                  /* wall time of saamg_setup */
+  int sell_index_bytes[SAAMG_MAX_LEVELS]; /* smoother layout of A_l: 0 CSR (level 0: the
+                                             stencil), 4 SELL with 32-bit columns, 2 SELL
+                                             with 16-bit column offsets from the row */
 } saamg_hierarchy_info;
 
 typedef struct saamg_operator saamg_operator;

@@ -1231,6 +1231,7 @@ saamg_status saamg_hierarchy_get_info(const saamg_hierarchy* h, saamg_hierarchy_
       info->nnz[l] = h->lev[l]->nnz;
       info->nnz_p[l] = h->lev[l]->P.nnz;
       info->lambda[l] = h->lev[l]->lambda;
+      info->sell_index_bytes[l] = h->lev[l]->As.n > 0 ? h->lev[l]->As.index_bytes : 0;
     }
     info->device_bytes = h->bytes;
     info->setup_ms = h->setup_ms;

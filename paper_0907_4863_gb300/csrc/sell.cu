@@ -51,6 +51,7 @@ __global__ void sell_width_k(int nslices, const int* __restrict__ rowptr,
 __global__ void sell_fill_k(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
                             const double* __restrict__ val, const int* __restrict__ perm,
                             const int* __restrict__ soff, int* __restrict__ scol,
+                            short* __restrict__ sdcol, int* __restrict__ wide,
                             double* __restrict__ sval, float* __restrict__ sval32,
                             __nv_bfloat16* __restrict__ sval16) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -59,21 +60,28 @@ __global__ void sell_fill_k(int n, const int* __restrict__ rowptr, const int* __
   const int w = (soff[s + 1] - soff[s]) >> 5;
   const int p0 = rowptr[r], len = rowptr[r + 1] - p0;
   const int padc = len > 0 ? col[p0 + len - 1] : 0;
+  bool far = false;
   for (int k = 0; k < w; ++k) {
     const int e = soff[s] + 32 * k + lane;
     const bool real = k < len;
     const double v = real ? val[p0 + k] : 0.0;
-    scol[e] = real ? col[p0 + k] : padc;
+    const int c = real ? col[p0 + k] : padc;
+    scol[e] = c;
+    const int d = c - r;
+    far |= d < -32767 || d > 32767;
+    sdcol[e] = (short)(far ? 0 : d);
     if (sval) sval[e] = v;
     if (sval32) sval32[e] = (float)v;
     if (sval16) sval16[e] = __double2bfloat16(v);
   }
+  if (far) atomicOr(wide, 1);
 }
 
-template <class TV, class TM, int MODE>
+template <class TV, class TM, int MODE, bool REL>
 __global__ void __launch_bounds__(256) sell_k(int n, int nslices, const int* __restrict__ perm,
                                               const int* __restrict__ soff,
                                               const int* __restrict__ col,
+                                              const short* __restrict__ dcol,
                                               const TM* __restrict__ val, const TV* __restrict__ x,
                                               TV* __restrict__ y, const TV* __restrict__ b,
                                               TV* __restrict__ d, const TV* __restrict__ invd,
@@ -94,7 +102,10 @@ __global__ void __launch_bounds__(256) sell_k(int n, int nslices, const int* __r
       // four independent (column, value, x) loads in flight per lane
       for (; k + 4 <= w; k += 4) {
         const int e = e0 + 32 * k;
-        const int k0 = col[e], k1 = col[e + 32], k2 = col[e + 64], k3 = col[e + 96];
+        const int k0 = REL ? row + dcol[e] : col[e];
+        const int k1 = REL ? row + dcol[e + 32] : col[e + 32];
+        const int k2 = REL ? row + dcol[e + 64] : col[e + 64];
+        const int k3 = REL ? row + dcol[e + 96] : col[e + 96];
         const TV a0 = (TV)ld(val, e), a1 = (TV)ld(val, e + 32), a2 = (TV)ld(val, e + 64),
                  a3 = (TV)ld(val, e + 96);
         const TV x0 = x[k0], x1 = x[k1], x2 = x[k2], x3 = x[k3];
@@ -105,7 +116,7 @@ __global__ void __launch_bounds__(256) sell_k(int n, int nslices, const int* __r
       }
       for (; k < w; ++k) {
         const int e = e0 + 32 * k;
-        acc = fma((TV)ld(val, e), x[col[e]], acc);
+        acc = fma((TV)ld(val, e), x[REL ? row + dcol[e] : col[e]], acc);
       }
     }
     if (MODE == CSR_SPMV) {
@@ -172,14 +183,28 @@ void sell_from_csr(const DevCsr& A, DevSell& S, bool f64, bool f32, bool bf16, c
   if (nent > 0x7fffffffLL) fail(SAAMG_EINVAL, "SELL layout above 2^31 entries");
   S.nent = nent;
   S.col.alloc(nent, s);
+  S.dcol.alloc(nent, s);
   if (f64) S.val.alloc(nent, s);
   if (f32) S.val32.alloc(nent, s);
   if (bf16) S.val16.alloc(nent, s);
+  Buf<int> wide;
+  wide.alloc(1, s);
+  fill_int(wide.p, 0, 1, s);
   sell_fill_k<<<(A.n + 255) / 256, 256, 0, s>>>(A.n, A.rowptr.p, A.col.p, A.val.p, S.perm.p,
-                                                S.soff.p, S.col.p, f64 ? S.val.p : nullptr,
+                                                S.soff.p, S.col.p, S.dcol.p, wide.p,
+                                                f64 ? S.val.p : nullptr,
                                                 f32 ? S.val32.p : nullptr,
                                                 bf16 ? S.val16.p : nullptr);
   SAAMG_LAUNCH();
+  int hw = 0;
+  d2h_sync(&hw, wide.p, sizeof(int), s);
+  if (hw) {  // some column is more than 32767 rows away: 32-bit columns
+    S.dcol.release();
+    S.index_bytes = 4;
+  } else {
+    S.col.release();
+    S.index_bytes = 2;
+  }
 }
 
 template <class TV, class TM>
@@ -197,8 +222,14 @@ void sell_apply(int mode, const DevSell& S, const TM* val, const TV* x, TV* y, c
       mode == CSR_SPMV_DINV_DOT ? kRedBlocks : (int)(need < 152 * 16 ? need : 152 * 16);
 #define SAAMG_SELL_CASE(M)                                                                    \
   case M:                                                                                     \
-    sell_k<TV, TM, M><<<blocks, 256, 0, s>>>(S.n, S.nslices, S.perm.p, S.soff.p, S.col.p, val, \
-                                             x, y, b, d, invd, c1, c2, partials, xscale);      \
+    if (S.index_bytes == 2)                                                                   \
+      sell_k<TV, TM, M, true><<<blocks, 256, 0, s>>>(S.n, S.nslices, S.perm.p, S.soff.p,      \
+                                                     nullptr, S.dcol.p, val, x, y, b, d, invd, \
+                                                     c1, c2, partials, xscale);               \
+    else                                                                                      \
+      sell_k<TV, TM, M, false><<<blocks, 256, 0, s>>>(S.n, S.nslices, S.perm.p, S.soff.p,     \
+                                                      S.col.p, nullptr, val, x, y, b, d, invd, \
+                                                      c1, c2, partials, xscale);              \
     break;
   switch (mode) {
     SAAMG_SELL_CASE(CSR_SPMV)

@@ -6,7 +6,10 @@
 // stores its entries column-major, entry k of the slice's lane l at soff[s] + 32 k + l, with
 // width (soff[s+1] - soff[s]) / 32 = the longest row of the slice.  A shorter row is padded
 // with zero values at its own last column, so the padding adds exact zeros and never
-// reads a value the row does not already read.  One thread owns one row and sums its
+// reads a value the row does not already read.  When every column lies within 32767 of its
+// row (aggregates are numbered by their root's lattice index, so a coarse row's neighbours
+// are close to it), the columns are stored as 16-bit offsets from the row: 2 bytes per entry
+// instead of 4.  One thread owns one row and sums its
 // entries in column order; every load of the entry arrays is one contiguous 128-byte
 // (float/int) or 256-byte (double) warp access.
 #pragma once
@@ -26,13 +29,15 @@ struct DevSell {
   long long nent = 0;           // stored entries, padding included
   Buf<int> perm;                // sorted position -> row
   Buf<int> soff;                // nslices + 1 slice offsets
-  Buf<int> col;
+  Buf<int> col;                 // column of each stored entry, or (index_bytes == 2) ...
+  Buf<short> dcol;              // ... its offset from the row, when every offset fits 16 bits
+  int index_bytes = 4;
   Buf<double> val;              // FP64 values (FP64 V-cycle)
   Buf<float> val32;             // FP32 values (mixed precision)
   Buf<__nv_bfloat16> val16;     // BF16 values (mixed precision, BF16 storage)
   size_t bytes() const {
-    return perm.bytes() + soff.bytes() + col.bytes() + val.bytes() + val32.bytes() +
-           val16.bytes();
+    return perm.bytes() + soff.bytes() + col.bytes() + dcol.bytes() + val.bytes() +
+           val32.bytes() + val16.bytes();
   }
 };
 

@@ -57,12 +57,13 @@ class HierarchyInfo(C.Structure):
     _fields_ = [("levels", C.c_int), ("n", C.c_int * MAX_LEVELS),
                 ("nnz", C.c_longlong * MAX_LEVELS), ("nnz_p", C.c_longlong * MAX_LEVELS),
                 ("lambda_", C.c_double * MAX_LEVELS), ("device_bytes", C.c_longlong),
-                ("setup_ms", C.c_double)]
+                ("setup_ms", C.c_double), ("sell_index_bytes", C.c_int * MAX_LEVELS)]
 
     def as_dict(self):
         L = self.levels
         return dict(levels=L, n=list(self.n[:L]), nnz=list(self.nnz[:L]), nnz_p=list(self.nnz_p[:L]),
-                    lam=list(self.lambda_[:L]), device_bytes=self.device_bytes, setup_ms=self.setup_ms)
+                    lam=list(self.lambda_[:L]), device_bytes=self.device_bytes, setup_ms=self.setup_ms,
+                    sell_index_bytes=list(self.sell_index_bytes[:L]))
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

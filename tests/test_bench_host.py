@@ -93,3 +93,15 @@ def test_solve_hbm_counts_cg_vectors_and_one_vcycle_per_iteration(bench):
     assert r["bytes_per_iteration"] == 88000 + vc
     assert r["achieved_gbs"] == pytest.approx((88000 + vc) * 10 / 2e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved_gbs"] / r["peak_gbs"])
+
+
+def test_level1_smoother_counts_its_column_bytes(bench):
+    # 16-bit column offsets: 2 + 4 B per entry in FP32, 2 + 8 in FP64; transfers keep 4-byte columns
+    assert bench.roofline("coarse_csr", (1.0, 10, 10_000_000), 1, index_bytes=2)[
+        "algorithmic_bytes_per_launch"] == pytest.approx(6e6)
+    assert bench.roofline("coarse_csr", (1.0, 10, 10_000_000), 0, index_bytes=2)[
+        "algorithmic_bytes_per_launch"] == pytest.approx(10e6)
+    assert bench.roofline("transfer", (1.0, 10, 10_000_000), 1, index_bytes=2)[
+        "algorithmic_bytes_per_launch"] == pytest.approx(8e6)
+    assert bench.level1_index_bytes({"sell_index_bytes": [0, 2, 0]}) == 2
+    assert bench.level1_index_bytes({"sell_index_bytes": [0, 0, 0]}) == 4
