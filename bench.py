@@ -386,6 +386,35 @@ def extra_legs(S, torch, w, dom, grid, rho, args):
         }
         h.free()
         op.free()
+    # hierarchy reuse (Sec. 5.2): an operator with the same pattern (here the other boundary
+    # mode on the same domain and grid) keeps the aggregates of an existing hierarchy
+    params = S.params_default(max_coarse=4096)
+    other = I.QUADRATIC if w.mode != I.QUADRATIC else I.LINEAR
+    op1 = S.build_operator(dom, grid, w.mode)
+    h1 = S.setup(op1, params)
+    op2 = S.build_operator(dom, grid, other)
+    S.setup_reuse(op2, h1, params).free()  # warm-up of both paths
+    S.setup(op2, params).free()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hf = S.setup(op2, params)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    hr = S.setup_reuse(op2, h1, params)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    its = []
+    for hh in (hf, hr):
+        phi = torch.zeros_like(rho)
+        its.append(S.solve(hh, rho, phi, rtol=RTOL)["iters"])
+    out["hierarchy_reuse"] = {
+        "operator": "same domain and grid, the other boundary mode (same pattern)",
+        "fresh_setup_ms": 1e3 * (t1 - t0), "reuse_setup_ms": 1e3 * (t2 - t1),
+        "iters_fresh": its[0], "iters_reuse": its[1]}
+    for hh in (hf, hr, h1):
+        hh.free()
+    op1.free()
+    op2.free()
     return out
 
 
@@ -587,6 +616,7 @@ def sizes_leg(S, torch, sizes=(128, 256, 512)):
                 op.free()
             out[f"{n}^3_{pname}"] = {
                 "unknowns": hi["n"][0], "levels": hi["n"], "iters": info["iters"],
+                "sell_index_bytes": hi.get("sell_index_bytes"),
                 "relres_true": info["relres_true"], "build_setup_ms": 1e3 * (t1 - t0),
                 "solve_ms": 1e3 * (t2 - t1), "full_pipeline_solves_per_s": 1.0 / (t2 - t0)}
         del rho

@@ -378,6 +378,15 @@ static bool same_pattern(const DevCsr& a, const DevCsr& b, cudaStream_t s) {
 
 // prev != NULL: the aggregates of every level are copied from prev (whose level-0 pattern
 // must equal op's) instead of being recomputed; everything numeric is rebuilt.
+// A second stream for setup work that overlaps the work on the caller's stream (created once).
+static cudaStream_t aux_stream() {
+  static std::mutex mu;
+  static cudaStream_t st = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!st) SAAMG_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  return st;
+}
+
 // SELL copy of a coarse level's operator with the value arrays of the V-cycle's precision.
 static void build_level_sell(saamg_hierarchy* h, Level& L, cudaStream_t s) {
   const bool f64 = !mixed(h), f32 = h->prm.precision == SAAMG_PREC_FP32;
@@ -419,6 +428,27 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
     int nagg = 0;
     Buf<unsigned> next_ids;
     int next_dims[3] = {0, 0, 0};
+    // The spectral bound of a level that will be coarsened only reads A_l (or the level-0
+    // stencil, or the SELL copy): it runs on a second stream while the aggregation (latency-
+    // bound, where the power iteration is FP64-bound) runs on s.
+    const bool coarsen = prev ? l + 1 < (int)prev->lev.size()
+                              : !(L.n <= prm.max_coarse || l == prm.max_levels - 1 ||
+                                  l == SAAMG_MAX_LEVELS - 1);
+    PowerRun power;
+    cudaStream_t s2 = aux_stream();
+    if (coarsen) {
+      // a smoothed level >= 1 large enough for SELL gets its SELL copy now (it is not the
+      // coarsest), so that in the FP64 V-cycle the power iteration runs on it too
+      if (l >= 1 && L.n >= kSellMinRows && L.As.n == 0) build_level_sell(h, L, s);
+      const StencilDev<double> S0 = od.view<double>();
+      cudaEvent_t fork;
+      SAAMG_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+      SAAMG_CUDA(cudaEventRecord(fork, s));
+      SAAMG_CUDA(cudaStreamWaitEvent(s2, fork, 0));
+      cudaEventDestroy(fork);
+      power_lambda_start(A, L.invd.p, ids, prm.power_iters, s2, power, l == 0 ? &S0 : nullptr,
+                         l >= 1 && L.As.n > 0 ? &L.As : nullptr);
+    }
     if (prev) {
       // reuse: the previous hierarchy decides the levels and the aggregates
       if (l + 1 >= (int)prev->lev.size()) break;
@@ -456,18 +486,14 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
       }
       pt.mark("L" + std::to_string(l) + ".agg");
       if (10LL * nagg > 9LL * L.n) {  // coarsening stalled
+        power_lambda_finish(power, s2);
         L.root.release();
         L.agg.release();
+        L.As = DevSell();  // the coarsest level keeps CSR
         break;
       }
     }
-    const StencilDev<double> S0 = od.view<double>();
-    // a smoothed level >= 1 large enough for SELL gets its SELL copy now (it is not the
-    // coarsest: that one stops before its spectral bound), so that in the FP64 V-cycle the
-    // power iteration runs on it too
-    if (l >= 1 && L.n >= kSellMinRows && L.As.n == 0) build_level_sell(h, L, s);
-    L.lambda = power_lambda(A, L.invd.p, ids, prm.power_iters, s, l == 0 ? &S0 : nullptr,
-                            l >= 1 && L.As.n > 0 ? &L.As : nullptr);
+    L.lambda = power_lambda_finish(power, s2);
     L.omega = 4.0 / (3.0 * L.lambda);
     pt.mark("L" + std::to_string(l) + ".lambda");
     DevCsr AP;

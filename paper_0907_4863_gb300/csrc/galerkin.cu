@@ -841,37 +841,54 @@ CsrView view(const DevCsr& a) { return CsrView{a.rowptr.p, a.col.p, a.val.p}; }
 
 }  // namespace
 
-double power_lambda(const DevCsr& A, const double* invd, const unsigned* ids, int iters,
-                    cudaStream_t s, const StencilDev<double>* S, const DevSell* As) {
-  int n = A.n;
-  if (n == 0) return 1.0;
+void power_lambda_start(const DevCsr& A, const double* invd, const unsigned* ids, int iters,
+                        cudaStream_t s, PowerRun& run, const StencilDev<double>* S,
+                        const DevSell* As) {
+  const int n = A.n;
+  run.n = n;
+  if (n == 0) return;
   // v_{k+1} = D^-1 A v_k / |D^-1 A v_k|: the pass that forms D^-1 A v_{k+1} applies the
   // division by the previous norm to its output (one multiply per row, no separate sweep)
-  Buf<double> v, w, part, nrm2;
-  v.alloc(n, s);
-  w.alloc(n, s);
-  part.alloc(kRedBlocks, s);
-  nrm2.alloc(2, s);  // |w|^2 and 1 / |w|
-  power_init_k<<<blocks_for(n), 256, 0, s>>>(n, ids, v.p);
+  run.v.alloc(n, s);
+  run.w.alloc(n, s);
+  run.part.alloc(kRedBlocks, s);
+  run.nrm2.alloc(2, s);  // |w|^2 and 1 / |w|
+  power_init_k<<<blocks_for(n), 256, 0, s>>>(n, ids, run.v.p);
   SAAMG_LAUNCH();
-  double avg = (double)A.nnz / n;
+  const double avg = (double)A.nnz / n;
   for (int it = 0; it <= iters; ++it) {
-    const double* xscale = it > 0 ? nrm2.p + 1 : nullptr;
+    const double* xscale = it > 0 ? run.nrm2.p + 1 : nullptr;
     if (S)
-      stencil_apply<double>(*S, ST_DINV_DOT, v.p, w.p, nullptr, nullptr, 0.0, 0.0, part.p, s,
-                            xscale);
+      stencil_apply<double>(*S, ST_DINV_DOT, run.v.p, run.w.p, nullptr, nullptr, 0.0, 0.0,
+                            run.part.p, s, xscale);
     else if (As && As->val.p)
-      sell_apply<double, double>(CSR_SPMV_DINV_DOT, *As, As->val.p, v.p, w.p, nullptr, nullptr,
-                                 invd, 0.0, 0.0, s, -1, part.p, xscale);
+      sell_apply<double, double>(CSR_SPMV_DINV_DOT, *As, As->val.p, run.v.p, run.w.p, nullptr,
+                                 nullptr, invd, 0.0, 0.0, s, -1, run.part.p, xscale);
     else
-      csr_apply<double, double>(CSR_SPMV_DINV_DOT, n, A.rowptr.p, A.col.p, A.val.p, avg, v.p,
-                                w.p, nullptr, nullptr, invd, 0.0, 0.0, part.p, s, -1, xscale);
-    sum_partials(part.p, kRedBlocks, nrm2.p, s, nrm2.p + 1);
-    v.swap(w);
+      csr_apply<double, double>(CSR_SPMV_DINV_DOT, n, A.rowptr.p, A.col.p, A.val.p, avg,
+                                run.v.p, run.w.p, nullptr, nullptr, invd, 0.0, 0.0, run.part.p,
+                                s, -1, xscale);
+    sum_partials(run.part.p, kRedBlocks, run.nrm2.p, s, run.nrm2.p + 1);
+    run.v.swap(run.w);
   }
+}
+
+double power_lambda_finish(PowerRun& run, cudaStream_t s) {
+  if (run.n == 0) return 1.0;
   double h = 0;
-  d2h_sync(&h, nrm2.p, sizeof(double), s);
+  d2h_sync(&h, run.nrm2.p, sizeof(double), s);
+  run.v.release();
+  run.w.release();
+  run.part.release();
+  run.nrm2.release();
   return sqrt(h);
+}
+
+double power_lambda(const DevCsr& A, const double* invd, const unsigned* ids, int iters,
+                    cudaStream_t s, const StencilDev<double>* S, const DevSell* As) {
+  PowerRun run;
+  power_lambda_start(A, invd, ids, iters, s, run, S, As);
+  return power_lambda_finish(run, s);
 }
 
 void tentative(const int* agg, int n, int nagg, DevCsr& T, cudaStream_t s) {

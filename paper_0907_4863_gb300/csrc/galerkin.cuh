@@ -15,6 +15,16 @@ struct DevSell;
 double power_lambda(const DevCsr& A, const double* invd, const unsigned* ids, int iters,
                     cudaStream_t s, const StencilDev<double>* S = nullptr,
                     const DevSell* As = nullptr);
+// The same in two halves, so that other work can run meanwhile: _start enqueues the steps on
+// s (run keeps their buffers), _finish waits for s and returns lambda_hat.
+struct PowerRun {
+  int n = 0;
+  Buf<double> v, w, part, nrm2;
+};
+void power_lambda_start(const DevCsr& A, const double* invd, const unsigned* ids, int iters,
+                        cudaStream_t s, PowerRun& run, const StencilDev<double>* S = nullptr,
+                        const DevSell* As = nullptr);
+double power_lambda_finish(PowerRun& run, cudaStream_t s);
 
 // C = X Y with a structural pattern (entries that cancel are kept), columns ascending in
 // every row; every entry is summed in an order fixed by the row's product counts (X's

@@ -65,6 +65,8 @@ def test_vcycle_and_solve_256_match_oracle(S, world256):
     w, o, g, h = world256
     oh = oracle_hierarchy(o, max_coarse=4096)
     assert [oh.n(l) for l in range(oh.levels)] == h.info()["n"]
+    # level 1 runs its smoother on SELL with 16-bit column offsets (the path checked here)
+    assert h.info()["sell_index_bytes"][:2] == [0, 2]
     r = np.random.default_rng(9).standard_normal(o.n)
     z = torch.empty(o.n, dtype=torch.float64, device="cuda")
     S.vcycle(h, torch.from_numpy(r).cuda(), z)
