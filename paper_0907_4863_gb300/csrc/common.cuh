@@ -138,6 +138,7 @@ struct StencilDev {
   const int4* nbr;
   const int2* chunks;  // (line, offset of the first of <= 32 consecutive unknowns)
   int nchunks;
+  const int* rline;    // line of every compact row (the FP64 passes take 32 consecutive rows)
   int n;               // unknowns
   int nx, ny, nz;
   const T* table;      // 8 per table row: self, -x, +x, -y, +y, -z, +z, 1/self

@@ -185,6 +185,17 @@ __global__ void set_start_and_chunks_k(LineInfo* lines, const int* start, const 
   for (int off = 0, c = c0; off < cnt; off += 32, ++c) chunks[c] = make_int2(L, off);
 }
 
+// Warp per chunk: the line of each of its rows.
+__global__ void row_lines_k(const LineInfo* __restrict__ lines, const int2* __restrict__ chunks,
+                            int nchunks, int* __restrict__ rline) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= nchunks) return;
+  const int2 ch = chunks[c];
+  const LineInfo me = lines[ch.x];
+  if (me.lo + ch.y + lane <= me.hi) rline[me.start + ch.y + lane] = ch.x;
+}
+
 // Thread per line: row offsets to the four neighbouring lines (0 where a line is missing).
 __global__ void line_deltas_k(const LineInfo* __restrict__ lines, int nlines, int ny,
                               int4* __restrict__ nbr) {
@@ -565,6 +576,12 @@ void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op) 
   op.nbr.alloc(nlines, s);
   line_deltas_k<<<(nlines + 255) / 256, 256, 0, s>>>(op.lines.p, nlines, g.ny, op.nbr.p);
   SAAMG_LAUNCH();
+  op.rline.alloc(op.n, s);
+  if (op.n > 0) {
+    row_lines_k<<<warp_blocks(nchunks), 256, 0, s>>>(op.lines.p, op.chunks.p, op.nchunks,
+                                                      op.rline.p);
+    SAAMG_LAUNCH();
+  }
 
   Buf<double> rc;
   rc.alloc(8, s);
@@ -642,6 +659,7 @@ StencilDev<double> OperatorData::view<double>() const {
   v.nbr = nbr.p;
   v.chunks = chunks.p;
   v.nchunks = nchunks;
+  v.rline = rline.p;
   v.n = n;
   v.nx = g.nx;
   v.ny = g.ny;
@@ -662,6 +680,7 @@ StencilDev<float> OperatorData::view<float>() const {
   v.nbr = nbr.p;
   v.chunks = chunks.p;
   v.nchunks = nchunks;
+  v.rline = rline.p;
   v.n = n;
   v.nx = g.nx;
   v.ny = g.ny;

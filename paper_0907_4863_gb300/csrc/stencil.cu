@@ -52,19 +52,32 @@ __device__ __forceinline__ void load8(const float* p, float v[8]) {
 // coefficients and the line's neighbour offsets; a table row (only its selection below
 // diverges, and it holds no floating-point work) takes its own coefficients, and a missing
 // neighbour (coefficient 0) points at the row itself.
-template <class T, int MODE>
+// PACKED: chunk c is the compact rows [32 c, 32 c + 32), each lane finds its own line (no lane
+// idles at the end of a line); otherwise chunk c is (line, offset) from the chunk list.
+template <class T, int MODE, bool PACKED>
 __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int lane,
                                             const T* __restrict__ x, T* __restrict__ y,
                                             const T* __restrict__ b, T* __restrict__ d, T c1,
                                             T c2, T c2invd0, double& dacc,
                                             const int* __restrict__ agg) {
-    const int2 ch = S.chunks[c];
-    const int L = ch.x;
-    const LineInfo me = S.lines[L];
-    const int4 nb = S.nbr[L];
-    const int i = me.lo + ch.y + lane;
-    if (i > me.hi) return;
-    const int row = me.start + ch.y + lane;
+    int row, i;
+    LineInfo me;
+    int4 nb;
+    if (PACKED) {
+      row = 32 * c + lane;
+      if (row >= S.n) return;
+      const int L = S.rline[row];
+      me = S.lines[L];
+      nb = S.nbr[L];
+      i = me.lo + (row - me.start);
+    } else {
+      const int2 ch = S.chunks[c];
+      me = S.lines[ch.x];
+      nb = S.nbr[ch.x];
+      i = me.lo + ch.y + lane;
+      if (i > me.hi) return;
+      row = me.start + ch.y + lane;
+    }
     T a0 = S.c0, axm = S.cx, axp = S.cx, aym = S.cy, ayp = S.cy, azm = S.cz, azp = S.cz;
     T c2i = c2invd0;
     int oxm = -1, oxp = 1, oym = nb.x, oyp = nb.y, ozm = nb.z, ozp = nb.w;
@@ -152,6 +165,14 @@ __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int l
     }
 }
 
+// The FP64 passes are bound by FP64 issue, where an idle lane costs as much as a busy one: they
+// take 32 consecutive rows per warp across line ends (one more 4-byte load per row, the line
+// index); the latency-bound FP32 passes keep the line chunks.
+template <class T>
+__host__ __device__ constexpr bool packed_rows() {
+  return sizeof(T) == 8;
+}
+
 // K chunks per warp iteration: the unrolled copies let the read-only loads of the next chunk
 // be issued before the stores of the current one (more bytes in flight per warp).
 template <class T, int MODE, int K>
@@ -169,11 +190,13 @@ __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __res
     c2invd0 = c2 * S.invd0;
   }
   double dacc = 0.0;
-  for (int c0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * K; c0 < S.nchunks; c0 += nw * K) {
+  constexpr bool kPacked = packed_rows<T>();
+  const int nch = kPacked ? (S.n + 31) / 32 : S.nchunks;
+  for (int c0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * K; c0 < nch; c0 += nw * K) {
 #pragma unroll
     for (int k = 0; k < K; ++k)
-      if (c0 + k < S.nchunks)
-        stencil_row<T, MODE>(S, c0 + k, lane, x, y, b, d, c1, c2, c2invd0, dacc, agg);
+      if (c0 + k < nch)
+        stencil_row<T, MODE, kPacked>(S, c0 + k, lane, x, y, b, d, c1, c2, c2invd0, dacc, agg);
   }
   if (MODE == ST_SPMV_DOT || MODE == ST_DINV_DOT) {
     __shared__ double sh[32];
@@ -205,6 +228,7 @@ void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* 
     if (mode == ST_SPMV_DOT || mode == ST_DINV_DOT) fill_double(partials, 0.0, kRedBlocks, s);
     return;
   }
+  const long long nch = packed_rows<T>() ? ((long long)S.n + 31) / 32 : S.nchunks;
   // the smoother class holds only the full Chebyshev step (fixed work per row); the
   // other modes of the same kernel are timed as "apply"
   // one timing class per kind of pass (each has a fixed amount of work per row)
@@ -217,7 +241,7 @@ void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* 
   // Reductions use the fixed grid so that partial sums are always taken the same way.
   int blocks = kRedBlocks;
   if (mode != ST_SPMV_DOT && mode != ST_DINV_DOT) {
-    long long need = ((long long)S.nchunks + 8 * kChunks<T>() - 1) / (8 * kChunks<T>());
+    long long need = (nch + 8 * kChunks<T>() - 1) / (8 * kChunks<T>());
     blocks = (int)(need < 152 * 16 ? need : 152 * 16);
   }
   // c2 / diag of the regular rows, formed here: a kernel that forms it from c2 lets the
