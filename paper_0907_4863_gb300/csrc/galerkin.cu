@@ -58,6 +58,18 @@ __device__ __forceinline__ int hash_insert(int* keys, int logcap, int key) {
   return -1;
 }
 
+// Inserts key (absent from the table); returns its slot, -1 if the table is full.
+__device__ __forceinline__ int hash_insert_slot(int* keys, int logcap, int key) {
+  const int cap = 1 << logcap;
+  int slot = hash_slot(key, logcap);
+  for (int probe = 0; probe < cap; ++probe) {
+    const int old = atomicCAS(&keys[slot], -1, key);
+    if (old == -1 || old == key) return slot;
+    slot = (slot + 1) & (cap - 1);
+  }
+  return -1;
+}
+
 __device__ __forceinline__ int hash_find(const int* keys, int logcap, int key) {
   const int cap = 1 << logcap;
   int slot = hash_slot(key, logcap);
@@ -109,11 +121,15 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int* total) {
 __global__ void __launch_bounds__(128) spgemm_hash_symbolic_k(const int* __restrict__ list,
                                                               int nlist, int logcap, CsrView X,
                                                               CsrView Y, int* __restrict__ count,
-                                                              int* __restrict__ overflow) {
+                                                              int* __restrict__ overflow,
+                                                              int* __restrict__ skeys,
+                                                              const int* __restrict__ soff) {
   extern __shared__ int smem_i[];
   const int lane = threadIdx.x & 31;
   const int cap = 1 << logcap;
-  int* keys = smem_i + (threadIdx.x >> 5) * cap;
+  // per warp: the table, then (skeys given) cap / 2 compacted keys
+  int* keys = smem_i + (threadIdx.x >> 5) * (skeys ? cap + cap / 2 : cap);
+  int* uniq = keys + cap;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int t = gw; t < nlist; t += nw) {
@@ -147,10 +163,30 @@ __global__ void __launch_bounds__(128) spgemm_hash_symbolic_k(const int* __restr
       cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
       full |= __shfl_xor_sync(0xffffffffu, full, o);
     }
+    const bool over = full || 2 * cnt > cap;
     if (lane == 0) {
-      const bool over = full || 2 * cnt > cap;
       count[i] = over ? -1 : cnt;
       if (over) atomicAdd(overflow, 1);
+    }
+    if (skeys && !over) {
+      // the distinct columns in ascending order, for the numeric pass (no second insertion
+      // of every product there)
+      __syncwarp();
+      int nu = 0;
+      for (int q0 = 0; q0 < cap; q0 += 32) {
+        const int key = keys[q0 + lane];
+        const unsigned bm = __ballot_sync(0xffffffffu, key >= 0);
+        if (key >= 0) uniq[nu + __popc(bm & ((1u << lane) - 1u))] = key;
+        nu += __popc(bm);
+      }
+      __syncwarp();
+      int* out = skeys + soff[i];
+      for (int u = lane; u < nu; u += 32) {
+        const int key = uniq[u];
+        int r = 0;
+        for (int v = 0; v < nu; ++v) r += uniq[v] < key;
+        out[r] = key;
+      }
     }
     __syncwarp();
   }
@@ -171,7 +207,9 @@ __global__ void __launch_bounds__(128, 16) spgemm_hash_numeric_k(const int* __re
                                                              CsrView Y,
                                                              const int* __restrict__ crowptr,
                                                              int* __restrict__ ccol,
-                                                             double* __restrict__ cval) {
+                                                             double* __restrict__ cval,
+                                                             const int* __restrict__ skeys,
+                                                             const int* __restrict__ soff) {
   extern __shared__ double smem_d[];
   constexpr int GL = 32 / NG;
   const int lane = threadIdx.x & 31;
@@ -194,39 +232,50 @@ __global__ void __launch_bounds__(128, 16) spgemm_hash_numeric_k(const int* __re
     for (int q = lane; q < cstride * NG; q += 32) vals[q] = 0.0;
     __syncwarp();
     const int p0 = X.rowptr[i], p1 = X.rowptr[i + 1];
-    for (int pb = p0; pb < p1; pb += 32) {
-      const int p = pb + lane;
-      if (p < p1) {
-        const int k = X.col[p];
-        const int q1 = Y.rowptr[k + 1];
-        for (int q = Y.rowptr[k]; q < q1; q += 4) {
-          int c[4];
+    if (skeys && soff[i + 1] > soff[i]) {
+      // the symbolic pass left the row's columns in ascending order: each one's place is its rank
+      const int* in = skeys + soff[i];
+      const int cnt = crowptr[i + 1] - crowptr[i];
+      for (int u = lane; u < cnt; u += 32) {
+        const int slot = hash_insert_slot(keys, logcap, in[u]);  // never full: cap >= 2 cnt
+        if (slot >= 0) rank[slot] = u;
+      }
+      __syncwarp();
+    } else {
+      for (int pb = p0; pb < p1; pb += 32) {
+        const int p = pb + lane;
+        if (p < p1) {
+          const int k = X.col[p];
+          const int q1 = Y.rowptr[k + 1];
+          for (int q = Y.rowptr[k]; q < q1; q += 4) {
+            int c[4];
 #pragma unroll
-          for (int b = 0; b < 4; ++b) c[b] = q + b < q1 ? Y.col[q + b] : -1;
+            for (int b = 0; b < 4; ++b) c[b] = q + b < q1 ? Y.col[q + b] : -1;
 #pragma unroll
-          for (int b = 0; b < 4; ++b)
-            if (c[b] >= 0) hash_insert(keys, logcap, c[b]);
+            for (int b = 0; b < 4; ++b)
+              if (c[b] >= 0) hash_insert(keys, logcap, c[b]);
+          }
         }
       }
+      __syncwarp();
+      // compact the distinct columns
+      int nu = 0;
+      for (int q0 = 0; q0 < cap; q0 += 32) {
+        const int key = keys[q0 + lane];
+        const unsigned bm = __ballot_sync(0xffffffffu, key >= 0);
+        if (key >= 0) uniq[nu + __popc(bm & ((1u << lane) - 1u))] = key;
+        nu += __popc(bm);
+      }
+      __syncwarp();
+      for (int q = lane; q < cap; q += 32) {
+        const int key = keys[q];
+        if (key < 0) continue;
+        int r = 0;
+        for (int u = 0; u < nu; ++u) r += uniq[u] < key;
+        rank[q] = r;
+      }
+      __syncwarp();
     }
-    __syncwarp();
-    // compact the distinct columns
-    int nu = 0;
-    for (int q0 = 0; q0 < cap; q0 += 32) {
-      const int key = keys[q0 + lane];
-      const unsigned bm = __ballot_sync(0xffffffffu, key >= 0);
-      if (key >= 0) uniq[nu + __popc(bm & ((1u << lane) - 1u))] = key;
-      nu += __popc(bm);
-    }
-    __syncwarp();
-    for (int q = lane; q < cap; q += 32) {
-      const int key = keys[q];
-      if (key < 0) continue;
-      int r = 0;
-      for (int u = 0; u < nu; ++u) r += uniq[u] < key;
-      rank[q] = r;
-    }
-    __syncwarp();
     double* mine = vals + (size_t)grp * cstride;
     for (int pb = p0; pb < p1; pb += NG) {
       const int p = pb + grp;
@@ -577,6 +626,15 @@ __global__ void classify_rows_k(int n, const int* __restrict__ xrowptr,
   if (threadIdx.x < kClasses && sh[threadIdx.x]) atomicAdd(&hist[threadIdx.x], sh[threadIdx.x]);
 }
 
+// Room for the sorted columns a symbolic hash pass leaves for the numeric one:
+// min(products, columns) for the rows of the warp hash classes, 0 for the others.
+__global__ void hash_caps_k(int n, const int* __restrict__ cls, const int* __restrict__ nprod,
+                            int m, unsigned warp_classes, int* __restrict__ caps) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) caps[i] = ((warp_classes >> cls[i]) & 1u) ? min(nprod[i], m) : 0;
+  if (i == n) caps[n] = 0;
+}
+
 // Rows into per-class lists (order inside a class is irrelevant: rows are independent).
 __global__ void scatter_rows_k(int n, const int* __restrict__ cls, int* __restrict__ cursor,
                                int* __restrict__ list) {
@@ -922,7 +980,7 @@ void bin_rows(int n, const int* xrowptr, const int* nprod, const int* cnt, int m
 template <bool NUMERIC>
 void run_class(int c, const int* list, int nl, CsrView X, CsrView Y, double yavg,
                const int* crowptr, int* count, int* overflow, int* ccol, double* cval,
-               cudaStream_t s) {
+               int* skeys, const int* soff, cudaStream_t s) {
   if (nl == 0) return;
   KernelTimer kt(SAAMG_KT_SPGEMM, nl, s);
   const int threads = 32 * kSpgemmWarps;
@@ -972,11 +1030,12 @@ void run_class(int c, const int* list, int nl, CsrView X, CsrView Y, double yavg
     return;
   }
   if (!NUMERIC) {
-    const size_t sm = (size_t)kSpgemmWarps * cap * sizeof(int);
+    const size_t sm = (size_t)kSpgemmWarps * (skeys ? cap + cap / 2 : cap) * sizeof(int);
     if (sm > 48 * 1024)
       SAAMG_CUDA(cudaFuncSetAttribute(spgemm_hash_symbolic_k,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    spgemm_hash_symbolic_k<<<blocks, threads, sm, s>>>(list, nl, lg, X, Y, count, overflow);
+    spgemm_hash_symbolic_k<<<blocks, threads, sm, s>>>(list, nl, lg, X, Y, count, overflow,
+                                                       skeys, soff);
   } else {
     // lane groups sized to Y's rows (one group covers a typical row in one pass)
     const int ng = yavg <= 7.0 ? 4 : (yavg <= 14.0 ? 2 : 1);
@@ -991,7 +1050,7 @@ void run_class(int c, const int* list, int nl, CsrView X, CsrView Y, double yavg
       if (sm > 48 * 1024)
         SAAMG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)sm));
-      kernel<<<nb, 32 * wpb, sm, s>>>(list, nl, lg, X, Y, crowptr, ccol, cval);
+      kernel<<<nb, 32 * wpb, sm, s>>>(list, nl, lg, X, Y, crowptr, ccol, cval, skeys, soff);
     };
     if (ng == 4) launch(spgemm_hash_numeric_k<4>);
     else if (ng == 2) launch(spgemm_hash_numeric_k<2>);
@@ -1032,9 +1091,25 @@ void spgemm(const DevCsr& X, const DevCsr& Y, DevCsr& C, cudaStream_t s) {
   int hist[kClasses], start[kClasses + 1];
   // symbolic: distinct columns per row
   bin_rows(n, X.rowptr.p, nprod.p, nullptr, Y.m, cls.p, list.p, ctl.p, hist, start, s);
+  // the warp hash passes leave each row's sorted columns for the numeric pass (room
+  // min(products, columns) per row) when the total fits 32-bit offsets
+  unsigned warp_classes = 0;
+  for (int c = 2; c < kClasses; ++c)
+    if (hist[c] > kFewRows) warp_classes |= 1u << c;
+  Buf<int> soff, skeys;
+  if (warp_classes) {
+    Buf<int> caps;
+    caps.alloc(n + 1, s);
+    hash_caps_k<<<blocks_for(n + 1), 256, 0, s>>>(n, cls.p, nprod.p, Y.m, warp_classes, caps.p);
+    SAAMG_LAUNCH();
+    soff.alloc(n + 1, s);
+    const long long total = exclusive_scan(caps.p, soff.p, n + 1, s);
+    if (total > 0 && total < 0x7fffffffLL) skeys.alloc(total, s);
+    else soff.release();
+  }
   for (int c = 0; c < kClasses; ++c)
     run_class<false>(c, list.p + start[c], hist[c], view(X), view(Y), yavg, nullptr, cnt.p, overflow,
-                     nullptr, nullptr, s);
+                     nullptr, nullptr, skeys.p, soff.p, s);
   int nover = 0;
   d2h_sync(&nover, overflow, sizeof(int), s);
   if (nover) fail(SAAMG_UNIMPLEMENTED, "sparse product row with more than 2048 distinct columns");
@@ -1048,7 +1123,7 @@ void spgemm(const DevCsr& X, const DevCsr& Y, DevCsr& C, cudaStream_t s) {
   bin_rows(n, X.rowptr.p, nprod.p, cnt.p, Y.m, cls.p, list.p, ctl.p, hist, start, s);
   for (int c = 0; c < kClasses; ++c)
     run_class<true>(c, list.p + start[c], hist[c], view(X), view(Y), yavg, C.rowptr.p, nullptr, nullptr,
-                    C.col.p, C.val.p, s);
+                    C.col.p, C.val.p, skeys.p, soff.p, s);
 }
 
 void smoothed_prolongator(DevCsr& AT, const int* agg, const double* invd, double omega,
