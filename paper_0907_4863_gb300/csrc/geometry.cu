@@ -710,21 +710,15 @@ __device__ double axis_derivative(double h, bool in_m, bool in_p, double pm, dou
 
 __device__ __forceinline__ bool line_has(const LineInfo& l, int i) { return i >= l.lo && i <= l.hi; }
 
-// E = -grad phi at the unknowns (warp per chunk, lane per unknown).  Neighbours inside
+// E = -grad phi at unknown (i, line L) of chunk offset row `q` in the box.  Neighbours inside
 // Omega_h use their phi; an outside neighbour is replaced by the wall point at the boundary
 // fraction with phi = 0; on a Robin end plane the z-derivative is the Robin condition's.
-__global__ void field_gradient_k(GeomParams g, const LineInfo* __restrict__ lines,
-                                 const int2* __restrict__ chunks, int nchunks,
-                                 const double* __restrict__ phi, double* __restrict__ ex,
-                                 double* __restrict__ ey, double* __restrict__ ez) {
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (c >= nchunks) return;
-  const int2 ch = chunks[c];
-  const int L = ch.x;
-  const LineInfo me = lines[L];
-  const int i = me.lo + ch.y + lane;
-  if (i > me.hi) return;
+__device__ __forceinline__ void gradient_node(const GeomParams& g,
+                                              const LineInfo* __restrict__ lines, int L,
+                                              const LineInfo& me, int i,
+                                              const double* __restrict__ phi,
+                                              double* __restrict__ ex, double* __restrict__ ey,
+                                              double* __restrict__ ez) {
   const int j = L % g.ny, k = L / g.ny;
   const size_t sy = (size_t)g.nx, sz = (size_t)g.nx * g.ny;
   const size_t q = (size_t)i + sy * (size_t)j + sz * (size_t)k;
@@ -759,6 +753,61 @@ __global__ void field_gradient_k(GeomParams g, const LineInfo* __restrict__ line
   }
 }
 
+// Warp per chunk, lane per unknown: the nodes whose six neighbours are all unknowns (and not
+// on a Robin plane) take central differences here; the others -- a few per cent, where the
+// boundary fractions, their divisions and square roots would hold a whole warp on the FP64
+// pipe for one lane -- are listed for gradient_boundary_k, one per lane of a full warp.
+__global__ void field_gradient_k(GeomParams g, const LineInfo* __restrict__ lines,
+                                 const int2* __restrict__ chunks, int nchunks,
+                                 const double* __restrict__ phi, double* __restrict__ ex,
+                                 double* __restrict__ ey, double* __restrict__ ez,
+                                 int2* __restrict__ list, int* __restrict__ nlist) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= nchunks) return;  // warp-uniform
+  const int2 ch = chunks[c];
+  const int L = ch.x;
+  const LineInfo me = lines[L];
+  const int i = me.lo + ch.y + lane;
+  const bool active = i <= me.hi;
+  bool inner = false;
+  if (active) {
+    const int j = L % g.ny, k = L / g.ny;
+    const bool robin = g.zbc == SAAMG_Z_ROBIN && (k == 0 || k == g.nz - 1);
+    inner = !robin && i - 1 >= me.lo && i + 1 <= me.hi && j > 0 && j < g.ny - 1 && k > 0 &&
+            k < g.nz - 1 && line_has(lines[L - 1], i) && line_has(lines[L + 1], i) &&
+            line_has(lines[L - g.ny], i) && line_has(lines[L + g.ny], i);
+    if (inner) {
+      const size_t sy = (size_t)g.nx, sz = (size_t)g.nx * g.ny;
+      const size_t q = (size_t)i + sy * (size_t)j + sz * (size_t)k;
+      // the central differences of axis_derivative, same operations
+      ex[q] = -((phi[q + 1] - phi[q - 1]) / (2.0 * g.h[0]));
+      ey[q] = -((phi[q + sy] - phi[q - sy]) / (2.0 * g.h[1]));
+      ez[q] = -((phi[q + sz] - phi[q - sz]) / (2.0 * g.h[2]));
+    }
+  }
+  const unsigned need = __ballot_sync(0xffffffffu, active && !inner);
+  if (!need) return;
+  int base = 0;
+  if (lane == 0) base = atomicAdd(nlist, __popc(need));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (active && !inner) list[base + __popc(need & ((1u << lane) - 1u))] = make_int2(c, lane);
+}
+
+__global__ void gradient_boundary_k(GeomParams g, const LineInfo* __restrict__ lines,
+                                    const int2* __restrict__ chunks,
+                                    const int2* __restrict__ list, const int* __restrict__ nlist,
+                                    const double* __restrict__ phi, double* __restrict__ ex,
+                                    double* __restrict__ ey, double* __restrict__ ez) {
+  const int cnt = *nlist;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+    const int2 it = list[e];
+    const int2 ch = chunks[it.x];
+    const LineInfo me = lines[ch.x];
+    gradient_node(g, lines, ch.x, me, me.lo + ch.y + it.y, phi, ex, ey, ez);
+  }
+}
+
 }  // namespace
 
 void field_gradient(const OperatorData& op, const double* phi, double* ex, double* ey,
@@ -768,8 +817,17 @@ void field_gradient(const OperatorData& op, const double* phi, double* ex, doubl
   SAAMG_CUDA(cudaMemsetAsync(ey, 0, nbox * sizeof(double), s));
   SAAMG_CUDA(cudaMemsetAsync(ez, 0, nbox * sizeof(double), s));
   if (op.n == 0) return;
+  Buf<int2> list;
+  Buf<int> count;
+  list.alloc(op.n, s);
+  count.alloc(1, s);
+  fill_int(count.p, 0, 1, s);
   field_gradient_k<<<warp_blocks(op.nchunks), 256, 0, s>>>(op.g, op.lines.p, op.chunks.p,
-                                                            op.nchunks, phi, ex, ey, ez);
+                                                            op.nchunks, phi, ex, ey, ez, list.p,
+                                                            count.p);
+  SAAMG_LAUNCH();
+  gradient_boundary_k<<<152 * 8, 256, 0, s>>>(op.g, op.lines.p, op.chunks.p, list.p, count.p,
+                                              phi, ex, ey, ez);
   SAAMG_LAUNCH();
 }
 
