@@ -139,23 +139,81 @@ __device__ void neighbour_rows(const GeomParams& g, const LineInfo* lines, int L
 // --- kernels ---------------------------------------------------------------
 
 // Warp per x-line: first/last inside node and count; flags a non-contiguous line.
-__global__ void classify_lines_k(GeomParams g, int nlines, LineInfo* lines, int* count,
-                                 int* err) {
-  int L = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (L >= nlines) return;
-  int j = L % g.ny, k = L / g.ny;
-  int first = INT_MAX, last = -1, cnt = 0;
-  for (int base = 0; base < g.nx; base += 32) {
-    int i = base + lane;
-    bool in = (i < g.nx) && node_inside(g, i, j, k);
-    unsigned m = __ballot_sync(0xffffffffu, in);
+// Exact inside test of the nodes [a, b] of line (j, k), 32 at a time: first and last inside
+// node and their number (warp-uniform results).
+__device__ void scan_line(const GeomParams& g, int j, int k, int a, int b, int lane, int& first,
+                          int& last, int& cnt) {
+  first = INT_MAX;
+  last = -1;
+  cnt = 0;
+  for (int base = a; base <= b; base += 32) {
+    const int i = base + lane;
+    const bool in = i <= b && node_inside(g, i, j, k);
+    const unsigned m = __ballot_sync(0xffffffffu, in);
     if (m) {
       if (first == INT_MAX) first = base + __ffs(m) - 1;
       last = base + 31 - __clz(m);
       cnt += __popc(m);
     }
   }
+}
+
+// Warp per x-line: first/last inside node and count; flags a non-contiguous line.  The line
+// meets the cross-section in |x - cx| < w with w = a sigma sqrt(1 - v^2); nodes two or more
+// spacings from either end of that interval are classified the same by the exact test (|F| is
+// there far above its rounding error), so only the nodes within two spacings of the ends are
+// tested exactly; a line whose ends do not look as expected (an end at the box face, a short
+// interval, or any surprise) is scanned node by node.
+__global__ void classify_lines_k(GeomParams g, int nlines, LineInfo* lines, int* count,
+                                 int* err) {
+  const int L = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (L >= nlines) return;
+  const int j = L % g.ny, k = L / g.ny;
+  int first = INT_MAX, last = -1, cnt = 0;
+  bool done = false;
+  if (g.zbc == SAAMG_Z_DIRICHLET && (k == 0 || k == g.nz - 1)) {
+    done = true;  // known zeros
+  } else {
+    const double y = node_coord(g.o[1], j, g.h[1]);
+    const double z = node_coord(g.o[2], k, g.h[2]);
+    const double sg = taper_sigma(g, z);
+    const double v = (y - g.cy) / (g.b * sg);
+    const double vv = v * v;
+    if (vv >= 1.0) {
+      done = true;  // u*u + v*v >= 1 for every node: F >= 0
+    } else if (vv < 1.0) {
+      const double w = (g.a * sg) * sqrt(1.0 - vv);
+      const double xl = (g.cx - w - g.o[0]) / g.h[0], xh = (g.cx + w - g.o[0]) / g.h[0];
+      const double A = fmax(0.0, ceil(xl) - 2.0), B = fmin((double)(g.nx - 1), floor(xh) + 2.0);
+      if (A > B) {
+        done = true;  // the interval holds no node, nor any within two spacings
+      } else if (B - A >= 64.0) {
+        const int a = (int)A, b = (int)B;
+        // the five nodes at each end: outside ... inside at the low end, inside ... outside at
+        // the high end, with one change each
+        const int i = lane < 5 ? a + lane : b - 4 + (lane - 5);
+        const bool in = lane < 10 && node_inside(g, i, j, k);
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        const unsigned mlo = m & 0x1fu, mhi = (m >> 5) & 0x1fu;
+        // low end: bit 0 clear and the set bits contiguous up to bit 4; high end: bit 4 clear
+        // and the set bits contiguous from bit 0
+        const bool lo_ok = mlo != 0 && (mlo & 1u) == 0 && ((mlo | (mlo - 1u)) & 0x1fu) == 0x1fu &&
+                           __popc(mlo) == 5 - (__ffs(mlo) - 1);
+        const bool hi_ok = mhi != 0 && (mhi & 0x10u) == 0 && (mhi & (mhi + 1u)) == 0;
+        if (lo_ok && hi_ok) {
+          first = a + __ffs(mlo) - 1;
+          last = b - 4 + (31 - __clz(mhi));
+          cnt = last - first + 1;
+          done = true;
+        }
+      } else {
+        scan_line(g, j, k, (int)A, (int)B, lane, first, last, cnt);
+        done = true;
+      }
+    }
+  }
+  if (!done) scan_line(g, j, k, 0, g.nx - 1, lane, first, last, cnt);
   if (lane == 0) {
     LineInfo l;
     l.lo = cnt ? first : 0;
