@@ -134,6 +134,103 @@ __global__ void mis_or2_k(int n, const int* __restrict__ rowptr, const int* __re
   if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(undecided, cnt);
 }
 
+// --- late rounds on a list of the undecided rows ---------------------------------------
+// Once few rows are undecided, a round visits only them: the join test looks at the closed
+// distance-2 neighbourhood of a listed row directly (the same set max1 / max2 cover), joins
+// are applied after every test has read the snapshot, and then the listed rows with a member
+// within distance 2 leave.  The list order does not matter: every decision reads the same
+// state.
+
+__global__ void mis_list_k(int n, const unsigned char* __restrict__ state, int* __restrict__ list,
+                           int* __restrict__ nlist) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool und = i < n && state[i] == 0;
+  const unsigned m = __ballot_sync(0xffffffffu, und);
+  if (!m) return;  // the whole warp
+  int base = 0;
+  if (lane == 0) base = atomicAdd(nlist, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (und) list[base + __popc(m & ((1u << lane) - 1u))] = i;
+}
+
+// join[i] = 1 if the priority of listed row i is the largest over the undecided rows within
+// distance 2 (G lanes per row split the closed neighbourhood N[i]; each lane walks N[j]).
+template <int G>
+__global__ void mis_join_list_k(const int* __restrict__ list, const int* __restrict__ nlist,
+                                const int* __restrict__ rowptr, const int* __restrict__ col,
+                                const unsigned char* __restrict__ state,
+                                const unsigned* __restrict__ ids, uint32_t seed,
+                                unsigned char* __restrict__ join) {
+  const int n = *nlist;
+  SAAMG_ROW_LOOP(G) {
+    const int t = wbase + lane / G;
+    const bool ok = t < n;
+    const int i = ok ? list[t] : 0;
+    unsigned long long acc = 0;
+    if (ok) {
+      const int p0 = rowptr[i], p1 = rowptr[i + 1];
+      for (int p = p0 - 1 + gl; p < p1; p += G) {  // p0 - 1 stands for i itself
+        const int j = p < p0 ? i : col[p];
+        if (state[j] == 0) {
+          const unsigned long long k = prio(ids, j, seed);
+          acc = k > acc ? k : acc;
+        }
+        for (int q = rowptr[j]; q < rowptr[j + 1]; ++q) {
+          const int u = col[q];
+          if (state[u] == 0) {
+            const unsigned long long k = prio(ids, u, seed);
+            acc = k > acc ? k : acc;
+          }
+        }
+      }
+    }
+    acc = group_max(acc, G);
+    if (ok && gl == 0) join[i] = acc == prio(ids, i, seed) ? 1 : 0;
+  }
+}
+
+__global__ void mis_set_list_k(const int* __restrict__ list, const int* __restrict__ nlist,
+                               const unsigned char* __restrict__ join,
+                               unsigned char* __restrict__ state) {
+  const int n = *nlist;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int i = list[t];
+    if (join[i]) state[i] = 1;
+  }
+}
+
+// listed rows still undecided leave when a member lies within distance 2; count the rest
+template <int G>
+__global__ void mis_leave_list_k(const int* __restrict__ list, const int* __restrict__ nlist,
+                                 const int* __restrict__ rowptr, const int* __restrict__ col,
+                                 unsigned char* __restrict__ state, int* __restrict__ undecided) {
+  const int n = *nlist;
+  int cnt = 0;
+  SAAMG_ROW_LOOP(G) {
+    const int t = wbase + lane / G;
+    const bool ok = t < n;
+    const int i = ok ? list[t] : 0;
+    const bool und = ok && state[i] == 0;
+    int any = 0;
+    if (und) {
+      const int p0 = rowptr[i], p1 = rowptr[i + 1];
+      for (int p = p0 - 1 + gl; p < p1 && !any; p += G) {
+        const int j = p < p0 ? i : col[p];
+        any |= state[j] == 1;
+        for (int q = rowptr[j]; q < rowptr[j + 1] && !any; ++q) any |= state[col[q]] == 1;
+      }
+    }
+    any = group_or(any, G);
+    if (und && gl == 0) {
+      if (any) state[i] = 2;
+      else ++cnt;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(undecided, cnt);
+}
+
 __global__ void roots_from_state_k(int n, const unsigned char* __restrict__ state,
                                    unsigned char* __restrict__ root) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -390,11 +487,35 @@ __global__ void cube_ids_k(int ncubes, const unsigned char* __restrict__ used,
 template <int G>
 int rounds(int n, const int* rowptr, const int* col, const unsigned* ids, uint32_t seed,
            unsigned char* state, unsigned long long* m1, unsigned char* o1, int* counter,
-           cudaStream_t s) {
+           int* list, cudaStream_t s) {
   long long need = ((long long)n * G + 255) / 256;
   int blocks = (int)(need < 152 * 16 ? (need > 0 ? need : 1) : 152 * 16);
   int rounds_done = 0;
+  int left = n;
   for (;;) {
+    if (list && n >= 200000 && left < n / 16) {
+      // few undecided rows of a large level: a round on their list (o1 holds the join flags,
+      // counter[1] the list length; on small levels the full rounds are cheaper than the
+      // distance-2 walks of the listed rows)
+      SAAMG_CUDA(cudaMemsetAsync(counter, 0, 2 * sizeof(int), s));
+      mis_list_k<<<(n + 255) / 256, 256, 0, s>>>(n, state, list, counter + 1);
+      SAAMG_LAUNCH();
+      const long long lneed = ((long long)left * G + 255) / 256;
+      const int lblocks = (int)(lneed < 152 * 16 ? (lneed > 0 ? lneed : 1) : 152 * 16);
+      mis_join_list_k<G><<<lblocks, 256, 0, s>>>(list, counter + 1, rowptr, col, state, ids,
+                                                 seed, o1);
+      SAAMG_LAUNCH();
+      mis_set_list_k<<<(left + 255) / 256, 256, 0, s>>>(list, counter + 1, o1, state);
+      SAAMG_LAUNCH();
+      mis_leave_list_k<G><<<lblocks, 256, 0, s>>>(list, counter + 1, rowptr, col, state,
+                                                  counter);
+      SAAMG_LAUNCH();
+      ++rounds_done;
+      d2h_sync(&left, counter, sizeof(int), s);
+      if (left == 0) break;
+      if (rounds_done > n + 1) fail(SAAMG_NUMERICAL, "MIS-2 rounds did not terminate");
+      continue;
+    }
     mis_max1_k<G><<<blocks, 256, 0, s>>>(n, rowptr, col, state, ids, seed, m1);
     SAAMG_LAUNCH();
     mis_max2_k<G><<<blocks, 256, 0, s>>>(n, rowptr, col, state, ids, seed, m1);
@@ -405,7 +526,6 @@ int rounds(int n, const int* rowptr, const int* col, const unsigned* ids, uint32
     mis_or2_k<G><<<blocks, 256, 0, s>>>(n, rowptr, col, state, o1, counter);
     SAAMG_LAUNCH();
     ++rounds_done;
-    int left = 0;
     d2h_sync(&left, counter, sizeof(int), s);
     if (left == 0) break;
     // every round removes at least the undecided node of largest priority
@@ -432,13 +552,13 @@ int mis2_aggregate(int n, const int* rowptr, const int* col, long long nnz, cons
   double avg = (double)nnz / (double)n;
   SAAMG_CUDA(cudaMemsetAsync(w.state, 0, (size_t)n, s));
   if (avg <= 8.0)
-    rounds<4>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, s);
+    rounds<4>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, w.list, s);
   else if (avg <= 24.0)
-    rounds<8>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, s);
+    rounds<8>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, w.list, s);
   else if (avg <= 64.0)
-    rounds<16>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, s);
+    rounds<16>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, w.list, s);
   else
-    rounds<32>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, s);
+    rounds<32>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, w.list, s);
   roots_from_state_k<<<(n + 255) / 256, 256, 0, s>>>(n, w.state, root);
   SAAMG_LAUNCH();
   fill_int(w.root1, -1, (size_t)n, s);
@@ -539,13 +659,13 @@ int mis2_aggregate_into(int n, const int* rowptr, const int* col, long long nnz,
   double avg = (double)nnz / (double)n;
   SAAMG_CUDA(cudaMemsetAsync(w.state, 0, (size_t)n, s));
   if (avg <= 8.0)
-    rounds<4>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, s);
+    rounds<4>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, nullptr, s);
   else if (avg <= 24.0)
-    rounds<8>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, s);
+    rounds<8>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, nullptr, s);
   else if (avg <= 64.0)
-    rounds<16>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, s);
+    rounds<16>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, nullptr, s);
   else
-    rounds<32>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, s);
+    rounds<32>(n, rowptr, col, ids, seed, w.state, w.m1, w.o1, w.counter, nullptr, s);
   roots_from_state_k<<<(n + 255) / 256, 256, 0, s>>>(n, w.state, root);
   SAAMG_LAUNCH();
   fill_int(w.root1, -1, (size_t)n, s);
@@ -573,7 +693,7 @@ void AggScratchBufs::alloc(int n, cudaStream_t s) {
   state.alloc(n, s);
   o1.alloc(n, s);
   m1.alloc(n, s);
-  counter.alloc(1, s);
+  counter.alloc(2, s);
   root1.alloc(n, s);
   aggroot.alloc(n, s);
   rank.alloc(n, s);
@@ -588,6 +708,7 @@ AggScratch AggScratchBufs::view() const {
   w.root1 = root1.p;
   w.aggroot = aggroot.p;
   w.rank = rank.p;
+  w.list = root1.p;  // the rounds' list of undecided rows (root1 is filled only afterwards)
   return w;
 }
 

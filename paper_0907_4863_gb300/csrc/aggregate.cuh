@@ -10,10 +10,11 @@ struct AggScratch {
   unsigned char* state;
   unsigned char* o1;
   unsigned long long* m1;
-  int* counter;
+  int* counter;   // 2 ints
   int* root1;
   int* aggroot;
   int* rank;
+  int* list = nullptr;  // n ints for the late MIS-2 rounds (NULL: every round visits all rows)
 };
 
 struct AggScratchBufs {
