@@ -262,3 +262,35 @@ def test_mis2_aggregate_standalone(S, trial):
     assert nagg == nagg_ref
     assert np.array_equal(root.cpu().numpy(), root_ref)
     assert np.array_equal(agg.cpu().numpy(), agg_ref)
+
+
+@pytest.mark.parametrize("deg,loops", [(7.0, True), (30.0, False)], ids=["deg7", "deg30"])
+def test_mis2_aggregate_large_graph(S, deg, loops):
+    """300k nodes: the late rounds run on the list of undecided rows (large levels only); the
+    set and the aggregates still equal the sequential greedy oracle's."""
+    import torch
+    rng = np.random.default_rng(7 + int(deg))
+    n = 300_000
+    m = int(n * deg / 2)
+    r, c = rng.integers(0, n, m), rng.integers(0, n, m)
+    keep = r != c
+    G = sps.coo_matrix((np.ones(int(keep.sum())), (r[keep], c[keep])), shape=(n, n)).tocsr()
+    G = ((G + G.T) > 0).astype(float).tocsr()
+    if loops:
+        G = (G + sps.eye(n)).tocsr()
+    G.sort_indices()
+    rp, cc = G.indptr.astype(np.int32), G.indices.astype(np.int32)
+    ids = rng.permutation(4 * n)[:n].astype(np.uint32)
+    seed = int(rng.integers(0, 2 ** 32))
+    A = sps.csr_matrix((np.ones(len(cc)), cc, rp), shape=(n, n)) + sps.eye(n)
+    A = A.tocsr()
+    A.sort_indices()
+    root_ref = O.mis2(A.indptr, A.indices, ids, seed)
+    agg_ref, nagg_ref = O.aggregate(A.indptr, A.indices, ids, seed, root_ref)
+    root = torch.empty(n, dtype=torch.uint8, device="cuda")
+    agg = torch.empty(n, dtype=torch.int32, device="cuda")
+    nagg = S.mis2_aggregate(torch.from_numpy(rp).cuda(), torch.from_numpy(cc).cuda(),
+                            torch.from_numpy(ids.view(np.int32)).cuda(), seed, root, agg)
+    assert nagg == nagg_ref
+    assert np.array_equal(root.cpu().numpy(), root_ref)
+    assert np.array_equal(agg.cpu().numpy(), agg_ref)
