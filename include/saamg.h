@@ -109,6 +109,10 @@ typedef struct {
   int aggregation;    /* saamg_aggregation (MIS-2) */
   int coarse_solver;  /* saamg_coarse_solver (dense LU) */
   int coarse_sweeps;  /* Gauss-Seidel steps per coarse solve (3, Sec. 3.2) */
+  int device_loop;    /* 1: saamg_solve / saamg_solve_host run the PCG loop on the device (the
+                         graph of saamg_solve_async: no host round trip per iteration); 0: a
+                         host-driven loop with one synchronisation per iteration.  Both run the
+                         same kernels in the same order and give the same bits. (1) */
 } saamg_params;
 
 typedef struct {

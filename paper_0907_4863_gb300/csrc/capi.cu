@@ -281,6 +281,7 @@ struct saamg_hierarchy {
   // identity for cached batch graphs: a new value at creation and whenever the V-cycle
   // changes (a cached graph never outlives the kernels and pointers it was captured with)
   unsigned long long version = 0;
+  long long gk_fixed = 0, gk_body = 0;  // kernels of the device-loop graph (fixed, per pass)
   // device-loop solve: the whole PCG as one graph (conditional while node)
   cudaGraph_t graph = nullptr;      // owns the conditional handle: lives as long as gexec
   cudaGraphExec_t gexec = nullptr;
@@ -326,6 +327,7 @@ static void check_params_ext(const saamg_params& p) {
   if (p.coarse_solver != SAAMG_COARSE_LU && p.coarse_solver != SAAMG_COARSE_GS)
     fail(SAAMG_EINVAL, "unknown coarse solver");
   if (p.coarse_sweeps < 1 || p.coarse_sweeps > 64) fail(SAAMG_EINVAL, "coarse_sweeps must be in 1..64");
+  if (p.device_loop != 0 && p.device_loop != 1) fail(SAAMG_EINVAL, "device_loop must be 0 or 1");
 }
 
 // Matrix of level l (level 0 = the operator's CSR)
@@ -895,6 +897,11 @@ static void pcg_pass(saamg_hierarchy* h, cudaGraphConditionalHandle cond, cudaSt
   pcg_graph_check(h->part1.p, ctl, cond, h->prm.maxit, s);
 }
 
+// Kernels of a captured solve: `fixed` run once per graph launch, `body` once per PCG pass.
+struct GraphKernels {
+  long long fixed = 0, body = 0;
+};
+
 // Capture needs a stream that can be captured (not the legacy default stream): the graph is
 // recorded on private streams (nothing executes during capture) and launched on the caller's
 // stream.  Stream 0 records the graph, stream 1 the body of a conditional node, the others
@@ -921,8 +928,10 @@ static unsigned long long next_version() {
 // One whole PCG solve into the graph that stream s is capturing: prologue (||b||, r = b - A x,
 // the loop condition), a conditional while node whose body (captured on body_s) is one PCG
 // pass, and the epilogue (true residual).  cond belongs to the graph being captured.
-static void capture_pcg(saamg_hierarchy* h, cudaGraphConditionalHandle cond, cudaStream_t s,
-                        cudaStream_t body_s) {
+static GraphKernels capture_pcg(saamg_hierarchy* h, cudaGraphConditionalHandle cond,
+                                cudaStream_t s, cudaStream_t body_s) {
+  CaptureCount counting;
+  const long long k0 = captured();
   const OperatorData& od = h->op->d;
   const int n = od.n;
   const StencilDev<double> S = od.view<double>();
@@ -949,6 +958,7 @@ static void capture_pcg(saamg_hierarchy* h, cudaGraphConditionalHandle cond, cud
   stencil_apply<double>(S, ST_RESID, h->xhat.p, h->q.p, h->bhat.p, nullptr, 0.0, 0.0, nullptr, s);
   dot_partials<double, double>(n, h->q.p, h->q.p, h->part0.p, s);
   pcg_store_true(h->part0.p, h->ctl.p, s);
+  const long long k1 = captured();
   SAAMG_CUDA(cudaStreamBeginCaptureToGraph(body_s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   try {
     pcg_pass(h, cond, body_s);
@@ -958,6 +968,7 @@ static void capture_pcg(saamg_hierarchy* h, cudaGraphConditionalHandle cond, cud
     throw;
   }
   SAAMG_CUDA(cudaStreamEndCapture(body_s, &body));
+  return GraphKernels{k1 - k0, captured() - k1};
 }
 
 static void build_solve_graph(saamg_hierarchy* h) {
@@ -971,7 +982,9 @@ static void build_solve_graph(saamg_hierarchy* h) {
     SAAMG_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault));
     SAAMG_CUDA(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     capturing = true;
-    capture_pcg(h, cond, s, capture_stream(1));
+    const GraphKernels gk = capture_pcg(h, cond, s, capture_stream(1));
+    h->gk_fixed = gk.fixed;
+    h->gk_body = gk.body;
     capturing = false;
     SAAMG_CUDA(cudaStreamEndCapture(s, &g));
     SAAMG_CUDA(cudaGraphInstantiate(&h->gexec, g, 0));
@@ -1060,6 +1073,7 @@ saamg_status saamg_params_default(saamg_params* p) {
   p->aggregation = SAAMG_AGG_MIS2;
   p->coarse_solver = SAAMG_COARSE_LU;
   p->coarse_sweeps = 3;
+  p->device_loop = 1;
   return SAAMG_OK;
 }
 
@@ -1313,6 +1327,19 @@ saamg_status saamg_vcycle(const saamg_hierarchy* hc, const double* r, double* z,
   });
 }
 
+// The device-loop solve (the graph of saamg_solve_async), waited for; the breakdown status
+// carries a message like the host loop's.
+static int solve_device(saamg_hierarchy* h, const double* rho, double* phi, double rtol,
+                        cudaStream_t s, saamg_solve_info* info) {
+  solve_async_impl(h, rho, phi, rtol, s, h->result);
+  SAAMG_CUDA(cudaEventSynchronize(h->done));
+  if (h->op->d.n > 0) count_launches(h->gk_fixed + h->result->iters * h->gk_body);
+  const saamg_status st = info_from_ctl(*h->result, info);
+  if (st == SAAMG_NUMERICAL)
+    set_last_error("saamg_solve: breakdown (NaN/Inf in the right-hand side or p'Ap = 0)");
+  return st;
+}
+
 saamg_status saamg_solve(saamg_hierarchy* h, const double* rho, double* phi, double rtol,
                          void* stream, saamg_solve_info* info) {
   saamg_solve_info local{};
@@ -1325,6 +1352,10 @@ saamg_status saamg_solve(saamg_hierarchy* h, const double* rho, double* phi, dou
     if (!(rtol > 0.0) || !std::isfinite(rtol)) fail(SAAMG_EINVAL, "rtol must be positive");
     cudaStream_t s = (cudaStream_t)stream;
     const OperatorData& od = h->op->d;
+    if (h->prm.device_loop) {
+      st = solve_device(h, rho, phi, rtol, s, info);
+      return;
+    }
     gather_rhs(od, rho, phi, h->bhat.p, h->xhat.p, s);
     st = pcg_impl(h, rtol, s, info);
     scatter_solution(od, h->xhat.p, phi, s);
@@ -1352,9 +1383,13 @@ saamg_status saamg_solve_host(saamg_hierarchy* h, const double* rho_host, double
     phi.alloc(nbox, s);
     SAAMG_CUDA(cudaMemcpyAsync(rho.p, rho_host, nbox * 8, cudaMemcpyHostToDevice, s));
     SAAMG_CUDA(cudaMemcpyAsync(phi.p, phi_host, nbox * 8, cudaMemcpyHostToDevice, s));
-    gather_rhs(od, rho.p, phi.p, h->bhat.p, h->xhat.p, s);
-    st = pcg_impl(h, rtol, s, info);
-    scatter_solution(od, h->xhat.p, phi.p, s);
+    if (h->prm.device_loop) {
+      st = solve_device(h, rho.p, phi.p, rtol, s, info);
+    } else {
+      gather_rhs(od, rho.p, phi.p, h->bhat.p, h->xhat.p, s);
+      st = pcg_impl(h, rtol, s, info);
+      scatter_solution(od, h->xhat.p, phi.p, s);
+    }
     SAAMG_CUDA(cudaMemcpyAsync(phi_host, phi.p, nbox * 8, cudaMemcpyDeviceToHost, s));
     SAAMG_CUDA(cudaStreamSynchronize(s));
   });
@@ -1390,6 +1425,7 @@ saamg_status saamg_solve_wait(saamg_hierarchy* h, saamg_solve_info* info) {
   saamg_status g = guard("saamg_solve_wait", [&] {
     if (!h || h->magic != kHierMagic) fail(SAAMG_EINVAL, "not a hierarchy handle");
     if (h->done) SAAMG_CUDA(cudaEventSynchronize(h->done));
+    if (h->gexec && h->op->d.n > 0) count_launches(h->gk_fixed + h->result->iters * h->gk_body);
     st = info_from_ctl(*h->result, info);
     if (st == SAAMG_NUMERICAL) set_last_error("saamg_solve_wait: breakdown (NaN/Inf or p'Ap = 0)");
   });
@@ -1411,6 +1447,7 @@ struct BatchGraph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   PcgCtl* res = nullptr;  // pinned, one per solve
+  std::vector<long long> kfixed, kbody;  // kernels of each solve: once, and per PCG pass
   ~BatchGraph() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -1457,6 +1494,9 @@ static std::unique_ptr<BatchGraph> build_batch_graph(
         SAAMG_CUDA(cudaGraphConditionalHandleCreate(&conds[j], g, 0, cudaGraphCondAssignDefault));
     SAAMG_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     capturing = true;
+    CaptureCount counting;  // the graph's kernels are counted when it runs
+    bg->kfixed.assign(count, 0);
+    bg->kbody.assign(count, 0);
     cudaEvent_t fork;
     SAAMG_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
     evs.push_back(fork);
@@ -1467,6 +1507,7 @@ static std::unique_ptr<BatchGraph> build_batch_graph(
       const OperatorData& od = h->op->d;
       cudaStream_t ps = capture_stream(2 + (int)(gi % nbr));
       for (int j : groups[h]) {
+        const long long c0 = captured();
         if (od.n == 0) {  // no unknowns: phi = 0, converged at once
           bg->res[j] = PcgCtl{};
           bg->res[j].converged = 1;
@@ -1476,9 +1517,11 @@ static std::unique_ptr<BatchGraph> build_batch_graph(
         gather_rhs(od, rho[j], phi[j], h->bhat.p, h->xhat.p, ps);
         set_rtol_k<<<1, 1, 0, ps>>>(h->ctl.p, rtol);
         SAAMG_LAUNCH();
-        capture_pcg(h, conds[j], ps, body);
+        const GraphKernels gk = capture_pcg(h, conds[j], ps, body);
         SAAMG_CUDA(cudaMemcpyAsync(&bg->res[j], h->ctl.p, sizeof(PcgCtl), cudaMemcpyDeviceToHost, ps));
         scatter_solution(od, h->xhat.p, phi[j], ps);
+        bg->kfixed[j] = captured() - c0 - gk.body;
+        bg->kbody[j] = gk.body;
       }
     }
     for (int k = 0; k < nbr; ++k) {
@@ -1552,6 +1595,9 @@ saamg_status saamg_solve_batched(saamg_hierarchy* const* hs, const double* const
       SAAMG_CUDA(cudaEventRecord(h->done, s));
     }
     SAAMG_CUDA(cudaStreamSynchronize(s));
+    long long kernels = 0;
+    for (int j = 0; j < count; ++j) kernels += bg->kfixed[j] + bg->res[j].iters * bg->kbody[j];
+    count_launches(kernels);
     for (int j = 0; j < count; ++j) {
       saamg_status st = info_from_ctl(bg->res[j], &infos[j]);
       if (st < 0 && worst >= 0) worst = st;

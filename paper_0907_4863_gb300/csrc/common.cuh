@@ -25,6 +25,15 @@ struct Error {
 void check_cuda(cudaError_t e, const char* what, const char* file, int line);
 
 void count_launch();
+// Launch accounting across graph capture: while a CaptureCount is alive on this thread, launches
+// are not counted as executed but tallied in captured(); the graph's executions are counted
+// afterwards with count_launches (the kernels a run of the graph executed).
+void count_launches(long long k);
+long long captured();
+struct CaptureCount {
+  CaptureCount();
+  ~CaptureCount();
+};
 // Stores the message returned by saamg_last_error() for the calling thread.
 void set_last_error(const std::string& msg);
 

@@ -48,7 +48,19 @@ void drain(ClassLog& L) {
 }
 }  // namespace
 
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+namespace {
+thread_local int t_capturing = 0;
+thread_local long long t_captured = 0;
+}  // namespace
+
+void count_launch() {
+  if (t_capturing) ++t_captured;
+  else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long captured() { return t_captured; }
+CaptureCount::CaptureCount() { ++t_capturing; }
+CaptureCount::~CaptureCount() { --t_capturing; }
 
 KernelTimer::KernelTimer(int kclass, long long nrows, cudaStream_t stream)
     : cls(kclass), rows(nrows), s(stream) {

@@ -42,7 +42,8 @@ class Params(C.Structure):
     _fields_ = [("cheb_degree", C.c_int), ("cheb_ratio", C.c_double), ("cheb_safety", C.c_double),
                 ("max_coarse", C.c_int), ("max_levels", C.c_int), ("power_iters", C.c_int),
                 ("precision", C.c_int), ("beta_rule", C.c_int), ("maxit", C.c_int),
-                ("aggregation", C.c_int), ("coarse_solver", C.c_int), ("coarse_sweeps", C.c_int)]
+                ("aggregation", C.c_int), ("coarse_solver", C.c_int), ("coarse_sweeps", C.c_int),
+                ("device_loop", C.c_int)]
 
 
 class SolveInfo(C.Structure):

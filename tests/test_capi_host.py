@@ -62,7 +62,8 @@ def test_struct_layouts_match_header(S, tmp_path):
 def test_params_default(S):
     p = S.params_default()
     assert (p.cheb_degree, p.cheb_ratio, p.cheb_safety, p.max_coarse, p.max_levels, p.power_iters,
-            p.precision, p.beta_rule, p.maxit) == (2, 30.0, 1.1, 1000, 10, 10, 0, 0, 1000)
+            p.precision, p.beta_rule, p.maxit, p.device_loop) == (2, 30.0, 1.1, 1000, 10, 10, 0, 0,
+                                                                1000, 1)
     assert S.lib().saamg_params_default(None) == S.EINVAL
 
 

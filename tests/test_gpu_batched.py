@@ -34,7 +34,8 @@ def _rho(w, seed):
                          ids=lambda w: w.name)
 def test_device_loop_equals_host_loop(S, w, prec):
     import torch
-    prm = dict(max_coarse=100, precision=prec, beta_rule=1 if prec else 0)
+    # the synchronous call on the host-driven loop, the asynchronous one on the device loop
+    prm = dict(max_coarse=100, precision=prec, beta_rule=1 if prec else 0, device_loop=0)
     h = _setup(S, w, **prm)
     rho = _rho(w, 1)
     a = torch.zeros_like(rho)
