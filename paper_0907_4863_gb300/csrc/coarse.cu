@@ -161,6 +161,229 @@ __global__ void __launch_bounds__(kGjThreads) gj_step_k(int n, int k, int cpb,
   }
 }
 
+// Panel form with the panel factored in every block (no exchange between blocks inside a
+// launch).  A launch takes b pivot steps k0 .. k0 + b - 1.  Each block loads those b columns
+// and runs the b steps on them in shared memory: pivot search, exchanged column c_s, and the
+// step on the panel columns not yet pivoted.  It then moves its own columns through the b
+// steps (a panel column from its own step on, where it becomes 1 / pivot in row k and
+// -c_s(i) / pivot elsewhere).  For one column only the rows k_s and p_s follow special
+// formulas; one warp walks those rows (one per lane) through the steps, which gives
+// r_s = x_{p_s} / pivot_s of every step, and every other row takes x <- x - c_s(i) r_s.
+// Every element sees the operations of the one-launch-per-step form in the same order.  A
+// launch reads src and writes every column to dst, so no block overwrites a column that
+// another block of the same launch may still be loading.  The own columns are copied to
+// shared memory asynchronously while the panel is factored.
+constexpr int kGjRpThreads = 256;
+constexpr int kGjRpWidth = 4;  // pivot steps per launch
+
+// Pivot keys: the bits of |v| as an integer, which order like |v| for every non-NaN v; a NaN
+// gets -1 and is never chosen, as with a floating-point comparison.  The search then runs
+// on the integer units instead of the FP64 pipe.
+__device__ __forceinline__ long long pivot_key(double v) {
+  const long long b = __double_as_longlong(v) & 0x7fffffffffffffffLL;
+  return b > 0x7ff0000000000000LL ? -1LL : b;
+}
+
+// (key, index) maximum over a warp, lowest index on ties; every lane holds the result
+__device__ __forceinline__ void rp_warp_argmax(long long& best, int& bi) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+}
+
+// the same over the block; after the barrier inside, every lane of warp 0 holds the result
+__device__ __forceinline__ void rp_block_argmax(long long& best, int& bi, long long* sv, int* si) {
+  rp_warp_argmax(best, bi);
+  if ((threadIdx.x & 31) == 0) {
+    sv[threadIdx.x >> 5] = best;
+    si[threadIdx.x >> 5] = bi;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = blockDim.x >> 5;
+    best = threadIdx.x < nw ? sv[threadIdx.x] : -1LL;
+    bi = threadIdx.x < nw ? si[threadIdx.x] : 0x7fffffff;
+    rp_warp_argmax(best, bi);
+  }
+}
+
+template <int B, int NT, bool STAGE>
+__global__ void __launch_bounds__(NT) gj_rp_k(int n, int k0, int cpb,
+                                                        const double* __restrict__ src,
+                                                        double* __restrict__ dst,
+                                                        int* __restrict__ pivrow,
+                                                        int* __restrict__ err) {
+  extern __shared__ double rp_smem[];
+  double* pan = rp_smem;                      // B columns of n
+  double* cs = rp_smem + (size_t)B * n;       // c_s of every step, B x n
+  // the block's own columns: a shared copy, or (too large for it) src itself
+  const double* own;
+  __shared__ long long sv[NT / 32];
+  __shared__ int si[NT / 32];
+  __shared__ int sp[B];
+  __shared__ double sip[B], s_xk[B], s_r[B];
+  __shared__ double s_ck, s_cp;
+  __shared__ int srow[2 * B];
+  __shared__ int nspec;
+  __shared__ double rr[kGjMaxCols][B];        // r_s of each own column
+  __shared__ double fin[kGjMaxCols][2 * B];  // final values of its special rows
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int bw = min(B, n - k0);
+  const int c0 = blockIdx.x * cpb, c1 = min(n, c0 + cpb);
+  const int ncols = max(0, c1 - c0), nown = ncols * n;
+  if constexpr (STAGE) {
+    double* own_s = rp_smem + (size_t)2 * B * n;
+    for (int e = tid; e < nown; e += nt) {
+      const unsigned d = (unsigned)__cvta_generic_to_shared(own_s + e);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d),
+                   "l"(src + (size_t)c0 * n + e)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    own = own_s;
+  } else {
+    own = src + (size_t)c0 * n;
+  }
+  for (int e = tid; e < bw * n; e += nt) pan[e] = src[(size_t)k0 * n + e];
+  __syncthreads();
+  // pivot search of the first panel column (rows k0 .. n - 1; ascending i per thread keeps
+  // the first maximum)
+  long long best = -1;
+  int bi = n;
+  for (int i = k0 + tid; i < n; i += nt) {
+    const long long v = pivot_key(pan[i]);
+    if (v > best) {
+      best = v;
+      bi = i;
+    }
+  }
+  for (int s = 0; s < bw; ++s) {
+    const int k = k0 + s;
+    rp_block_argmax(best, bi, sv, si);
+    if (tid < 32) {
+      if (best <= 0) {  // a zero or NaN column: flagged, the pivot stays a valid row
+        if (blockIdx.x == 0 && tid == 0) atomicOr(err, 1);
+        bi = k;
+      }
+      const double* col = pan + (size_t)s * n;
+      const double ip = 1.0 / col[bi];
+      if (tid == 0) {
+        sp[s] = bi;
+        sip[s] = ip;
+        s_ck = col[k];
+        s_cp = col[bi];
+      }
+      if (tid < bw) {
+        s_xk[tid] = pan[(size_t)tid * n + k];
+        s_r[tid] = pan[(size_t)tid * n + bi] * ip;  // the new row k (row p before the exchange)
+      }
+    }
+    __syncthreads();
+    const int p = sp[s];
+    const double ip = sip[s], ck = s_ck, cpv = s_cp;
+    double* c = cs + (size_t)s * n;
+    // c_s (column k with rows k and p exchanged), the step on the panel columns still to be
+    // pivoted and the pivot search of the next one (rows > k), row by row
+    best = -1;
+    bi = n;
+    for (int i = tid; i < n; i += nt) {
+      const double ci = i == k ? cpv : (i == p ? ck : pan[(size_t)s * n + i]);
+      c[i] = ci;
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        if (j >= bw) break;
+        if (j <= s) continue;  // pivoted panel columns are finished by their owner
+        const double v =
+            i == k ? s_r[j] : (i == p ? s_xk[j] : pan[(size_t)j * n + i]) - ci * s_r[j];
+        pan[(size_t)j * n + i] = v;
+        if (j == s + 1 && i > k) {
+          const long long av = pivot_key(v);
+          if (av > best) {
+            best = av;
+            bi = i;
+          }
+        }
+      }
+    }
+  }
+  // the special rows: k0 .. k0 + bw - 1 and the pivot rows, each once
+  if (tid == 0) {
+    int m = 0;
+    for (int s = 0; s < bw; ++s) srow[m++] = k0 + s;
+    for (int s = 0; s < bw; ++s) {
+      bool seen = false;
+      for (int u = 0; u < m; ++u) seen |= srow[u] == sp[s];
+      if (!seen) srow[m++] = sp[s];
+    }
+    nspec = m;
+    if (blockIdx.x == 0)
+      for (int s = 0; s < bw; ++s) pivrow[k0 + s] = sp[s];
+  }
+  if constexpr (STAGE) asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  const int m = nspec;
+  // one warp per own column walks its special rows (one per lane) through the b steps
+  for (int t = warp; t < ncols; t += nw) {
+    const int j = c0 + t;
+    // a panel column starts after its own step s0: the inverse's column, 1 / pivot in row
+    // k_s0 and -c_s0(i) / pivot elsewhere
+    const int s0 = j >= k0 && j < k0 + bw ? j - k0 : -1;
+    const int row = lane < m ? srow[lane] : -1;
+    double x = 0.0;
+    if (lane < m) {
+      if (s0 < 0) x = own[(size_t)t * n + row];
+      else x = row == k0 + s0 ? sip[s0] : -cs[(size_t)s0 * n + row] * sip[s0];
+    }
+    for (int s = s0 + 1; s < bw; ++s) {
+      const int k = k0 + s, p = sp[s];
+      const int uk = __ffs(__ballot_sync(0xffffffffu, row == k)) - 1;
+      const int up = __ffs(__ballot_sync(0xffffffffu, row == p)) - 1;
+      const double r = __shfl_sync(0xffffffffu, x, up) * sip[s];  // the new row k
+      const double xk = __shfl_sync(0xffffffffu, x, uk);
+      if (lane == 0) rr[t][s] = r;
+      if (lane < m) {
+        const double ci = cs[(size_t)s * n + row];
+        x = row == k ? r : (row == p ? xk : x) - ci * r;
+      }
+    }
+    if (lane < m) fin[t][lane] = x;
+  }
+  __syncthreads();
+  // every row of the own columns: x <- x - c_s(i) r_s over the steps s > s0 (the special
+  // rows are rewritten below)
+  {
+    int t = tid / max(n, 1), i = tid - t * n;
+    for (int e = tid; e < nown; e += nt) {
+      const int j = c0 + t;
+      const int s0 = j >= k0 && j < k0 + bw ? j - k0 : -1;
+      double x;
+      if (s0 < 0) x = own[e];
+      else x = i == k0 + s0 ? sip[s0] : -cs[(size_t)s0 * n + i] * sip[s0];
+#pragma unroll
+      for (int s = 0; s < B; ++s)
+        if (s > s0 && s < bw) x = x - cs[(size_t)s * n + i] * rr[t][s];
+      dst[(size_t)c0 * n + e] = x;
+      i += nt;
+      while (i >= n) {
+        i -= n;
+        ++t;
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < ncols * m; e += nt) {
+    const int t = e / m, u = e - t * m;
+    dst[(size_t)(c0 + t) * n + srow[u]] = fin[t][u];
+  }
+}
+
 // inverse(:, j) = work(:, q_j), q: the exchanges undone in reverse order (one thread)
 __global__ void gj_perm_k(int n, const int* __restrict__ pivrow, int* __restrict__ q) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -375,7 +598,7 @@ void coarse_factor(const DevCsr& A, CoarseSolver& cs, cudaStream_t s) {
   cs.n = n;
   cs.inv.alloc((size_t)n * n, s);
   if (n == 0) return;
-  Buf<double> w, colk;
+  Buf<double> w, w2, colk;
   Buf<int> pivrow, q, err;
   w.alloc((size_t)n * n, s);
   colk.alloc(2 * (size_t)n, s);
@@ -386,15 +609,59 @@ void coarse_factor(const DevCsr& A, CoarseSolver& cs, cudaStream_t s) {
   fill_int(err.p, 0, 1, s);
   densify_k<<<(n + 255) / 256, 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, w.p);
   SAAMG_LAUNCH();
-  gj_first_k<<<1, kGjThreads, 0, s>>>(n, w.p, colk.p, pivrow.p, err.p);
-  SAAMG_LAUNCH();
-  // about two blocks per SM, at most kGjMaxCols columns each
-  const int cpb = std::min(kGjMaxCols, std::max(1, (n + 303) / 304));
-  const int blocks = (n + cpb - 1) / cpb;
-  for (int k = 0; k < n; ++k) {
-    gj_step_k<<<blocks, kGjThreads, 0, s>>>(n, k, cpb, w.p, colk.p + (size_t)(k & 1) * n,
-                                            colk.p + (size_t)((k + 1) & 1) * n, pivrow.p, err.p);
+  // b pivot steps per launch with the panel factored in every block (one block per SM, its
+  // own columns in a contiguous range); the panel and the b exchanged columns must fit
+  // shared memory, else one launch per step
+  int nsm = 152;
+  {
+    int dev = 0;
+    SAAMG_CUDA(cudaGetDevice(&dev));
+    SAAMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int rcpb = (n + nsm - 1) / nsm;
+  // the widest panel (5 .. 2 steps) whose shared arrays fit, with the own columns staged if
+  // possible
+  constexpr size_t kRpSmem = 212u << 10;
+  int B = 0;
+  bool stage = false;
+  for (int b = 5; b >= 2 && !B; --b)
+    if ((size_t)(2 * b + rcpb) * n * sizeof(double) <= kRpSmem) B = b, stage = true;
+  for (int b = 5; b >= 2 && !B; --b)
+    if ((size_t)(2 * b) * n * sizeof(double) <= kRpSmem) B = b;
+  if (B && rcpb <= kGjMaxCols) {
+    const size_t rsm = (size_t)(2 * B + (stage ? rcpb : 0)) * n * sizeof(double);
+    const int rblocks = (n + rcpb - 1) / rcpb;
+    w2.alloc((size_t)n * n, s);
+    auto run = [&](auto kern) {
+      SAAMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+      for (int k0 = 0; k0 < n; k0 += B) {
+        kern<<<rblocks, kGjRpThreads, rsm, s>>>(n, k0, rcpb, w.p, w2.p, pivrow.p, err.p);
+        SAAMG_LAUNCH();
+        w.swap(w2);
+      }
+    };
+    switch (B * 2 + (stage ? 1 : 0)) {
+      case 11: run(gj_rp_k<5, kGjRpThreads, true>); break;
+      case 10: run(gj_rp_k<5, kGjRpThreads, false>); break;
+      case 9: run(gj_rp_k<4, kGjRpThreads, true>); break;
+      case 8: run(gj_rp_k<4, kGjRpThreads, false>); break;
+      case 7: run(gj_rp_k<3, kGjRpThreads, true>); break;
+      case 6: run(gj_rp_k<3, kGjRpThreads, false>); break;
+      case 5: run(gj_rp_k<2, kGjRpThreads, true>); break;
+      default: run(gj_rp_k<2, kGjRpThreads, false>); break;
+    }
+  } else {
+    gj_first_k<<<1, kGjThreads, 0, s>>>(n, w.p, colk.p, pivrow.p, err.p);
     SAAMG_LAUNCH();
+    // about two blocks per SM, at most kGjMaxCols columns each
+    const int cpb = std::min(kGjMaxCols, std::max(1, (n + 303) / 304));
+    const int blocks = (n + cpb - 1) / cpb;
+    for (int k = 0; k < n; ++k) {
+      gj_step_k<<<blocks, kGjThreads, 0, s>>>(n, k, cpb, w.p, colk.p + (size_t)(k & 1) * n,
+                                              colk.p + (size_t)((k + 1) & 1) * n, pivrow.p,
+                                              err.p);
+      SAAMG_LAUNCH();
+    }
   }
   gj_perm_k<<<1, 32, 0, s>>>(n, pivrow.p, q.p);
   SAAMG_LAUNCH();

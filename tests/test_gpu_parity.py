@@ -217,6 +217,23 @@ def test_solve_edge_cases(S):
         S.setup(g, S.params_default(cheb_degree=0))
 
 
+@pytest.mark.parametrize("n", [10, 13, 16, 18])
+def test_dense_coarse_inverse_sizes(S, n):
+    """A single level of 600 .. 3744 unknowns: the coarse inverse takes a panel of
+    5, 4, 5 and 3 pivot steps per launch, the own columns staged in shared memory for the
+    two smaller sizes and read from the matrix for the two larger.  The V-cycle is then the
+    exact inverse: PCG stops after one iteration with the true residual at rounding level."""
+    import torch
+    w = I.cylinder_workload(n, I.LINEAR)
+    h = S.setup(gpu_op(S, w), S.params_default(max_coarse=10 ** 6))
+    assert h.info()["levels"] == 1
+    phi = torch.zeros(w.grid.nbox, dtype=torch.float64, device="cuda")
+    rho = torch.from_numpy(I.gaussian_bunch(w.grid, w.centre, w.sigma, 0)).cuda()
+    info = S.solve(h, rho, phi, rtol=1e-10)
+    assert info["iters"] == 1
+    assert info["relres_true"] < 1e-11
+
+
 def test_determinism(S):
     import torch
     w = I.pipe_workload(32, I.QUADRATIC)
