@@ -3,7 +3,8 @@
 // inverse is formed once, densely in FP64, by Gauss-Jordan elimination with the pivoting of
 // an LU with partial pivoting (largest |a_ik|, lowest row on ties), so that every V-cycle
 // applies x = A_L^-1 b as one dense product.
-// All dense arrays are column-major: a(i, j) at [j * n + i].
+// The elimination works on column-major arrays, a(i, j) at [j * n + i]; the finished inverse
+// is stored by rows, A_L^-1(i, j) at [i * n + j], for the per-cycle product.
 #include "coarse.cuh"
 
 namespace saamg {
@@ -396,19 +397,28 @@ __global__ void gj_perm_k(int n, const int* __restrict__ pivrow, int* __restrict
   }
 }
 
-__global__ void gj_gather_k(int n, const double* __restrict__ w, const int* __restrict__ q,
-                            double* __restrict__ inv) {
-  const size_t total = (size_t)n * n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const size_t j = e / n, i = e - j * n;
-    inv[e] = w[(size_t)q[j] * n + i];
+// inverse(i, j) = work(i, q_j), stored by rows: a 32 x 32 tile read along the work's columns
+// and written along the inverse's rows through shared memory
+__global__ void __launch_bounds__(256) gj_gather_k(int n, const double* __restrict__ w,
+                                                   const int* __restrict__ q,
+                                                   double* __restrict__ inv) {
+  __shared__ double tile[32][33];
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int j = j0 + jj, i = i0 + tx;
+    if (j < n && i < n) tile[jj][tx] = w[(size_t)q[j] * n + i];
+  }
+  __syncthreads();
+  for (int ii = ty; ii < 32; ii += 8) {
+    const int i = i0 + ii, j = j0 + tx;
+    if (i < n && j < n) inv[(size_t)i * n + j] = tile[tx][ii];
   }
 }
 
-// x_i = sum_c inv(i, c) b_c, FP64 accumulation.  A block covers 32 consecutive rows (lane =
-// row, so every load of a column is one coalesced access) with kGemvWarps warps, warp w
-// summing the columns c = w mod kGemvWarps; the warps' partial sums are added in warp order.
+// x_i = sum_c inv(i, c) b_c, FP64 accumulation: one warp per row (the row is contiguous, so
+// every load is coalesced), lane l summing the columns c = l mod 32, the lanes' partial sums
+// added by a fixed butterfly
 constexpr int kGemvWarps = 8;
 
 template <class TV>
@@ -416,20 +426,15 @@ __global__ void __launch_bounds__(32 * kGemvWarps) coarse_apply_k(int n,
                                                                   const double* __restrict__ inv,
                                                                   const TV* __restrict__ b,
                                                                   TV* __restrict__ x) {
-  __shared__ double part[kGemvWarps][32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int i = blockIdx.x * 32 + lane;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kGemvWarps + (threadIdx.x >> 5);
+  if (i >= n) return;  // whole warps leave together
+  const double* row = inv + (size_t)i * n;
   double acc = 0.0;
-  if (i < n)
-    for (int c = w; c < n; c += kGemvWarps) acc += inv[(size_t)c * n + i] * (double)b[c];
-  part[w][lane] = acc;
-  __syncthreads();
-  if (w == 0 && i < n) {
-    double t = part[0][lane];
+  for (int c = lane; c < n; c += 32) acc += row[c] * (double)b[c];
 #pragma unroll
-    for (int q = 1; q < kGemvWarps; ++q) t += part[q][lane];
-    x[i] = (TV)t;
-  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) x[i] = (TV)acc;
 }
 
 // --- Gauss-Seidel (one CTA) ---------------------------------------------------------
@@ -665,9 +670,8 @@ void coarse_factor(const DevCsr& A, CoarseSolver& cs, cudaStream_t s) {
   }
   gj_perm_k<<<1, 32, 0, s>>>(n, pivrow.p, q.p);
   SAAMG_LAUNCH();
-  const size_t total = (size_t)n * n;
-  gj_gather_k<<<(int)std::min<size_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(n, w.p, q.p,
-                                                                                  cs.inv.p);
+  const dim3 tiles((n + 31) / 32, (n + 31) / 32);
+  gj_gather_k<<<tiles, 256, 0, s>>>(n, w.p, q.p, cs.inv.p);
   SAAMG_LAUNCH();
   int herr = 0;
   d2h_sync(&herr, err.p, sizeof(int), s);
@@ -684,7 +688,8 @@ void coarse_apply(const CoarseSolver& cs, const TV* b, TV* x, cudaStream_t s) {
     SAAMG_LAUNCH();
     return;
   }
-  coarse_apply_k<TV><<<(cs.n + 31) / 32, 32 * kGemvWarps, 0, s>>>(cs.n, cs.inv.p, b, x);
+  coarse_apply_k<TV><<<(cs.n + kGemvWarps - 1) / kGemvWarps, 32 * kGemvWarps, 0, s>>>(
+      cs.n, cs.inv.p, b, x);
   SAAMG_LAUNCH();
 }
 

@@ -8,7 +8,7 @@ namespace saamg {
 struct CoarseSolver {
   int n = 0;
   int kind = 0;     // SAAMG_COARSE_LU or SAAMG_COARSE_GS
-  Buf<double> inv;  // LU: A_L^-1, column-major
+  Buf<double> inv;  // LU: A_L^-1, row-major
   // Gauss-Seidel: A_L (borrowed from the hierarchy), 1 / a_ii, rows sorted by colour
   const int* rowptr = nullptr;
   const int* col = nullptr;
