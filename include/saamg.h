@@ -176,6 +176,16 @@ saamg_status saamg_operator_copy(const saamg_operator *op, int *node_of_row, dou
 saamg_status saamg_operator_apply(const saamg_operator *op, const double *x, double *y,
                                   void *stream);
 
+/* inv = A^-1 for a dense n x n matrix: the coarsest-level direct solver of Sec. 3.2 ("Coarse
+ * level solver") on its own.  a and inv are device arrays stored by rows (a[i * n + j] =
+ * A(i, j)); a is only read, and inv must not overlap it.  Gauss-Jordan elimination with the
+ * pivot choice of an LU with partial pivoting (largest |a_ik| among the rows not yet
+ * pivoted, the lowest row on ties; a NaN is never chosen), FP64 throughout.  Temporary
+ * device memory: 2 n^2 doubles.  Synchronises the stream (it reads the pivot flag).
+ * Errors: EINVAL (n < 0 or n > 16384, NULL array with n > 0), ENOMEM, ECUDA, NUMERICAL (a
+ * pivot column without a nonzero finite candidate). */
+saamg_status saamg_dense_inverse(int n, const double *a, double *inv, void *stream);
+
 /* Sets up the SA-AMG hierarchy of Sec. 3.2 on the device: MIS-2 aggregation of the
  * adjacency graph of A_l, tentative prolongator, lambda_hat by power iteration, damped-
  * Jacobi smoothed prolongator P_l, R_l = P_l^T, Galerkin A_{l+1} = R_l A_l P_l, and a

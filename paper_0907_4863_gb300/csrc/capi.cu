@@ -1175,6 +1175,16 @@ saamg_status saamg_operator_apply(const saamg_operator* op, const double* x, dou
   });
 }
 
+saamg_status saamg_dense_inverse(int n, const double* a, double* inv, void* stream) {
+  return guard("saamg_dense_inverse", [&] {
+    if (n < 0 || n > 16384) fail(SAAMG_EINVAL, "n out of range");
+    if (n > 0 && (!a || !inv)) fail(SAAMG_EINVAL, "NULL array");
+    const uintptr_t a0 = (uintptr_t)a, i0 = (uintptr_t)inv, len = (uintptr_t)n * n * 8;
+    if (n > 0 && a0 < i0 + len && i0 < a0 + len) fail(SAAMG_EINVAL, "inv overlaps a");
+    dense_inverse(n, a, inv, (cudaStream_t)stream);
+  });
+}
+
 static void check_grid(const saamg_grid* g) {
   if (!g) fail(SAAMG_EINVAL, "NULL grid");
   for (int d = 0; d < 3; ++d)

@@ -398,7 +398,7 @@ __global__ void gj_perm_k(int n, const int* __restrict__ pivrow, int* __restrict
 }
 
 // inverse(i, j) = work(i, q_j), stored by rows: a 32 x 32 tile read along the work's columns
-// and written along the inverse's rows through shared memory
+// and written along the inverse's rows through shared memory (q = NULL: a plain transpose)
 __global__ void __launch_bounds__(256) gj_gather_k(int n, const double* __restrict__ w,
                                                    const int* __restrict__ q,
                                                    double* __restrict__ inv) {
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(256) gj_gather_k(int n, const double* __restri
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int jj = ty; jj < 32; jj += 8) {
     const int j = j0 + jj, i = i0 + tx;
-    if (j < n && i < n) tile[jj][tx] = w[(size_t)q[j] * n + i];
+    if (j < n && i < n) tile[jj][tx] = w[(size_t)(q ? q[j] : j) * n + i];
   }
   __syncthreads();
   for (int ii = ty; ii < 32; ii += 8) {
@@ -598,22 +598,16 @@ void coarse_gs_setup(const DevCsr& A, const double* invd, const unsigned* ids, i
   cs.ncolours = h;
 }
 
-void coarse_factor(const DevCsr& A, CoarseSolver& cs, cudaStream_t s) {
-  const int n = A.n;
-  cs.n = n;
-  cs.inv.alloc((size_t)n * n, s);
-  if (n == 0) return;
-  Buf<double> w, w2, colk;
+// A^-1 by Gauss-Jordan elimination of the column-major n x n work array w (overwritten),
+// written by rows to inv; synchronises to read the zero-pivot flag
+static void gauss_jordan_inverse(int n, Buf<double>& w, double* inv, cudaStream_t s) {
+  Buf<double> w2, colk;
   Buf<int> pivrow, q, err;
-  w.alloc((size_t)n * n, s);
   colk.alloc(2 * (size_t)n, s);
   pivrow.alloc(n, s);
   q.alloc(n, s);
   err.alloc(1, s);
-  SAAMG_CUDA(cudaMemsetAsync(w.p, 0, sizeof(double) * (size_t)n * n, s));
   fill_int(err.p, 0, 1, s);
-  densify_k<<<(n + 255) / 256, 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, w.p);
-  SAAMG_LAUNCH();
   // b pivot steps per launch with the panel factored in every block (one block per SM, its
   // own columns in a contiguous range); the panel and the b exchanged columns must fit
   // shared memory, else one launch per step
@@ -671,11 +665,34 @@ void coarse_factor(const DevCsr& A, CoarseSolver& cs, cudaStream_t s) {
   gj_perm_k<<<1, 32, 0, s>>>(n, pivrow.p, q.p);
   SAAMG_LAUNCH();
   const dim3 tiles((n + 31) / 32, (n + 31) / 32);
-  gj_gather_k<<<tiles, 256, 0, s>>>(n, w.p, q.p, cs.inv.p);
+  gj_gather_k<<<tiles, 256, 0, s>>>(n, w.p, q.p, inv);
   SAAMG_LAUNCH();
   int herr = 0;
   d2h_sync(&herr, err.p, sizeof(int), s);
   if (herr) fail(SAAMG_NUMERICAL, "zero pivot in the coarse factorisation");
+}
+
+void coarse_factor(const DevCsr& A, CoarseSolver& cs, cudaStream_t s) {
+  const int n = A.n;
+  cs.n = n;
+  cs.inv.alloc((size_t)n * n, s);
+  if (n == 0) return;
+  Buf<double> w;
+  w.alloc((size_t)n * n, s);
+  SAAMG_CUDA(cudaMemsetAsync(w.p, 0, sizeof(double) * (size_t)n * n, s));
+  densify_k<<<(n + 255) / 256, 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, w.p);
+  SAAMG_LAUNCH();
+  gauss_jordan_inverse(n, w, cs.inv.p, s);
+}
+
+void dense_inverse(int n, const double* a, double* inv, cudaStream_t s) {
+  if (n == 0) return;
+  Buf<double> w;
+  w.alloc((size_t)n * n, s);
+  const dim3 tiles((n + 31) / 32, (n + 31) / 32);
+  gj_gather_k<<<tiles, 256, 0, s>>>(n, a, nullptr, w.p);  // rows of a -> columns of w
+  SAAMG_LAUNCH();
+  gauss_jordan_inverse(n, w, inv, s);
 }
 
 template <class TV>

@@ -21,6 +21,9 @@ struct CoarseSolver {
 
 // Dense LU with partial pivoting of A_L and its explicit inverse (synchronises).
 void coarse_factor(const DevCsr& A, CoarseSolver& cs, cudaStream_t s);
+// inv = A^-1 of the dense row-major n x n device matrix a, into row-major inv (synchronises;
+// SAAMG_NUMERICAL on a zero pivot)
+void dense_inverse(int n, const double* a, double* inv, cudaStream_t s);
 // Gauss-Seidel coarse solver (Sec. 3.2): colours A_L's graph by synchronous rounds of local
 // maxima of key(v) = (fmix32(id_v ^ 0x2545F491), id_v) (ids NULL: the row index) and sorts
 // the rows by colour; each solve then runs `steps` symmetric multicolour sweeps from x = 0.

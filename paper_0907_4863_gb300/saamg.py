@@ -104,6 +104,7 @@ def lib():
         "saamg_operator_size": [_p, C.POINTER(_i), C.POINTER(C.c_longlong)],
         "saamg_operator_copy": [_p, _p, _p, _p, _p, _p, _p, _p],
         "saamg_operator_apply": [_p, _p, _p, _p],
+        "saamg_dense_inverse": [_i, _p, _p, _p],
         "saamg_setup": [_p, C.POINTER(Params), _p, C.POINTER(_p)],
         "saamg_setup_reuse": [_p, _p, C.POINTER(Params), _p, C.POINTER(_p)],
         "saamg_hierarchy_get_info": [_p, C.POINTER(HierarchyInfo)],
@@ -299,6 +300,19 @@ def operator_copy(op: Operator, stream=None):
 @_entry
 def operator_apply(op: Operator, x, y, stream=None):
     _check(lib().saamg_operator_apply(op.handle, _ptr(x), _ptr(y), _stream(stream)))
+
+
+@_entry
+def dense_inverse(a, inv, stream=None):
+    """inv = a^-1 for a dense n x n FP64 device matrix (row-major tensors; synchronises)."""
+    import torch
+    n = int(a.shape[0]) if a.dim() == 2 else -1
+    if a.dim() != 2 or tuple(a.shape) != (n, n) or tuple(inv.shape) != (n, n):
+        raise ValueError("a and inv must be n x n")
+    for t in (a, inv):
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("a and inv must be contiguous float64 device tensors")
+    _check(lib().saamg_dense_inverse(n, _ptr(a), _ptr(inv), _stream(stream)))
 
 
 @_entry
