@@ -151,6 +151,8 @@ struct StencilDev {
   int n;               // unknowns
   int nx, ny, nz;
   const T* table;      // 8 per table row: self, -x, +x, -y, +y, -z, +z, 1/self
+  const int* trow;     // compact row of every table row
+  int ntable;
   T c0, cx, cy, cz, invd0;  // regular-row coefficients (scaled)
 };
 

@@ -536,7 +536,7 @@ __global__ void fill_table_k(const LineInfo* __restrict__ lines, const int2* __r
                              int nchunks, const double* __restrict__ coef,
                              const unsigned char* __restrict__ regular,
                              const double* __restrict__ rc, double* __restrict__ table,
-                             float* __restrict__ table32) {
+                             float* __restrict__ table32, int* __restrict__ trow) {
   int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (c >= nchunks) return;
@@ -549,6 +549,7 @@ __global__ void fill_table_k(const LineInfo* __restrict__ lines, const int2* __r
   int t = me.tstart + (i < me.rlo ? i - me.lo : (me.rlo - me.lo) + (i - me.rhi - 1));
   // a regular row outside the line's longest regular run holds the interior constants
   const bool reg = regular[row] != 0;
+  trow[t] = row;
   const double cst[8] = {rc[0], rc[1], rc[1], rc[2], rc[2], rc[3], rc[3], rc[4]};
   for (int q = 0; q < 8; ++q) {
     double v = reg ? cst[q] : coef[8 * (size_t)row + q];
@@ -700,10 +701,11 @@ void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op) 
   SAAMG_LAUNCH();
   op.table.alloc((size_t)nt * 8, s);
   op.table32.alloc((size_t)nt * 8, s);
+  op.trow.alloc((size_t)nt, s);
   if (op.n > 0) {
     fill_table_k<<<warp_blocks(nchunks), 256, 0, s>>>(op.lines.p, op.chunks.p, op.nchunks, coef.p,
                                                        op.regular.p, rc.p, op.table.p,
-                                                       op.table32.p);
+                                                       op.table32.p, op.trow.p);
     SAAMG_LAUNCH();
   }
 
@@ -723,6 +725,8 @@ StencilDev<double> OperatorData::view<double>() const {
   v.ny = g.ny;
   v.nz = g.nz;
   v.table = table.p;
+  v.trow = trow.p;
+  v.ntable = ntable;
   v.c0 = c0;
   v.cx = cx;
   v.cy = cy;
@@ -744,6 +748,8 @@ StencilDev<float> OperatorData::view<float>() const {
   v.ny = g.ny;
   v.nz = g.nz;
   v.table = table32.p;
+  v.trow = trow.p;
+  v.ntable = ntable;
   v.c0 = (float)c0;
   v.cx = (float)cx;
   v.cy = (float)cy;

@@ -28,6 +28,7 @@ struct OperatorData {
   Buf<int> rline;       // line of every compact row
   Buf<double> table;    // 8 doubles per table row
   Buf<float> table32;
+  Buf<int> trow;        // compact row of every table row
   int ntable = 0;
   double c0 = 0, cx = 0, cy = 0, cz = 0, invd0 = 0;  // regular-row coefficients
   Buf<double> scale;    // s_i = a_ii^-1/2 (unscaled diagonal)
@@ -37,7 +38,7 @@ struct OperatorData {
   DevCsr A;             // explicit scaled CSR (used by the AMG setup)
   size_t bytes() const {
     return lines.bytes() + nbr.bytes() + chunks.bytes() + rline.bytes() + table.bytes() +
-           table32.bytes() + scale.bytes() +
+           table32.bytes() + trow.bytes() + scale.bytes() +
            ids.bytes() + regular.bytes() + nbmask.bytes() + A.bytes();
   }
   template <class T>

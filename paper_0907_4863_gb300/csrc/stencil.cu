@@ -53,8 +53,10 @@ __device__ __forceinline__ void load8(const float* p, float v[8]) {
 // diverges, and it holds no floating-point work) takes its own coefficients, and a missing
 // neighbour (coefficient 0) points at the row itself.
 // PACKED: chunk c is the compact rows [32 c, 32 c + 32), each lane finds its own line (no lane
-// idles at the end of a line); otherwise chunk c is (line, offset) from the chunk list.
-template <class T, int MODE, bool PACKED>
+// idles at the end of a line) and only the rows of the regular runs are applied; chunk c of
+// the TABLE phase is the table rows [32 c, 32 c + 32), so no warp runs both kinds of row.
+// Otherwise chunk c is (line, offset) from the chunk list.
+template <class T, int MODE, bool PACKED, bool TABLE = false>
 __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int lane,
                                             const T* __restrict__ x, T* __restrict__ y,
                                             const T* __restrict__ b, T* __restrict__ d, T c1,
@@ -63,13 +65,20 @@ __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int l
     int row, i;
     LineInfo me;
     int4 nb;
-    if (PACKED) {
+    int t = -1;  // table row, if any
+    if (TABLE) {
+      t = 32 * c + lane;
+      if (t >= S.ntable) return;
+      row = S.trow[t];
+      nb = S.nbr[S.rline[row]];
+    } else if (PACKED) {
       row = 32 * c + lane;
       if (row >= S.n) return;
       const int L = S.rline[row];
       me = S.lines[L];
-      nb = S.nbr[L];
       i = me.lo + (row - me.start);
+      if (i < me.rlo || i > me.rhi) return;  // applied in the table phase
+      nb = S.nbr[L];
     } else {
       const int2 ch = S.chunks[c];
       me = S.lines[ch.x];
@@ -81,8 +90,9 @@ __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int l
     T a0 = S.c0, axm = S.cx, axp = S.cx, aym = S.cy, ayp = S.cy, azm = S.cz, azp = S.cz;
     T c2i = c2invd0;
     int oxm = -1, oxp = 1, oym = nb.x, oyp = nb.y, ozm = nb.z, ozp = nb.w;
-    if (i < me.rlo || i > me.rhi) {
-      const int t = me.tstart + (i < me.rlo ? i - me.lo : (me.rlo - me.lo) + (i - me.rhi - 1));
+    if (!TABLE && !PACKED && (i < me.rlo || i > me.rhi))
+      t = me.tstart + (i < me.rlo ? i - me.lo : (me.rlo - me.lo) + (i - me.rhi - 1));
+    if (TABLE || (!PACKED && t >= 0)) {
       T tb[8];
       load8(S.table + 8 * (size_t)t, tb);
       a0 = tb[0];
@@ -167,7 +177,9 @@ __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int l
 
 // The FP64 passes are bound by FP64 issue, where an idle lane costs as much as a busy one: they
 // take 32 consecutive rows per warp across line ends (one more 4-byte load per row, the line
-// index); the latency-bound FP32 passes keep the line chunks.
+// index), and the table rows 32 at a time in a second phase, so that a warp never issues
+// the table rows' extra multiply for a few lanes; the latency-bound FP32 passes keep the
+// line chunks.
 template <class T>
 __host__ __device__ constexpr bool packed_rows() {
   return sizeof(T) == 8;
@@ -191,12 +203,20 @@ __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __res
   }
   double dacc = 0.0;
   constexpr bool kPacked = packed_rows<T>();
-  const int nch = kPacked ? (S.n + 31) / 32 : S.nchunks;
+  // packed: the regular-run chunks, then the table chunks (the branch is uniform per warp)
+  const int nreg = kPacked ? (S.n + 31) / 32 : S.nchunks;
+  const int nch = kPacked ? nreg + (S.ntable + 31) / 32 : nreg;
   for (int c0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * K; c0 < nch; c0 += nw * K) {
 #pragma unroll
     for (int k = 0; k < K; ++k)
-      if (c0 + k < nch)
-        stencil_row<T, MODE, kPacked>(S, c0 + k, lane, x, y, b, d, c1, c2, c2invd0, dacc, agg);
+      if (c0 + k < nch) {
+        if (kPacked && c0 + k >= nreg)
+          stencil_row<T, MODE, true, true>(S, c0 + k - nreg, lane, x, y, b, d, c1, c2, c2invd0,
+                                           dacc, agg);
+        else
+          stencil_row<T, MODE, kPacked>(S, c0 + k, lane, x, y, b, d, c1, c2, c2invd0, dacc,
+                                        agg);
+      }
   }
   if (MODE == ST_SPMV_DOT || MODE == ST_DINV_DOT) {
     __shared__ double sh[32];
@@ -228,7 +248,8 @@ void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* 
     if (mode == ST_SPMV_DOT || mode == ST_DINV_DOT) fill_double(partials, 0.0, kRedBlocks, s);
     return;
   }
-  const long long nch = packed_rows<T>() ? ((long long)S.n + 31) / 32 : S.nchunks;
+  const long long nch = packed_rows<T>() ? ((long long)S.n + 31) / 32 + (S.ntable + 31) / 32
+                                         : S.nchunks;
   // the smoother class holds only the full Chebyshev step (fixed work per row); the
   // other modes of the same kernel are timed as "apply"
   // one timing class per kind of pass (each has a fixed amount of work per row)
