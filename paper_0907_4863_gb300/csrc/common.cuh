@@ -153,6 +153,8 @@ struct StencilDev {
   const T* table;      // 8 per table row: self, -x, +x, -y, +y, -z, +z, 1/self
   const int* trow;     // compact row of every table row
   int ntable;
+  const int2* rrow;    // (compact row, line) of the lines' regular-run rows, in order
+  int nrun;
   T c0, cx, cy, cz, invd0;  // regular-row coefficients (scaled)
 };
 

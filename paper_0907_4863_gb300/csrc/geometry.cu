@@ -531,6 +531,23 @@ __global__ void set_tstart_k(LineInfo* lines, const int* tstart, int nlines) {
   if (L < nlines) lines[L].tstart = tstart[L];
 }
 
+// Thread per line: rows in the regular run.
+__global__ void run_counts_k(const LineInfo* __restrict__ lines, int nlines, int* __restrict__ cnt) {
+  const int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L < nlines) cnt[L] = max(0, lines[L].rhi - lines[L].rlo + 1);
+}
+
+// Warp per line: (compact row, line) of its regular run, at the line's offset in the list.
+__global__ void run_rows_k(const LineInfo* __restrict__ lines, int nlines,
+                           const int* __restrict__ rstart, int2* __restrict__ rrow) {
+  const int L = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (L >= nlines) return;
+  const LineInfo l = lines[L];
+  const int first = l.start + (l.rlo - l.lo), cnt = l.rhi - l.rlo + 1;
+  for (int k = lane; k < cnt; k += 32) rrow[rstart[L] + k] = make_int2(first + k, L);
+}
+
 // Warp per chunk: table rows copy their 7 scaled coefficients and 1/diag.
 __global__ void fill_table_k(const LineInfo* __restrict__ lines, const int2* __restrict__ chunks,
                              int nchunks, const double* __restrict__ coef,
@@ -699,6 +716,19 @@ void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op) 
   op.ntable = (int)nt;
   set_tstart_k<<<(nlines + 255) / 256, 256, 0, s>>>(op.lines.p, tstart.p, nlines);
   SAAMG_LAUNCH();
+  {
+    Buf<int> rcnt, rstart;
+    rcnt.alloc(nlines, s);
+    rstart.alloc(nlines, s);
+    run_counts_k<<<(nlines + 255) / 256, 256, 0, s>>>(op.lines.p, nlines, rcnt.p);
+    SAAMG_LAUNCH();
+    op.nrun = (int)exclusive_scan(rcnt.p, rstart.p, nlines, s);
+    op.rrow.alloc((size_t)op.nrun, s);
+    if (op.nrun > 0) {
+      run_rows_k<<<warp_blocks(nlines), 256, 0, s>>>(op.lines.p, nlines, rstart.p, op.rrow.p);
+      SAAMG_LAUNCH();
+    }
+  }
   op.table.alloc((size_t)nt * 8, s);
   op.table32.alloc((size_t)nt * 8, s);
   op.trow.alloc((size_t)nt, s);
@@ -727,6 +757,8 @@ StencilDev<double> OperatorData::view<double>() const {
   v.table = table.p;
   v.trow = trow.p;
   v.ntable = ntable;
+  v.rrow = rrow.p;
+  v.nrun = nrun;
   v.c0 = c0;
   v.cx = cx;
   v.cy = cy;
@@ -750,6 +782,8 @@ StencilDev<float> OperatorData::view<float>() const {
   v.table = table32.p;
   v.trow = trow.p;
   v.ntable = ntable;
+  v.rrow = rrow.p;
+  v.nrun = nrun;
   v.c0 = (float)c0;
   v.cx = (float)cx;
   v.cy = (float)cy;

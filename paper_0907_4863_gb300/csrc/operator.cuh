@@ -30,6 +30,8 @@ struct OperatorData {
   Buf<float> table32;
   Buf<int> trow;        // compact row of every table row
   int ntable = 0;
+  Buf<int2> rrow;       // (compact row, line) of the lines' regular-run rows, in order
+  int nrun = 0;
   double c0 = 0, cx = 0, cy = 0, cz = 0, invd0 = 0;  // regular-row coefficients
   Buf<double> scale;    // s_i = a_ii^-1/2 (unscaled diagonal)
   Buf<unsigned> ids;    // box index of each unknown
@@ -38,7 +40,7 @@ struct OperatorData {
   DevCsr A;             // explicit scaled CSR (used by the AMG setup)
   size_t bytes() const {
     return lines.bytes() + nbr.bytes() + chunks.bytes() + rline.bytes() + table.bytes() +
-           table32.bytes() + trow.bytes() + scale.bytes() +
+           table32.bytes() + trow.bytes() + rrow.bytes() + scale.bytes() +
            ids.bytes() + regular.bytes() + nbmask.bytes() + A.bytes();
   }
   template <class T>

@@ -52,9 +52,9 @@ __device__ __forceinline__ void load8(const float* p, float v[8]) {
 // coefficients and the line's neighbour offsets; a table row (only its selection below
 // diverges, and it holds no floating-point work) takes its own coefficients, and a missing
 // neighbour (coefficient 0) points at the row itself.
-// PACKED: chunk c is the compact rows [32 c, 32 c + 32), each lane finds its own line (no lane
-// idles at the end of a line) and only the rows of the regular runs are applied; chunk c of
-// the TABLE phase is the table rows [32 c, 32 c + 32), so no warp runs both kinds of row.
+// PACKED: chunk c is entries [32 c, 32 c + 32) of the list of regular-run rows, each lane
+// finding its own line (no lane idles at the end of a line or on a table row); chunk c of the
+// TABLE phase is the table rows [32 c, 32 c + 32), so no warp runs both kinds of row.
 // Otherwise chunk c is (line, offset) from the chunk list.
 template <class T, int MODE, bool PACKED, bool TABLE = false>
 __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int lane,
@@ -72,13 +72,11 @@ __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int l
       row = S.trow[t];
       nb = S.nbr[S.rline[row]];
     } else if (PACKED) {
-      row = 32 * c + lane;
-      if (row >= S.n) return;
-      const int L = S.rline[row];
-      me = S.lines[L];
-      i = me.lo + (row - me.start);
-      if (i < me.rlo || i > me.rhi) return;  // applied in the table phase
-      nb = S.nbr[L];
+      const int k = 32 * c + lane;
+      if (k >= S.nrun) return;
+      const int2 rl = S.rrow[k];
+      row = rl.x;
+      nb = S.nbr[rl.y];
     } else {
       const int2 ch = S.chunks[c];
       me = S.lines[ch.x];
@@ -176,10 +174,10 @@ __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int l
 }
 
 // The FP64 passes are bound by FP64 issue, where an idle lane costs as much as a busy one: they
-// take 32 consecutive rows per warp across line ends (one more 4-byte load per row, the line
-// index), and the table rows 32 at a time in a second phase, so that a warp never issues
-// the table rows' extra multiply for a few lanes; the latency-bound FP32 passes keep the
-// line chunks.
+// take 32 regular-run rows per warp across line ends (one more 8-byte load per row: the row
+// and its line), and the table rows 32 at a time in a second phase, so that no lane idles and
+// no warp issues the table rows' extra multiply for a few lanes; the latency-bound FP32
+// passes keep the line chunks.
 template <class T>
 __host__ __device__ constexpr bool packed_rows() {
   return sizeof(T) == 8;
@@ -204,7 +202,7 @@ __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __res
   double dacc = 0.0;
   constexpr bool kPacked = packed_rows<T>();
   // packed: the regular-run chunks, then the table chunks (the branch is uniform per warp)
-  const int nreg = kPacked ? (S.n + 31) / 32 : S.nchunks;
+  const int nreg = kPacked ? (S.nrun + 31) / 32 : S.nchunks;
   const int nch = kPacked ? nreg + (S.ntable + 31) / 32 : nreg;
   for (int c0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * K; c0 < nch; c0 += nw * K) {
 #pragma unroll
@@ -248,7 +246,7 @@ void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* 
     if (mode == ST_SPMV_DOT || mode == ST_DINV_DOT) fill_double(partials, 0.0, kRedBlocks, s);
     return;
   }
-  const long long nch = packed_rows<T>() ? ((long long)S.n + 31) / 32 + (S.ntable + 31) / 32
+  const long long nch = packed_rows<T>() ? ((long long)S.nrun + 31) / 32 + (S.ntable + 31) / 32
                                          : S.nchunks;
   // the smoother class holds only the full Chebyshev step (fixed work per row); the
   // other modes of the same kernel are timed as "apply"
