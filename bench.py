@@ -31,7 +31,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 f
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP64 level-0 Chebyshev step
 # on the 256^3 elliptic pipe (profiles/stencil_cheb_fp64_pipe256.md); None for other kernels or
 # sizes, and to be reset whenever that kernel changes
-TRAFFIC_BYTES = {}  # (class, precision, n) -> DRAM bytes per launch (ncu), for the kernels as they are now
+TRAFFIC_BYTES = {("stencil_smooth", 0, 256): 366.19e6}  # (class, precision, n) -> DRAM bytes per launch (ncu)
 # kernel timing classes of the solve phase (one kernel template each)
 SOLVE_CLASSES = ("stencil_smooth", "stencil_apply", "stencil_resid", "stencil_first",
                  "coarse_csr", "coarse_deep", "transfer", "transfer_deep", "prolong0")
