@@ -250,8 +250,8 @@ saamg_status saamg_solve_test(const saamg_hierarchy *h);
  * (solve_ms is left 0). */
 saamg_status saamg_solve_wait(saamg_hierarchy *h, saamg_solve_info *info);
 
-/* Many solves in one call (the benchmark spec batching): count right-hand sides rho[j] -> phi[j]
- * (device box arrays) on hierarchies hs[j] of any sizes.  Solves of the same hierarchy
+/* Many solves in one call (batched serving of many geometries): count right-hand sides
+ * rho[j] -> phi[j] (device box arrays) on hierarchies hs[j] of any sizes.  Solves of the same hierarchy
  * run in the given order on one stream; different hierarchies run concurrently on a pool
  * of up to 32 library streams, each solve being one device-loop graph launch.  Joins back
  * into `stream` and returns when all are done; infos[j] per solve (solve_ms = the wall
