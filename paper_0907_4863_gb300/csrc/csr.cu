@@ -91,6 +91,38 @@ __global__ void __launch_bounds__(256) csr_k(int n, const int* __restrict__ rowp
   }
 }
 
+// Thread per row for the short rows of the prolongators (a handful of entries each): the
+// first kShortWin entries of a row are loaded under predicates, so all of the row's column,
+// value and gather loads are in flight at once, and a warp keeps 32 rows in flight.  The
+// row is summed in entry order; longer rows finish in a plain loop.
+constexpr int kShortWin = 6;
+
+template <class TV, class TM, int MODE>
+__global__ void __launch_bounds__(256) csr_short_k(int n, const int* __restrict__ rowptr,
+                                                   const int* __restrict__ col,
+                                                   const TM* __restrict__ val,
+                                                   const TV* __restrict__ x, TV* __restrict__ y) {
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n;
+       row += gridDim.x * blockDim.x) {
+    const int p0 = rowptr[row], p1 = rowptr[row + 1];
+    const TV y0 = MODE == CSR_ADD ? y[row] : TV(0);
+    int k[kShortWin];
+    TV a[kShortWin];
+#pragma unroll
+    for (int q = 0; q < kShortWin; ++q) {
+      const bool on = p0 + q < p1;
+      k[q] = on ? col[p0 + q] : 0;
+      a[q] = on ? (TV)ld(val, p0 + q) : TV(0);
+    }
+    TV acc = TV(0);
+#pragma unroll
+    for (int q = 0; q < kShortWin; ++q)
+      if (p0 + q < p1) acc += a[q] * x[k[q]];
+    for (int p = p0 + kShortWin; p < p1; ++p) acc += (TV)ld(val, p) * x[col[p]];
+    y[row] = MODE == CSR_ADD ? y0 + acc : acc;
+  }
+}
+
 template <class TV, class TM, int G>
 void launch_g(int mode, int n, const int* rowptr, const int* col, const TM* val, const TV* x,
               TV* y, const TV* b, TV* d, const TV* invd, TV c1, TV c2, double* partials,
@@ -169,6 +201,17 @@ void csr_apply(int mode, int n, const int* rowptr, const int* col, const TM* val
   // double vectors use few lanes (FP32 can afford wider groups for better coalescing) -- but
   // a small level (few rows, long rows: the deep levels of the hierarchy) needs wider groups
   // to fill the GPU at all: enough lanes for ~150 k threads, never more than the row length.
+  // the prolongators' short rows on a large level: a thread per row
+  if ((mode == CSR_ADD || mode == CSR_SPMV) && avg_nnz <= kShortWin && n >= 100000) {
+    const long long need = ((long long)n + 255) / 256;
+    const int blocks = (int)(need < 152 * 16 ? need : 152 * 16);
+    if (mode == CSR_ADD)
+      csr_short_k<TV, TM, CSR_ADD><<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y);
+    else
+      csr_short_k<TV, TM, CSR_SPMV><<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y);
+    SAAMG_LAUNCH();
+    return;
+  }
   int g = sizeof(TV) == 8 ? (avg_nnz <= 10.0 ? 2 : (avg_nnz <= 48.0 ? 4 : 8))
                           : (avg_nnz <= 6.0 ? 2 : (avg_nnz <= 20.0 ? 4 : (avg_nnz <= 64.0 ? 8 : 16)));
   int gpar = 1;
