@@ -404,6 +404,85 @@ __global__ void __launch_bounds__(256) mis0_or2_k(GridGraph g, unsigned char* __
   if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(undecided, cnt);
 }
 
+// Late rounds on the list of undecided rows, on the line structure: a thread per listed row
+// walks its closed distance-2 neighbourhood directly (the set max1 / max2 and or1 / or2
+// cover), so a list round decides exactly as a full round.
+__device__ __forceinline__ Nb0 grid_node(const GridGraph& g, int row) {
+  Nb0 r;
+  const int L = g.rline[row];
+  const LineInfo me = g.lines[L];
+  const int4 nb = g.nbr[L];
+  r.row = row;
+  r.id = (unsigned)(me.lo + (row - me.start)) + g.nx * (unsigned)L;
+  r.mask = g.nbmask[row];
+  r.off[0] = -1;
+  r.off[1] = 1;
+  r.off[2] = nb.x;
+  r.off[3] = nb.y;
+  r.off[4] = nb.z;
+  r.off[5] = nb.w;
+  return r;
+}
+
+__global__ void __launch_bounds__(256) mis0_join_list_k(const int* __restrict__ list,
+                                                        const int* __restrict__ nlist,
+                                                        GridGraph g,
+                                                        const unsigned char* __restrict__ state,
+                                                        uint32_t seed,
+                                                        unsigned char* __restrict__ join) {
+  const int n = *nlist;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const Nb0 a = grid_node(g, list[t]);
+    const unsigned long long mine = prio_id(a.id, a.row, seed);
+    unsigned long long acc = state[a.row] == 0 ? mine : 0ull;
+    for (int q = 0; q < 6; ++q) {
+      if (!((a.mask >> q) & 1u)) continue;
+      const Nb0 b = grid_node(g, a.row + a.off[q]);
+      if (state[b.row] == 0) {
+        const unsigned long long k = prio_id(b.id, b.row, seed);
+        acc = k > acc ? k : acc;
+      }
+      for (int q2 = 0; q2 < 6; ++q2) {
+        if (!((b.mask >> q2) & 1u)) continue;
+        const int v = b.row + b.off[q2];
+        if (state[v] == 0) {
+          const unsigned long long k = prio_id(nb_id(g, b.id, q2), v, seed);
+          acc = k > acc ? k : acc;
+        }
+      }
+    }
+    join[a.row] = acc == mine ? 1 : 0;
+  }
+}
+
+// listed rows still undecided leave when a member lies within distance 2; count the rest
+__global__ void __launch_bounds__(256) mis0_leave_list_k(const int* __restrict__ list,
+                                                         const int* __restrict__ nlist,
+                                                         GridGraph g,
+                                                         unsigned char* __restrict__ state,
+                                                         int* __restrict__ undecided) {
+  const int n = *nlist;
+  int cnt = 0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int i = list[t];
+    if (state[i] != 0) continue;
+    const Nb0 a = grid_node(g, i);
+    int any = 0;
+    for (int q = 0; q < 6 && !any; ++q) {
+      if (!((a.mask >> q) & 1u)) continue;
+      const int u = i + a.off[q];
+      any |= state[u] == 1;
+      const Nb0 b = grid_node(g, u);
+      for (int q2 = 0; q2 < 6 && !any; ++q2)
+        if ((b.mask >> q2) & 1u) any |= state[u + b.off[q2]] == 1;
+    }
+    if (any) state[i] = 2;
+    else ++cnt;
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(undecided, cnt);
+}
+
 __global__ void __launch_bounds__(256) agg0_phase1_k(GridGraph g,
                                                      const unsigned char* __restrict__ root,
                                                      int* __restrict__ root1) {
@@ -588,7 +667,25 @@ int mis2_aggregate_grid(int n, const GridGraph& g, const unsigned* ids, uint32_t
   const long long need = ((long long)g.nchunks + 7) / 8;
   const int blocks = (int)(need < 152 * 16 ? (need > 0 ? need : 1) : 152 * 16);
   SAAMG_CUDA(cudaMemsetAsync(w.state, 0, (size_t)n, s));
-  for (int done = 0;;) {
+  for (int done = 0, left = n;;) {
+    if (g.rline && w.list && n >= 200000 && left < n / 16) {
+      // few undecided rows of a large level: a round on their list (o1 holds the join
+      // flags, counter[1] the list length)
+      SAAMG_CUDA(cudaMemsetAsync(w.counter, 0, 2 * sizeof(int), s));
+      mis_list_k<<<(n + 255) / 256, 256, 0, s>>>(n, w.state, w.list, w.counter + 1);
+      SAAMG_LAUNCH();
+      const int lblocks = (int)std::min<long long>(((long long)left + 255) / 256, 152 * 16);
+      mis0_join_list_k<<<lblocks, 256, 0, s>>>(w.list, w.counter + 1, g, w.state, seed, w.o1);
+      SAAMG_LAUNCH();
+      mis_set_list_k<<<lblocks, 256, 0, s>>>(w.list, w.counter + 1, w.o1, w.state);
+      SAAMG_LAUNCH();
+      mis0_leave_list_k<<<lblocks, 256, 0, s>>>(w.list, w.counter + 1, g, w.state, w.counter);
+      SAAMG_LAUNCH();
+      d2h_sync(&left, w.counter, sizeof(int), s);
+      if (left == 0) break;
+      if (++done > n + 1) fail(SAAMG_NUMERICAL, "MIS-2 rounds did not terminate");
+      continue;
+    }
     mis0_max1_k<<<blocks, 256, 0, s>>>(g, w.state, seed, w.m1);
     SAAMG_LAUNCH();
     mis0_max2_k<<<blocks, 256, 0, s>>>(g, w.state, seed, w.m1);
@@ -598,7 +695,6 @@ int mis2_aggregate_grid(int n, const GridGraph& g, const unsigned* ids, uint32_t
     SAAMG_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(int), s));
     mis0_or2_k<<<blocks, 256, 0, s>>>(g, w.state, w.o1, w.counter);
     SAAMG_LAUNCH();
-    int left = 0;
     d2h_sync(&left, w.counter, sizeof(int), s);
     if (left == 0) break;
     if (++done > n + 1) fail(SAAMG_NUMERICAL, "MIS-2 rounds did not terminate");

@@ -42,6 +42,7 @@ struct GridGraph {
   int nchunks;
   const unsigned char* nbmask;
   unsigned nx, nxy;     // id strides in y and z
+  const int* rline;     // line of every row (the list rounds start from a row)
 };
 
 // mis2_aggregate on the level-0 graph, walking the line structure instead of a CSR pattern;

@@ -480,7 +480,7 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
       } else if (l == 0) {
         // level 0: the graph of the 7-point star, walked on the line structure
         GridGraph gg{od.lines.p, od.nbr.p, od.chunks.p, od.nchunks, od.nbmask.p,
-                     (unsigned)od.g.nx, (unsigned)od.g.nx * (unsigned)od.g.ny};
+                     (unsigned)od.g.nx, (unsigned)od.g.nx * (unsigned)od.g.ny, od.rline.p};
         nagg = mis2_aggregate_grid(L.n, gg, ids, seed, L.root.p, L.agg.p, agg_scratch.view(), s);
       } else {
         nagg = mis2_aggregate(L.n, A.rowptr.p, A.col.p, A.nnz, ids, seed, L.root.p, L.agg.p,
