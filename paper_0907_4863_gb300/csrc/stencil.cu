@@ -1,12 +1,14 @@
 // Matrix-free level-0 operator: the 7-point star of Eq. (6) with the boundary rows of
 // Sec. 2, scaled by D^-1/2 on both sides, applied on compact vectors.
 //
-// One warp per chunk of <= 32 consecutive unknowns of one x-line.  The x-neighbours are
-// the adjacent compact rows; the y- and z-neighbours of a row are at a fixed offset per
-// pair of lines (row + (start' - lo') - (start - lo)), so every warp load is a contiguous
-// run.  Rows inside the line's regular run use the four interior coefficients held in
-// registers; the remaining rows (near-boundary rows and their neighbours, about 5-8 % of
-// all rows) read their 7 coefficients and 1/diag from the table.
+// The x-neighbours of a row are the adjacent compact rows; its y- and z-neighbours are at a
+// fixed offset per pair of lines (row + (start' - lo') - (start - lo)), so the loads of
+// consecutive rows are contiguous runs.  Rows inside the line's regular run use the four
+// interior coefficients held in registers; the remaining rows (near-boundary rows and their
+// neighbours, about 5-8 % of all rows) read their 7 coefficients and 1/diag from the table.
+// FP32 passes: one warp per chunk of <= 32 consecutive unknowns of one x-line.  FP64 passes
+// (bound by FP64 issue): first 32 regular-run rows per warp from a (row, line) list, then
+// 32 table rows per warp from the table-row list.
 #include "operator.cuh"
 
 namespace saamg {
