@@ -723,6 +723,10 @@ void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op) 
     run_counts_k<<<(nlines + 255) / 256, 256, 0, s>>>(op.lines.p, nlines, rcnt.p);
     SAAMG_LAUNCH();
     op.nrun = (int)exclusive_scan(rcnt.p, rstart.p, nlines, s);
+    // every unknown lies in its line's regular run or is a table row: the FP64 passes apply
+    // the two lists and nothing else
+    if ((long long)op.nrun + op.ntable != op.n)
+      fail(SAAMG_ECUDA, "regular-run and table rows do not cover the unknowns");
     op.rrow.alloc((size_t)op.nrun, s);
     if (op.nrun > 0) {
       run_rows_k<<<warp_blocks(nlines), 256, 0, s>>>(op.lines.p, nlines, rstart.p, op.rrow.p);
