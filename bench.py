@@ -27,14 +27,30 @@ RTOL = 1e-8
 METRIC = "solves/s to rel-residual 1e-8 at 256^3 (mixed/batched vs FP64 GPU); HBM GB/s; p99"
 UNIT = "solves/s"
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP64 level-0 Chebyshev step
-# on the 256^3 elliptic pipe (profiles/stencil_cheb_fp64_pipe256.md); None for other kernels or
-# sizes, and to be reset whenever that kernel changes
+# on the 256^3 elliptic pipe, from its ncu capture; None for other kernels or sizes, and to be
+# reset whenever that kernel changes
 TRAFFIC_BYTES = {("stencil_smooth", 0, 256): 366.19e6}  # (class, precision, n) -> DRAM bytes per launch (ncu)
 # kernel timing classes of the solve phase (one kernel template each)
 SOLVE_CLASSES = ("stencil_smooth", "stencil_apply", "stencil_resid", "stencil_first",
                  "coarse_csr", "coarse_deep", "transfer", "transfer_deep", "prolong0")
+
+
+def fp64_peak(device=0, sm_max_mhz=None):
+    """FP64 issue roof of the device: SMs x 2 FP64 FMA per clock x 2 flop x maximum SM clock.
+    The SM count is the device's own; the clock is the maximum nvidia-smi reported during the
+    run, else the one recorded with the measured peaks, else GB300's 2070 MHz."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    if not sm_max_mhz:
+        path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        peaks = json.load(open(path)) if os.path.exists(path) else {}
+        sm_max_mhz = peaks.get("sm_max_mhz", 2070.0)
+    return {"tflops": sms * 2 * 2 * sm_max_mhz * 1e6 / 1e12,
+            "source": f"derived: {sms} SMs x 2 FP64 FMA/clk x 2 flop x {sm_max_mhz:.0f} MHz"}
+
+
+FP64_PEAK = {"tflops": 152 * 2 * 2 * 2.07e9 / 1e12, "source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz"}
 
 
 def parse():
@@ -221,6 +237,7 @@ def run_ours(args):
     # --- roofline of the dominant kernel (live, CUDA events on the launching stream).  Each
     # solve-phase class is one kernel template; the sparse products of the setup are several
     # different kernels, reported as a class time only.
+    FP64_PEAK.update(fp64_peak(local, clk.get("sm_max_mhz")))
     dom_name = max(SOLVE_CLASSES, key=lambda k: ktime[k][0])
     ib1 = level1_index_bytes(hinfo)
     roof = roofline(dom_name, ktime[dom_name], prec, args.n, ib1)
@@ -340,9 +357,8 @@ def roofline(name, rec, prec, n=256, index_bytes=4):
     # HBM is their tighter roofline, as for every FP32 / BF16 pass
     if prec == 0 and (name.startswith("stencil") or name == "prolong0"):
         ach = flops / avg_s / 1e12
-        out.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS,
-                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"})
+        out.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK["tflops"], "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK["tflops"], "peak_source": FP64_PEAK["source"]})
     else:
         ach = nbytes / avg_s / 1e9
         out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",

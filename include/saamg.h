@@ -286,9 +286,10 @@ saamg_status saamg_mis2_aggregate(int n, const int *rowptr, const int *col, cons
  * code inside a fixed memory pool or a callback that must not re-enter the allocator).
  * Same arguments, rule and results as saamg_mis2_aggregate.  Its scratch is one static
  * device array of about 5.8 MB per device that loads the library, held until the process
- * exits; graphs with more than 262,144 nodes are rejected with EINVAL.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress), so make that first
- * call before any stream capture.  Calls share the array: two calls whose GPU work
+ * exits; graphs with more than 262,144 nodes are rejected with EINVAL.  Every call looks up
+ * the array's device address (cudaGetSymbolAddress, which allocates nothing); the first call
+ * on a device also loads the library's device code there, so make that first call before
+ * any stream capture.  Calls share the array: two calls whose GPU work
  * overlaps (other streams, other host threads) race and give undefined results.  Nothing
  * from an earlier call is read: every call initialises the parts it uses. */
 saamg_status saamg_mis2_aggregate_noalloc(int n, const int *rowptr, const int *col,

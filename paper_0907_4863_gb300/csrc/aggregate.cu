@@ -568,7 +568,7 @@ int rounds(int n, const int* rowptr, const int* col, const unsigned* ids, uint32
            unsigned char* state, unsigned long long* m1, unsigned char* o1, int* counter,
            int* list, cudaStream_t s) {
   long long need = ((long long)n * G + 255) / 256;
-  int blocks = (int)(need < 152 * 16 ? (need > 0 ? need : 1) : 152 * 16);
+  int blocks = (int)(need < sm_count() * 16 ? (need > 0 ? need : 1) : sm_count() * 16);
   int rounds_done = 0;
   int left = n;
   for (;;) {
@@ -580,7 +580,7 @@ int rounds(int n, const int* rowptr, const int* col, const unsigned* ids, uint32
       mis_list_k<<<(n + 255) / 256, 256, 0, s>>>(n, state, list, counter + 1);
       SAAMG_LAUNCH();
       const long long lneed = ((long long)left * G + 255) / 256;
-      const int lblocks = (int)(lneed < 152 * 16 ? (lneed > 0 ? lneed : 1) : 152 * 16);
+      const int lblocks = (int)(lneed < sm_count() * 16 ? (lneed > 0 ? lneed : 1) : sm_count() * 16);
       mis_join_list_k<G><<<lblocks, 256, 0, s>>>(list, counter + 1, rowptr, col, state, ids,
                                                  seed, o1);
       SAAMG_LAUNCH();
@@ -617,7 +617,7 @@ template <int G>
 void phase2(int n, const int* rowptr, const int* col, const unsigned* ids, uint32_t seed,
             const int* root1, int* aggroot, int* err, cudaStream_t s) {
   long long need = ((long long)n * G + 255) / 256;
-  int blocks = (int)(need < 152 * 16 ? (need > 0 ? need : 1) : 152 * 16);
+  int blocks = (int)(need < sm_count() * 16 ? (need > 0 ? need : 1) : sm_count() * 16);
   agg_phase2_k<G><<<blocks, 256, 0, s>>>(n, rowptr, col, ids, seed, root1, aggroot, err);
   SAAMG_LAUNCH();
 }
@@ -665,7 +665,7 @@ int mis2_aggregate_grid(int n, const GridGraph& g, const unsigned* ids, uint32_t
                         unsigned char* root, int* agg, const AggScratch& w, cudaStream_t s) {
   if (n <= 0) return 0;
   const long long need = ((long long)g.nchunks + 7) / 8;
-  const int blocks = (int)(need < 152 * 16 ? (need > 0 ? need : 1) : 152 * 16);
+  const int blocks = (int)(need < sm_count() * 16 ? (need > 0 ? need : 1) : sm_count() * 16);
   SAAMG_CUDA(cudaMemsetAsync(w.state, 0, (size_t)n, s));
   for (int done = 0, left = n;;) {
     if (g.rline && w.list && n >= 200000 && left < n / 16) {
@@ -674,7 +674,7 @@ int mis2_aggregate_grid(int n, const GridGraph& g, const unsigned* ids, uint32_t
       SAAMG_CUDA(cudaMemsetAsync(w.counter, 0, 2 * sizeof(int), s));
       mis_list_k<<<(n + 255) / 256, 256, 0, s>>>(n, w.state, w.list, w.counter + 1);
       SAAMG_LAUNCH();
-      const int lblocks = (int)std::min<long long>(((long long)left + 255) / 256, 152 * 16);
+      const int lblocks = (int)std::min<long long>(((long long)left + 255) / 256, sm_count() * 16);
       mis0_join_list_k<<<lblocks, 256, 0, s>>>(w.list, w.counter + 1, g, w.state, seed, w.o1);
       SAAMG_LAUNCH();
       mis_set_list_k<<<lblocks, 256, 0, s>>>(w.list, w.counter + 1, w.o1, w.state);
@@ -841,27 +841,20 @@ constexpr size_t kNoallocBytes = kOffTiles + kAlignN(sizeof(long long) * kTileEn
 // it; nothing carries over between calls.
 static __device__ __align__(256) unsigned char g_mis2_scratch[kNoallocBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-unsigned char* g_noalloc_ptr[kMaxDevices] = {};
-
-// Device address of the scratch on the current device, looked up once per device.
+// Device address of the scratch in the current context.  Looked up on every call: once the
+// module is loaded the lookup is a table search that allocates nothing, and a cached address
+// would go stale when the device is reset and the module is loaded again at another address.
+// The very first lookup on a device loads the module, which must not happen inside a stream
+// capture.
 unsigned char* noalloc_scratch() {
-  int dev = 0;
-  SAAMG_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) fail(SAAMG_EINVAL, "device index out of range");
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_mis2_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      cudaGetLastError();
-      fail(SAAMG_ECUDA, std::string("cudaGetSymbolAddress of the aggregation scratch: ") +
-                            cudaGetErrorString(e));
-    }
-    g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_mis2_scratch);
+  if (e != cudaSuccess || p == nullptr) {
+    cudaGetLastError();
+    fail(SAAMG_ECUDA, std::string("cudaGetSymbolAddress of the aggregation scratch: ") +
+                          cudaGetErrorString(e));
   }
-  return g_noalloc_ptr[dev];
+  return static_cast<unsigned char*>(p);
 }
 
 }  // namespace
@@ -899,6 +892,9 @@ extern "C" saamg_status saamg_mis2_aggregate_noalloc(int n, const int* rowptr, c
   } catch (const Error& e) {
     set_last_error(std::string("saamg_mis2_aggregate_noalloc: ") + e.msg);
     return e.status;
+  } catch (const std::bad_alloc&) {
+    set_last_error("saamg_mis2_aggregate_noalloc: out of host memory");
+    return SAAMG_ENOMEM;
   } catch (...) {
     set_last_error("saamg_mis2_aggregate_noalloc: unexpected exception");
     return SAAMG_ECUDA;

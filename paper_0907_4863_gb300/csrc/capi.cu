@@ -161,6 +161,21 @@ void* HostScratch::need(size_t b) {
   return p;
 }
 
+int sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  SAAMG_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int n = 0;
+  SAAMG_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  if (n < 1) n = 1;
+  if (dev >= 0 && dev < 64) cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
+
 void d2h_sync(void* host, const void* dev, size_t bytes, cudaStream_t s) {
   SAAMG_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, s));
   SAAMG_CUDA(cudaStreamSynchronize(s));
@@ -370,7 +385,7 @@ static bool same_pattern(const DevCsr& a, const DevCsr& b, cudaStream_t s) {
   Buf<int> diff;
   diff.alloc(1, s);
   SAAMG_CUDA(cudaMemsetAsync(diff.p, 0, sizeof(int), s));
-  pattern_diff_k<<<std::min((a.n + 255) / 256, 152 * 8), 256, 0, s>>>(a.n, a.rowptr.p, a.col.p,
+  pattern_diff_k<<<std::min((a.n + 255) / 256, sm_count() * 8), 256, 0, s>>>(a.n, a.rowptr.p, a.col.p,
                                                                       b.rowptr.p, b.col.p, diff.p);
   SAAMG_LAUNCH();
   int h = 0;

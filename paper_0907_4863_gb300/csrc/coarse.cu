@@ -611,12 +611,7 @@ static void gauss_jordan_inverse(int n, Buf<double>& w, double* inv, cudaStream_
   // b pivot steps per launch with the panel factored in every block (one block per SM, its
   // own columns in a contiguous range); the panel and the b exchanged columns must fit
   // shared memory, else one launch per step
-  int nsm = 152;
-  {
-    int dev = 0;
-    SAAMG_CUDA(cudaGetDevice(&dev));
-    SAAMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  }
+  const int nsm = sm_count();
   const int rcpb = (n + nsm - 1) / nsm;
   // the widest panel (5 .. 2 steps) whose shared arrays fit, with the own columns staged if
   // possible

@@ -176,7 +176,9 @@ struct DevCsr {
 // Reduction partials: kernels that reduce write one double per block into a fixed
 // array, and a single block adds them in index order, so results do not depend on
 // scheduling.
-constexpr int kRedBlocks = 608;  // 4 x 152 SMs
+// The count is fixed (4 per SM of a 152-SM GB300) and not taken from the device: it defines
+// the summation tree, which must not change with the part the library runs on.
+constexpr int kRedBlocks = 608;
 constexpr int kRedThreads = 256;
 
 // ---------------------------------------------------------------------------
@@ -194,6 +196,9 @@ void fill_int(int* p, int v, size_t n, cudaStream_t s);
 void fill_double(double* p, double v, size_t n, cudaStream_t s);
 void sum_partials(const double* partials, int count, double* out, cudaStream_t s,
                   double* inv_sqrt = nullptr);
+// Number of SMs of the current device (cached per device); grids of grid-stride kernels are
+// sized as multiples of it.
+int sm_count();
 // Copies `bytes` from device to host and waits.
 void d2h_sync(void* host, const void* dev, size_t bytes, cudaStream_t s);
 

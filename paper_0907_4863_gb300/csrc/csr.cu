@@ -132,7 +132,7 @@ void launch_g(int mode, int n, const int* rowptr, const int* col, const TM* val,
     blocks = kRedBlocks;
   } else {
     long long need = ((long long)n * G + 255) / 256;
-    blocks = (int)(need < 152 * 16 ? (need > 0 ? need : 1) : 152 * 16);
+    blocks = (int)(need < sm_count() * 16 ? (need > 0 ? need : 1) : sm_count() * 16);
   }
 #define SAAMG_CSR_CASE(M)                                                                  \
   case M:                                                                                  \
@@ -204,7 +204,7 @@ void csr_apply(int mode, int n, const int* rowptr, const int* col, const TM* val
   // the prolongators' short rows on a large level: a thread per row
   if ((mode == CSR_ADD || mode == CSR_SPMV) && avg_nnz <= kShortWin && n >= 100000) {
     const long long need = ((long long)n + 255) / 256;
-    const int blocks = (int)(need < 152 * 16 ? need : 152 * 16);
+    const int blocks = (int)(need < sm_count() * 16 ? need : sm_count() * 16);
     if (mode == CSR_ADD)
       csr_short_k<TV, TM, CSR_ADD><<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y);
     else

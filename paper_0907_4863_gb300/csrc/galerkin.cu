@@ -985,12 +985,12 @@ void run_class(int c, const int* list, int nl, CsrView X, CsrView Y, double yavg
   KernelTimer kt(SAAMG_KT_SPGEMM, nl, s);
   const int threads = 32 * kSpgemmWarps;
   if (c == 0) {
-    const int blocks = std::max(1, std::min((nl + 127) / 128, 152 * 16));
+    const int blocks = std::max(1, std::min((nl + 127) / 128, sm_count() * 16));
     spgemm_merge_k<NUMERIC><<<blocks, 128, 0, s>>>(list, nl, X, Y, crowptr, count, ccol, cval);
     SAAMG_LAUNCH();
     return;
   }
-  const int blocks = std::max(1, std::min((nl + kSpgemmWarps - 1) / kSpgemmWarps, 152 * 16));
+  const int blocks = std::max(1, std::min((nl + kSpgemmWarps - 1) / kSpgemmWarps, sm_count() * 16));
   if (c == 1) {
     const size_t sm = (size_t)kSpgemmWarps * 64 * (NUMERIC ? 16 : 8);
     spgemm_esc_k<64, NUMERIC><<<blocks, threads, sm, s>>>(list, nl, X, Y, crowptr, count, ccol, cval);
@@ -1000,7 +1000,7 @@ void run_class(int c, const int* list, int nl, CsrView X, CsrView Y, double yavg
   const int lg = kHashMinLog + (c - 2);
   const int cap = 1 << lg;
   if (nl <= kFewRows) {  // few rows: a block per row
-    const int nb = std::min(nl, 152 * 4);
+    const int nb = std::min(nl, sm_count() * 4);
     if (!NUMERIC) {
       const size_t sm = (size_t)cap * sizeof(int);
       if (sm > 48 * 1024)
@@ -1045,7 +1045,7 @@ void run_class(int c, const int* list, int nl, CsrView X, CsrView Y, double yavg
     const int wpb =
         (int)std::max<size_t>(1, std::min<size_t>(kSpgemmWarps, (size_t)(200 << 10) / per_warp));
     const size_t sm = (size_t)wpb * per_warp;
-    const int nb = std::max(1, std::min((nl + wpb - 1) / wpb, 152 * 16));
+    const int nb = std::max(1, std::min((nl + wpb - 1) / wpb, sm_count() * 16));
     auto launch = [&](auto kernel) {
       if (sm > 48 * 1024)
         SAAMG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1150,7 +1150,7 @@ void prolongator(const DevCsr& A, const int* agg, int nagg, const double* invd, 
   cnt.alloc(n + 1, s);
   const int G = avg <= 16.0 ? 16 : 32;
   const bool sortable = nagg < (1 << 25);  // (aggregate << 6 | entry) stays below 0xffffffff
-  const int blocks = (int)std::min<long long>(((long long)n * G + 255) / 256, 152 * 32);
+  const int blocks = (int)std::min<long long>(((long long)n * G + 255) / 256, sm_count() * 32);
   {
     KernelTimer kt(SAAMG_KT_SPGEMM, n, s);
     if (G == 16)
@@ -1211,12 +1211,12 @@ void transpose(const DevCsr& P, DevCsr& R, cudaStream_t s) {
     SAAMG_LAUNCH();
   }
   if (R.n > 0 && R.n < 65536 && P.nnz > 64LL * R.n) {  // few long rows
-    rank_rows_block_k<<<std::min(R.n, 152 * 8), 256, 0, s>>>(R.n, R.rowptr.p, tcol.p, tval.p,
+    rank_rows_block_k<<<std::min(R.n, sm_count() * 8), 256, 0, s>>>(R.n, R.rowptr.p, tcol.p, tval.p,
                                                             R.col.p, R.val.p);
     SAAMG_LAUNCH();
   } else if (R.n > 0) {
     long long warps = R.n;
-    int blocks = (int)std::min<long long>((warps * 32 + 255) / 256, 152 * 32);
+    int blocks = (int)std::min<long long>((warps * 32 + 255) / 256, sm_count() * 32);
     rank_rows_k<<<blocks, 256, 0, s>>>(R.n, R.rowptr.p, tcol.p, tval.p, R.col.p, R.val.p);
     SAAMG_LAUNCH();
   }

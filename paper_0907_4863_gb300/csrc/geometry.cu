@@ -689,7 +689,7 @@ void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op) 
                                                               op.nchunks, op.scale.p, rowlen.p,
                                                               op.ids.p, rc.p, blist.p, bcount.p);
     SAAMG_LAUNCH();
-    assemble_boundary_k<<<152 * 8, 256, 0, s>>>(g, op.lines.p, op.chunks.p, blist.p, bcount.p,
+    assemble_boundary_k<<<sm_count() * 8, 256, 0, s>>>(g, op.lines.p, op.chunks.p, blist.p, bcount.p,
                                                 coef.p, op.scale.p, rowlen.p);
     SAAMG_LAUNCH();
   }
@@ -928,7 +928,7 @@ void field_gradient(const OperatorData& op, const double* phi, double* ex, doubl
                                                             op.nchunks, phi, ex, ey, ez, list.p,
                                                             count.p);
   SAAMG_LAUNCH();
-  gradient_boundary_k<<<152 * 8, 256, 0, s>>>(op.g, op.lines.p, op.chunks.p, list.p, count.p,
+  gradient_boundary_k<<<sm_count() * 8, 256, 0, s>>>(op.g, op.lines.p, op.chunks.p, list.p, count.p,
                                               phi, ex, ey, ez);
   SAAMG_LAUNCH();
 }

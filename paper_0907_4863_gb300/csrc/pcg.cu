@@ -233,7 +233,7 @@ __global__ void store_true_k(const double* __restrict__ part, PcgCtl* ctl) {
 
 inline int vec_blocks(int n) {
   int b = (n + 255) / 256;
-  return b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8;
+  return b < sm_count() * 8 ? (b > 0 ? b : 1) : sm_count() * 8;
 }
 
 }  // namespace

@@ -150,7 +150,7 @@ void deposit_cic(const saamg_grid& grid, int np, const double* x, const double* 
     cic_deposit_k<<<(np + 255) / 256, 256, 0, s>>>(g, np, x, y, z, q, vol, exp.p, acc.p);
     SAAMG_LAUNCH();
   }
-  const int blocks = (int)std::min<size_t>((nbox + 255) / 256, 152 * 16);
+  const int blocks = (int)std::min<size_t>((nbox + 255) / 256, sm_count() * 16);
   fixed_to_double_k<<<blocks, 256, 0, s>>>(nbox, acc.p, exp.p, rho);
   SAAMG_LAUNCH();
 }

@@ -219,7 +219,7 @@ void sell_apply(int mode, const DevSell& S, const TM* val, const TV* x, TV* y, c
   if (mode == CSR_CHEB && c1 == TV(0)) mode = kSellCheb1;
   const long long need = ((long long)S.nslices + 7) / 8;
   const int blocks =
-      mode == CSR_SPMV_DINV_DOT ? kRedBlocks : (int)(need < 152 * 16 ? need : 152 * 16);
+      mode == CSR_SPMV_DINV_DOT ? kRedBlocks : (int)(need < sm_count() * 16 ? need : sm_count() * 16);
 #define SAAMG_SELL_CASE(M)                                                                    \
   case M:                                                                                     \
     if (S.index_bytes == 2)                                                                   \

@@ -263,7 +263,7 @@ void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* 
   int blocks = kRedBlocks;
   if (mode != ST_SPMV_DOT && mode != ST_DINV_DOT) {
     long long need = (nch + 8 * kChunks<T>() - 1) / (8 * kChunks<T>());
-    blocks = (int)(need < 152 * 16 ? need : 152 * 16);
+    blocks = (int)(need < sm_count() * 16 ? need : sm_count() * 16);
   }
   // c2 / diag of the regular rows, formed here: a kernel that forms it from c2 lets the
   // compiler merge it with the table rows' c2 * (1/diag) into one multiply on every row
@@ -309,7 +309,7 @@ void stencil_prolong(const StencilDev<T>& S, const int* agg, T omega, const T* v
   if (S.nchunks == 0) return;
   KernelTimer kt(SAAMG_KT_PROLONG0, S.n, s);
   const long long need = ((long long)S.nchunks + 8 * kChunks<T>() - 1) / (8 * kChunks<T>());
-  const int blocks = (int)(need < 152 * 16 ? need : 152 * 16);
+  const int blocks = (int)(need < sm_count() * 16 ? need : sm_count() * 16);
   stencil_k<T, ST_PROLONG, kChunks<T>()><<<blocks, 256, 0, s>>>(
       S, v, y, nullptr, nullptr, T(0), omega, T(omega * S.invd0), nullptr, nullptr, agg);
   SAAMG_LAUNCH();

@@ -75,6 +75,53 @@ def test_fmix32_is_a_bijection_sample():
     assert len(vals) == 1 << 14
 
 
+def _murmur3_x86_32(data, seed):
+    """MurmurHash3_x86_32 (Appleby) written from its description: 4-byte little-endian
+    blocks mixed into h (k *= c1, rotl 15, k *= c2; h ^= k, rotl 13, h = 5 h + 0xe6546b64),
+    the tail bytes mixed the same way without the h rotation, h ^= length, and the finaliser
+    taken from the oracle."""
+    m = 0xFFFFFFFF
+    rotl = lambda x, r: ((x << r) | (x >> (32 - r))) & m  # noqa: E731
+    c1, c2 = 0xCC9E2D51, 0x1B873593
+    h = seed
+    nb = len(data) // 4
+    for i in range(nb):
+        k = int.from_bytes(data[4 * i:4 * i + 4], "little")
+        k = rotl((k * c1) & m, 15)
+        h ^= (k * c2) & m
+        h = (rotl(h, 13) * 5 + 0xE6546B64) & m
+    tail = data[4 * nb:]
+    if tail:
+        k = int.from_bytes(tail, "little")
+        k = rotl((k * c1) & m, 15)
+        h ^= (k * c2) & m
+    return O.fmix32(h ^ len(data))
+
+
+# Published known answers of MurmurHash3_x86_32 (the reference implementation's widely
+# quoted test values).  For the empty key the hash is fmix32(seed), so the first three pin
+# the finaliser directly; the others reach it through the block and tail mixing.
+_MURMUR3_KNOWN = [
+    (b"", 0x00000000, 0x00000000),
+    (b"", 0x00000001, 0x514E28B7),
+    (b"", 0xFFFFFFFF, 0x81F16F39),
+    (b"\x00\x00\x00\x00", 0x00000000, 0x2362F9DE),
+    (b"\xff\xff\xff\xff", 0x00000000, 0x76293B50),
+    (b"!Ce\x87", 0x00000000, 0xF55B516B),
+    (b"abc", 0x00000000, 0xB3DD93FA),
+    (b"aaaa", 0x9747B28C, 0x5A97808A),
+    (b"Hello, world!", 0x9747B28C, 0x24884CBA),
+    (b"The quick brown fox jumps over the lazy dog", 0x9747B28C, 0x2FA826CD),
+]
+
+
+@pytest.mark.parametrize("data,seed,want", _MURMUR3_KNOWN)
+def test_fmix32_known_answers(data, seed, want):
+    """The priority hash is the MurmurHash3 finaliser: a mistyped shift or multiplier would be
+    a bijection all the same, but it would miss these published values."""
+    assert _murmur3_x86_32(data, seed) == want
+
+
 @pytest.mark.parametrize("trial", range(12))
 def test_mis2_bruteforce_and_rounds(trial):
     rng = np.random.default_rng(trial)
@@ -155,6 +202,39 @@ def test_power_lambda_bounds_spectrum():
     assert lam10 <= lam_max * (1 + 1e-12)
     assert lam10 > 0.8 * lam_max
     assert abs(lam400 - lam_max) < 2e-3 * lam_max
+
+
+@pytest.mark.parametrize("n,iters", [(10, 10), (13, 10), (10, 3), (16, 25)])
+def test_power_lambda_closed_form_path_graph(n, iters):
+    """The estimate after exactly `iters` steps, in closed form.  For the path-graph Laplacian
+    tridiag(-1, 2, -1), D^-1 A has eigenvalues mu_k = 1 - cos(k pi / (n + 1)) with the sine
+    eigenvectors e_k(j) = sqrt(2 / (n + 1)) sin(j k pi / (n + 1)).  Steps that normalise
+    v <- M v / ||M v|| and end with ||M v|| give ||M^(K+1) v0|| / ||M^K v0|| for K = iters, i.e.
+    sqrt(sum mu^(2K+2) c^2 / sum mu^(2K) c^2) with c_k = e_k . v0; one step more or fewer
+    changes the value by about 1e-2 here."""
+    ids = np.arange(n, dtype=np.uint32)
+    rowptr, col, val = [0], [], []
+    for i in range(n):
+        for j, v in ((i - 1, -1.0), (i, 2.0), (i + 1, -1.0)):
+            if 0 <= j < n:
+                col.append(j)
+                val.append(v)
+        rowptr.append(len(col))
+    rowptr, col, val = (np.array(rowptr, np.int32), np.array(col, np.int32), np.array(val))
+    v0 = np.array([0.5 + O.fmix32(int(i) ^ 0xA5A5A5A5) / 2.0 ** 32 for i in ids])
+    k = np.arange(1, n + 1)
+    j = np.arange(1, n + 1)
+    mu = 1.0 - np.cos(k * np.pi / (n + 1))
+    E = np.sqrt(2.0 / (n + 1)) * np.sin(np.outer(k, j) * np.pi / (n + 1))
+    c2 = (E @ v0) ** 2
+
+    def closed(K):
+        return np.sqrt(np.sum(mu ** (2 * K + 2) * c2) / np.sum(mu ** (2 * K) * c2))
+
+    lam = O.power_lambda(rowptr, col, val, ids, iters)
+    assert abs(lam - closed(iters)) <= 1e-13 * closed(iters)
+    for other in (iters - 1, iters + 1):
+        assert abs(lam - closed(other)) > 1e-6 * closed(iters)
 
 
 def _dense(rowptr, col, val, n, m):

@@ -76,3 +76,47 @@ def test_noalloc_rejects_graphs_over_the_limit(S):
     st = L.saamg_mis2_aggregate_noalloc(MAX_NODES + 1, p, p, None, 0, p, p, C.byref(nagg), None)
     assert st == S.EINVAL and nagg.value == 0
     assert "262144" in S.last_error()
+
+
+def test_noalloc_calls_no_allocator(S):
+    """The point of the entry point: with an allocator hook that refuses every request and
+    counts the requests, the allocation-free call still succeeds and the hook is never
+    called, while the regular entry point asks the hook and fails with ENOMEM."""
+    L = S.lib()
+    rp, cc, ids = _graph(60_000, 8, 3)
+    # warm-up call: loads the library's device code and the scratch on this device
+    want = _run(S, L.saamg_mis2_aggregate_noalloc, rp, cc, ids, 0x51)
+    counts = {"alloc": 0, "free": 0}
+
+    def _alloc(nbytes, stream, ctx):
+        counts["alloc"] += 1
+        return None
+
+    def _free(ptr, stream, ctx):
+        counts["free"] += 1
+
+    hooks = (S.ALLOC_FN(_alloc), S.FREE_FN(_free))
+    saved = S._hooks
+    assert L.saamg_set_allocator(hooks[0], hooks[1], None) == S.OK
+    try:
+        got = _run(S, L.saamg_mis2_aggregate_noalloc, rp, cc, ids, 0x51)
+        assert counts == {"alloc": 0, "free": 0}
+        assert got[0] == want[0] and np.array_equal(got[1], want[1]) and np.array_equal(got[2], want[2])
+        # control: the regular entry point does allocate, so the refusing hook makes it fail
+        import torch
+        n = len(rp) - 1
+        rp_d, cc_d = torch.from_numpy(rp).cuda(), torch.from_numpy(cc).cuda()
+        root = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        agg = torch.zeros(n, dtype=torch.int32, device="cuda")
+        nagg = C.c_int(-1)
+        st = L.saamg_mis2_aggregate(n, C.c_void_p(rp_d.data_ptr()), C.c_void_p(cc_d.data_ptr()),
+                                    None, 0x51, C.c_void_p(root.data_ptr()),
+                                    C.c_void_p(agg.data_ptr()), C.byref(nagg),
+                                    C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert st == S.ENOMEM and counts["alloc"] > 0
+        torch.cuda.synchronize()
+    finally:
+        if saved is not None:
+            L.saamg_set_allocator(saved[0], saved[1], None)
+        else:
+            L.saamg_set_allocator(S.ALLOC_FN(), S.FREE_FN(), None)
