@@ -302,7 +302,7 @@ def run_ours(args):
     out.update(extra)
     if rank == 0:
         if not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(w, iters[-1])
+            out["cpu_baseline"] = cpu_baseline(args.n)
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -465,7 +465,7 @@ def mixed_quadratic_leg(S, torch, args):
     w = I.pipe_workload(args.n, I.QUADRATIC)
     dom, grid = S.make_domain(w.domain), S.make_grid(w.grid)
     rho = torch.from_numpy(I.gaussian_bunch(w.grid, w.centre, w.sigma, seed=77)).cuda()
-    out, ref = {}, None
+    out, ref, sols = {}, None, {}
     for name, prec in (("fp64", 0), ("fp32", 1), ("bf16", 2)):
         params = S.params_default(max_coarse=4096, precision=prec, beta_rule=1)
         torch.cuda.synchronize()
@@ -490,8 +490,17 @@ def mixed_quadratic_leg(S, torch, args):
         out[name] = {"full_pipeline_solves_per_s": 1.0 / full, "solve_only_solves_per_s": 1.0 / min(ts),
                      "iters": info["iters"], "relres_true": info["relres_true"],
                      "max_rel_diff_vs_fp64_gpu": err}
+        sols[name] = phi.cpu().numpy()
         h.free()
         op.free()
+    # error of every result against the FP64 oracle (multi-threaded build, same rhs): against
+    # its solution at the same tolerance and against its rtol-1e-12 solution
+    orc = oracle_solutions([{"workload": w, "seed": 77, "rtol": [1e-8, 1e-12], "beta_rule": 1}])
+    if orc is not None:
+        o8, o12 = orc["0_0"], orc["0_1"]
+        for name, x in sols.items():
+            out[name]["max_rel_err_vs_oracle"] = float(abs(x - o8).max() / abs(o8).max())
+            out[name]["max_rel_err_vs_oracle_rtol_1e-12"] = float(abs(x - o12).max() / abs(o12).max())
     return {"mixed_quadratic_c3": {"workload": f"{w.name}, quadratic extrapolation, rtol 1e-8", **out}}
 
 
@@ -677,7 +686,8 @@ def batched_leg(S, torch):
         op = S.build_operator(dom, grid, w.mode)
         h32 = S.setup(op, S.params_default(max_coarse=4096, precision=1, beta_rule=1))
         h64 = S.setup(op, S.params_default(max_coarse=4096))
-        r = [I.gaussian_bunch_torch(w.grid, w.centre, w.sigma, 1234 + 4 * k + j) for j in range(4)]
+        r = [torch.from_numpy(I.gaussian_bunch(w.grid, w.centre, w.sigma, 1234 + 4 * k + j)).cuda()
+             for j in range(4)]
         best, _ = S.autotune_cheb_degree(h32, r[0], 2, 4)
         degrees.append(best)
         hs32.append(h32)
@@ -705,6 +715,20 @@ def batched_leg(S, torch):
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
     err = max(float((a - b).abs().max() / b.abs().max()) for a, b in zip(X, X64))
+    # error against the FP64 oracle on a sample: every 8th instance, its 4 right-hand sides,
+    # the oracle hierarchy with the instance's autotuned degree
+    sample = list(range(0, len(inst), 8))
+    cases = [{"workload": inst[k], "seed": 1234 + 4 * k + j, "rtol": [1e-8], "beta_rule": 1,
+              "cheb_degree": degrees[k]} for k in sample for j in range(4)]
+    orc = oracle_solutions(cases)
+    err_orc = None
+    if orc is not None:
+        err_orc = {"fp32_batched": 0.0, "fp64_sequential": 0.0}
+        for c, (k, j) in enumerate((k, j) for k in sample for j in range(4)):
+            o = orc[f"{c}_0"]
+            for key, xs in (("fp32_batched", X), ("fp64_sequential", X64)):
+                x = xs[4 * k + j].cpu().numpy()
+                err_orc[key] = max(err_orc[key], float(abs(x - o).max() / abs(o).max()))
     out = {"instances": len(inst), "solves": len(R),
            "unknowns_total": int(sum(h.info()["n"][0] for h in hs32) * 4),
            "batched_fp32_solves_per_s": len(R) / t_batched,
@@ -713,6 +737,8 @@ def batched_leg(S, torch):
            "all_converged": all(i["converged"] == 1 for i in infos),
            "max_relres_true": max(i["relres_true"] for i in infos),
            "max_rel_diff_vs_fp64": err,
+           "max_rel_err_vs_oracle": err_orc,
+           "oracle_sample": f"instances {sample} x 4 rhs ({len(cases)} solves)",
            "autotuned_degrees": {d: degrees.count(d) for d in sorted(set(degrees))},
            "iters_fp32_mean": statistics.fmean(i["iters"] for i in infos),
            "iters_fp64_mean": statistics.fmean(its64)}
@@ -741,56 +767,79 @@ def serving_leg(S, torch, nreq):
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle (baseline / reference arm)
+# CPU oracle (baseline / reference arm, errors against the oracle).  The oracle runs in a
+# process of its own (python -m oracle.baseline): its OpenMP threads stay out of this one.
 # ---------------------------------------------------------------------------
-def oracle_sample(w, iters_needed, capped_iters=4):
-    """Oracle on the full workload: build + setup + `capped_iters` PCG iterations, the solve
-    time scaled to the iterations the solve needs.  Returns seconds per solve."""
-    from oracle import oracle as O
-    d, g = w.domain, w.grid
-    rho = I.gaussian_bunch(g, w.centre, w.sigma, seed=0)
-    t0 = time.perf_counter()
-    op = O.Operator(g.n, g.h, g.origin, d.a, d.b, d.taper, d.cx, d.cy, d.zbc, d.symmetrize, w.mode)
-    h = O.Hierarchy(op, max_coarse=4096)
-    t1 = time.perf_counter()
-    _, info = h.solve(rho, rtol=RTOL, maxit=capped_iters)
-    t2 = time.perf_counter()
-    per_iter = (t2 - t1) / max(1, info["iters"])
-    return (t1 - t0) + per_iter * iters_needed, (t1 - t0), per_iter
+def oracle_process(extra, timeout=900):
+    """Runs oracle/baseline.py with the given arguments; its JSON line, or None on failure."""
+    cmd = [sys.executable, "-m", "oracle.baseline"] + [str(a) for a in extra]
+    try:
+        p = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=timeout)
+    except subprocess.TimeoutExpired:
+        print("oracle process timed out: " + " ".join(cmd), file=sys.stderr)
+        return None
+    if p.returncode != 0:
+        print("oracle process failed: " + p.stderr[-2000:], file=sys.stderr)
+        return None
+    return json.loads(p.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline(w, iters_needed):
-    sec, setup_s, per_iter = oracle_sample(w, iters_needed)
-    return {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"single-thread FP64 oracle on {w.name}: build + setup + 4 PCG iterations, "
-                      f"solve scaled to {iters_needed} iterations (setup {setup_s:.1f} s, "
-                      f"{per_iter:.2f} s/iteration)"}
+def oracle_solutions(cases, timeout=900):
+    """The FP64 oracle's solutions of the cases (see oracle.baseline.solve_cases), computed
+    by its multi-threaded build on this host's cores; None if it is unavailable."""
+    import tempfile
+    import numpy as np
+    from oracle.baseline import workload_to_dict
+    with tempfile.TemporaryDirectory() as d:
+        spec = os.path.join(d, "cases.json")
+        out = os.path.join(d, "sol.npz")
+        json.dump([{**c, "workload": workload_to_dict(c["workload"])} for c in cases], open(spec, "w"))
+        if oracle_process(["--solve", spec, "--out", out, "--openmp"], timeout) is None:
+            return None
+        z = np.load(out)
+        return {k: z[k] for k in z.files}
+
+
+def cpu_baseline(n=256):
+    """One full oracle pass (build + setup + PCG to rtol 1e-8) on the workload, OpenMP build
+    on every core of the host, timed in its own process."""
+    r = oracle_process(["--n", n, "--mode", "linear", "--passes", 1, "--openmp"])
+    if r is None:
+        return {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+                "sample": "the oracle process failed"}
+    return {"value": r["solves_per_s"], "unit": UNIT, "cores": r["threads"], "kind": "oracle",
+            "sample": f"one full FP64 oracle pass on {r['workload']} (build {r['build_s']:.2f} s + "
+                      f"setup {r['setup_s']:.2f} s + PCG {r['solve_s']:.2f} s, {r['iters'][0]} "
+                      f"iterations to rtol 1e-8), OpenMP build of the oracle on {r['threads']} threads",
+            "build_s": r["build_s"], "setup_s": r["setup_s"], "solve_s": r["solve_s"]}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the paper ships no code; the oracle is the one
+    implementation of the method besides this library), OpenMP build on every host core,
+    each step one full pass of the workload: build + setup + PCG to rtol 1e-8, measured."""
     rank, _, world = dist_env()
     if rank != 0:
         return
+    r = oracle_process(["--n", args.n, "--mode", "linear", "--passes", args.steps,
+                        "--warmup", args.warmup, "--openmp"], timeout=3600)
+    if r is None:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle process failed"}), flush=True)
+        return
+    value = r["solves_per_s"]
     w = workload(args.n)
-    iters_needed = 21 if args.n == 256 else 20
-    for _ in range(args.warmup):
-        oracle_sample(w, iters_needed, capped_iters=1)
-    secs = []
-    for _ in range(args.steps):
-        s, _, _ = oracle_sample(w, iters_needed, capped_iters=2)
-        secs.append(s)
-    total = sum(secs)
-    value = args.steps / total
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["total_s"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded Gaussian bunch, no dataset)",
            "config": {"workload": f"{w.name}, linear extrapolation, Robin ends, rtol 1e-8, coarse <= 4096; "
                                   "step = build operator + AMG setup + PCG solve",
-                      "grid": list(w.grid.n), "parallelism": "single CPU thread"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": "each step: FP64 oracle build + setup + 2 PCG iterations on the full "
-                                      f"workload, solve scaled to {iters_needed} iterations"},
+                      "grid": list(w.grid.n), "parallelism": f"CPU, {r['threads']} OpenMP threads"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["threads"], "kind": "oracle",
+                            "sample": f"each step one full FP64 oracle pass (build + setup + PCG to rtol 1e-8), "
+                                      f"OpenMP build on {r['threads']} of {r['host_cores']} host cores"},
+           "phases_s": {k: r[k] for k in ("build_s", "setup_s", "solve_s")}, "iters": r["iters"],
+           "relres_true_max": r["relres_true_max"],
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

@@ -23,9 +23,16 @@ _p = C.c_void_p
 
 
 def lib():
+    """The sequential oracle (parity), or the OpenMP baseline build when the environment
+    variable SAAMG_ORACLE_OPENMP is 1 when the library is first loaded."""
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = None
+        if os.environ.get("SAAMG_ORACLE_OPENMP") == "1":
+            path = _build.build_omp()
+            if path is None:
+                raise RuntimeError("the OpenMP build of the oracle is not available")
+        path = path or _build.build()
         L = C.CDLL(path)
         L.orc_build_operator.restype = _p
         L.orc_build_operator.argtypes = [_i, _i, _i, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d,

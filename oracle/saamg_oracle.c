@@ -8,6 +8,13 @@
  * an unknown, the boundary fractions s, t) must be taken with the same IEEE
  * operations, in the same order, as any implementation compared against this one.
  *
+ * The same source also builds, with -fopenmp, a multi-threaded CPU baseline (never
+ * the parity reference): row loops and vector loops are split into static chunks
+ * (every row still summed in the order written here, so those results are bitwise
+ * those of the sequential build), and a dot product adds its chunk sums in thread
+ * order, which makes it reproducible for a given thread count but not bitwise equal
+ * to the sequential sum.  Without -fopenmp the pragmas are ignored.
+ *
  * Paper: Adelmann, Arbenz, Ineichen, "A Fast Parallel Poisson Solver on Irregular
  * Domains Applied to Beam Dynamic Simulations" (J. Comput. Phys.).
  *
@@ -19,6 +26,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------------- */
 /* Small CSR container                                                        */
@@ -49,6 +59,7 @@ static void csr_alloc(csr_t *a, int n, int m, long nnz) {
 
 /* y = A x, each row summed in column order. */
 static void csr_spmv(const csr_t *a, const double *x, double *y) {
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < a->n; ++i) {
     double acc = 0.0;
     for (int p = a->rowptr[i]; p < a->rowptr[i + 1]; ++p) acc += a->val[p] * x[a->col[p]];
@@ -57,9 +68,31 @@ static void csr_spmv(const csr_t *a, const double *x, double *y) {
 }
 
 static double dot(int n, const double *x, const double *y) {
+#ifdef _OPENMP
+  /* multi-threaded baseline build: static chunks summed in index order, then the chunk
+   * sums in thread order */
+  double part[1024];
+  int nt = omp_get_max_threads();
+  if (nt > 1024) nt = 1024;
+#pragma omp parallel num_threads(nt)
+  {
+    int t = omp_get_thread_num(), T = omp_get_num_threads();
+    long lo = (long)n * t / T, hi = (long)n * (t + 1) / T;
+    double a = 0.0;
+    for (long i = lo; i < hi; ++i) a += x[i] * y[i];
+    part[t] = a;
+#pragma omp barrier
+#pragma omp single
+    nt = T;
+  }
+  double acc = 0.0;
+  for (int t = 0; t < nt; ++t) acc += part[t];
+  return acc;
+#else
   double acc = 0.0;
   for (int i = 0; i < n; ++i) acc += x[i] * y[i];
   return acc;
+#endif
 }
 
 /* ------------------------------------------------------------------------- */
@@ -232,13 +265,15 @@ orc_op *orc_build_operator(int nx, int ny, int nz, double hx, double hy, double 
 
   long nbox = (long)nx * ny * nz;
   op->row_of_node = (int *)malloc((size_t)nbox * sizeof(int));
-  int n = 0;
+  /* inside test of every node, then rows numbered in ascending box index */
+#pragma omp parallel for schedule(static)
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
-      for (int i = 0; i < nx; ++i) {
-        int in = orc_node_inside(op, i, j, k);
-        op->row_of_node[box_index(op, i, j, k)] = in ? n++ : -1;
-      }
+      for (int i = 0; i < nx; ++i)
+        op->row_of_node[box_index(op, i, j, k)] = orc_node_inside(op, i, j, k) ? 0 : -1;
+  int n = 0;
+  for (long q = 0; q < nbox; ++q)
+    if (op->row_of_node[q] >= 0) op->row_of_node[q] = n++;
   op->n = n;
   op->node_of_row = (int *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int));
   for (long q = 0; q < nbox; ++q)
@@ -252,8 +287,20 @@ orc_op *orc_build_operator(int nx, int ny, int nz, double hx, double hy, double 
   const double cdir[3] = {1.0 / (hx * hx), 1.0 / (hy * hy), 1.0 / (hz * hz)};
   /* Robin distance d: half the extent of Omega in z (Sec. 2, after Eq. (5)). */
   const double dist = 0.5 * ((double)(nz - 1) * hz);
-  long p = 0;
+  /* row r takes the diagonal and one entry per neighbour that is an unknown */
+#pragma omp parallel for schedule(static)
   for (int r = 0; r < n; ++r) {
+    int q = op->node_of_row[r];
+    int i = q % nx, j = (q / nx) % ny, k = q / (nx * ny);
+    op->A.rowptr[r + 1] = 1 + is_unknown(op, i - 1, j, k) + is_unknown(op, i + 1, j, k) +
+                          is_unknown(op, i, j - 1, k) + is_unknown(op, i, j + 1, k) +
+                          is_unknown(op, i, j, k - 1) + is_unknown(op, i, j, k + 1);
+  }
+  op->A.rowptr[0] = 0;
+  for (int r = 0; r < n; ++r) op->A.rowptr[r + 1] += op->A.rowptr[r];
+#pragma omp parallel for schedule(static)
+  for (int r = 0; r < n; ++r) {
+    long p = op->A.rowptr[r];
     int q = op->node_of_row[r];
     int i = q % nx, j = (q / nx) % ny, k = q / (nx * ny);
     int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k},
@@ -315,7 +362,6 @@ orc_op *orc_build_operator(int nx, int ny, int nz, double hx, double hy, double 
     op->bfac[r] = bf;
     /* CSR row in ascending column order: -z, -y, -x, self, +x, +y, +z */
     const int order[7] = {4, 2, 0, -1, 1, 3, 5};
-    op->A.rowptr[r] = (int)p;
     for (int o = 0; o < 7; ++o) {
       int d6 = order[o];
       if (d6 < 0) {
@@ -331,13 +377,14 @@ orc_op *orc_build_operator(int nx, int ny, int nz, double hx, double hy, double 
     }
     op->scale[r] = 1.0 / sqrt(diag);
   }
-  op->A.rowptr[n] = (int)p;
+  long p = op->A.rowptr[n];
   op->A.nnz = p;
 
   /* Symmetric diagonal scaling (Sec. 2, last paragraph): ahat_ij = a_ij (s_i s_j). */
   csr_alloc(&op->Ahat, n, n, p);
   memcpy(op->Ahat.rowptr, op->A.rowptr, (size_t)(n + 1) * sizeof(int));
   memcpy(op->Ahat.col, op->A.col, (size_t)(p > 0 ? p : 1) * sizeof(int));
+#pragma omp parallel for schedule(static)
   for (int r = 0; r < n; ++r)
     for (int e = op->A.rowptr[r]; e < op->A.rowptr[r + 1]; ++e)
       op->Ahat.val[e] = op->A.val[e] * (op->scale[r] * op->scale[op->A.col[e]]);
@@ -529,6 +576,44 @@ static int cmp_key_desc(const void *pa, const void *pb) {
   return (a < b) - (a > b);
 }
 
+/* Nodes by decreasing key.  The keys are distinct, so every correct sort gives the same
+ * order; the multi-threaded baseline build sorts static chunks in parallel and merges them
+ * pairwise. */
+static void sort_keys_desc(keyrow_t *a, int n) {
+#ifdef _OPENMP
+  int T = omp_get_max_threads();
+  if (T > 64) T = 64;
+  if (T > 1 && n >= 65536) {
+    long b[65];
+    for (int t = 0; t <= T; ++t) b[t] = (long)n * t / T;
+#pragma omp parallel for num_threads(T) schedule(static, 1)
+    for (int t = 0; t < T; ++t) qsort(a + b[t], (size_t)(b[t + 1] - b[t]), sizeof(keyrow_t), cmp_key_desc);
+    keyrow_t *src = a, *dst = (keyrow_t *)malloc((size_t)n * sizeof(keyrow_t));
+    for (int w = 1; w < T; w *= 2) {
+#pragma omp parallel for schedule(static, 1)
+      for (int t = 0; t < T; t += 2 * w) {
+        long lo = b[t], mid = b[t + w < T ? t + w : T], hi = b[t + 2 * w < T ? t + 2 * w : T];
+        long i = lo, j = mid, o = lo;
+        while (i < mid && j < hi) dst[o++] = src[i].key > src[j].key ? src[i++] : src[j++];
+        while (i < mid) dst[o++] = src[i++];
+        while (j < hi) dst[o++] = src[j++];
+      }
+      keyrow_t *tmp = src;
+      src = dst;
+      dst = tmp;
+    }
+    if (src != a) {
+      memcpy(a, src, (size_t)n * sizeof(keyrow_t));
+      free(src);
+    } else {
+      free(dst);
+    }
+    return;
+  }
+#endif
+  qsort(a, (size_t)n, sizeof(keyrow_t), cmp_key_desc);
+}
+
 /* READING: the paper aggregates with per-processor 3^d cubes ("uncoupled", Sec. 3.2,
  * Table 1).  Here aggregates are seeded by a distance-2 maximal independent set of
  * the adjacency graph G_l of A_l (the graph named in Sec. 3.2), computed by the
@@ -543,7 +628,7 @@ void orc_mis2(int n, const int *rowptr, const int *col, const unsigned int *ids,
     order[i].row = i;
     is_root[i] = 0;
   }
-  qsort(order, (size_t)n, sizeof(keyrow_t), cmp_key_desc);
+  sort_keys_desc(order, n);
   for (int o = 0; o < n; ++o) {
     int v = order[o].row;
     if (blocked[v]) continue;
@@ -624,6 +709,7 @@ double orc_power_lambda(int n, const int *rowptr, const int *col, const double *
   }
   double lam = 0.0;
   for (int it = 0; it <= iters; ++it) {
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) {
       double acc = 0.0;
       for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) acc += val[p] * v[col[p]];
@@ -632,6 +718,7 @@ double orc_power_lambda(int n, const int *rowptr, const int *col, const double *
     double nrm = sqrt(dot(n, w, w));
     lam = nrm;
     if (it == iters) break;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) v[i] = w[i] / nrm;
   }
   free(v);
@@ -662,20 +749,25 @@ void orc_cheb_smooth(int n, const int *rowptr, const int *col, const double *val
   csr_t a = {n, n, rowptr[n], (int *)rowptr, (int *)col, (double *)val};
   for (int step = 0; step < degree; ++step) {
     if (step == 0 && x_is_zero) {
+#pragma omp parallel for schedule(static)
       for (int i = 0; i < n; ++i) r[i] = b[i];
     } else {
       csr_spmv(&a, x, r);
+#pragma omp parallel for schedule(static)
       for (int i = 0; i < n; ++i) r[i] = b[i] - r[i];
     }
     if (step == 0) {
       double c2 = 1.0 / theta;
+#pragma omp parallel for schedule(static)
       for (int i = 0; i < n; ++i) d[i] = c2 * (invd[i] * r[i]);
     } else {
       double rho = 1.0 / (2.0 * sigma - rho_prev);
       double c1 = rho * rho_prev, c2 = (2.0 * rho) / delta;
+#pragma omp parallel for schedule(static)
       for (int i = 0; i < n; ++i) d[i] = c1 * d[i] + c2 * (invd[i] * r[i]);
       rho_prev = rho;
     }
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) x[i] = x[i] + d[i];
   }
   free(r);
@@ -723,6 +815,7 @@ static int dense_lu_factor(dense_lu_t *f, int n, const double *a) {
       f->perm[p] = tp;
     }
     double piv = m[(size_t)k * n + k];
+#pragma omp parallel for schedule(static) if (n - k > 256)
     for (int i = k + 1; i < n; ++i) {
       double l = m[(size_t)i * n + k] / piv;
       m[(size_t)i * n + k] = l;
@@ -770,55 +863,75 @@ static int cmp_int(const void *pa, const void *pb) {
 
 /* C = X Y, row by row (Gustavson).  Each entry is summed in the order the products
  * arise: X's row in column order, then Y's row in column order.  The pattern is
- * structural (an entry whose value cancels to zero is kept). */
+ * structural (an entry whose value cancels to zero is kept).  A first pass counts each
+ * row's distinct columns, a second one forms the rows in place. */
 static void csr_matmul(const csr_t *x, const csr_t *y, csr_t *c) {
   int n = x->n, m = y->m;
-  int *mark = (int *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int));
-  double *acc = (double *)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
-  int *cols = (int *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int));
-  for (int j = 0; j < m; ++j) mark[j] = -1;
-  long cap = x->nnz + 16, nnz = 0;
-  int *rowptr = (int *)malloc((size_t)(n + 1) * sizeof(int));
-  int *ccol = (int *)malloc((size_t)cap * sizeof(int));
-  double *cval = (double *)malloc((size_t)cap * sizeof(double));
-  for (int i = 0; i < n; ++i) {
-    int cnt = 0;
-    for (int p = x->rowptr[i]; p < x->rowptr[i + 1]; ++p) {
-      int k = x->col[p];
-      double xv = x->val[p];
-      for (int q = y->rowptr[k]; q < y->rowptr[k + 1]; ++q) {
-        int j = y->col[q];
-        if (mark[j] != i) {
-          mark[j] = i;
-          acc[j] = 0.0;
-          cols[cnt++] = j;
+  int *rowptr = (int *)calloc((size_t)n + 1, sizeof(int));
+#pragma omp parallel
+  {
+    int *mark = (int *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int));
+    for (int j = 0; j < m; ++j) mark[j] = -1;
+#pragma omp for schedule(static)
+    for (int i = 0; i < n; ++i) {
+      int cnt = 0;
+      for (int p = x->rowptr[i]; p < x->rowptr[i + 1]; ++p) {
+        int k = x->col[p];
+        for (int q = y->rowptr[k]; q < y->rowptr[k + 1]; ++q) {
+          int j = y->col[q];
+          if (mark[j] != i) {
+            mark[j] = i;
+            ++cnt;
+          }
         }
-        acc[j] += xv * y->val[q];
+      }
+      rowptr[i + 1] = cnt;
+    }
+    free(mark);
+  }
+  for (int i = 0; i < n; ++i) rowptr[i + 1] += rowptr[i];
+  long nnz = rowptr[n];
+  int *ccol = (int *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int));
+  double *cval = (double *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
+#pragma omp parallel
+  {
+    int *mark = (int *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int));
+    double *acc = (double *)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
+    int *cols = (int *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int));
+    for (int j = 0; j < m; ++j) mark[j] = -1;
+#pragma omp for schedule(static)
+    for (int i = 0; i < n; ++i) {
+      int cnt = 0;
+      for (int p = x->rowptr[i]; p < x->rowptr[i + 1]; ++p) {
+        int k = x->col[p];
+        double xv = x->val[p];
+        for (int q = y->rowptr[k]; q < y->rowptr[k + 1]; ++q) {
+          int j = y->col[q];
+          if (mark[j] != i) {
+            mark[j] = i;
+            acc[j] = 0.0;
+            cols[cnt++] = j;
+          }
+          acc[j] += xv * y->val[q];
+        }
+      }
+      qsort(cols, (size_t)cnt, sizeof(int), cmp_int);
+      long o = rowptr[i];
+      for (int t = 0; t < cnt; ++t) {
+        ccol[o + t] = cols[t];
+        cval[o + t] = acc[cols[t]];
       }
     }
-    qsort(cols, (size_t)cnt, sizeof(int), cmp_int);
-    if (nnz + cnt > cap) {
-      while (nnz + cnt > cap) cap *= 2;
-      ccol = (int *)realloc(ccol, (size_t)cap * sizeof(int));
-      cval = (double *)realloc(cval, (size_t)cap * sizeof(double));
-    }
-    rowptr[i] = (int)nnz;
-    for (int t = 0; t < cnt; ++t) {
-      ccol[nnz] = cols[t];
-      cval[nnz] = acc[cols[t]];
-      ++nnz;
-    }
+    free(mark);
+    free(acc);
+    free(cols);
   }
-  rowptr[n] = (int)nnz;
   c->n = n;
   c->m = m;
   c->nnz = nnz;
   c->rowptr = rowptr;
   c->col = ccol;
   c->val = cval;
-  free(mark);
-  free(acc);
-  free(cols);
 }
 
 /* Explicit transpose; each row of the result lists its columns in ascending order. */
@@ -977,6 +1090,7 @@ struct orc_hier {
 
 static double *diag_inverse(const csr_t *a) {
   double *invd = (double *)malloc((size_t)(a->n > 0 ? a->n : 1) * sizeof(double));
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < a->n; ++i) {
     double d = 0.0;
     for (int p = a->rowptr[i]; p < a->rowptr[i + 1]; ++p)
@@ -995,50 +1109,72 @@ static void csr_copy(const csr_t *src, csr_t *dst) {
 
 /* Smoothed prolongator P = (I - omega D^-1 A) T = T - omega D^-1 (A T), with
  * T(i, agg(i)) = 1 the tentative prolongator (Sec. 3.2) and omega = 4 / (3 lambda).
- * (A T)_iJ sums a_ij over the row in column order for all j with agg(j) = J. */
+ * (A T)_iJ sums a_ij over the row in column order for all j with agg(j) = J.  A first
+ * pass counts each row's distinct aggregates, a second one forms the rows in place. */
 static void smoothed_prolongator(const csr_t *a, const double *invd, const int *agg,
                                  int nagg, double omega, csr_t *p) {
   int n = a->n;
-  long cap = a->nnz + 16, nnz = 0;
-  int *rowptr = (int *)malloc((size_t)(n + 1) * sizeof(int));
-  int *pcol = (int *)malloc((size_t)cap * sizeof(int));
-  double *pval = (double *)malloc((size_t)cap * sizeof(double));
-  int *mark = (int *)malloc((size_t)(nagg > 0 ? nagg : 1) * sizeof(int));
-  double *acc = (double *)calloc((size_t)(nagg > 0 ? nagg : 1), sizeof(double));
-  int *cols = (int *)malloc((size_t)(nagg > 0 ? nagg : 1) * sizeof(int));
-  for (int J = 0; J < nagg; ++J) mark[J] = -1;
-  for (int i = 0; i < n; ++i) {
-    int cnt = 0;
-    for (int q = a->rowptr[i]; q < a->rowptr[i + 1]; ++q) {
-      int J = agg[a->col[q]];
-      if (mark[J] != i) {
-        mark[J] = i;
-        acc[J] = 0.0;
-        cols[cnt++] = J;
+  int *rowptr = (int *)calloc((size_t)n + 1, sizeof(int));
+#pragma omp parallel
+  {
+    int *mark = (int *)malloc((size_t)(nagg > 0 ? nagg : 1) * sizeof(int));
+    for (int J = 0; J < nagg; ++J) mark[J] = -1;
+#pragma omp for schedule(static)
+    for (int i = 0; i < n; ++i) {
+      int cnt = 0;
+      for (int q = a->rowptr[i]; q < a->rowptr[i + 1]; ++q) {
+        int J = agg[a->col[q]];
+        if (mark[J] != i) {
+          mark[J] = i;
+          ++cnt;
+        }
       }
-      acc[J] += a->val[q];
+      rowptr[i + 1] = cnt;
     }
-    qsort(cols, (size_t)cnt, sizeof(int), cmp_int);
-    double w = omega * invd[i];
-    rowptr[i] = (int)nnz;
-    for (int t = 0; t < cnt; ++t) {
-      int J = cols[t];
-      double tij = (J == agg[i]) ? 1.0 : 0.0;
-      pcol[nnz] = J;
-      pval[nnz] = tij - w * acc[J];
-      ++nnz;
-    }
+    free(mark);
   }
-  rowptr[n] = (int)nnz;
+  for (int i = 0; i < n; ++i) rowptr[i + 1] += rowptr[i];
+  long nnz = rowptr[n];
+  int *pcol = (int *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int));
+  double *pval = (double *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
+#pragma omp parallel
+  {
+    int *mark = (int *)malloc((size_t)(nagg > 0 ? nagg : 1) * sizeof(int));
+    double *acc = (double *)calloc((size_t)(nagg > 0 ? nagg : 1), sizeof(double));
+    int *cols = (int *)malloc((size_t)(nagg > 0 ? nagg : 1) * sizeof(int));
+    for (int J = 0; J < nagg; ++J) mark[J] = -1;
+#pragma omp for schedule(static)
+    for (int i = 0; i < n; ++i) {
+      int cnt = 0;
+      for (int q = a->rowptr[i]; q < a->rowptr[i + 1]; ++q) {
+        int J = agg[a->col[q]];
+        if (mark[J] != i) {
+          mark[J] = i;
+          acc[J] = 0.0;
+          cols[cnt++] = J;
+        }
+        acc[J] += a->val[q];
+      }
+      qsort(cols, (size_t)cnt, sizeof(int), cmp_int);
+      double w = omega * invd[i];
+      long o = rowptr[i];
+      for (int t = 0; t < cnt; ++t) {
+        int J = cols[t];
+        double tij = (J == agg[i]) ? 1.0 : 0.0;
+        pcol[o + t] = J;
+        pval[o + t] = tij - w * acc[J];
+      }
+    }
+    free(mark);
+    free(acc);
+    free(cols);
+  }
   p->n = n;
   p->m = nagg;
   p->nnz = nnz;
   p->rowptr = rowptr;
   p->col = pcol;
   p->val = pval;
-  free(mark);
-  free(acc);
-  free(cols);
 }
 
 orc_hier *orc_setup(const orc_op *op, int cheb_degree, double cheb_ratio,
@@ -1232,12 +1368,14 @@ static void mg_solve(const orc_hier *h, int l, const double *b, double *x) {
     return;
   }
   /* presmoothing from x = 0 */
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) x[i] = 0.0;
   orc_cheb_smooth(n, lv->A.rowptr, lv->A.col, lv->A.val, lv->invd, lv->lambda, h->ratio,
                   h->safety, h->degree, b, x, 1);
   /* residual r = b - A x */
   double *r = h->wr[l];
   csr_spmv(&lv->A, x, r);
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) r[i] = b[i] - r[i];
   /* restriction b_{l+1} = R r ; v_{l+1} = 0 ; recurse */
   double *bc = h->wb[l + 1], *vc = h->wx[l + 1];
@@ -1245,6 +1383,7 @@ static void mg_solve(const orc_hier *h, int l, const double *b, double *x) {
   mg_solve(h, l + 1, bc, vc);
   /* coarse-grid correction x += P v */
   csr_spmv(&lv->P, vc, r);
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) x[i] = x[i] + r[i];
   /* postsmoothing: same polynomial */
   orc_cheb_smooth(n, lv->A.rowptr, lv->A.col, lv->A.val, lv->invd, lv->lambda, h->ratio,
@@ -1278,6 +1417,7 @@ int orc_pcg(const orc_hier *h, const double *bhat, double *xhat, double rtol, in
   double *p = (double *)malloc((size_t)n * sizeof(double));
   double *q = (double *)malloc((size_t)n * sizeof(double));
   csr_spmv(a, xhat, q);
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) r[i] = bhat[i] - q[i];
   double rnorm = sqrt(dot(n, r, r));
   int rc = 1;
@@ -1285,6 +1425,7 @@ int orc_pcg(const orc_hier *h, const double *bhat, double *xhat, double rtol, in
     rc = 0;
   } else {
     orc_vcycle(h, r, z);
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) p[i] = z[i];
     double rz = dot(n, r, z);
     for (int it = 1; it <= maxit; ++it) {
@@ -1296,6 +1437,7 @@ int orc_pcg(const orc_hier *h, const double *bhat, double *xhat, double rtol, in
         break;
       }
       double alpha = rz / pq;
+#pragma omp parallel for schedule(static)
       for (int i = 0; i < n; ++i) {
         xhat[i] = xhat[i] + alpha * p[i];
         r[i] = r[i] - alpha * q[i];
@@ -1320,6 +1462,7 @@ int orc_pcg(const orc_hier *h, const double *bhat, double *xhat, double rtol, in
       } else {
         beta = rz_new / rz;
       }
+#pragma omp parallel for schedule(static)
       for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
       rz = rz_new;
     }

@@ -20,7 +20,7 @@ def test_fp64_stencil_is_reported_against_the_fp64_issue_peak(bench):
     r = bench.roofline("stencil_smooth", (1.0, 10, 10_000_000), 0, n=128)
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert r["achieved"] == pytest.approx(0.19)
-    assert r["frac"] == pytest.approx(0.19 / bench.FP64_PEAK_TFLOPS)
+    assert r["frac"] == pytest.approx(0.19 / bench.FP64_PEAK["tflops"])
     assert r["algorithmic_bytes_per_launch"] == pytest.approx(40e6)
     assert r["traffic"] is None  # no capture for this size
 

@@ -87,6 +87,40 @@ def test_vcycle_and_solve_256_match_oracle(S, world256):
     assert np.linalg.norm(res) <= 1.01e-8 * np.linalg.norm(bh)
 
 
+def test_quadratic_256_fp64_fp32_bf16_match_oracle(S):
+    """The mixed-precision configuration at full size: the 256^3 elliptic pipe in quadratic
+    mode (the nonsymmetric rows of Eqs. (9)-(10)).  FP64 V-cycle within 1e-10 of the oracle with
+    iterations +-1; FP32 and BF16 V-cycles (FP64 outer CG) at the recomputed residual target
+    and within 10x the oracle's own rtol-1e-8 error against its rtol-1e-12 solution."""
+    import torch
+    w = I.pipe_workload(256, I.QUADRATIC)
+    o = oracle_operator(w)
+    oh = oracle_hierarchy(o, max_coarse=4096)
+    rho = I.gaussian_bunch(w.grid, w.centre, w.sigma, seed=77)
+    g = S.build_operator(S.make_domain(w.domain), S.make_grid(w.grid), w.mode)
+    assert g.size() == (o.n, o.nnz)
+    rho_d = torch.from_numpy(rho).cuda()
+    exact, _ = oh.solve(rho, rtol=1e-12)
+    scale = np.max(np.abs(exact))
+    for prec, beta in ((0, 0), (1, 1), (2, 1)):
+        h = S.setup(g, S.params_default(max_coarse=4096, precision=prec, beta_rule=beta))
+        assert h.info()["n"] == [oh.n(l) for l in range(oh.levels)]
+        phi = torch.zeros(w.grid.nbox, dtype=torch.float64, device="cuda")
+        info = S.solve(h, rho_d, phi, rtol=1e-8)
+        got = phi.cpu().numpy()
+        h.free()
+        ref, oinfo = oh.solve(rho, rtol=1e-8, beta_rule=beta)
+        assert info["converged"] == 1 and info["relres_true"] <= 1.5e-8, (prec, info)
+        if prec == 0:
+            assert abs(info["iters"] - oinfo["iters"]) <= 1, (info, oinfo)
+            assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
+        else:
+            assert info["iters"] <= oinfo["iters"] + (2 if prec == 1 else 4), (prec, info, oinfo)
+            err = np.max(np.abs(got - exact)) / scale
+            err_ref = np.max(np.abs(ref - exact)) / scale
+            assert err <= max(10 * err_ref, 1e-7), (prec, err, err_ref)
+
+
 def test_solve_512_properties(S):
     """5.7e7 unknowns: convergence, the recomputed residual, the FP32 V-cycle reaching the same
     accuracy, and the iteration count staying in the grid-independent range."""
