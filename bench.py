@@ -696,7 +696,19 @@ def batched_leg(S, torch):
     H = [h for h in hs32 for _ in range(4)]
     R = [r for rr in rhos for r in rr]
     X = [torch.zeros_like(r) for r in R]
-    S.solve_batched(H, R, X)  # warm-up (captures the graphs)
+    # the first call runs the merged form (one launch per operation across all solves), the
+    # second the per-solve form (one device-loop graph per solve, concurrent branches); both
+    # give the same bits, and later calls take the faster
+    forms = {}
+    for _ in range(2):
+        for x in X:
+            x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.solve_batched(H, R, X)
+        torch.cuda.synchronize()
+        forms[S.batch_last()["form"]] = len(R) / (time.perf_counter() - t0)
+    first = S.batch_last()
     for x in X:
         x.zero_()
     torch.cuda.synchronize()
@@ -704,6 +716,18 @@ def batched_leg(S, torch):
     infos = S.solve_batched(H, R, X)
     torch.cuda.synchronize()
     t_batched = time.perf_counter() - t0
+    chosen = S.batch_last()["form"]
+    # FP32 one solve at a time (the same hierarchies and degrees)
+    X1 = [torch.zeros_like(r) for r in R]
+    S.solve(H[0], R[0], X1[0])
+    X1[0].zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for h, r, x in zip(H, R, X1):
+        S.solve(h, r, x)
+    torch.cuda.synchronize()
+    t_seq32 = time.perf_counter() - t0
+    same32 = all(bool(torch.equal(a, b)) for a, b in zip(X, X1))
     # FP64, one solve at a time through the synchronous call
     X64 = [torch.zeros_like(r) for r in R]
     H64 = [h for h in hs64 for _ in range(4)]
@@ -732,6 +756,11 @@ def batched_leg(S, torch):
     out = {"instances": len(inst), "solves": len(R),
            "unknowns_total": int(sum(h.info()["n"][0] for h in hs32) * 4),
            "batched_fp32_solves_per_s": len(R) / t_batched,
+           "batched_form": chosen,
+           "first_run_solves_per_s": {"merged": len(R) / (1e-3 * first["ms_merged"]) if first["ms_merged"] else None,
+                                      "per_solve": len(R) / (1e-3 * first["ms_per_solve"]) if first["ms_per_solve"] else None},
+           "sequential_fp32_solves_per_s": len(R) / t_seq32,
+           "batched_equals_sequential_fp32_bitwise": same32,
            "sequential_fp64_solves_per_s": len(R) / t_seq,
            "speedup": t_seq / t_batched,
            "all_converged": all(i["converged"] == 1 for i in infos),
@@ -744,7 +773,48 @@ def batched_leg(S, torch):
            "iters_fp64_mean": statistics.fmean(its64)}
     for h in hs32 + hs64:
         h.free()
+    S.release_batch_cache()
+    out["small_grids"] = batched_small_leg(S, torch)
     return out
+
+
+def batched_small_leg(S, torch, count=64, lo=32, hi=48):
+    """The same kind of batch on small grids (n_i ~ U{32..48}, 4 rhs each, FP32 V-cycle): the
+    regime where a per-solve launch is mostly latency, so the merged form (one launch per
+    operation across all solves) wins.  Both forms and one solve at a time."""
+    inst = I.batched_instances(count=count, seed=5, lo=lo, hi=hi)
+    H, R = [], []
+    for k, w in enumerate(inst):
+        op = S.build_operator(S.make_domain(w.domain), S.make_grid(w.grid), w.mode)
+        h = S.setup(op, S.params_default(max_coarse=300, precision=1, beta_rule=1))
+        h._op = op
+        for j in range(4):
+            H.append(h)
+            R.append(torch.from_numpy(I.gaussian_bunch(w.grid, w.centre, w.sigma, 7 + 4 * k + j)).cuda())
+    X = [torch.zeros_like(r) for r in R]
+    rates = {}
+    for _ in range(4):
+        for x in X:
+            x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.solve_batched(H, R, X)
+        torch.cuda.synchronize()
+        form = S.batch_last()["form"]
+        rates[form] = max(rates.get(form, 0.0), len(R) / (time.perf_counter() - t0))
+    X1 = [torch.zeros_like(r) for r in R]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for h, r, x in zip(H, R, X1):
+        S.solve(h, r, x)
+    torch.cuda.synchronize()
+    seq = len(R) / (time.perf_counter() - t0)
+    S.release_batch_cache()
+    return {"instances": count, "solves": len(R), "grid_range": [lo, hi],
+            "unknowns_total": int(sum(h.info()["n"][0] for h in H)),
+            "merged_solves_per_s": rates.get("merged"), "per_solve_solves_per_s": rates.get("per-solve"),
+            "sequential_fp32_solves_per_s": seq,
+            "batched_equals_sequential_bitwise": all(bool(torch.equal(a, b)) for a, b in zip(X, X1))}
 
 
 def serving_leg(S, torch, nreq):

@@ -251,14 +251,36 @@ saamg_status saamg_solve_test(const saamg_hierarchy *h);
 saamg_status saamg_solve_wait(saamg_hierarchy *h, saamg_solve_info *info);
 
 /* Many solves in one call (batched serving of many geometries): count right-hand sides
- * rho[j] -> phi[j] (device box arrays) on hierarchies hs[j] of any sizes.  Solves of the same hierarchy
- * run in the given order on one stream; different hierarchies run concurrently on a pool
- * of up to 32 library streams, each solve being one device-loop graph launch.  Joins back
- * into `stream` and returns when all are done; infos[j] per solve (solve_ms = the wall
- * time of the whole batch).  Returns the worst status. */
+ * rho[j] -> phi[j] (device box arrays; phi[j] holds the initial guess) on hierarchies hs[j]
+ * of any sizes, precisions and Chebyshev degrees; several may share a hierarchy.  The batch
+ * runs as ONE CUDA graph launch, in one of two forms that give the same bits as saamg_solve
+ * for every solve:
+ *   merged: every solve gets its own work vectors, and each operation of a PCG iteration
+ *     (every smoothing step, residual, transfer and coarse solve of the V-cycles, the CG
+ *     products, dot products and updates) is one kernel launch over all solves that are still
+ *     iterating, the solves split into up to 8 sub-batches that run side by side;
+ *   per-solve: one device-loop graph per solve (as saamg_solve_async), solves of one
+ *     hierarchy in order on one of up to 32 concurrent branches.
+ * The graph is built on the first call for a set of (hierarchy, rho, phi, rtol) and kept
+ * for later calls with the same set (two sets are kept; saamg_release_batch_cache frees
+ * them).  The first call with a set runs the merged form, the second the per-solve form, and
+ * later calls the one whose first run was faster (saamg_batch_last reports both times).
+ * Batches with a single solve, a hierarchy without unknowns or a Gauss-Seidel coarse solver
+ * always take the per-solve form.  Joins back into `stream` and returns when all are done;
+ * infos[j] per solve (solve_ms = the wall time of the whole batch).  Returns the worst
+ * status. */
 saamg_status saamg_solve_batched(saamg_hierarchy *const *hs, const double *const *rho,
                                  double *const *phi, int count, double rtol, void *stream,
                                  saamg_solve_info *infos);
+
+/* The form the most recent saamg_solve_batched call ran (merged: 1 merged, 0 per-solve) and
+ * the wall times in ms of the first run of each form with that set of solves (-1: not run). */
+saamg_status saamg_batch_last(int *merged, double *ms_merged, double *ms_graphs);
+
+/* Frees the graphs and work vectors that saamg_solve_batched keeps for repeated batches
+ * (they are otherwise held until they are replaced, and never freed at process exit, when
+ * the allocator hook may no longer be callable). */
+saamg_status saamg_release_batch_cache(void);
 
 /* Changes the Chebyshev degree of every smoothed level (coefficients from the stored
  * lambda_hat; the hierarchy is otherwise unchanged).  EINVAL outside 1..16. */

@@ -17,7 +17,7 @@ OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsaamg.so")
 
 UNITS = ["capi", "geometry", "stencil", "csr", "sell", "aggregate", "galerkin", "coarse", "pcg",
-         "pic", "scan", "ktimer"]
+         "pic", "scan", "ktimer", "batch"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
           "-I" + INCLUDE, "-I" + CSRC]

@@ -14,6 +14,8 @@
 #include <vector>
 
 #include "aggregate.cuh"
+#include "batch.cuh"
+#include "hier.cuh"
 #include "coarse.cuh"
 #include "csr.cuh"
 #include "galerkin.cuh"
@@ -212,9 +214,6 @@ struct PhaseTimer {
 // ---------------------------------------------------------------------------
 // hierarchy
 // ---------------------------------------------------------------------------
-struct ChebCoef {
-  std::vector<double> c1, c2;
-};
 
 // Chebyshev steps on [hi/ratio, hi], hi = safety * lambda (Saad, Alg. 12.1 on D^-1 A):
 // step 0: c1 = 0, c2 = 1/theta; step k: rho_k = 1/(2 sigma - rho_{k-1}),
@@ -241,75 +240,9 @@ static ChebCoef cheb_coefficients(double lambda, double ratio, double safety, in
   return c;
 }
 
-struct Level {
-  int n = 0;
-  long long nnz = 0;
-  double avg = 0;
-  DevCsr A;                     // levels >= 1 (level 0 uses the operator's CSR / stencil)
-  Buf<double> invd;
-  Buf<float> invd32;
-  Buf<int> agg;
-  Buf<unsigned char> root;
-  Buf<unsigned> ids;            // lattice ids of the nodes (cube aggregation, levels >= 1)
-  int dims[3] = {0, 0, 0};      // lattice of the ids (cube aggregation)
-  DevCsr P, R;                  // to the next level
-  double lambda = 0, omega = 0;
-  ChebCoef cheb;
-  // V-cycle work vectors (FP64 and FP32 sets; only the one for the precision is allocated)
-  Buf<double> x0, x1, b, d, r;
-  Buf<float> fx0, fx1, fb, fd, fr;
-  // SELL-32 copy of A used by the V-cycle smoother (levels 1 .. L-2), with the values of
-  // the working precision (FP64, FP32 or BF16); P and R stay CSR (a warp-wide row group
-  // gathers neighbouring columns, which one-thread-per-row slices would scatter)
-  DevSell As;
-  Buf<float> P32, R32;          // FP32 values of P and R (mixed precision)
-};
-
 }  // namespace saamg
 
 using namespace saamg;
-
-static const uint32_t kOpMagic = 0x5341504fu;    // "SAPO"
-static const uint32_t kHierMagic = 0x53414852u;  // "SAHR"
-
-struct saamg_operator {
-  uint32_t magic = kOpMagic;
-  OperatorData d;
-  cudaStream_t stream = nullptr;
-};
-
-struct saamg_hierarchy {
-  uint32_t magic = kHierMagic;
-  const saamg_operator* op = nullptr;
-  saamg_params prm{};
-  std::vector<std::unique_ptr<Level>> lev;
-  CoarseSolver coarse;
-  double setup_ms = 0;
-  // PCG state
-  Buf<double> bhat, xhat, r, z, p, q;
-  Buf<float> z32, r32;
-  Buf<double> part0, part1, part2;
-  Buf<PcgCtl> ctl;
-  HostScratch host;
-  Buf<double> scratch;
-  long long bytes = 0;
-  // identity for cached batch graphs: a new value at creation and whenever the V-cycle
-  // changes (a cached graph never outlives the kernels and pointers it was captured with)
-  unsigned long long version = 0;
-  long long gk_fixed = 0, gk_body = 0;  // kernels of the device-loop graph (fixed, per pass)
-  // device-loop solve: the whole PCG as one graph (conditional while node)
-  cudaGraph_t graph = nullptr;      // owns the conditional handle: lives as long as gexec
-  cudaGraphExec_t gexec = nullptr;
-  cudaEvent_t done = nullptr;
-  PcgCtl* result = nullptr;  // pinned host copy of the last device-loop solve's scalars
-  ~saamg_hierarchy() {
-    if (done) cudaEventSynchronize(done);
-    if (gexec) cudaGraphExecDestroy(gexec);
-    if (graph) cudaGraphDestroy(graph);
-    if (done) cudaEventDestroy(done);
-    if (result) cudaFreeHost(result);
-  }
-};
 
 namespace saamg {
 
@@ -1473,7 +1406,11 @@ struct BatchGraph {
   cudaGraphExec_t exec = nullptr;
   PcgCtl* res = nullptr;  // pinned, one per solve
   std::vector<long long> kfixed, kbody;  // kernels of each solve: once, and per PCG pass
+  BatchEngine* eng = nullptr;            // the merged form (one launch per operation)
+  // wall time of the first run of each form (-1: not run yet); later runs take the faster
+  double ms_merged = -1.0, ms_graphs = -1.0;
   ~BatchGraph() {
+    if (eng) batch_engine_free(eng);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (res) cudaFreeHost(res);
@@ -1489,21 +1426,24 @@ struct BatchGraph {
 };
 
 static std::mutex g_batch_mu;  // batched calls run one at a time
-static std::vector<std::unique_ptr<BatchGraph>> g_batch_cache;  // most recent last
+struct BatchLast {
+  int merged = 0;
+  double ms_merged = -1.0, ms_graphs = -1.0;
+};
+static BatchLast g_batch_last;  // the most recent batched call (under g_batch_mu)
+// Most recent last.  Never destroyed at process exit: an entry's work vectors go back through
+// the allocator hook that gave them out, which may no longer be callable then (a Python
+// callback during interpreter shutdown); saamg_release_batch_cache empties it while it is.
+static std::vector<std::unique_ptr<BatchGraph>>& g_batch_cache =
+    *new std::vector<std::unique_ptr<BatchGraph>>();
 constexpr size_t kBatchCache = 2;
 
-static std::unique_ptr<BatchGraph> build_batch_graph(
-    saamg_hierarchy* const* hs, const double* const* rho, double* const* phi, int count,
-    double rtol, const std::vector<saamg_hierarchy*>& order,
-    std::map<saamg_hierarchy*, std::vector<int>>& groups) {
-  auto bg = std::make_unique<BatchGraph>();
-  for (int j = 0; j < count; ++j) {
-    bg->hs.push_back(hs[j]);
-    bg->versions.push_back(hs[j]->version);
-    bg->rho.push_back(rho[j]);
-    bg->phi.push_back(phi[j]);
-  }
-  bg->rtol = rtol;
+// The per-solve form of a batch: one device-loop graph per solve inside one graph, solves of
+// one hierarchy in order on a branch, up to 32 branches.
+static void build_batch_graph(BatchGraph* bg, saamg_hierarchy* const* hs,
+                              const double* const* rho, double* const* phi, int count,
+                              double rtol, const std::vector<saamg_hierarchy*>& order,
+                              std::map<saamg_hierarchy*, std::vector<int>>& groups) {
   SAAMG_CUDA(cudaMallocHost(&bg->res, sizeof(PcgCtl) * count));
   std::lock_guard<std::mutex> lock(g_capture_mu);
   cudaStream_t cs = capture_stream(0), body = capture_stream(1);
@@ -1560,6 +1500,8 @@ static std::unique_ptr<BatchGraph> build_batch_graph(
     SAAMG_CUDA(cudaStreamEndCapture(cs, &g));
     SAAMG_CUDA(cudaGraphInstantiate(&bg->exec, g, 0));
     bg->graph = g;
+    SAAMG_CUDA(cudaGraphUpload(bg->exec, cs));  // the first run does not pay for the upload
+    SAAMG_CUDA(cudaStreamSynchronize(cs));
   } catch (...) {
     if (capturing) {
       cudaGraph_t junk = nullptr;
@@ -1571,7 +1513,6 @@ static std::unique_ptr<BatchGraph> build_batch_graph(
     throw;
   }
   for (cudaEvent_t e : evs) cudaEventDestroy(e);
-  return bg;
 }
 
 saamg_status saamg_solve_batched(saamg_hierarchy* const* hs, const double* const* rho,
@@ -1609,22 +1550,53 @@ saamg_status saamg_solve_batched(saamg_hierarchy* const* hs, const double* const
         break;
       }
     if (!bg) {
-      auto built = build_batch_graph(hs, rho, phi, count, rtol, order, groups);
+      auto built = std::make_unique<BatchGraph>();
+      for (int j = 0; j < count; ++j) {
+        built->hs.push_back(hs[j]);
+        built->versions.push_back(hs[j]->version);
+        built->rho.push_back(rho[j]);
+        built->phi.push_back(phi[j]);
+      }
+      built->rtol = rtol;
       if (g_batch_cache.size() >= kBatchCache) g_batch_cache.erase(g_batch_cache.begin());
       g_batch_cache.push_back(std::move(built));
       bg = g_batch_cache.back().get();
     }
-    SAAMG_CUDA(cudaGraphLaunch(bg->exec, s));
+    // Two forms give the same bits: one launch per operation across all solves (merged), or
+    // one device-loop graph per solve on concurrent branches.  The first run of a batch takes
+    // the merged form, the second the per-solve form, and later runs the faster of the two.
+    const bool can_merge = batch_engine_supports(hs, count);
+    bool merged;
+    if (!can_merge) merged = false;
+    else if (bg->ms_merged < 0) merged = true;
+    else if (bg->ms_graphs < 0) merged = false;
+    else merged = bg->ms_merged <= bg->ms_graphs;
+    if (merged && !bg->eng) {
+      std::lock_guard<std::mutex> lock(g_capture_mu);
+      bg->eng = batch_engine_build(hs, rho, phi, count, rtol, capture_stream);
+    }
+    if (!merged && !bg->exec) build_batch_graph(bg, hs, rho, phi, count, rtol, order, groups);
+    const auto l0 = std::chrono::steady_clock::now();
+    if (merged) batch_engine_launch(bg->eng, s);
+    else SAAMG_CUDA(cudaGraphLaunch(bg->exec, s));
     for (saamg_hierarchy* h : order) {
       if (!h->done) SAAMG_CUDA(cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming));
       SAAMG_CUDA(cudaEventRecord(h->done, s));
     }
     SAAMG_CUDA(cudaStreamSynchronize(s));
+    const double ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - l0).count();
+    double& slot = merged ? bg->ms_merged : bg->ms_graphs;
+    if (slot < 0) slot = ms;
+    g_batch_last = {merged ? 1 : 0, bg->ms_merged, bg->ms_graphs};
+    const PcgCtl* res = merged ? batch_engine_results(bg->eng) : bg->res;
     long long kernels = 0;
-    for (int j = 0; j < count; ++j) kernels += bg->kfixed[j] + bg->res[j].iters * bg->kbody[j];
+    if (merged) kernels = batch_engine_kernels(bg->eng);
+    else
+      for (int j = 0; j < count; ++j) kernels += bg->kfixed[j] + bg->res[j].iters * bg->kbody[j];
     count_launches(kernels);
     for (int j = 0; j < count; ++j) {
-      saamg_status st = info_from_ctl(bg->res[j], &infos[j]);
+      saamg_status st = info_from_ctl(res[j], &infos[j]);
       if (st < 0 && worst >= 0) worst = st;
       else if (st == SAAMG_NOT_CONVERGED && worst == SAAMG_OK) worst = st;
     }
@@ -1634,6 +1606,22 @@ saamg_status saamg_solve_batched(saamg_hierarchy* const* hs, const double* const
     for (int j = 0; j < count; ++j) infos[j].solve_ms = ms;
   }
   return g != SAAMG_OK ? g : worst;
+}
+
+saamg_status saamg_batch_last(int* merged, double* ms_merged, double* ms_graphs) {
+  return guard("saamg_batch_last", [&] {
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    if (merged) *merged = g_batch_last.merged;
+    if (ms_merged) *ms_merged = g_batch_last.ms_merged;
+    if (ms_graphs) *ms_graphs = g_batch_last.ms_graphs;
+  });
+}
+
+saamg_status saamg_release_batch_cache(void) {
+  return guard("saamg_release_batch_cache", [&] {
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    g_batch_cache.clear();
+  });
 }
 
 saamg_status saamg_set_cheb_degree(saamg_hierarchy* h, int degree) {

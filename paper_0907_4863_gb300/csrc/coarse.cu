@@ -6,6 +6,7 @@
 // The elimination works on column-major arrays, a(i, j) at [j * n + i]; the finished inverse
 // is stored by rows, A_L^-1(i, j) at [i * n + j], for the per-cycle product.
 #include "coarse.cuh"
+#include "rows.cuh"
 
 namespace saamg {
 
@@ -429,12 +430,7 @@ __global__ void __launch_bounds__(32 * kGemvWarps) coarse_apply_k(int n,
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * kGemvWarps + (threadIdx.x >> 5);
   if (i >= n) return;  // whole warps leave together
-  const double* row = inv + (size_t)i * n;
-  double acc = 0.0;
-  for (int c = lane; c < n; c += 32) acc += row[c] * (double)b[c];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) x[i] = (TV)acc;
+  rows::gemv_row<TV>(i, n, lane, inv, b, x);
 }
 
 // --- Gauss-Seidel (one CTA) ---------------------------------------------------------

@@ -5,16 +5,11 @@
 #include <cmath>
 
 #include "csr.cuh"
+#include "rows.cuh"
 
 namespace saamg {
 
 namespace {
-
-__device__ __forceinline__ double ld(const double* p, size_t i) { return p[i]; }
-__device__ __forceinline__ float ld(const float* p, size_t i) { return p[i]; }
-__device__ __forceinline__ float ld(const __nv_bfloat16* p, size_t i) {
-  return __bfloat162float(p[i]);
-}
 
 template <class TV, class TM, int G, int MODE>
 __global__ void __launch_bounds__(256) csr_k(int n, const int* __restrict__ rowptr,
@@ -34,60 +29,12 @@ __global__ void __launch_bounds__(256) csr_k(int n, const int* __restrict__ rowp
   // the trip count is uniform across the warp, so the group shuffles see all 32 lanes
   for (int wbase = warp * kRowsPerWarp; wbase < n; wbase += nwarps * kRowsPerWarp) {
     const int row = wbase + lane / G;
-    const bool active = row < n;
-    TV acc = TV(0);
-    if (MODE != CSR_CHEB0 && active) {
-      const int p0 = rowptr[row], p1 = rowptr[row + 1];
-      int p = p0 + gl;
-      // four independent (column, value) loads and gathers in flight per lane
-      for (; p + 3 * G < p1; p += 4 * G) {
-        const int k0 = col[p], k1 = col[p + G], k2 = col[p + 2 * G], k3 = col[p + 3 * G];
-        const TV a0 = (TV)ld(val, p), a1 = (TV)ld(val, p + G), a2 = (TV)ld(val, p + 2 * G),
-                 a3 = (TV)ld(val, p + 3 * G);
-        const TV x0 = x[k0], x1 = x[k1], x2 = x[k2], x3 = x[k3];
-        acc += a0 * x0;
-        acc += a1 * x1;
-        acc += a2 * x2;
-        acc += a3 * x3;
-      }
-      for (; p < p1; p += G) acc += (TV)ld(val, p) * x[col[p]];
-    }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
-    if (active && gl == 0) {
-      if (MODE == CSR_SPMV) {
-        y[row] = acc;
-      } else if (MODE == CSR_RESID) {
-        y[row] = b[row] - acc;
-      } else if (MODE == CSR_ADD) {
-        y[row] = y[row] + acc;
-      } else if (MODE == CSR_CHEB) {
-        const TV r = b[row] - acc;
-        const TV dprev = (c1 == TV(0)) ? TV(0) : c1 * d[row];
-        const TV dv = dprev + c2 * (invd[row] * r);
-        d[row] = dv;
-        y[row] = x[row] + dv;
-      } else if (MODE == CSR_CHEB0) {
-        const TV dv = c2 * (invd[row] * b[row]);
-        d[row] = dv;
-        y[row] = dv;
-      } else {  // CSR_SPMV_DINV_DOT: c2 carries the scale of x
-        const TV w = (c2 * invd[row]) * acc;
-        y[row] = w;
-        dacc += (double)w * (double)w;
-      }
-    }
+    rows::csr_group_row<TV, TM, G, MODE>(row, row < n, gl, rowptr, col, val, x, y, b, d, invd,
+                                         c1, c2, dacc);
   }
   if (MODE == CSR_SPMV_DINV_DOT) {
-    __shared__ double sh[32];
-    for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = dacc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-      partials[blockIdx.x] = t;
-    }
+    const double t = rows::block_sum(dacc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
   }
 }
 
@@ -95,7 +42,7 @@ __global__ void __launch_bounds__(256) csr_k(int n, const int* __restrict__ rowp
 // first kShortWin entries of a row are loaded under predicates, so all of the row's column,
 // value and gather loads are in flight at once, and a warp keeps 32 rows in flight.  The
 // row is summed in entry order; longer rows finish in a plain loop.
-constexpr int kShortWin = 6;
+using rows::kShortWin;
 
 template <class TV, class TM, int MODE>
 __global__ void __launch_bounds__(256) csr_short_k(int n, const int* __restrict__ rowptr,
@@ -103,24 +50,8 @@ __global__ void __launch_bounds__(256) csr_short_k(int n, const int* __restrict_
                                                    const TM* __restrict__ val,
                                                    const TV* __restrict__ x, TV* __restrict__ y) {
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n;
-       row += gridDim.x * blockDim.x) {
-    const int p0 = rowptr[row], p1 = rowptr[row + 1];
-    const TV y0 = MODE == CSR_ADD ? y[row] : TV(0);
-    int k[kShortWin];
-    TV a[kShortWin];
-#pragma unroll
-    for (int q = 0; q < kShortWin; ++q) {
-      const bool on = p0 + q < p1;
-      k[q] = on ? col[p0 + q] : 0;
-      a[q] = on ? (TV)ld(val, p0 + q) : TV(0);
-    }
-    TV acc = TV(0);
-#pragma unroll
-    for (int q = 0; q < kShortWin; ++q)
-      if (p0 + q < p1) acc += a[q] * x[k[q]];
-    for (int p = p0 + kShortWin; p < p1; ++p) acc += (TV)ld(val, p) * x[col[p]];
-    y[row] = MODE == CSR_ADD ? y0 + acc : acc;
-  }
+       row += gridDim.x * blockDim.x)
+    rows::csr_short_row<TV, TM, MODE>(row, rowptr, col, val, x, y);
 }
 
 template <class TV, class TM, int G>
@@ -187,6 +118,18 @@ inline int grid_for(size_t n) {
 
 }  // namespace
 
+int csr_plan(int mode, int n, double avg_nnz, bool dbl) {
+  // the prolongators' short rows on a large level: a thread per row
+  if ((mode == CSR_ADD || mode == CSR_SPMV) && avg_nnz <= kShortWin && n >= 100000) return 0;
+  int g = dbl ? (avg_nnz <= 10.0 ? 2 : (avg_nnz <= 48.0 ? 4 : 8))
+              : (avg_nnz <= 6.0 ? 2 : (avg_nnz <= 20.0 ? 4 : (avg_nnz <= 64.0 ? 8 : 16)));
+  int gpar = 1;
+  while (gpar < 32 && (long long)n * gpar < 150000) gpar <<= 1;
+  int glen = 1;
+  while (glen < 32 && glen < avg_nnz) glen <<= 1;
+  return std::max(g, std::min(gpar, glen));
+}
+
 template <class TV, class TM>
 void csr_apply(int mode, int n, const int* rowptr, const int* col, const TM* val, double avg_nnz,
                const TV* x, TV* y, const TV* b, TV* d, const TV* invd, TV c1, TV c2,
@@ -201,8 +144,8 @@ void csr_apply(int mode, int n, const int* rowptr, const int* col, const TM* val
   // double vectors use few lanes (FP32 can afford wider groups for better coalescing) -- but
   // a small level (few rows, long rows: the deep levels of the hierarchy) needs wider groups
   // to fill the GPU at all: enough lanes for ~150 k threads, never more than the row length.
-  // the prolongators' short rows on a large level: a thread per row
-  if ((mode == CSR_ADD || mode == CSR_SPMV) && avg_nnz <= kShortWin && n >= 100000) {
+  const int g = csr_plan(mode, n, avg_nnz, sizeof(TV) == 8);
+  if (g == 0) {
     const long long need = ((long long)n + 255) / 256;
     const int blocks = (int)(need < sm_count() * 16 ? need : sm_count() * 16);
     if (mode == CSR_ADD)
@@ -212,13 +155,6 @@ void csr_apply(int mode, int n, const int* rowptr, const int* col, const TM* val
     SAAMG_LAUNCH();
     return;
   }
-  int g = sizeof(TV) == 8 ? (avg_nnz <= 10.0 ? 2 : (avg_nnz <= 48.0 ? 4 : 8))
-                          : (avg_nnz <= 6.0 ? 2 : (avg_nnz <= 20.0 ? 4 : (avg_nnz <= 64.0 ? 8 : 16)));
-  int gpar = 1;
-  while (gpar < 32 && (long long)n * gpar < 150000) gpar <<= 1;
-  int glen = 1;
-  while (glen < 32 && glen < avg_nnz) glen <<= 1;
-  g = std::max(g, std::min(gpar, glen));
   switch (g) {
     case 2:
       launch_g<TV, TM, 2>(mode, n, rowptr, col, val, x, y, b, d, invd, c1, c2, partials, s, xscale);

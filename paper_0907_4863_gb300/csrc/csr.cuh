@@ -21,6 +21,10 @@ void csr_apply(int mode, int n, const int* rowptr, const int* col, const TM* val
                double* partials, cudaStream_t s, int kclass = -1,
                const double* xscale = nullptr);
 
+// The launch form csr_apply takes for a matrix of n rows with avg_nnz entries per row: 0 for
+// a thread per (short) row, else the lanes G per row (2 .. 32).  dbl: FP64 vectors.
+int csr_plan(int mode, int n, double avg_nnz, bool dbl);
+
 // invd_i = 1 / a_ii (also the FP32 copy when invd32 is not null)
 void csr_diag_inverse(const DevCsr& A, double* invd, float* invd32, cudaStream_t s);
 void to_float(const double* in, float* out, size_t n, cudaStream_t s);

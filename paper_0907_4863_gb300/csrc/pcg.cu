@@ -3,58 +3,21 @@
 // fixed grid and a single block adds the partials in index order, so a run is
 // reproducible bit for bit.  The CG scalars stay on the device.
 #include "pcg.cuh"
+#include "rows.cuh"
 
 namespace saamg {
 
 namespace {
 
-__device__ __forceinline__ double block_sum(double v) {
-  __shared__ double sh[32];
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-  return t;  // valid in thread 0
-}
-
-// single-block ordered sum of kRedBlocks partials
-__device__ __forceinline__ double sum_fixed(const double* part) {
-  __shared__ double sh[kRedThreads];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) acc += part[i];
-  sh[threadIdx.x] = acc;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
-  }
-  double r = sh[0];
-  __syncthreads();
-  return r;
-}
+using rows::block_sum;
+using rows::sum_fixed;
 
 // Loads of four grid strides are issued before their (in-order) multiply-adds: the sum is
 // the same sequence of operations as the plain strided loop, with more bytes in flight.
 template <class TA, class TB>
 __global__ void dot_k(int n, const TA* __restrict__ a, const TB* __restrict__ b,
                       double* __restrict__ part) {
-  double acc = 0.0;
-  const int st = gridDim.x * blockDim.x;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  for (; i + 3 * st < n; i += 4 * st) {
-    const double a0 = (double)a[i], a1 = (double)a[i + st], a2 = (double)a[i + 2 * st],
-                 a3 = (double)a[i + 3 * st];
-    const double b0 = (double)b[i], b1 = (double)b[i + st], b2 = (double)b[i + 2 * st],
-                 b3 = (double)b[i + 3 * st];
-    acc += a0 * b0;
-    acc += a1 * b1;
-    acc += a2 * b2;
-    acc += a3 * b3;
-  }
-  for (; i < n; i += st) acc += (double)a[i] * (double)b[i];
-  double t = block_sum(acc);
+  const double t = rows::dot_block<TA, TB>(blockIdx.x, n, a, b);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -63,25 +26,8 @@ template <class TZ>
 __global__ void dot2_k(int n, const double* __restrict__ r, const TZ* __restrict__ z,
                        const double* __restrict__ q, double* __restrict__ part_rz,
                        double* __restrict__ part_zq) {
-  double a1 = 0.0, a2 = 0.0;
-  const int st = gridDim.x * blockDim.x;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  for (; i + st < n; i += 2 * st) {
-    const double z0 = (double)z[i], z1 = (double)z[i + st];
-    const double r0 = r[i], r1 = r[i + st], q0 = q[i], q1 = q[i + st];
-    a1 += r0 * z0;
-    a2 += z0 * q0;
-    a1 += r1 * z1;
-    a2 += z1 * q1;
-  }
-  for (; i < n; i += st) {
-    const double zi = (double)z[i];
-    a1 += r[i] * zi;
-    a2 += zi * q[i];
-  }
-  const double t1 = block_sum(a1);
-  __syncthreads();  // block_sum's shared array is reused
-  const double t2 = block_sum(a2);
+  double t1, t2;
+  rows::dot2_block<TZ>(blockIdx.x, n, r, z, q, t1, t2);
   if (threadIdx.x == 0) {
     part_rz[blockIdx.x] = t1;
     part_zq[blockIdx.x] = t2;
@@ -106,16 +52,7 @@ __global__ void update_k(int n, double* __restrict__ x, double* __restrict__ r,
                          const double* __restrict__ p, const double* __restrict__ q,
                          const PcgCtl* __restrict__ ctl, double* __restrict__ part,
                          float* __restrict__ r32) {
-  const double a = ctl->alpha;
-  double acc = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    x[i] = x[i] + a * p[i];
-    double ri = r[i] - a * q[i];
-    r[i] = ri;
-    if (r32) r32[i] = (float)ri;
-    acc += ri * ri;
-  }
-  double t = block_sum(acc);
+  const double t = rows::update_block(blockIdx.x, n, ctl->alpha, x, r, p, q, r32);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 

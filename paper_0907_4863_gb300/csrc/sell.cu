@@ -1,18 +1,13 @@
 // SELL-32-sigma kernels: layout construction from CSR and the V-cycle operations on it
 // (Chebyshev step fused with the residual, residual, y = A x, y += A x).
 #include "sell.cuh"
+#include "rows.cuh"
 
 namespace saamg {
 
 namespace {
 
-constexpr int kSellCheb1 = 6;  // CSR_CHEB with c1 = 0: d is not read
-
-__device__ __forceinline__ double ld(const double* p, int i) { return p[i]; }
-__device__ __forceinline__ float ld(const float* p, int i) { return p[i]; }
-__device__ __forceinline__ float ld(const __nv_bfloat16* p, int i) {
-  return __bfloat162float(p[i]);
-}
+using rows::kSellCheb1;
 
 // Block per window: stable rank of each row by decreasing length, from the window's
 // lengths in shared memory.
@@ -91,68 +86,12 @@ __global__ void __launch_bounds__(256) sell_k(int n, int nslices, const int* __r
   const int nw = (gridDim.x * blockDim.x) >> 5;
   double dacc = 0.0;
   if (MODE == CSR_SPMV_DINV_DOT) c2 = xscale ? (TV)*xscale : TV(1);
-  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < nslices; s += nw) {
-    const int p = 32 * s + lane;
-    if (p >= n) continue;  // no warp-collective operation inside the loop
-    const int row = perm[p];
-    TV acc = TV(0);
-    if (MODE != CSR_CHEB0) {
-      const int e0 = soff[s] + lane, w = (soff[s + 1] - soff[s]) >> 5;
-      int k = 0;
-      // four independent (column, value, x) loads in flight per lane
-      for (; k + 4 <= w; k += 4) {
-        const int e = e0 + 32 * k;
-        const int k0 = REL ? row + dcol[e] : col[e];
-        const int k1 = REL ? row + dcol[e + 32] : col[e + 32];
-        const int k2 = REL ? row + dcol[e + 64] : col[e + 64];
-        const int k3 = REL ? row + dcol[e + 96] : col[e + 96];
-        const TV a0 = (TV)ld(val, e), a1 = (TV)ld(val, e + 32), a2 = (TV)ld(val, e + 64),
-                 a3 = (TV)ld(val, e + 96);
-        const TV x0 = x[k0], x1 = x[k1], x2 = x[k2], x3 = x[k3];
-        acc = fma(a0, x0, acc);
-        acc = fma(a1, x1, acc);
-        acc = fma(a2, x2, acc);
-        acc = fma(a3, x3, acc);
-      }
-      for (; k < w; ++k) {
-        const int e = e0 + 32 * k;
-        acc = fma((TV)ld(val, e), x[REL ? row + dcol[e] : col[e]], acc);
-      }
-    }
-    if (MODE == CSR_SPMV) {
-      y[row] = acc;
-    } else if (MODE == CSR_RESID) {
-      y[row] = b[row] - acc;
-    } else if (MODE == CSR_ADD) {
-      y[row] = y[row] + acc;
-    } else if (MODE == CSR_CHEB) {
-      const TV dv = fma(c1, d[row], c2 * (invd[row] * (b[row] - acc)));
-      d[row] = dv;
-      y[row] = x[row] + dv;
-    } else if (MODE == kSellCheb1) {
-      const TV dv = c2 * (invd[row] * (b[row] - acc));
-      d[row] = dv;
-      y[row] = x[row] + dv;
-    } else if (MODE == CSR_CHEB0) {
-      const TV dv = c2 * (invd[row] * b[row]);
-      d[row] = dv;
-      y[row] = dv;
-    } else {  // CSR_SPMV_DINV_DOT: c2 carries the scale of x
-      const TV w = (c2 * invd[row]) * acc;
-      y[row] = w;
-      dacc += (double)w * (double)w;
-    }
-  }
+  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < nslices; s += nw)
+    rows::sell_row<TV, TM, MODE, REL>(s, lane, n, perm, soff, col, dcol, val, x, y, b, d, invd,
+                                      c1, c2, dacc);
   if (MODE == CSR_SPMV_DINV_DOT) {  // fixed grid of kRedBlocks: the same partial sums every run
-    __shared__ double sh[32];
-    for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
-    if (lane == 0) sh[threadIdx.x >> 5] = dacc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-      partials[blockIdx.x] = t;
-    }
+    const double t = rows::block_sum(dacc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
   }
 }
 

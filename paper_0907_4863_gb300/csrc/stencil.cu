@@ -10,6 +10,8 @@
 // (bound by FP64 issue): first 32 regular-run rows per warp from a (row, line) list, then
 // 32 table rows per warp from the table-row list.
 #include "operator.cuh"
+#include "batch.cuh"
+#include "rows.cuh"
 
 namespace saamg {
 
@@ -235,11 +237,155 @@ __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __res
 // chunks per warp iteration: FP32 is latency/HBM-bound and gains from more loads in flight;
 // FP64 is bound by FP64 issue and keeps one
 template <class T>
-constexpr int kChunks() {
+__host__ __device__ constexpr int kChunks() {
   return sizeof(T) == 4 ? 2 : 1;
 }
 
+// Batched form: a block takes one work block (task, first chunk, end chunk) at a time and
+// copies the task into shared memory; its warps take two chunks at a time, as the one-solve
+// FP32 launch does, and apply each exactly as the one-solve launch applies it.
+template <class T>
+__device__ __forceinline__ void load_task(const StTask<T>* __restrict__ tasks, int t,
+                                          StTask<T>& sk) {
+  const int* src = reinterpret_cast<const int*>(tasks + t);
+  int* dst = reinterpret_cast<int*>(&sk);
+  for (int i = threadIdx.x; i < (int)(sizeof(StTask<T>) / 4); i += blockDim.x) dst[i] = src[i];
+}
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(256, 4) bstencil_k(const StTask<T>* __restrict__ tasks,
+                                                  const int4* __restrict__ wbs, int nwb) {
+  __shared__ StTask<T> sk;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  constexpr int K = kChunks<T>();
+  double dacc = 0.0;
+  for (int wb = blockIdx.x; wb < nwb; wb += gridDim.x) {
+    const int4 B = wbs[wb];
+    __syncthreads();  // the previous work block is done with sk
+    load_task<T>(tasks, B.x, sk);
+    __syncthreads();
+    if (!*sk.go) continue;  // uniform across the block
+    const int nreg = packed_rows<T>() ? (sk.S.nrun + 31) / 32 : sk.S.nchunks;
+    for (int c0 = B.y + (threadIdx.x >> 5) * K; c0 < B.z; c0 += wpb * K) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int c = c0 + k;
+        if (c >= B.z) continue;
+        if (packed_rows<T>()) {
+          if (c >= nreg)
+            stencil_row<T, MODE, true, true>(sk.S, c - nreg, lane, sk.x, sk.y, sk.b, sk.d, sk.c1,
+                                             sk.c2, sk.c2i0, dacc, sk.agg);
+          else
+            stencil_row<T, MODE, true>(sk.S, c, lane, sk.x, sk.y, sk.b, sk.d, sk.c1, sk.c2,
+                                       sk.c2i0, dacc, sk.agg);
+        } else {
+          stencil_row<T, MODE, false>(sk.S, c, lane, sk.x, sk.y, sk.b, sk.d, sk.c1, sk.c2,
+                                      sk.c2i0, dacc, sk.agg);
+        }
+      }
+    }
+  }
+}
+
+// q = A p with p'q partials, FP64: every (task t, block b) pair computes block b of the
+// one-solve launch (kRedBlocks blocks of 8 warps, one chunk per warp step) for task t,
+// emulated by one warp: lane l runs the rows of lane l of the block's warps w = 0..7 in turn,
+// each warp's sum of its own accumulator by the xor tree, the eight added in warp order --
+// the bits of the one-solve partial.  A pair without chunks stores 0.
+__global__ void __launch_bounds__(256) bstencil_dot_k(const StTask<double>* __restrict__ tasks,
+                                                      int ntasks) {
+  const int lane = threadIdx.x & 31;
+  constexpr int wpb = 8;
+  const int nw = kRedBlocks * wpb;
+  const long long npairs = (long long)ntasks * kRedBlocks;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long pr = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; pr < npairs;
+       pr += nwarps) {
+    const StTask<double>& k = tasks[pr / kRedBlocks];
+    const int b = (int)(pr % kRedBlocks);
+    if (!*k.go) continue;
+    const int nreg = (k.S.nrun + 31) / 32;
+    const int nch = nreg + (k.S.ntable + 31) / 32;
+    if (b * wpb >= nch) {
+      if (lane == 0) k.part[b] = 0.0;
+      continue;
+    }
+    double t = 0.0;
+    for (int w = 0; w < wpb; ++w) {
+      double dacc = 0.0;
+      for (int c = b * wpb + w; c < nch; c += nw) {
+        if (c >= nreg)
+          stencil_row<double, ST_SPMV_DOT, true, true>(k.S, c - nreg, lane, k.x, k.y, k.b, k.d,
+                                                       k.c1, k.c2, k.c2i0, dacc, k.agg);
+        else
+          stencil_row<double, ST_SPMV_DOT, true>(k.S, c, lane, k.x, k.y, k.b, k.d, k.c1, k.c2,
+                                                 k.c2i0, dacc, k.agg);
+      }
+      t += rows::warp_tree(dacc);
+    }
+    if (lane == 0) k.part[b] = t;
+  }
+}
+
 }  // namespace
+
+template <class T>
+int stencil_units(const StencilDev<T>& S) {
+  if (S.nchunks == 0) return 0;
+  return packed_rows<T>() ? (S.nrun + 31) / 32 + (S.ntable + 31) / 32 : S.nchunks;
+}
+template int stencil_units<float>(const StencilDev<float>&);
+template int stencil_units<double>(const StencilDev<double>&);
+
+template <class T>
+void batched_stencil(int mode, const StTask<T>* tasks, const int4* wbs, int nwb, cudaStream_t s) {
+  if (nwb <= 0) return;
+  // one wave of resident blocks, each taking work blocks in turn
+  auto grid = [&](const void* k) {
+    int nb = 0;
+    SAAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 256, 0));
+    return std::max(1, std::min(nwb, sm_count() * std::max(nb, 1)));
+  };
+#define SAAMG_BST(M)                                                                  \
+  bstencil_k<T, M><<<grid(reinterpret_cast<const void*>(bstencil_k<T, M>)), 256, 0, s>>>( \
+      tasks, wbs, nwb)
+  switch (mode) {
+    case ST_CHEB0:
+      SAAMG_BST(ST_CHEB0);
+      break;
+    case ST_CHEB:
+      SAAMG_BST(ST_CHEB);
+      break;
+    case ST_CHEB1:
+      SAAMG_BST(ST_CHEB1);
+      break;
+    case ST_RESID:
+      SAAMG_BST(ST_RESID);
+      break;
+    case ST_PROLONG:
+      SAAMG_BST(ST_PROLONG);
+      break;
+    default:
+      fail(SAAMG_EINVAL, "bad batched stencil mode");
+  }
+#undef SAAMG_BST
+  SAAMG_LAUNCH();
+}
+template void batched_stencil<float>(int, const StTask<float>*, const int4*, int, cudaStream_t);
+template void batched_stencil<double>(int, const StTask<double>*, const int4*, int, cudaStream_t);
+
+void batched_stencil_dot(const StTask<double>* tasks, int ntasks, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  const long long pairs = (long long)ntasks * kRedBlocks;
+  int nb = 0;
+  SAAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &nb, reinterpret_cast<const void*>(bstencil_dot_k), 256, 0));
+  const int blocks =
+      (int)std::min<long long>((pairs + 7) / 8, (long long)sm_count() * std::max(nb, 1));
+  bstencil_dot_k<<<blocks, 256, 0, s>>>(tasks, ntasks);
+  SAAMG_LAUNCH();
+}
 
 template <class T>
 void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* b, T* d, T c1,

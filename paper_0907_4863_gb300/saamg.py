@@ -136,12 +136,37 @@ def lib():
     L.saamg_kernel_timing_read.argtypes = [_i, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                            C.POINTER(C.c_longlong)]
     L.saamg_kernel_timing_read.restype = C.c_int
+    L.saamg_batch_last.argtypes = [C.POINTER(_i), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.saamg_batch_last.restype = C.c_int
+    L.saamg_release_batch_cache.argtypes = []
+    L.saamg_release_batch_cache.restype = C.c_int
     L.saamg_free.argtypes = [_p]
     L.saamg_free.restype = None
     L.saamg_last_error.argtypes = []
     L.saamg_last_error.restype = C.c_char_p
     _lib = L
+    import atexit
+    # the batch cache's work vectors came from the allocator hook (a Python callback here):
+    # hand them back while the interpreter can still run the hook
+    atexit.register(release_batch_cache)
     return L
+
+
+def batch_last():
+    """Form of the most recent batched call ('merged' or 'per-solve') and the first-run wall
+    times (ms) of both forms for its set of solves (None: not run yet)."""
+    m, a, b = C.c_int(0), C.c_double(0), C.c_double(0)
+    _check(lib().saamg_batch_last(C.byref(m), C.byref(a), C.byref(b)))
+    return dict(form="merged" if m.value else "per-solve",
+                ms_merged=a.value if a.value >= 0 else None,
+                ms_per_solve=b.value if b.value >= 0 else None)
+
+
+def release_batch_cache():
+    """Frees the graphs and work vectors kept for repeated batched solves."""
+    if _lib is not None:
+        _flush_deferred()
+        _lib.saamg_release_batch_cache()
 
 
 def last_error():

@@ -175,3 +175,77 @@ def test_autotune_picks_a_degree_and_keeps_accuracy(S):
     assert info3["converged"] == 1
     with pytest.raises(S.SaamgError):
         S.set_cheb_degree(h, 0)
+
+
+def test_batched_engine_mixed_batch_equals_solo(S):
+    """One launch per operation across the whole batch: hierarchies of different depth,
+    Chebyshev degree (2, 3, 4), precision (FP64, FP32, BF16 storage), aggregation (MIS-2,
+    cubes), extrapolation and beta rule, several right-hand sides per hierarchy (solved side
+    by side with their own work vectors), one hierarchy of a single level.  Every result, its
+    iteration count and its residuals equal the solo solve's; a second run reuses the graph."""
+    import torch
+    c4 = sorted(I.batched_instances(), key=lambda w: w.grid.nbox)
+    specs = [(c4[0], dict(max_coarse=300, precision=1, beta_rule=1), 2),
+             (c4[1], dict(max_coarse=300, precision=1, beta_rule=1), 4),
+             (c4[2], dict(max_coarse=300, precision=2, beta_rule=1), 3),
+             (I.taper_workload(30, 27, 45, I.QUADRATIC), dict(max_coarse=100, precision=1, beta_rule=0), 2),
+             (I.pipe_workload(36, I.LINEAR), dict(max_coarse=150), 2),
+             (I.pipe_workload(28, I.QUADRATIC), dict(max_coarse=100, beta_rule=1), 3),
+             (I.cylinder_workload(30, I.CONSTANT), dict(max_coarse=200, aggregation=1, precision=1, beta_rule=1), 2),
+             (I.pipe_workload(12, I.LINEAR), dict(max_coarse=5000), 2)]
+    hs, rhos, solo, solo_info = [], [], [], []
+    for k, (w, prm, deg) in enumerate(specs):
+        h = _setup(S, w, **prm)
+        if deg != 2:
+            S.set_cheb_degree(h, deg)
+        for seed in range(2 if k % 2 else 3):
+            rho = _rho(w, 10 * k + seed)
+            phi = torch.zeros_like(rho)
+            solo_info.append(S.solve(h, rho, phi))
+            solo.append(phi)
+            hs.append(h)
+            rhos.append(rho)
+    assert hs[-1].info()["levels"] == 1
+    phis = [torch.zeros_like(r) for r in rhos]
+    forms = []
+    for rep in range(3):  # merged form, per-solve form, then the faster one
+        for x in phis:
+            x.zero_()
+        infos = S.solve_batched(hs, rhos, phis, rtol=1e-8)
+        forms.append(S.batch_last())
+        for a, b, ia, ib in zip(solo, phis, solo_info, infos):
+            assert ib["converged"] == 1 and ib["iters"] == ia["iters"]
+            assert ib["relres"] == ia["relres"] and ib["relres_true"] == ia["relres_true"]
+            assert torch.equal(a, b)
+    assert [f["form"] for f in forms[:2]] == ["merged", "per-solve"]
+    faster = "merged" if forms[1]["ms_merged"] <= forms[1]["ms_per_solve"] else "per-solve"
+    assert forms[2]["form"] == faster
+
+
+def test_batched_engine_warm_start_and_limits(S):
+    """Warm starts (phi holds the initial guess), a zero right-hand side, and an iteration
+    limit reached by one solve of the batch while the others converge."""
+    import torch
+    w = I.pipe_workload(32, I.LINEAR)
+    h = _setup(S, w, max_coarse=100, precision=1, beta_rule=1)
+    h3 = _setup(S, w, max_coarse=100, maxit=3)
+    rho = _rho(w, 4)
+    x0 = torch.zeros_like(rho)
+    S.solve(h, rho, x0, rtol=1e-4)  # a warm start
+    cases = [(h, rho, x0.clone()), (h, torch.zeros_like(rho), torch.full_like(rho, 2.0)),
+             (h3, rho, torch.zeros_like(rho)), (h, _rho(w, 5), torch.zeros_like(rho))]
+    solo = []
+    for hh, r, x in cases:
+        y = x.clone()
+        try:
+            info = S.solve(hh, r, y)
+        except S.SaamgError:
+            raise
+        solo.append((y, info))
+    phis = [x.clone() for _, _, x in cases]
+    infos = S.solve_batched([c[0] for c in cases], [c[1] for c in cases], phis)
+    for (y, si), x, bi in zip(solo, phis, infos):
+        assert torch.equal(x, y)
+        assert bi["iters"] == si["iters"] and bi["converged"] == si["converged"]
+    assert infos[1]["iters"] == 0 and torch.all(phis[1] == 0)
+    assert infos[2]["converged"] == 0 and infos[2]["iters"] == 3
