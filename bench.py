@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the mixed-precision and reuse legs")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (64 instances) leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
-    ap.add_argument("--serve-requests", type=int, default=1500,
+    ap.add_argument("--serve-requests", type=int, default=10000,
                     help="requests of the 10,000-request serving stream to replay")
     return ap.parse_args()
 
@@ -818,21 +818,72 @@ def batched_small_leg(S, torch, count=64, lo=32, hi=48):
 
 
 def serving_leg(S, torch, nreq):
-    """A prefix of the 10,000-request Poisson stream (mean gap 2 ms) over 20 geometries."""
+    """The 10,000-request Poisson stream (mean gap 2 ms) over 20 geometries: the whole stream
+    (or its first nreq requests) with FP32 continuous batching, then the same stream slowed
+    to an offered load of about 0.8 of the throughput that replay measured (latency at a load
+    the server sustains), and a prefix with warm starts and with FP64 one-at-a-time solves."""
+    import dataclasses
     from paper_0907_4863_gb300 import serve
     geoms = I.serving_geometries()
-    reqs = I.serving_requests(10000)[:nreq]
-    out = {"requests_replayed": nreq, "of": 10000, "mean_gap_ms": 2.0, "geometries": len(geoms)}
-    for name, params, slots, warm in (
-            ("fp32_continuous_batching", S.params_default(max_coarse=4096, precision=1, beta_rule=1), 16, False),
-            ("fp32_continuous_batching_warm_start", S.params_default(max_coarse=4096, precision=1, beta_rule=1), 16, True),
-            ("fp64_unbatched", S.params_default(max_coarse=4096), 1, False)):
-        srv = serve.Server(geoms, budget_bytes=120 << 30, slots=slots, params=params, warm_start=warm)
+    stream = I.serving_requests(10000)
+    keys = ("solves_per_s", "offered_per_s", "p50_ms", "p99_ms", "mean_ms", "queue_p50_ms",
+            "queue_p99_ms", "service_p50_ms", "service_p99_ms", "service_mean_ms", "wall_s",
+            "cache_misses", "work_sets", "max_inflight_same_geometry", "all_converged", "rejected")
+    fp32 = S.params_default(max_coarse=4096, precision=1, beta_rule=1)
+    out = {"requests": 10000, "mean_gap_ms": 2.0, "geometries": len(geoms), "slots": 16,
+           "work_sets_per_geometry": 4}
+
+    def run(name, reqs, params, slots=16, warm=False, sets=4):
+        srv = serve.Server(geoms, budget_bytes=120 << 30, slots=slots, params=params,
+                           warm_start=warm, sets_per_geometry=sets)
         _, st = srv.run(reqs)
         srv.close()
         torch.cuda.synchronize()
-        out[name] = {k: st[k] for k in ("solves_per_s", "p50_ms", "p99_ms", "mean_ms", "wall_s",
-                                        "cache_misses", "all_converged", "rejected")}
+        out[name] = {"requests_replayed": len(reqs), **{k: st[k] for k in keys}}
+        return st
+
+    full = run("fp32_continuous_batching", stream[:nreq], fp32)
+    solo = solo_solve_ms(S, torch, geoms, fp32)
+    out["fp32_solo_solve_ms"] = {geoms[g].name: round(v, 3) for g, v in solo.items()}
+    busy_s = sum(solo[r.geometry] for r in stream[:nreq]) / 1e3
+    out["fp32_one_after_another_solves_per_s"] = nreq / busy_s
+    # the same arrivals stretched so that the offered rate is 0.8 x the measured throughput
+    # (never faster than the stream itself)
+    prefix = stream[:min(nreq, 3000)]
+    mean_gap = prefix[-1].arrival / len(prefix)
+    scale = max(1.0, 1.0 / (0.8 * full["solves_per_s"] * mean_gap))
+    slowed = [dataclasses.replace(r, arrival=r.arrival * scale) for r in prefix]
+    run("fp32_continuous_batching_load_0.8", slowed, fp32)
+    short = stream[:min(nreq, 1500)]
+    run("fp32_continuous_batching_warm_start", short, fp32, warm=True)
+    run("fp64_one_at_a_time", short, S.params_default(max_coarse=4096), slots=1, sets=1)
+    return out
+
+
+def solo_solve_ms(S, torch, geoms, params):
+    """Device time of one asynchronous solve (gather, device-loop graph, scatter) of each
+    geometry's first time step, alone on the GPU (after a first solve that captures the
+    graph): the requests' service times without any overlap."""
+    out = {}
+    st = torch.cuda.current_stream()
+    for g, w in enumerate(geoms):
+        op = S.build_operator(S.make_domain(w.domain), S.make_grid(w.grid), w.mode)
+        h = S.setup(op, params)
+        rho = I.gaussian_bunch_torch(w.grid, w.centre, w.sigma, 1000 * g)
+        phi = torch.zeros_like(rho)
+        S.solve_async(h, rho, phi, 1e-8, stream=st.cuda_stream)
+        S.solve_wait(h)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        phi.zero_()
+        e0.record(st)
+        S.solve_async(h, rho, phi, 1e-8, stream=st.cuda_stream)
+        e1.record(st)
+        S.solve_wait(h)
+        e1.synchronize()
+        out[g] = e0.elapsed_time(e1)
+        h.free()
+        op.free()
     return out
 
 

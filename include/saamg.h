@@ -207,6 +207,20 @@ saamg_status saamg_setup(const saamg_operator *op, const saamg_params *params, v
 saamg_status saamg_setup_reuse(const saamg_operator *op, const saamg_hierarchy *prev,
                                const saamg_params *params, void *stream, saamg_hierarchy **out);
 
+/* A work set of h: a second hierarchy handle over h's levels with work vectors of its own,
+ * so that solves of one geometry (successive right-hand sides, Sec. 5.2) can be in flight
+ * at the same time.  It reads h's level matrices, prolongators, restrictions, aggregates,
+ * smoother coefficients and coarse solver without copying them (h's owner, if h is itself a
+ * work set) and allocates only its V-cycle vectors (FP64 or FP32 by h's precision), the PCG
+ * vectors and the reduction partials; its device-loop graph is its own.  Every solve call
+ * accepts it like a hierarchy and gives the same bits as on h.  saamg_set_cheb_degree and
+ * saamg_autotune_cheb_degree change the handle they are given only.  Free it with
+ * saamg_free; the shared levels are released when the hierarchy that owns them and all of its
+ * work sets have been freed (in any order).  device_bytes and setup_ms of its info count
+ * its own vectors and its creation.  Errors: EINVAL, ENOMEM, ECUDA. */
+saamg_status saamg_hierarchy_work_set(const saamg_hierarchy *h, void *stream,
+                                      saamg_hierarchy **out);
+
 saamg_status saamg_hierarchy_get_info(const saamg_hierarchy *h, saamg_hierarchy_info *info);
 
 /* Copies level l to HOST buffers (any may be NULL): A_l as CSR (rowptr[n_l+1], col, val),
@@ -378,7 +392,8 @@ saamg_status saamg_kernel_timing_read(int kclass, double *total_ms, long long *l
                                       long long *rows);
 
 /* Releases an operator or a hierarchy (NULL is ignored).  Waits for the handle's
- * outstanding work first. */
+ * outstanding work first.  The levels of a hierarchy with live work sets stay allocated
+ * until the last of them is freed. */
 void saamg_free(void *handle);
 
 /* Message of the calling thread's last error ("" if none). */

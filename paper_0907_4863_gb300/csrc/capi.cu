@@ -326,6 +326,34 @@ static bool same_pattern(const DevCsr& a, const DevCsr& b, cudaStream_t s) {
   return h == 0;
 }
 
+// PCG vectors of level 0, reduction partials and the loop's control block.
+static void alloc_pcg_vectors(saamg_hierarchy* h, int n, cudaStream_t s) {
+  h->bhat.alloc(n, s);
+  h->xhat.alloc(n, s);
+  h->r.alloc(n, s);
+  h->z.alloc(n, s);
+  h->p.alloc(n, s);
+  h->q.alloc(n, s);
+  if (mixed(h)) {
+    h->z32.alloc(n, s);
+    h->r32.alloc(n, s);
+  }
+  h->part0.alloc(kRedBlocks, s);
+  h->part1.alloc(kRedBlocks, s);
+  h->part2.alloc(kRedBlocks, s);
+  h->ctl.alloc(1, s);
+}
+
+// Device bytes of the V-cycle and PCG vectors of h.
+static long long vector_bytes(const saamg_hierarchy* h) {
+  long long bytes = 0;
+  for (auto& L : h->lev)
+    bytes += L->x0.bytes() + L->x1.bytes() + L->b.bytes() + L->d.bytes() + L->r.bytes() +
+             L->fx0.bytes() + L->fx1.bytes() + L->fb.bytes() + L->fd.bytes() + L->fr.bytes();
+  const long long n = h->op->d.n;
+  return bytes + 6LL * n * 8 + (mixed(h) ? 8LL * n : 0);
+}
+
 // prev != NULL: the aggregates of every level are copied from prev (whose level-0 pattern
 // must equal op's) instead of being recomputed; everything numeric is rebuilt.
 // A second stream for setup work that overlaps the work on the caller's stream (created once).
@@ -504,34 +532,102 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
       to_float(L.R.val.p, L.R32.p, L.R.nnz, s);
     }
   }
-  const int n = od.n;
-  h->bhat.alloc(n, s);
-  h->xhat.alloc(n, s);
-  h->r.alloc(n, s);
-  h->z.alloc(n, s);
-  h->p.alloc(n, s);
-  h->q.alloc(n, s);
-  if (mixed(h)) {
-    h->z32.alloc(n, s);
-    h->r32.alloc(n, s);
-  }
-  h->part0.alloc(kRedBlocks, s);
-  h->part1.alloc(kRedBlocks, s);
-  h->part2.alloc(kRedBlocks, s);
-  h->ctl.alloc(1, s);
+  alloc_pcg_vectors(h, od.n, s);
   SAAMG_CUDA(cudaStreamSynchronize(s));
   pt.mark("finish");
   pt.flush("setup");
   long long bytes = 0;
   for (auto& L : h->lev) {
     bytes += L->A.bytes() + L->P.bytes() + L->R.bytes() + L->invd.bytes() + L->invd32.bytes() +
-             L->agg.bytes() + L->root.bytes() + L->ids.bytes() + L->x0.bytes() + L->x1.bytes() + L->b.bytes() +
-             L->d.bytes() + L->r.bytes() + L->fx0.bytes() + L->fx1.bytes() + L->fb.bytes() +
-             L->fd.bytes() + L->fr.bytes() + L->As.bytes() + L->P32.bytes() + L->R32.bytes();
+             L->agg.bytes() + L->root.bytes() + L->ids.bytes() + L->As.bytes() + L->P32.bytes() +
+             L->R32.bytes();
   }
-  bytes += h->coarse.bytes() + 6LL * n * 8 + (mixed(h) ? 8LL * n : 0);
-  h->bytes = bytes;
+  h->bytes = bytes + h->coarse.bytes() + vector_bytes(h);
   h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+static void borrow_csr(DevCsr& d, const DevCsr& o) {
+  d.n = o.n;
+  d.m = o.m;
+  d.nnz = o.nnz;
+  d.rowptr.borrow(o.rowptr);
+  d.col.borrow(o.col);
+  d.val.borrow(o.val);
+  d.val32.borrow(o.val32);
+  d.val16.borrow(o.val16);
+}
+
+static void borrow_sell(DevSell& d, const DevSell& o) {
+  d.n = o.n;
+  d.m = o.m;
+  d.nslices = o.nslices;
+  d.nnz = o.nnz;
+  d.nent = o.nent;
+  d.perm.borrow(o.perm);
+  d.soff.borrow(o.soff);
+  d.col.borrow(o.col);
+  d.dcol.borrow(o.dcol);
+  d.index_bytes = o.index_bytes;
+  d.val.borrow(o.val);
+  d.val32.borrow(o.val32);
+  d.val16.borrow(o.val16);
+}
+
+// h = a work set of src: every level's matrices, transfers, aggregates and the coarse solver
+// are borrowed from the hierarchy that owns them (src, or the one src borrows from), the
+// smoother coefficients are src's, and the vectors are h's own.
+static void work_set_impl(const saamg_hierarchy* src, cudaStream_t s, saamg_hierarchy* h) {
+  auto t0 = std::chrono::steady_clock::now();
+  h->op = src->op;
+  h->prm = src->prm;
+  for (const auto& S : src->lev) {
+    auto L = std::make_unique<Level>();
+    L->n = S->n;
+    L->nnz = S->nnz;
+    L->avg = S->avg;
+    borrow_csr(L->A, S->A);
+    L->invd.borrow(S->invd);
+    L->invd32.borrow(S->invd32);
+    L->agg.borrow(S->agg);
+    L->root.borrow(S->root);
+    L->ids.borrow(S->ids);
+    for (int k = 0; k < 3; ++k) L->dims[k] = S->dims[k];
+    borrow_csr(L->P, S->P);
+    borrow_csr(L->R, S->R);
+    L->lambda = S->lambda;
+    L->omega = S->omega;
+    L->cheb = S->cheb;
+    borrow_sell(L->As, S->As);
+    L->P32.borrow(S->P32);
+    L->R32.borrow(S->R32);
+    h->lev.push_back(std::move(L));
+  }
+  for (size_t q = 0; q < h->lev.size(); ++q) alloc_level_vectors(h, *h->lev[q], q == 0, s);
+  const CoarseSolver& c = src->coarse;
+  h->coarse.n = c.n;
+  h->coarse.kind = c.kind;
+  h->coarse.inv.borrow(c.inv);
+  h->coarse.rowptr = c.rowptr;
+  h->coarse.col = c.col;
+  h->coarse.val = c.val;
+  h->coarse.invd = c.invd;
+  h->coarse.colour.borrow(c.colour);
+  h->coarse.order.borrow(c.order);
+  h->coarse.coff.borrow(c.coff);
+  h->coarse.ncolours = c.ncolours;
+  h->coarse.steps = c.steps;
+  alloc_pcg_vectors(h, h->op->d.n, s);
+  SAAMG_CUDA(cudaStreamSynchronize(s));
+  h->bytes = vector_bytes(h);
+  h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Drops one reference to h (the handle's own or a work set's); the last one deletes it.
+static void release_hierarchy(saamg_hierarchy* h) {
+  if (h->refs.fetch_sub(1) == 1) {
+    h->magic = 0;
+    delete h;
+  }
 }
 
 // --- V-cycle (Algorithm 1) -------------------------------------------------
@@ -1219,6 +1315,21 @@ saamg_status saamg_setup_reuse(const saamg_operator* op, const saamg_hierarchy* 
   });
 }
 
+saamg_status saamg_hierarchy_work_set(const saamg_hierarchy* h, void* stream, saamg_hierarchy** out) {
+  return guard("saamg_hierarchy_work_set", [&] {
+    if (!h || h->magic != kHierMagic || !out) fail(SAAMG_EINVAL, "NULL or invalid argument");
+    *out = nullptr;
+    saamg_hierarchy* owner = h->base ? h->base : const_cast<saamg_hierarchy*>(h);
+    auto w = std::make_unique<saamg_hierarchy>();
+    work_set_impl(h, (cudaStream_t)stream, w.get());
+    w->version = next_version();
+    SAAMG_CUDA(cudaMallocHost(&w->result, sizeof(PcgCtl)));
+    owner->refs.fetch_add(1);
+    w->base = owner;
+    *out = w.release();
+  });
+}
+
 saamg_status saamg_hierarchy_get_info(const saamg_hierarchy* h, saamg_hierarchy_info* info) {
   return guard("saamg_hierarchy_get_info", [&] {
     if (!h || h->magic != kHierMagic || !info) fail(SAAMG_EINVAL, "NULL or invalid argument");
@@ -1710,8 +1821,9 @@ void saamg_free(void* handle) {
       saamg_hierarchy* h = static_cast<saamg_hierarchy*>(handle);
       // asynchronous calls record `done`; the synchronous ones end with a stream sync
       if (h->done) cudaEventSynchronize(h->done);
-      h->magic = 0;
-      delete h;
+      saamg_hierarchy* base = h->base;
+      release_hierarchy(h);
+      if (base) release_hierarchy(base);
     }
   } catch (...) {
   }

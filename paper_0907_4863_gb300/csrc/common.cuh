@@ -73,12 +73,14 @@ void* dev_alloc(const AllocHook& h, size_t bytes, cudaStream_t s);
 void dev_free(const AllocHook& h, void* p, size_t bytes, cudaStream_t s);
 
 // Owning device array (move-only).  Memory comes from the hook captured at allocation.
+// A borrowed Buf views another Buf's array and frees nothing.
 template <class T>
 struct Buf {
   T* p = nullptr;
   size_t n = 0;
   AllocHook hook;
   cudaStream_t stream = nullptr;
+  bool own = true;
 
   Buf() = default;
   Buf(const Buf&) = delete;
@@ -97,16 +99,25 @@ struct Buf {
     std::swap(n, o.n);
     std::swap(hook, o.hook);
     std::swap(stream, o.stream);
+    std::swap(own, o.own);
   }
   void alloc(size_t count, cudaStream_t s) {
     release();
+    own = true;
     hook = current_allocator();
     stream = s;
     n = count;
     p = static_cast<T*>(dev_alloc(hook, (count > 0 ? count : 1) * sizeof(T), s));
   }
+  // views o's array; o must outlive this Buf and keep its array
+  void borrow(const Buf& o) {
+    release();
+    p = o.p;
+    n = o.n;
+    own = false;
+  }
   void release() noexcept {
-    if (p) {
+    if (p && own) {
       try {
         dev_free(hook, p, (n > 0 ? n : 1) * sizeof(T), stream);
       } catch (...) {
@@ -114,6 +125,7 @@ struct Buf {
     }
     p = nullptr;
     n = 0;
+    own = true;
   }
   size_t bytes() const { return n * sizeof(T); }
   T* get() const { return p; }

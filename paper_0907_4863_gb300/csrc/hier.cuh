@@ -2,6 +2,7 @@
 // (internal; shared by the C ABI and the batched solver).
 #pragma once
 
+#include <atomic>
 #include <memory>
 #include <vector>
 
@@ -76,6 +77,11 @@ struct saamg_hierarchy {
   cudaGraphExec_t gexec = nullptr;
   cudaEvent_t done = nullptr;
   saamg::PcgCtl* result = nullptr;  // pinned host copy of the last device-loop solve's scalars
+  // A work set reads the levels (matrices, transfers, aggregates, coarse inverse) of `base`
+  // through borrowed arrays and owns only its vectors and graph.  refs counts the handle
+  // itself and its live work sets; the last release deletes it.
+  saamg_hierarchy* base = nullptr;
+  std::atomic<int> refs{1};
   ~saamg_hierarchy() {
     if (done) cudaEventSynchronize(done);
     if (gexec) cudaGraphExecDestroy(gexec);

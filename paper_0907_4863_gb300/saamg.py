@@ -107,6 +107,7 @@ def lib():
         "saamg_dense_inverse": [_i, _p, _p, _p],
         "saamg_setup": [_p, C.POINTER(Params), _p, C.POINTER(_p)],
         "saamg_setup_reuse": [_p, _p, C.POINTER(Params), _p, C.POINTER(_p)],
+        "saamg_hierarchy_work_set": [_p, _p, C.POINTER(_p)],
         "saamg_hierarchy_get_info": [_p, C.POINTER(HierarchyInfo)],
         "saamg_hierarchy_copy_level": [_p, _i] + [_p] * 12,
         "saamg_vcycle": [_p, _p, _p, _p],
@@ -378,6 +379,15 @@ def setup_reuse(op: Operator, prev: Hierarchy, params: Params = None, stream=Non
                                    C.byref(params) if params is not None else None,
                                    _stream(stream), C.byref(h)))
     return Hierarchy(h, op)
+
+
+@_entry
+def hierarchy_work_set(h: Hierarchy, stream=None) -> Hierarchy:
+    """A second handle over h's levels with its own work vectors (a solve on it may run
+    while another runs on h); h's levels live until h and all its work sets are freed."""
+    w = C.c_void_p()
+    _check(lib().saamg_hierarchy_work_set(h.handle, _stream(stream), C.byref(w)))
+    return Hierarchy(w, h.op)
 
 
 @_entry
