@@ -471,18 +471,36 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
         break;
       }
     }
+    // Reuse: the patterns of P, R, A P and A_{l+1} are prev's, so A T and the symbolic part
+    // of A P (neither depends on lambda_hat) run while the power iteration does, and R and
+    // R (A P) take their patterns from prev.
+    const Level* PL = prev ? prev->lev[l].get() : nullptr;
+    ProlongState pst;
+    SpgemmPlan ap_plan;
+    if (PL) {
+      prolongator_start(A, L.agg.p, nagg, pst, s, &PL->P);
+      spgemm_symbolic(A, PL->P, ap_plan, s);
+      pt.mark("L" + std::to_string(l) + ".early");
+    }
     L.lambda = power_lambda_finish(power, s2);
     L.omega = 4.0 / (3.0 * L.lambda);
     pt.mark("L" + std::to_string(l) + ".lambda");
-    DevCsr AP;
-    prolongator(A, L.agg.p, nagg, L.invd.p, L.omega, L.P, s);
+    if (!PL) prolongator_start(A, L.agg.p, nagg, pst, s);
+    prolongator_finish(pst, L.invd.p, L.omega, L.P, s);
     pt.mark("L" + std::to_string(l) + ".P");
-    transpose(L.P, L.R, s);
+    if (PL) transpose_known(L.P, PL->R, L.R, s);
+    else transpose(L.P, L.R, s);
     pt.mark("L" + std::to_string(l) + ".R");
-    spgemm(A, L.P, AP, s);
+    if (!PL) spgemm_symbolic(A, L.P, ap_plan, s);
+    DevCsr AP;
+    spgemm_numeric(A, L.P, ap_plan, AP, s);
     pt.mark("L" + std::to_string(l) + ".AP");
     auto N = std::make_unique<Level>();
-    spgemm(L.R, AP, N->A, s);
+    {
+      SpgemmPlan rap_plan;
+      spgemm_symbolic(L.R, AP, rap_plan, s, PL ? &prev->lev[l + 1]->A : nullptr);
+      spgemm_numeric(L.R, AP, rap_plan, N->A, s);
+    }
     pt.mark("L" + std::to_string(l) + ".RAP");
     N->n = N->A.n;
     N->nnz = N->A.nnz;

@@ -103,6 +103,63 @@ __device__ __forceinline__ void bitonic64(T& x0, T& x1, int lane) {
   }
 }
 
+// Adds x_p * Y(k_p, :) into the group's value copy for X's entries p = e0 + grp, e0 + grp + NG,
+// ... < e1 (k_p = X.col[p], x_p = X.val[p]); lane gl of a group takes the entries gl, gl + GL,
+// ... of each Y row, so no two lanes of a group add into the same slot at once and every slot
+// receives its products in the group's entry order.  Warp-collective (the whole warp calls it
+// with the same range).  The X entries, their Y row bounds and x_p are loaded 32 at a time, one
+// per lane, and handed to the groups by shuffles; the first Y entry of a group's next X entry
+// is loaded while the current one is added, so a step waits on one global load, not three.
+template <int NG>
+__device__ __forceinline__ void accumulate_entries(int e0, int e1, const CsrView& X,
+                                                   const CsrView& Y, const int* keys, int logcap,
+                                                   double* mine, int lane) {
+  constexpr int GL = 32 / NG;
+  const int grp = lane / GL, gl = lane % GL;
+  for (int cb = e0; cb < e1; cb += 32) {
+    const int cn = min(32, e1 - cb);
+    int rs = 0, re = 0;
+    double xs = 0.0;
+    if (lane < cn) {
+      const int k = X.col[cb + lane];
+      xs = X.val[cb + lane];
+      rs = Y.rowptr[k];
+      re = Y.rowptr[k + 1];
+    }
+    // the group's first entry of the chunk
+    int e = grp;
+    int ys = __shfl_sync(0xffffffffu, rs, e & 31), ye = __shfl_sync(0xffffffffu, re, e & 31);
+    double xv = __shfl_sync(0xffffffffu, xs, e & 31);
+    if (e >= cn) ye = ys;
+    int q = ys + gl;
+    int yc = q < ye ? Y.col[q] : -1;
+    double yv = q < ye ? Y.val[q] : 0.0;
+    for (int eb = 0; eb < cn; eb += NG) {
+      const int en = eb + NG + grp;
+      int nys = __shfl_sync(0xffffffffu, rs, en & 31), nye = __shfl_sync(0xffffffffu, re, en & 31);
+      const double nxv = __shfl_sync(0xffffffffu, xs, en & 31);
+      if (en >= cn) nye = nys;
+      const int nq = nys + gl;
+      const int nyc = nq < nye ? Y.col[nq] : -1;
+      const double nyv = nq < nye ? Y.val[nq] : 0.0;
+      if (yc >= 0) {
+        const int slot = hash_find(keys, logcap, yc);
+        if (slot >= 0) mine[slot] += xv * yv;
+      }
+      for (int qq = q + GL; qq < ye; qq += GL) {
+        const int slot = hash_find(keys, logcap, Y.col[qq]);
+        if (slot >= 0) mine[slot] += xv * Y.val[qq];
+      }
+      __syncwarp();
+      ye = nye;
+      xv = nxv;
+      q = nq;
+      yc = nyc;
+      yv = nyv;
+    }
+  }
+}
+
 // Warp-wide exclusive prefix of v; *total gets the sum over the warp.
 __device__ __forceinline__ int warp_excl_scan(int v, int lane, int* total) {
   int inc = v;
@@ -276,19 +333,7 @@ __global__ void __launch_bounds__(128, 16) spgemm_hash_numeric_k(const int* __re
       }
       __syncwarp();
     }
-    double* mine = vals + (size_t)grp * cstride;
-    for (int pb = p0; pb < p1; pb += NG) {
-      const int p = pb + grp;
-      if (p < p1) {
-        const int k = X.col[p];
-        const double xv = X.val[p];
-        for (int q = Y.rowptr[k] + gl; q < Y.rowptr[k + 1]; q += GL) {
-          const int slot = hash_find(keys, logcap, Y.col[q]);
-          if (slot >= 0) mine[slot] += xv * Y.val[q];
-        }
-      }
-      __syncwarp();
-    }
+    accumulate_entries<NG>(p0, p1, X, Y, keys, logcap, vals + (size_t)grp * cstride, lane);
     const int base = crowptr[i];
     for (int q = lane; q < cap; q += 32) {
       const int key = keys[q];
@@ -395,18 +440,7 @@ __global__ void __launch_bounds__(256) spgemm_hash_numeric_blk_k(const int* __re
     // warp w: entries [p0 + w * share, p0 + (w + 1) * share), its groups in turn
     const int share = (p1 - p0 + nwarps - 1) / nwarps;
     const int w0 = p0 + warp * share, w1 = min(p1, w0 + share);
-    for (int pb = w0; pb < w1; pb += NG) {
-      const int p = pb + grp;
-      if (p < w1) {
-        const int k = X.col[p];
-        const double xv = X.val[p];
-        for (int q = Y.rowptr[k] + gl; q < Y.rowptr[k + 1]; q += GL) {
-          const int slot = hash_find(keys, logcap, Y.col[q]);
-          if (slot >= 0) mine[slot] += xv * Y.val[q];
-        }
-      }
-      __syncwarp();
-    }
+    accumulate_entries<NG>(w0, w1, X, Y, keys, logcap, mine, lane);
     __syncthreads();
     const int base = crowptr[i];
     for (int q = threadIdx.x; q < cap; q += blockDim.x) {
@@ -652,6 +686,30 @@ __global__ void scatter_rows_k(int n, const int* __restrict__ cls, int* __restri
     base[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], cnt[threadIdx.x]);
   __syncthreads();
   if (c >= 0) list[base[c] + local] = i;
+}
+
+__global__ void row_lengths_k(int n, const int* __restrict__ rowptr, int* __restrict__ len) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) len[i] = rowptr[i + 1] - rowptr[i];
+}
+
+// Thread per row i of P: entry (i, J) goes to the place of column i in row J of R (columns
+// ascending: a binary search).
+__global__ void transpose_known_k(int n, const int* __restrict__ prow, const int* __restrict__ pcol,
+                                  const double* __restrict__ pval, const int* __restrict__ rrow,
+                                  const int* __restrict__ rcol, double* __restrict__ rval) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int p = prow[i]; p < prow[i + 1]; ++p) {
+    const int J = pcol[p];
+    int lo = rrow[J], hi = rrow[J + 1];
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (rcol[mid] < i) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo < rrow[J + 1] && rcol[lo] == i) rval[lo] = pval[p];
+  }
 }
 
 // P_iJ = [J == agg(i)] - (omega * invd_i) * (AT)_iJ
@@ -1061,119 +1119,179 @@ void run_class(int c, const int* list, int nl, CsrView X, CsrView Y, double yavg
 
 }  // namespace
 
-void spgemm(const DevCsr& X, const DevCsr& Y, DevCsr& C, cudaStream_t s) {
+void spgemm_symbolic(const DevCsr& X, const DevCsr& Y, SpgemmPlan& plan, cudaStream_t s,
+                     const DevCsr* known) {
   const int n = X.n;
-  C.n = n;
-  C.m = Y.m;
-  C.rowptr.alloc(n + 1, s);
+  plan.n = n;
+  plan.m = Y.m;
+  plan.rowptr.alloc(n + 1, s);
+  plan.hist.assign(kClasses, 0);
+  plan.start.assign(kClasses + 1, 0);
+  plan.keys = plan.koff = nullptr;
   if (n == 0) {
-    fill_int(C.rowptr.p, 0, 1, s);
-    C.nnz = 0;
-    C.col.alloc(0, s);
-    C.val.alloc(0, s);
+    fill_int(plan.rowptr.p, 0, 1, s);
+    plan.nnz = 0;
     return;
   }
-  const double yavg = Y.n > 0 ? (double)Y.nnz / Y.n : 0.0;
-  Buf<int> nprod, cls, list, cnt, ctl;
-  nprod.alloc(n, s);
-  cls.alloc(n, s);
-  list.alloc(n, s);
-  cnt.alloc(n + 1, s);
-  ctl.alloc(2 * kClasses + 1, s);
-  int* overflow = ctl.p + 2 * kClasses;
-  SAAMG_CUDA(cudaMemsetAsync(overflow, 0, sizeof(int), s));
+  plan.yavg = Y.n > 0 ? (double)Y.nnz / Y.n : 0.0;
+  plan.nprod.alloc(n, s);
+  plan.cls.alloc(n, s);
+  plan.list.alloc(n, s);
+  plan.ctl.alloc(2 * kClasses + 1, s);
+  int* nprod = plan.nprod.p;
+  int* ctl = plan.ctl.p;
   if (n < 32768 && (double)X.nnz > 32.0 * n) {
-    row_products_warp_k<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, view(X), view(Y), nprod.p);
+    row_products_warp_k<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, view(X), view(Y), nprod);
   } else {
-    row_products_k<<<blocks_for(n), 256, 0, s>>>(n, view(X), view(Y), nprod.p);
+    row_products_k<<<blocks_for(n), 256, 0, s>>>(n, view(X), view(Y), nprod);
   }
   SAAMG_LAUNCH();
-  int hist[kClasses], start[kClasses + 1];
-  // symbolic: distinct columns per row
-  bin_rows(n, X.rowptr.p, nprod.p, nullptr, Y.m, cls.p, list.p, ctl.p, hist, start, s);
-  // the warp hash passes leave each row's sorted columns for the numeric pass (room
-  // min(products, columns) per row) when the total fits 32-bit offsets
-  unsigned warp_classes = 0;
-  for (int c = 2; c < kClasses; ++c)
-    if (hist[c] > kFewRows) warp_classes |= 1u << c;
-  Buf<int> soff, skeys;
-  if (warp_classes) {
-    Buf<int> caps;
-    caps.alloc(n + 1, s);
-    hash_caps_k<<<blocks_for(n + 1), 256, 0, s>>>(n, cls.p, nprod.p, Y.m, warp_classes, caps.p);
+  Buf<int> cnt;
+  cnt.alloc(n + 1, s);
+  if (known) {
+    // C's pattern is known: its row lengths bin the rows, its columns are the sorted keys
+    if (known->n != n || known->m != Y.m) fail(SAAMG_EINVAL, "known product pattern has other sizes");
+    SAAMG_CUDA(cudaMemcpyAsync(plan.rowptr.p, known->rowptr.p, sizeof(int) * (n + 1),
+                               cudaMemcpyDeviceToDevice, s));
+    row_lengths_k<<<blocks_for(n), 256, 0, s>>>(n, known->rowptr.p, cnt.p);
     SAAMG_LAUNCH();
-    soff.alloc(n + 1, s);
-    const long long total = exclusive_scan(caps.p, soff.p, n + 1, s);
-    if (total > 0 && total < 0x7fffffffLL) skeys.alloc(total, s);
-    else soff.release();
+    plan.nnz = known->nnz;
+    plan.keys = known->col.p;
+    plan.koff = known->rowptr.p;
+  } else {
+    int* overflow = ctl + 2 * kClasses;
+    SAAMG_CUDA(cudaMemsetAsync(overflow, 0, sizeof(int), s));
+    int hist[kClasses], start[kClasses + 1];
+    // symbolic: distinct columns per row
+    bin_rows(n, X.rowptr.p, nprod, nullptr, Y.m, plan.cls.p, plan.list.p, ctl, hist, start, s);
+    // the warp hash passes leave each row's sorted columns for the numeric pass (room
+    // min(products, columns) per row) when the total fits 32-bit offsets
+    unsigned warp_classes = 0;
+    for (int c = 2; c < kClasses; ++c)
+      if (hist[c] > kFewRows) warp_classes |= 1u << c;
+    if (warp_classes) {
+      Buf<int> caps;
+      caps.alloc(n + 1, s);
+      hash_caps_k<<<blocks_for(n + 1), 256, 0, s>>>(n, plan.cls.p, nprod, Y.m, warp_classes, caps.p);
+      SAAMG_LAUNCH();
+      plan.soff.alloc(n + 1, s);
+      const long long total = exclusive_scan(caps.p, plan.soff.p, n + 1, s);
+      if (total > 0 && total < 0x7fffffffLL) plan.skeys.alloc(total, s);
+      else plan.soff.release();
+    }
+    for (int c = 0; c < kClasses; ++c)
+      run_class<false>(c, plan.list.p + start[c], hist[c], view(X), view(Y), plan.yavg, nullptr,
+                       cnt.p, overflow, nullptr, nullptr, plan.skeys.p, plan.soff.p, s);
+    int nover = 0;
+    d2h_sync(&nover, overflow, sizeof(int), s);
+    if (nover) fail(SAAMG_UNIMPLEMENTED, "sparse product row with more than 2048 distinct columns");
+    fill_int(cnt.p + n, 0, 1, s);
+    const long long nnz = exclusive_scan(cnt.p, plan.rowptr.p, n + 1, s);
+    if (nnz > 0x7fffffffLL) fail(SAAMG_EINVAL, "more than 2^31 nonzeros in a coarse operator");
+    plan.nnz = nnz;
+    plan.keys = plan.skeys.p;
+    plan.koff = plan.soff.p;
   }
+  // numeric classes: tables sized from the exact counts
+  bin_rows(n, X.rowptr.p, nprod, cnt.p, Y.m, plan.cls.p, plan.list.p, ctl, plan.hist.data(),
+           plan.start.data(), s);
+}
+
+void spgemm_numeric(const DevCsr& X, const DevCsr& Y, SpgemmPlan& plan, DevCsr& C, cudaStream_t s) {
+  const int n = plan.n;
+  C.n = n;
+  C.m = plan.m;
+  C.nnz = plan.nnz;
+  C.rowptr = std::move(plan.rowptr);
+  C.col.alloc(plan.nnz, s);
+  C.val.alloc(plan.nnz, s);
+  if (n == 0) return;
   for (int c = 0; c < kClasses; ++c)
-    run_class<false>(c, list.p + start[c], hist[c], view(X), view(Y), yavg, nullptr, cnt.p, overflow,
-                     nullptr, nullptr, skeys.p, soff.p, s);
-  int nover = 0;
-  d2h_sync(&nover, overflow, sizeof(int), s);
-  if (nover) fail(SAAMG_UNIMPLEMENTED, "sparse product row with more than 2048 distinct columns");
-  fill_int(cnt.p + n, 0, 1, s);
-  long long nnz = exclusive_scan(cnt.p, C.rowptr.p, n + 1, s);
-  if (nnz > 0x7fffffffLL) fail(SAAMG_EINVAL, "more than 2^31 nonzeros in a coarse operator");
-  C.nnz = nnz;
-  C.col.alloc(nnz, s);
-  C.val.alloc(nnz, s);
-  // numeric: tables sized from the exact counts
-  bin_rows(n, X.rowptr.p, nprod.p, cnt.p, Y.m, cls.p, list.p, ctl.p, hist, start, s);
-  for (int c = 0; c < kClasses; ++c)
-    run_class<true>(c, list.p + start[c], hist[c], view(X), view(Y), yavg, C.rowptr.p, nullptr, nullptr,
-                    C.col.p, C.val.p, skeys.p, soff.p, s);
+    run_class<true>(c, plan.list.p + plan.start[c], plan.hist[c], view(X), view(Y), plan.yavg,
+                    C.rowptr.p, nullptr, nullptr, C.col.p, C.val.p, const_cast<int*>(plan.keys), plan.koff, s);
+}
+
+void spgemm(const DevCsr& X, const DevCsr& Y, DevCsr& C, cudaStream_t s) {
+  SpgemmPlan plan;
+  spgemm_symbolic(X, Y, plan, s);
+  spgemm_numeric(X, Y, plan, C, s);
 }
 
 void smoothed_prolongator(DevCsr& AT, const int* agg, const double* invd, double omega,
                           DevCsr& P, cudaStream_t s);
 
-void prolongator(const DevCsr& A, const int* agg, int nagg, const double* invd, double omega,
-                 DevCsr& P, cudaStream_t s) {
+void prolongator_start(const DevCsr& A, const int* agg, int nagg, ProlongState& st,
+                       cudaStream_t s, const DevCsr* known) {
   const int n = A.n;
+  st.n = n;
+  st.nagg = nagg;
+  st.A = &A;
+  st.agg = agg;
   const double avg = n > 0 ? (double)A.nnz / n : 0.0;
-  if (avg <= 8.0) {  // short rows (level 0): T and the register k-way merge product
-    DevCsr T, AT;
+  st.lists = avg > 8.0;
+  if (!st.lists) {  // short rows (level 0): T and the register k-way merge product
+    DevCsr T;
     tentative(agg, n, nagg, T, s);
-    spgemm(A, T, AT, s);
-    smoothed_prolongator(AT, agg, invd, omega, P, s);
+    SpgemmPlan plan;
+    spgemm_symbolic(A, T, plan, s, known);
+    spgemm_numeric(A, T, plan, st.AT, s);
     return;
   }
+  DevCsr& P = st.AT;  // P's row pointers and size
   P.n = n;
   P.m = nagg;
   P.rowptr.alloc(n + 1, s);
-  Buf<int> lcol, cnt;
-  Buf<double> lval;
-  lcol.alloc(A.nnz, s);
-  lval.alloc(A.nnz, s);
+  Buf<int> cnt;
+  st.lcol.alloc(A.nnz, s);
+  st.lval.alloc(A.nnz, s);
   cnt.alloc(n + 1, s);
-  const int G = avg <= 16.0 ? 16 : 32;
+  st.G = avg <= 16.0 ? 16 : 32;
   const bool sortable = nagg < (1 << 25);  // (aggregate << 6 | entry) stays below 0xffffffff
-  const int blocks = (int)std::min<long long>(((long long)n * G + 255) / 256, sm_count() * 32);
+  const int blocks = (int)std::min<long long>(((long long)n * st.G + 255) / 256, sm_count() * 32);
   {
     KernelTimer kt(SAAMG_KT_SPGEMM, n, s);
-    if (G == 16)
-      at_lists_k<16><<<blocks, 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, agg, lcol.p, lval.p,
-                                            cnt.p, sortable);
+    if (st.G == 16)
+      at_lists_k<16><<<blocks, 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, agg, st.lcol.p,
+                                            st.lval.p, cnt.p, sortable);
     else
-      at_lists_k<32><<<blocks, 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, agg, lcol.p, lval.p,
-                                            cnt.p, sortable);
+      at_lists_k<32><<<blocks, 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, agg, st.lcol.p,
+                                            st.lval.p, cnt.p, sortable);
     SAAMG_LAUNCH();
   }
   fill_int(cnt.p + n, 0, 1, s);
-  const long long nnz = exclusive_scan(cnt.p, P.rowptr.p, n + 1, s);
-  P.nnz = nnz;
-  P.col.alloc(nnz, s);
-  P.val.alloc(nnz, s);
+  P.nnz = exclusive_scan(cnt.p, P.rowptr.p, n + 1, s);
+}
+
+void prolongator_finish(ProlongState& st, const double* invd, double omega, DevCsr& P,
+                        cudaStream_t s) {
+  if (!st.lists) {
+    smoothed_prolongator(st.AT, st.agg, invd, omega, P, s);
+    return;
+  }
+  const int n = st.n;
+  const DevCsr& A = *st.A;
+  P.n = n;
+  P.m = st.nagg;
+  P.nnz = st.AT.nnz;
+  P.rowptr = std::move(st.AT.rowptr);
+  P.col.alloc(P.nnz, s);
+  P.val.alloc(P.nnz, s);
+  const int blocks = (int)std::min<long long>(((long long)n * st.G + 255) / 256, sm_count() * 32);
   KernelTimer kt(SAAMG_KT_SPGEMM, n, s);
-  if (G == 16)
-    at_prolong_k<16><<<blocks, 256, 0, s>>>(n, A.rowptr.p, lcol.p, lval.p, P.rowptr.p, agg, invd,
-                                            omega, P.col.p, P.val.p);
+  if (st.G == 16)
+    at_prolong_k<16><<<blocks, 256, 0, s>>>(n, A.rowptr.p, st.lcol.p, st.lval.p, P.rowptr.p,
+                                            st.agg, invd, omega, P.col.p, P.val.p);
   else
-    at_prolong_k<32><<<blocks, 256, 0, s>>>(n, A.rowptr.p, lcol.p, lval.p, P.rowptr.p, agg, invd,
-                                            omega, P.col.p, P.val.p);
+    at_prolong_k<32><<<blocks, 256, 0, s>>>(n, A.rowptr.p, st.lcol.p, st.lval.p, P.rowptr.p,
+                                            st.agg, invd, omega, P.col.p, P.val.p);
   SAAMG_LAUNCH();
+}
+
+void prolongator(const DevCsr& A, const int* agg, int nagg, const double* invd, double omega,
+                 DevCsr& P, cudaStream_t s) {
+  ProlongState st;
+  prolongator_start(A, agg, nagg, st, s);
+  prolongator_finish(st, invd, omega, P, s);
 }
 
 void smoothed_prolongator(DevCsr& AT, const int* agg, const double* invd, double omega,
@@ -1220,6 +1338,24 @@ void transpose(const DevCsr& P, DevCsr& R, cudaStream_t s) {
     rank_rows_k<<<blocks, 256, 0, s>>>(R.n, R.rowptr.p, tcol.p, tval.p, R.col.p, R.val.p);
     SAAMG_LAUNCH();
   }
+}
+
+void transpose_known(const DevCsr& P, const DevCsr& known, DevCsr& R, cudaStream_t s) {
+  if (known.n != P.m || known.m != P.n || known.nnz != P.nnz)
+    fail(SAAMG_EINVAL, "known transpose pattern has other sizes");
+  R.n = P.m;
+  R.m = P.n;
+  R.nnz = P.nnz;
+  R.rowptr.alloc(R.n + 1, s);
+  R.col.alloc(R.nnz, s);
+  R.val.alloc(R.nnz, s);
+  SAAMG_CUDA(cudaMemcpyAsync(R.rowptr.p, known.rowptr.p, sizeof(int) * (R.n + 1),
+                             cudaMemcpyDeviceToDevice, s));
+  if (R.nnz == 0) return;
+  SAAMG_CUDA(cudaMemcpyAsync(R.col.p, known.col.p, sizeof(int) * R.nnz, cudaMemcpyDeviceToDevice, s));
+  transpose_known_k<<<blocks_for(P.n), 256, 0, s>>>(P.n, P.rowptr.p, P.col.p, P.val.p,
+                                                    known.rowptr.p, known.col.p, R.val.p);
+  SAAMG_LAUNCH();
 }
 
 }  // namespace saamg

@@ -1,6 +1,8 @@
 // Hierarchy construction kernels (internal): spectral bound, prolongator, Galerkin product.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace saamg {
@@ -32,12 +34,52 @@ double power_lambda_finish(PowerRun& run, cudaStream_t s);
 // product is bitwise reproducible.
 void spgemm(const DevCsr& X, const DevCsr& Y, DevCsr& C, cudaStream_t s);
 
+// The two phases of spgemm.  The symbolic phase reads the patterns of X and Y only and leaves
+// C's row pointers, the rows binned by the numeric kernel class and the sorted columns of the
+// hash rows in the plan; the numeric phase then needs matrices with those patterns and their
+// values.  With `known` given (the C of an earlier product whose factors had the patterns of
+// X and Y), C's pattern is taken from it and no symbolic pass runs; `known` must outlive the
+// numeric phase.  Either way the numeric phase gives the bits of spgemm.
+struct SpgemmPlan {
+  int n = 0, m = 0;
+  long long nnz = 0;
+  double yavg = 0;
+  Buf<int> rowptr;                 // C's row pointers
+  Buf<int> nprod, cls, list, ctl;
+  std::vector<int> hist, start;    // the numeric classes: row counts and list offsets
+  Buf<int> soff, skeys;            // sorted columns the symbolic hash passes wrote
+  const int* keys = nullptr;       // the sorted columns the numeric pass reads (or NULL) ...
+  const int* koff = nullptr;       // ... and their row offsets
+};
+void spgemm_symbolic(const DevCsr& X, const DevCsr& Y, SpgemmPlan& plan, cudaStream_t s,
+                     const DevCsr* known = nullptr);
+void spgemm_numeric(const DevCsr& X, const DevCsr& Y, SpgemmPlan& plan, DevCsr& C, cudaStream_t s);
+
 // P = (I - omega D^-1 A) T straight from A and the aggregates (T(i, agg(i)) = 1), without
 // forming T or a general sparse product; nagg = the number of aggregates.
 void prolongator(const DevCsr& A, const int* agg, int nagg, const double* invd, double omega,
                  DevCsr& P, cudaStream_t s);
+// The same in two halves: _start forms A T (the part that does not depend on omega; `known`,
+// a prolongator of the same pattern, spares the symbolic pass of the short-row path),
+// _finish the values of P.
+struct ProlongState {
+  int n = 0, nagg = 0, G = 0;
+  bool lists = false;              // rows of A longer than 8 entries: aggregate lists
+  DevCsr AT;                       // short rows: A T; lists: P's row pointers and counts
+  Buf<int> lcol;
+  Buf<double> lval;
+  const DevCsr* A = nullptr;
+  const int* agg = nullptr;
+};
+void prolongator_start(const DevCsr& A, const int* agg, int nagg, ProlongState& st,
+                       cudaStream_t s, const DevCsr* known = nullptr);
+void prolongator_finish(ProlongState& st, const double* invd, double omega, DevCsr& P,
+                        cudaStream_t s);
 
 // R = P^T with ascending columns in every row.
 void transpose(const DevCsr& P, DevCsr& R, cudaStream_t s);
+// The same when R's pattern is known (`known`, the transpose of a P of the same pattern):
+// the pattern is copied and every value moved to its place (a search in its row of R).
+void transpose_known(const DevCsr& P, const DevCsr& known, DevCsr& R, cudaStream_t s);
 
 }  // namespace saamg
