@@ -151,6 +151,19 @@ struct __align__(32) LineInfo {
   int lo, hi, start, rlo, rhi, tstart, pad0, pad1;
 };
 
+// One record per chunk of <= 32 consecutive unknowns of one line, everything a warp needs to
+// apply it in one 32-byte load: the chunk's first compact row, the table row of its lane 0
+// (left of the regular run), the lanes [a, b] of the chunk inside the regular run (the table
+// row of a lane j > b is tl + j + (a - b) - 1), the number of unknowns n, and the line's
+// neighbour row offsets (as nbr).
+struct __align__(32) ChunkRec {
+  int row0, tl;
+  short a, b;  // read as one int: a in the low half
+  int n;
+  int ym, yp, zm, zp;
+};
+static_assert(sizeof(ChunkRec) == 32, "ChunkRec is two 16-byte loads");
+
 template <class T>
 struct StencilDev {
   const LineInfo* lines;
@@ -158,6 +171,7 @@ struct StencilDev {
   // +z line (start' - lo') - (start - lo); 0 where that line does not exist or is empty
   const int4* nbr;
   const int2* chunks;  // (line, offset of the first of <= 32 consecutive unknowns)
+  const ChunkRec* crec;  // the same chunks as applied by the FP32 passes
   int nchunks;
   const int* rline;    // line of every compact row (the FP64 passes take 32 consecutive rows)
   int n;               // unknowns

@@ -617,10 +617,33 @@ __global__ void scatter_k(const GeomParams g, const LineInfo* __restrict__ lines
 
 inline int warp_blocks(long long warps) { return (int)((warps * 32 + 255) / 256); }
 
+__global__ void chunk_records_k(const LineInfo* __restrict__ lines, const int4* __restrict__ nbr,
+                                const int2* __restrict__ chunks, int nchunks,
+                                ChunkRec* __restrict__ crec) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nchunks) return;
+  const int2 ch = chunks[c];
+  const LineInfo me = lines[ch.x];
+  const int4 nb = nbr[ch.x];
+  ChunkRec r;
+  r.row0 = me.start + ch.y;
+  r.tl = me.tstart + ch.y;
+  r.a = (short)(me.rlo - me.lo - ch.y);
+  r.b = (short)(me.rhi - me.lo - ch.y);
+  r.n = min(32, me.hi - me.lo + 1 - ch.y);
+  r.ym = nb.x;
+  r.yp = nb.y;
+  r.zm = nb.z;
+  r.zp = nb.w;
+  crec[c] = r;
+}
+
 }  // namespace
 
 void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op) {
   op.g = g;
+  // chunk records hold lane offsets within a line as 16-bit values
+  if (g.nx > 30000) fail(SAAMG_EINVAL, "more than 30000 nodes along x");
   long long nl = (long long)g.ny * g.nz;
   if (nl > INT_MAX / 32) fail(SAAMG_EINVAL, "grid too large");
   int nlines = (int)nl;
@@ -716,6 +739,12 @@ void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op) 
   op.ntable = (int)nt;
   set_tstart_k<<<(nlines + 255) / 256, 256, 0, s>>>(op.lines.p, tstart.p, nlines);
   SAAMG_LAUNCH();
+  op.crec.alloc(op.nchunks, s);
+  if (op.nchunks > 0) {
+    chunk_records_k<<<(op.nchunks + 255) / 256, 256, 0, s>>>(op.lines.p, op.nbr.p, op.chunks.p,
+                                                            op.nchunks, op.crec.p);
+    SAAMG_LAUNCH();
+  }
   {
     Buf<int> rcnt, rstart;
     rcnt.alloc(nlines, s);
@@ -752,6 +781,7 @@ StencilDev<double> OperatorData::view<double>() const {
   v.lines = lines.p;
   v.nbr = nbr.p;
   v.chunks = chunks.p;
+  v.crec = crec.p;
   v.nchunks = nchunks;
   v.rline = rline.p;
   v.n = n;
@@ -777,6 +807,7 @@ StencilDev<float> OperatorData::view<float>() const {
   v.lines = lines.p;
   v.nbr = nbr.p;
   v.chunks = chunks.p;
+  v.crec = crec.p;
   v.nchunks = nchunks;
   v.rline = rline.p;
   v.n = n;

@@ -24,6 +24,7 @@ struct OperatorData {
   Buf<LineInfo> lines;
   Buf<int4> nbr;        // per line: row offsets to the -y, +y, -z, +z neighbour lines
   Buf<int2> chunks;
+  Buf<ChunkRec> crec;
   int nchunks = 0;
   Buf<int> rline;       // line of every compact row
   Buf<double> table;    // 8 doubles per table row
@@ -39,7 +40,7 @@ struct OperatorData {
   Buf<unsigned char> nbmask;  // bit q: neighbour q (-x,+x,-y,+y,-z,+z) is an unknown
   DevCsr A;             // explicit scaled CSR (used by the AMG setup)
   size_t bytes() const {
-    return lines.bytes() + nbr.bytes() + chunks.bytes() + rline.bytes() + table.bytes() +
+    return lines.bytes() + nbr.bytes() + chunks.bytes() + crec.bytes() + rline.bytes() + table.bytes() +
            table32.bytes() + trow.bytes() + rrow.bytes() + scale.bytes() +
            ids.bytes() + regular.bytes() + nbmask.bytes() + A.bytes();
   }

@@ -59,15 +59,15 @@ __device__ __forceinline__ void load8(const float* p, float v[8]) {
 // PACKED: chunk c is entries [32 c, 32 c + 32) of the list of regular-run rows, each lane
 // finding its own line (no lane idles at the end of a line or on a table row); chunk c of the
 // TABLE phase is the table rows [32 c, 32 c + 32), so no warp runs both kinds of row.
-// Otherwise chunk c is (line, offset) from the chunk list.
+// Otherwise chunk c is the chunk record c.
 template <class T, int MODE, bool PACKED, bool TABLE = false>
 __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int lane,
                                             const T* __restrict__ x, T* __restrict__ y,
                                             const T* __restrict__ b, T* __restrict__ d, T c1,
                                             T c2, T c2invd0, double& dacc,
                                             const int* __restrict__ agg) {
-    int row, i;
-    LineInfo me;
+    int row;
+    int ra = 0, rb = 0, tl = 0;  // chunk path: lanes of the regular run, table row of lane 0
     int4 nb;
     int t = -1;  // table row, if any
     if (TABLE) {
@@ -82,18 +82,21 @@ __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int l
       row = rl.x;
       nb = S.nbr[rl.y];
     } else {
-      const int2 ch = S.chunks[c];
-      me = S.lines[ch.x];
-      nb = S.nbr[ch.x];
-      i = me.lo + ch.y + lane;
-      if (i > me.hi) return;
-      row = me.start + ch.y + lane;
+      // the record as two 16-byte loads: (row0, tl, a | b << 16, n), then the offsets
+      const int4* q = reinterpret_cast<const int4*>(S.crec + c);
+      const int4 h0 = q[0];
+      nb = q[1];
+      if (lane >= h0.w) return;
+      row = h0.x + lane;
+      tl = h0.y;
+      ra = (int)(short)(h0.z & 0xffff);
+      rb = h0.z >> 16;
     }
     T a0 = S.c0, axm = S.cx, axp = S.cx, aym = S.cy, ayp = S.cy, azm = S.cz, azp = S.cz;
     T c2i = c2invd0;
     int oxm = -1, oxp = 1, oym = nb.x, oyp = nb.y, ozm = nb.z, ozp = nb.w;
-    if (!TABLE && !PACKED && (i < me.rlo || i > me.rhi))
-      t = me.tstart + (i < me.rlo ? i - me.lo : (me.rlo - me.lo) + (i - me.rhi - 1));
+    if (!TABLE && !PACKED && (lane < ra || lane > rb))
+      t = tl + lane + (lane < ra ? 0 : ra - rb - 1);
     if (TABLE || (!PACKED && t >= 0)) {
       T tb[8];
       load8(S.table + 8 * (size_t)t, tb);
