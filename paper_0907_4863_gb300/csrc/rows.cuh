@@ -234,13 +234,20 @@ __device__ __forceinline__ void dot2_block(int blk, int n, const double* __restr
   double a1 = 0.0, a2 = 0.0;
   const int st = kRedBlocks * kRedThreads;
   int i = blk * kRedThreads + threadIdx.x;
-  for (; i + st < n; i += 2 * st) {
-    const double z0 = (double)z[i], z1 = (double)z[i + st];
-    const double r0 = r[i], r1 = r[i + st], q0 = q[i], q1 = q[i + st];
-    a1 += r0 * z0;
-    a2 += z0 * q0;
-    a1 += r1 * z1;
-    a2 += z1 * q1;
+  // loads of four grid strides in flight (the fixed grid holds half the warps an SM can)
+  for (; i + 3 * st < n; i += 4 * st) {
+    double zz[4], rr[4], qq[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      zz[u] = (double)z[i + u * st];
+      rr[u] = r[i + u * st];
+      qq[u] = q[i + u * st];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a1 += rr[u] * zz[u];
+      a2 += zz[u] * qq[u];
+    }
   }
   for (; i < n; i += st) {
     const double zi = (double)z[i];
@@ -259,7 +266,24 @@ __device__ __forceinline__ double update_block(int blk, int n, double a, double*
                                                const double* __restrict__ q,
                                                float* __restrict__ r32) {
   double acc = 0.0;
-  for (int i = blk * kRedThreads + threadIdx.x; i < n; i += kRedBlocks * kRedThreads) {
+  const int st = kRedBlocks * kRedThreads;
+  int i = blk * kRedThreads + threadIdx.x;
+  // two grid strides per step, every load before the stores
+  for (; i + st < n; i += 2 * st) {
+    const double x0 = x[i], x1 = x[i + st], p0 = p[i], p1 = p[i + st];
+    const double rv0 = r[i], rv1 = r[i + st], q0 = q[i], q1 = q[i + st];
+    x[i] = x0 + a * p0;
+    const double ri0 = rv0 - a * q0;
+    r[i] = ri0;
+    if (r32) r32[i] = (float)ri0;
+    acc += ri0 * ri0;
+    x[i + st] = x1 + a * p1;
+    const double ri1 = rv1 - a * q1;
+    r[i + st] = ri1;
+    if (r32) r32[i + st] = (float)ri1;
+    acc += ri1 * ri1;
+  }
+  for (; i < n; i += st) {
     x[i] = x[i] + a * p[i];
     double ri = r[i] - a * q[i];
     r[i] = ri;

@@ -211,17 +211,24 @@ __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __res
   // packed: the regular-run chunks, then the table chunks (the branch is uniform per warp)
   const int nreg = kPacked ? (S.nrun + 31) / 32 : S.nchunks;
   const int nch = kPacked ? nreg + (S.ntable + 31) / 32 : nreg;
-  for (int c0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * K; c0 < nch; c0 += nw * K) {
+  // the reductions' fixed grid holds half the warps an SM can: there a step takes two grid
+  // strides (the chunks and their order per lane are those of one stride per step)
+  constexpr int U = (MODE == ST_SPMV_DOT || MODE == ST_DINV_DOT) ? 2 : 1;
+  for (int cs = (blockIdx.x * wpb + (threadIdx.x >> 5)) * K; cs < nch; cs += U * nw * K) {
 #pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (c0 + k < nch) {
-        if (kPacked && c0 + k >= nreg)
-          stencil_row<T, MODE, true, true>(S, c0 + k - nreg, lane, x, y, b, d, c1, c2, c2invd0,
-                                           dacc, agg);
-        else
-          stencil_row<T, MODE, kPacked>(S, c0 + k, lane, x, y, b, d, c1, c2, c2invd0, dacc,
-                                        agg);
-      }
+    for (int u = 0; u < U; ++u) {
+      const int c0 = cs + u * nw * K;
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (c0 + k < nch) {
+          if (kPacked && c0 + k >= nreg)
+            stencil_row<T, MODE, true, true>(S, c0 + k - nreg, lane, x, y, b, d, c1, c2,
+                                             c2invd0, dacc, agg);
+          else
+            stencil_row<T, MODE, kPacked>(S, c0 + k, lane, x, y, b, d, c1, c2, c2invd0, dacc,
+                                          agg);
+        }
+    }
   }
   if (MODE == ST_SPMV_DOT || MODE == ST_DINV_DOT) {
     __shared__ double sh[32];
