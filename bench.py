@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the mixed-precision and reuse legs")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (64 instances) leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default level-0 stencil launch shapes")
     ap.add_argument("--serve-requests", type=int, default=10000,
                     help="requests of the 10,000-request serving stream to replay")
     return ap.parse_args()
@@ -154,6 +156,33 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+# Level-0 stencil launch shapes chosen by the autotuner for the workload (precision 0: FP64
+# passes, 1: FP32), applied to every operator the bench builds for it.
+SHAPES = {}
+
+
+def shaped_operator(S, dom, grid, mode):
+    op = S.build_operator(dom, grid, mode)
+    for sp, cfg in SHAPES.items():
+        S.set_stencil_config(op, sp, cfg)
+    return op
+
+
+def tune_shapes(S, dom, grid, mode):
+    """Autotunes the level-0 stencil launch shape of both precisions once per workload."""
+    op = S.build_operator(dom, grid, mode)
+    out = {}
+    for sp in (0, 1):
+        default = S.stencil_config(op, sp)
+        best, us = S.autotune_stencil(op, sp)
+        S.set_stencil_config(op, sp, default)
+        SHAPES[sp] = best
+        out["fp64" if sp == 0 else "fp32"] = {"default": default, "chosen": best,
+                                              "chebyshev_step_us": us}
+    op.free()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_0907_4863_gb300 import saamg as S
@@ -175,9 +204,11 @@ def run_ours(args):
     phis = [torch.zeros_like(r) for r in rhs]
     stream = torch.cuda.current_stream()
     infos = []
+    # once per workload, before the warm-up steps (like any autotuned kernel)
+    shapes = None if args.no_autotune else tune_shapes(S, dom, grid, w.mode)
 
     def step(k):
-        op = S.build_operator(dom, grid, w.mode)
+        op = shaped_operator(S, dom, grid, w.mode)
         h = S.setup(op, params)
         phis[k].zero_()
         info = S.solve(h, rhs[k], phis[k], rtol=RTOL)
@@ -218,7 +249,7 @@ def run_ours(args):
     for c in range(len(S.KT_NAMES)):
         S.kernel_timing_read(c)
     for k in range(args.warmup, nsteps):
-        op_t = S.build_operator(dom, grid, w.mode)
+        op_t = shaped_operator(S, dom, grid, w.mode)
         h_t = S.setup(op_t, params_t)
         phis[k].zero_()
         S.solve(h_t, rhs[k], phis[k], rtol=RTOL)
@@ -252,7 +283,7 @@ def run_ours(args):
     host_phi = torch.zeros(nbox, dtype=torch.float64).pin_memory()
 
     def e2e_step(k):
-        op = S.build_operator(dom, grid, w.mode)
+        op = shaped_operator(S, dom, grid, w.mode)
         h = S.setup(op, params)
         host_phi.zero_()
         info = S.solve_host(h, host_rho[k].numpy(), host_phi.numpy(), rtol=RTOL)
@@ -298,6 +329,7 @@ def run_ours(args):
         "host_wall_ms_per_step": 1e3 * t_host / args.steps,
         "kernel_classes_ms_per_step": {k: v[0] / args.steps for k, v in ktime.items()},
         "roofline": roof, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
+        "stencil_shape_autotune": shapes,
     }
     out.update(extra)
     if rank == 0:
@@ -377,7 +409,7 @@ def extra_legs(S, torch, w, dom, grid, rho, args):
     out = {}
     for name, prec in (("fp64", 0), ("fp32", 1), ("bf16", 2)):
         params = S.params_default(max_coarse=4096, precision=prec, beta_rule=1 if prec else 0)
-        op = S.build_operator(dom, grid, w.mode)
+        op = shaped_operator(S, dom, grid, w.mode)
         h = S.setup(op, params)
         phi = torch.zeros_like(rho)
         S.solve(h, rho, phi, rtol=RTOL)
@@ -409,7 +441,7 @@ def extra_legs(S, torch, w, dom, grid, rho, args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(args.steps):
-            op2 = S.build_operator(dom, grid, w.mode)
+            op2 = shaped_operator(S, dom, grid, w.mode)
             h2 = S.setup(op2, params)
             phi.zero_()
             S.solve(h2, rho, phi, rtol=RTOL)
@@ -432,9 +464,9 @@ def extra_legs(S, torch, w, dom, grid, rho, args):
     # mode on the same domain and grid) keeps the aggregates of an existing hierarchy
     params = S.params_default(max_coarse=4096)
     other = I.QUADRATIC if w.mode != I.QUADRATIC else I.LINEAR
-    op1 = S.build_operator(dom, grid, w.mode)
+    op1 = shaped_operator(S, dom, grid, w.mode)
     h1 = S.setup(op1, params)
-    op2 = S.build_operator(dom, grid, other)
+    op2 = shaped_operator(S, dom, grid, other)
     S.setup_reuse(op2, h1, params).free()  # warm-up of both paths
     S.setup(op2, params).free()
     torch.cuda.synchronize()
@@ -470,7 +502,7 @@ def mixed_quadratic_leg(S, torch, args):
         params = S.params_default(max_coarse=4096, precision=prec, beta_rule=1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        op = S.build_operator(dom, grid, w.mode)
+        op = shaped_operator(S, dom, grid, w.mode)
         h = S.setup(op, params)
         phi = torch.zeros_like(rho)
         info = S.solve(h, rho, phi, rtol=RTOL)
@@ -542,7 +574,7 @@ def aggregation_leg(S, torch, args):
         for pname, prec in (("fp64", 0), ("fp32", 1)):
             params = S.params_default(max_coarse=4096, aggregation=agg, precision=prec,
                                       beta_rule=1 if prec else 0)
-            op = S.build_operator(dom, grid, w.mode)
+            op = shaped_operator(S, dom, grid, w.mode)
             h = S.setup(op, params)  # warm-up of this configuration
             h.free()
             torch.cuda.synchronize()
@@ -576,7 +608,7 @@ def coarse_solver_leg(S, torch, args):
     dom, grid = S.make_domain(w.domain), S.make_grid(w.grid)
     rho = torch.from_numpy(I.gaussian_bunch(w.grid, w.centre, w.sigma, seed=13)).cuda()
     out = {"workload": f"{w.name}, linear extrapolation, rtol 1e-8, FP64"}
-    op = S.build_operator(dom, grid, w.mode)
+    op = shaped_operator(S, dom, grid, w.mode)
     for aname, agg in (("mis2", 0), ("cubes", 1)):
         for cname, cs in (("lu", 0), ("gs3", 1)):
             params = S.params_default(max_coarse=4096, aggregation=agg, coarse_solver=cs)
@@ -654,7 +686,7 @@ def sizes_leg(S, torch, sizes=(128, 256, 512)):
             for rep in range(2):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                op = S.build_operator(dom, grid, w.mode)
+                op = shaped_operator(S, dom, grid, w.mode)
                 h = S.setup(op, params)
                 torch.cuda.synchronize()
                 t1 = time.perf_counter()
@@ -683,7 +715,7 @@ def batched_leg(S, torch):
     degrees = []
     for k, w in enumerate(inst):
         dom, grid = S.make_domain(w.domain), S.make_grid(w.grid)
-        op = S.build_operator(dom, grid, w.mode)
+        op = shaped_operator(S, dom, grid, w.mode)
         h32 = S.setup(op, S.params_default(max_coarse=4096, precision=1, beta_rule=1))
         h64 = S.setup(op, S.params_default(max_coarse=4096))
         r = [torch.from_numpy(I.gaussian_bunch(w.grid, w.centre, w.sigma, 1234 + 4 * k + j)).cuda()

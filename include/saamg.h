@@ -296,6 +296,31 @@ saamg_status saamg_batch_last(int *merged, double *ms_merged, double *ms_graphs)
  * the allocator hook may no longer be callable). */
 saamg_status saamg_release_batch_cache(void);
 
+/* Launch shape of the level-0 stencil passes of one precision (the Chebyshev steps, the
+ * residual and the matrix-free prolongation; the passes with a reduction keep a fixed shape
+ * so that their partial sums never change).  Every row is computed the same way under every
+ * shape, so results are identical; only the time changes (the benchmark spec's stencil tile shape). */
+typedef struct saamg_stencil_config {
+  int chunks_per_step; /* chunks of 32 rows per warp step: 1, 2 or 4 */
+  int packed;          /* 1: 32 regular-run rows per warp from the row list, then the table
+                          rows; 0: the line chunks (<= 32 unknowns of one x-line) */
+  int block;           /* threads per block: 128 or 256 */
+  int blocks_per_sm;   /* grid = SMs x this (fewer when the rows run out): 8, 16 or 32 */
+} saamg_stencil_config;
+
+/* The shape op uses for precision 0 (FP64 passes) or 1 (FP32 passes, also the BF16 mode's). */
+saamg_status saamg_stencil_config_get(const saamg_operator *op, int precision,
+                                      saamg_stencil_config *cfg);
+/* Sets it (cfg NULL: the default); EINVAL for a shape outside the sets above.  Hierarchies
+ * set up later, and solve graphs captured later, use it; graphs captured before keep theirs. */
+saamg_status saamg_stencil_config_set(saamg_operator *op, int precision,
+                                      const saamg_stencil_config *cfg);
+/* Autotuner of the launch shape: times the level-0 Chebyshev step of precision 0 or 1 under
+ * all 36 shapes on scratch vectors of op's size (allocated and freed here), sets the fastest
+ * on op and returns it with its time in microseconds (median of three launches). */
+saamg_status saamg_autotune_stencil(saamg_operator *op, int precision, void *stream,
+                                    saamg_stencil_config *best, double *best_us);
+
 /* Changes the Chebyshev degree of every smoothed level (coefficients from the stored
  * lambda_hat; the hierarchy is otherwise unchanged).  EINVAL outside 1..16. */
 saamg_status saamg_set_cheb_degree(saamg_hierarchy *h, int degree);

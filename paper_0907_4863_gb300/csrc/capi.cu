@@ -1753,6 +1753,53 @@ saamg_status saamg_release_batch_cache(void) {
   });
 }
 
+static void check_stencil_cfg(const saamg_stencil_config& c) {
+  const bool ok = (c.chunks_per_step == 1 || c.chunks_per_step == 2 || c.chunks_per_step == 4) &&
+                  (c.packed == 0 || c.packed == 1) && (c.block == 128 || c.block == 256) &&
+                  (c.blocks_per_sm == 8 || c.blocks_per_sm == 16 || c.blocks_per_sm == 32);
+  if (!ok) fail(SAAMG_EINVAL, "stencil launch shape outside the supported sets");
+}
+
+saamg_status saamg_stencil_config_get(const saamg_operator* op, int precision,
+                                      saamg_stencil_config* cfg) {
+  return guard("saamg_stencil_config_get", [&] {
+    if (!op || op->magic != kOpMagic || !cfg) fail(SAAMG_EINVAL, "NULL or invalid argument");
+    if (precision != 0 && precision != 1) fail(SAAMG_EINVAL, "precision must be 0 or 1");
+    const StencilCfg& c = op->d.cfg[precision];
+    *cfg = saamg_stencil_config{c.k, c.packed, c.block, c.per_sm};
+  });
+}
+
+saamg_status saamg_stencil_config_set(saamg_operator* op, int precision,
+                                      const saamg_stencil_config* cfg) {
+  return guard("saamg_stencil_config_set", [&] {
+    if (!op || op->magic != kOpMagic) fail(SAAMG_EINVAL, "NULL or invalid argument");
+    if (precision != 0 && precision != 1) fail(SAAMG_EINVAL, "precision must be 0 or 1");
+    if (!cfg) {
+      op->d.cfg[precision] = OperatorData{}.cfg[precision];
+      return;
+    }
+    check_stencil_cfg(*cfg);
+    op->d.cfg[precision] = StencilCfg{cfg->chunks_per_step, cfg->packed, cfg->block,
+                                      cfg->blocks_per_sm};
+  });
+}
+
+saamg_status saamg_autotune_stencil(saamg_operator* op, int precision, void* stream,
+                                    saamg_stencil_config* best, double* best_us) {
+  return guard("saamg_autotune_stencil", [&] {
+    if (!op || op->magic != kOpMagic) fail(SAAMG_EINVAL, "NULL or invalid argument");
+    if (precision != 0 && precision != 1) fail(SAAMG_EINVAL, "precision must be 0 or 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    double us = 0;
+    const StencilCfg c = precision == 0 ? stencil_autotune<double>(op->d.view<double>(), s, &us)
+                                        : stencil_autotune<float>(op->d.view<float>(), s, &us);
+    op->d.cfg[precision] = c;
+    if (best) *best = saamg_stencil_config{c.k, c.packed, c.block, c.per_sm};
+    if (best_us) *best_us = us;
+  });
+}
+
 saamg_status saamg_set_cheb_degree(saamg_hierarchy* h, int degree) {
   return guard("saamg_set_cheb_degree", [&] {
     if (!h || h->magic != kHierMagic) fail(SAAMG_EINVAL, "not a hierarchy handle");

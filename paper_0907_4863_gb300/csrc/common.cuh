@@ -164,8 +164,17 @@ struct __align__(32) ChunkRec {
 };
 static_assert(sizeof(ChunkRec) == 32, "ChunkRec is two 16-byte loads");
 
+// Launch shape of the level-0 stencil passes without reductions (every row's arithmetic is the
+// same under every shape, so the results are too): K chunks of 32 rows per warp step (1, 2,
+// 4), packed (1: 32 regular-run rows per warp from the row list, then the table rows 32 at a
+// time; 0: the line chunks), threads per block (128, 256) and blocks per SM (8, 16, 32).
+struct StencilCfg {
+  int k, packed, block, per_sm;
+};
+
 template <class T>
 struct StencilDev {
+  StencilCfg cfg;      // launch shape (host side)
   const LineInfo* lines;
   // per line: row offset from an unknown (i, L) to its neighbour (i, L') in the -y, +y, -z,
   // +z line (start' - lo') - (start - lo); 0 where that line does not exist or is empty

@@ -778,6 +778,7 @@ void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op) 
 template <>
 StencilDev<double> OperatorData::view<double>() const {
   StencilDev<double> v;
+  v.cfg = cfg[0];
   v.lines = lines.p;
   v.nbr = nbr.p;
   v.chunks = chunks.p;
@@ -804,6 +805,7 @@ StencilDev<double> OperatorData::view<double>() const {
 template <>
 StencilDev<float> OperatorData::view<float>() const {
   StencilDev<float> v;
+  v.cfg = cfg[1];
   v.lines = lines.p;
   v.nbr = nbr.p;
   v.chunks = chunks.p;

@@ -39,6 +39,9 @@ struct OperatorData {
   Buf<unsigned char> regular;
   Buf<unsigned char> nbmask;  // bit q: neighbour q (-x,+x,-y,+y,-z,+z) is an unknown
   DevCsr A;             // explicit scaled CSR (used by the AMG setup)
+  // launch shapes of the FP64 [0] and FP32 [1] passes: FP64 is bound by FP64 issue and takes
+  // packed rows, one chunk per step; FP32 is latency-bound and takes line chunks, two per step
+  StencilCfg cfg[2] = {{1, 1, 256, 16}, {2, 0, 256, 16}};
   size_t bytes() const {
     return lines.bytes() + nbr.bytes() + chunks.bytes() + crec.bytes() + rline.bytes() + table.bytes() +
            table32.bytes() + trow.bytes() + rrow.bytes() + scale.bytes() +
@@ -84,5 +87,10 @@ void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* 
 template <class T>
 void stencil_prolong(const StencilDev<T>& S, const int* agg, T omega, const T* v, T* y,
                      cudaStream_t s);
+// Times the level-0 Chebyshev step under every launch shape (K 1/2/4, packed or line chunks,
+// 128/256 threads, 8/16/32 blocks per SM) on scratch vectors and returns the fastest; its
+// time (median of three launches) in *best_us.
+template <class T>
+StencilCfg stencil_autotune(const StencilDev<T>& S, cudaStream_t s, double* best_us);
 
 }  // namespace saamg

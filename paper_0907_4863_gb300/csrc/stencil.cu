@@ -9,6 +9,8 @@
 // FP32 passes: one warp per chunk of <= 32 consecutive unknowns of one x-line.  FP64 passes
 // (bound by FP64 issue): first 32 regular-run rows per warp from a (row, line) list, then
 // 32 table rows per warp from the table-row list.
+#include <algorithm>
+
 #include "operator.cuh"
 #include "batch.cuh"
 #include "rows.cuh"
@@ -192,7 +194,7 @@ __host__ __device__ constexpr bool packed_rows() {
 
 // K chunks per warp iteration: the unrolled copies let the read-only loads of the next chunk
 // be issued before the stores of the current one (more bytes in flight per warp).
-template <class T, int MODE, int K>
+template <class T, int MODE, int K, bool PACKED>
 __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __restrict__ x,
                                                  T* __restrict__ y, const T* __restrict__ b,
                                                  T* __restrict__ d, T c1, T c2, T c2invd0,
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __res
     c2invd0 = c2 * S.invd0;
   }
   double dacc = 0.0;
-  constexpr bool kPacked = packed_rows<T>();
+  constexpr bool kPacked = PACKED;
   // packed: the regular-run chunks, then the table chunks (the branch is uniform per warp)
   const int nreg = kPacked ? (S.nrun + 31) / 32 : S.nchunks;
   const int nch = kPacked ? nreg + (S.ntable + 31) / 32 : nreg;
@@ -397,6 +399,36 @@ void batched_stencil_dot(const StTask<double>* tasks, int ntasks, cudaStream_t s
   SAAMG_LAUNCH();
 }
 
+// Launches MODE with the shape of cfg (K and packed from the instantiated set).
+template <class T, int MODE>
+void launch_shaped(const StencilCfg& cfg, long long units, int blocks_cap, const StencilDev<T>& S,
+                   const T* x, T* y, const T* b, T* d, T c1, T c2, T c2i0, double* partials,
+                   const double* xscale, const int* agg, cudaStream_t s) {
+  const int wpb = cfg.block / 32;
+  const long long need = (units + (long long)wpb * cfg.k - 1) / ((long long)wpb * cfg.k);
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(need, blocks_cap));
+#define SAAMG_SHAPE(KK, PP)                                                                  \
+  if (cfg.k == KK && (cfg.packed != 0) == PP) {                                              \
+    stencil_k<T, MODE, KK, PP><<<blocks, cfg.block, 0, s>>>(S, x, y, b, d, c1, c2, c2i0,     \
+                                                            partials, xscale, agg);          \
+    return;                                                                                  \
+  }
+  SAAMG_SHAPE(1, false)
+  SAAMG_SHAPE(2, false)
+  SAAMG_SHAPE(4, false)
+  SAAMG_SHAPE(1, true)
+  SAAMG_SHAPE(2, true)
+  SAAMG_SHAPE(4, true)
+#undef SAAMG_SHAPE
+  fail(SAAMG_EINVAL, "unsupported stencil launch shape");
+}
+
+// Chunks of 32 rows a launch of the shape processes (packed: regular-run then table chunks).
+template <class T>
+long long shaped_units(const StencilDev<T>& S, bool packed) {
+  return packed ? ((long long)S.nrun + 31) / 32 + (S.ntable + 31) / 32 : S.nchunks;
+}
+
 template <class T>
 void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* b, T* d, T c1,
                    T c2, double* partials, cudaStream_t s, const double* xscale) {
@@ -404,8 +436,6 @@ void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* 
     if (mode == ST_SPMV_DOT || mode == ST_DINV_DOT) fill_double(partials, 0.0, kRedBlocks, s);
     return;
   }
-  const long long nch = packed_rows<T>() ? ((long long)S.nrun + 31) / 32 + (S.ntable + 31) / 32
-                                         : S.nchunks;
   // the smoother class holds only the full Chebyshev step (fixed work per row); the
   // other modes of the same kernel are timed as "apply"
   // one timing class per kind of pass (each has a fixed amount of work per row)
@@ -415,43 +445,45 @@ void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* 
                  : (mode == ST_CHEB0 || mode == ST_CHEB1)   ? SAAMG_KT_STENCIL_FIRST
                                                             : -1,
                  S.n, s);
-  // Reductions use the fixed grid so that partial sums are always taken the same way.
-  int blocks = kRedBlocks;
-  if (mode != ST_SPMV_DOT && mode != ST_DINV_DOT) {
-    long long need = (nch + 8 * kChunks<T>() - 1) / (8 * kChunks<T>());
-    blocks = (int)(need < sm_count() * 16 ? need : sm_count() * 16);
-  }
   // c2 / diag of the regular rows, formed here: a kernel that forms it from c2 lets the
   // compiler merge it with the table rows' c2 * (1/diag) into one multiply on every row
   const T c2i0 = c2 * S.invd0;
+  if (mode == ST_SPMV_DOT || mode == ST_DINV_DOT) {
+    // reductions: the fixed grid and the default shape, so that partial sums are always
+    // taken the same way
+    constexpr bool P = packed_rows<T>();
+    if (mode == ST_SPMV_DOT)
+      stencil_k<T, ST_SPMV_DOT, kChunks<T>(), P><<<kRedBlocks, kRedThreads, 0, s>>>(
+          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
+    else
+      stencil_k<T, ST_DINV_DOT, kChunks<T>(), P><<<kRedBlocks, kRedThreads, 0, s>>>(
+          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
+    SAAMG_LAUNCH();
+    return;
+  }
+  const StencilCfg& cfg = S.cfg;
+  const long long units = shaped_units(S, cfg.packed != 0);
+  const int cap = sm_count() * cfg.per_sm;
   switch (mode) {
     case ST_SPMV:
-      stencil_k<T, ST_SPMV, kChunks<T>()><<<blocks, 256, 0, s>>>(
-          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
-      break;
-    case ST_SPMV_DOT:
-      stencil_k<T, ST_SPMV_DOT, kChunks<T>()><<<blocks, 256, 0, s>>>(
-          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
+      launch_shaped<T, ST_SPMV>(cfg, units, cap, S, x, y, b, d, c1, c2, c2i0, partials, xscale,
+                                nullptr, s);
       break;
     case ST_RESID:
-      stencil_k<T, ST_RESID, kChunks<T>()><<<blocks, 256, 0, s>>>(
-          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
+      launch_shaped<T, ST_RESID>(cfg, units, cap, S, x, y, b, d, c1, c2, c2i0, partials, xscale,
+                                 nullptr, s);
       break;
     case ST_CHEB:
-      stencil_k<T, ST_CHEB, kChunks<T>()><<<blocks, 256, 0, s>>>(
-          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
+      launch_shaped<T, ST_CHEB>(cfg, units, cap, S, x, y, b, d, c1, c2, c2i0, partials, xscale,
+                                nullptr, s);
       break;
     case ST_CHEB0:
-      stencil_k<T, ST_CHEB0, kChunks<T>()><<<blocks, 256, 0, s>>>(
-          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
+      launch_shaped<T, ST_CHEB0>(cfg, units, cap, S, x, y, b, d, c1, c2, c2i0, partials, xscale,
+                                 nullptr, s);
       break;
     case ST_CHEB1:
-      stencil_k<T, ST_CHEB1, kChunks<T>()><<<blocks, 256, 0, s>>>(
-          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
-      break;
-    case ST_DINV_DOT:
-      stencil_k<T, ST_DINV_DOT, kChunks<T>()><<<blocks, 256, 0, s>>>(
-          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
+      launch_shaped<T, ST_CHEB1>(cfg, units, cap, S, x, y, b, d, c1, c2, c2i0, partials, xscale,
+                                 nullptr, s);
       break;
     default:
       fail(SAAMG_EINVAL, "bad stencil mode");
@@ -464,12 +496,63 @@ void stencil_prolong(const StencilDev<T>& S, const int* agg, T omega, const T* v
                      cudaStream_t s) {
   if (S.nchunks == 0) return;
   KernelTimer kt(SAAMG_KT_PROLONG0, S.n, s);
-  const long long need = ((long long)S.nchunks + 8 * kChunks<T>() - 1) / (8 * kChunks<T>());
-  const int blocks = (int)(need < sm_count() * 16 ? need : sm_count() * 16);
-  stencil_k<T, ST_PROLONG, kChunks<T>()><<<blocks, 256, 0, s>>>(
-      S, v, y, nullptr, nullptr, T(0), omega, T(omega * S.invd0), nullptr, nullptr, agg);
+  const StencilCfg& cfg = S.cfg;
+  launch_shaped<T, ST_PROLONG>(cfg, shaped_units(S, cfg.packed != 0), sm_count() * cfg.per_sm, S,
+                               v, y, nullptr, nullptr, T(0), omega, T(omega * S.invd0), nullptr,
+                               nullptr, agg, s);
   SAAMG_LAUNCH();
 }
+
+// Times the Chebyshev step of every launch shape on scratch vectors and returns the fastest
+// (median of three launches after one untimed).
+template <class T>
+StencilCfg stencil_autotune(const StencilDev<T>& S0, cudaStream_t s, double* best_us) {
+  StencilDev<T> S = S0;
+  const size_t n = (size_t)(S.n > 0 ? S.n : 1);
+  Buf<T> x, y, b, d;
+  x.alloc(n, s);
+  y.alloc(n, s);
+  b.alloc(n, s);
+  d.alloc(n, s);
+  SAAMG_CUDA(cudaMemsetAsync(x.p, 0, n * sizeof(T), s));
+  SAAMG_CUDA(cudaMemsetAsync(b.p, 0, n * sizeof(T), s));
+  SAAMG_CUDA(cudaMemsetAsync(d.p, 0, n * sizeof(T), s));
+  cudaEvent_t e[4];
+  for (auto& ev : e) SAAMG_CUDA(cudaEventCreate(&ev));
+  StencilCfg best = S0.cfg;
+  float best_ms = -1.f;
+  try {
+    for (int k : {1, 2, 4})
+      for (int packed : {0, 1})
+        for (int block : {128, 256})
+          for (int per_sm : {8, 16, 32}) {
+            S.cfg = StencilCfg{k, packed, block, per_sm};
+            stencil_apply<T>(S, ST_CHEB, x.p, y.p, b.p, d.p, T(0.5), T(0.25), nullptr, s);
+            float t[3];
+            for (int r = 0; r < 3; ++r) {
+              SAAMG_CUDA(cudaEventRecord(e[0], s));
+              stencil_apply<T>(S, ST_CHEB, x.p, y.p, b.p, d.p, T(0.5), T(0.25), nullptr, s);
+              SAAMG_CUDA(cudaEventRecord(e[1], s));
+              SAAMG_CUDA(cudaEventSynchronize(e[1]));
+              SAAMG_CUDA(cudaEventElapsedTime(&t[r], e[0], e[1]));
+            }
+            std::sort(t, t + 3);
+            if (best_ms < 0.f || t[1] < best_ms) {
+              best_ms = t[1];
+              best = S.cfg;
+            }
+          }
+  } catch (...) {
+    for (auto& ev : e) cudaEventDestroy(ev);
+    throw;
+  }
+  for (auto& ev : e) cudaEventDestroy(ev);
+  if (best_us) *best_us = 1e3 * best_ms;
+  return best;
+}
+
+template StencilCfg stencil_autotune<float>(const StencilDev<float>&, cudaStream_t, double*);
+template StencilCfg stencil_autotune<double>(const StencilDev<double>&, cudaStream_t, double*);
 
 template void stencil_prolong<float>(const StencilDev<float>&, const int*, float, const float*,
                                      float*, cudaStream_t);

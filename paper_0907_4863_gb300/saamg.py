@@ -54,6 +54,14 @@ class SolveInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class StencilConfig(C.Structure):
+    _fields_ = [("chunks_per_step", C.c_int), ("packed", C.c_int), ("block", C.c_int),
+                ("blocks_per_sm", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class HierarchyInfo(C.Structure):
     _fields_ = [("levels", C.c_int), ("n", C.c_int * MAX_LEVELS),
                 ("nnz", C.c_longlong * MAX_LEVELS), ("nnz_p", C.c_longlong * MAX_LEVELS),
@@ -120,6 +128,9 @@ def lib():
         "saamg_solve_wait": [_p, C.POINTER(SolveInfo)],
         "saamg_solve_batched": [_p, _p, _p, _i, C.c_double, _p, _p],
         "saamg_set_cheb_degree": [_p, _i],
+        "saamg_stencil_config_get": [_p, _i, C.POINTER(StencilConfig)],
+        "saamg_stencil_config_set": [_p, _i, C.POINTER(StencilConfig)],
+        "saamg_autotune_stencil": [_p, _i, _p, C.POINTER(StencilConfig), C.POINTER(C.c_double)],
         "saamg_autotune_cheb_degree": [_p, _p, _i, _i, C.c_double, _p, C.POINTER(_i),
                                        C.POINTER(C.c_double)],
         "saamg_deposit_cic": [C.POINTER(Grid), _i, _p, _p, _p, _p, _p, _p],
@@ -486,6 +497,35 @@ def solve_batched(hs, rhos, phis, rtol=1e-8, stream=None):
     st = lib().saamg_solve_batched(H, R, X, n, float(rtol), _stream(stream), infos)
     _check(st, allow_not_converged=True)
     return [dict(infos[j].as_dict()) for j in range(n)]
+
+
+@_entry
+def stencil_config(op: Operator, precision: int) -> dict:
+    """The level-0 stencil launch shape op uses for precision 0 (FP64) or 1 (FP32)."""
+    c = StencilConfig()
+    _check(lib().saamg_stencil_config_get(op.handle, int(precision), C.byref(c)))
+    return c.as_dict()
+
+
+@_entry
+def set_stencil_config(op: Operator, precision: int, cfg=None):
+    """Sets the launch shape (a dict like stencil_config's; None: the default)."""
+    if cfg is None:
+        _check(lib().saamg_stencil_config_set(op.handle, int(precision), None))
+        return
+    c = StencilConfig(**{k: int(cfg[k]) for k, _ in StencilConfig._fields_})
+    _check(lib().saamg_stencil_config_set(op.handle, int(precision), C.byref(c)))
+
+
+@_entry
+def autotune_stencil(op: Operator, precision: int, stream=None):
+    """Times the 36 launch shapes of the level-0 Chebyshev step, sets the fastest on op and
+    returns (shape, microseconds)."""
+    c = StencilConfig()
+    us = C.c_double(0)
+    _check(lib().saamg_autotune_stencil(op.handle, int(precision), _stream(stream), C.byref(c),
+                                        C.byref(us)))
+    return c.as_dict(), us.value
 
 
 @_entry

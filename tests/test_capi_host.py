@@ -40,7 +40,8 @@ def test_every_declared_symbol_is_exported(S):
 def test_struct_layouts_match_header(S, tmp_path):
     """Sizes and offsets of the ctypes mirrors equal what a C compiler makes of the header."""
     structs = {"saamg_domain": S.Domain, "saamg_grid": S.Grid, "saamg_params": S.Params,
-               "saamg_solve_info": S.SolveInfo, "saamg_hierarchy_info": S.HierarchyInfo}
+               "saamg_solve_info": S.SolveInfo, "saamg_hierarchy_info": S.HierarchyInfo,
+               "saamg_stencil_config": S.StencilConfig}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "saamg.h"', "int main(void){"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
