@@ -350,16 +350,6 @@ __global__ void bany_k(const int* __restrict__ go, int count, cudaGraphCondition
   if (threadIdx.x == 0) cudaGraphSetConditional(cond, any ? 1u : 0u);
 }
 
-__global__ void set_go_k(int* go, int count, int v) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < count) go[j] = v;
-}
-
-inline int grid_of(long long units, int per_block) {
-  const long long need = (units + per_block - 1) / per_block;
-  return (int)std::max<long long>(1, std::min<long long>(need, (long long)sm_count() * 16));
-}
-
 // --- operation keys -------------------------------------------------------------------------
 enum Family { F_ST32, F_ST64, F_CSR, F_SHORT, F_SELL, F_GEMV, F_COPY };
 // value types: TV 0 double / 1 float; TM 0 double / 1 float / 2 bf16

@@ -672,17 +672,6 @@ struct LevelVecs<float> {
   static float* r(Level& L) { return L.fr.p; }
 };
 
-template <class T>
-static const T* invd_of(Level& L);
-template <>
-const double* invd_of<double>(Level& L) {
-  return L.invd.p;
-}
-template <>
-const float* invd_of<float>(Level& L) {
-  return L.invd32.p;
-}
-
 // y (+)= M x for a coarse matrix in the working precision
 template <class T>
 static void level_csr(saamg_hierarchy* h, int l, int mode, const T* x, T* y, const T* b, T* d,

@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(128, 16) spgemm_hash_numeric_k(const int* __re
   extern __shared__ double smem_d[];
   constexpr int GL = 32 / NG;
   const int lane = threadIdx.x & 31;
-  const int grp = lane / GL, gl = lane % GL;
+  const int grp = lane / GL;
   const int wib = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
   const int cap = 1 << logcap;
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(256) spgemm_hash_numeric_blk_k(const int* __re
   __shared__ int nus;
   constexpr int GL = 32 / NG;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int grp = lane / GL, gl = lane % GL;
+  const int grp = lane / GL;
   const int cap = 1 << logcap;
   const int cstride = cap + 1;
   double* vals = smem_bd;
