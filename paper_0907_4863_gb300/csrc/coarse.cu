@@ -176,7 +176,6 @@ __global__ void __launch_bounds__(kGjThreads) gj_step_k(int n, int k, int cpb,
 // another block of the same launch may still be loading.  The own columns are copied to
 // shared memory asynchronously while the panel is factored.
 constexpr int kGjRpThreads = 256;
-constexpr int kGjRpWidth = 4;  // pivot steps per launch
 
 // Pivot keys: the bits of |v| as an integer, which order like |v| for every non-NaN v; a NaN
 // gets -1 and is never chosen, as with a floating-point comparison.  The search then runs
