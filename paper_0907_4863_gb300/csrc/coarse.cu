@@ -426,6 +426,7 @@ __global__ void __launch_bounds__(32 * kGemvWarps) coarse_apply_k(int n,
                                                                   const double* __restrict__ inv,
                                                                   const TV* __restrict__ b,
                                                                   TV* __restrict__ x) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * kGemvWarps + (threadIdx.x >> 5);
   if (i >= n) return;  // whole warps leave together
@@ -695,8 +696,8 @@ void coarse_apply(const CoarseSolver& cs, const TV* b, TV* x, cudaStream_t s) {
     SAAMG_LAUNCH();
     return;
   }
-  coarse_apply_k<TV><<<(cs.n + kGemvWarps - 1) / kGemvWarps, 32 * kGemvWarps, 0, s>>>(
-      cs.n, cs.inv.p, b, x);
+  launch_pdl(coarse_apply_k<TV>, (cs.n + kGemvWarps - 1) / kGemvWarps, 32 * kGemvWarps, 0, s,
+             cs.n, cs.inv.p, b, x);
   SAAMG_LAUNCH();
 }
 

@@ -38,6 +38,36 @@ struct CaptureCount {
 void set_last_error(const std::string& msg);
 
 #define SAAMG_CUDA(x) ::saamg::check_cuda((x), #x, __FILE__, __LINE__)
+
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch.  The solve's kernels are launched with launch_pdl, so the
+// launch of a kernel is prepared while the kernel before it on the stream runs; its blocks wait
+// at pdl_wait (their first statement, before any memory access) until that kernel has finished
+// and its writes are visible.  No kernel signals its dependents early: measured at 256^3, an
+// early signal (at kernel entry) made the solve 5-8 % slower, none 0.8-1.3 % faster than plain
+// launches.  The order and the results of the work are those of plain launches; pdl_wait does
+// nothing in a kernel launched without the attribute.  SAAMG_PDL=0 in the environment turns
+// the attribute off.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+bool pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  check_cuda(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...), "cudaLaunchKernelEx",
+             __FILE__, __LINE__);
+}
 #define SAAMG_LAUNCH()                                                                  \
   do {                                                                                  \
     ::saamg::count_launch();                                                            \

@@ -19,6 +19,7 @@ __global__ void __launch_bounds__(256) csr_k(int n, const int* __restrict__ rowp
                                              TV* __restrict__ d, const TV* __restrict__ invd,
                                              TV c1, TV c2, double* __restrict__ partials,
                                              const double* __restrict__ xscale) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int gl = lane % G;
   constexpr int kRowsPerWarp = 32 / G;
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(256) csr_short_k(int n, const int* __restrict_
                                                    const int* __restrict__ col,
                                                    const TM* __restrict__ val,
                                                    const TV* __restrict__ x, TV* __restrict__ y) {
+  pdl_wait();
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n;
        row += gridDim.x * blockDim.x)
     rows::csr_short_row<TV, TM, MODE>(row, rowptr, col, val, x, y);
@@ -67,8 +69,8 @@ void launch_g(int mode, int n, const int* rowptr, const int* col, const TM* val,
   }
 #define SAAMG_CSR_CASE(M)                                                                  \
   case M:                                                                                  \
-    csr_k<TV, TM, G, M><<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y, b, d, invd, c1, c2, \
-                                                partials, xscale);                         \
+    launch_pdl(csr_k<TV, TM, G, M>, blocks, 256, 0, s, n, rowptr, col, val, x, y, b, d,   \
+               invd, c1, c2, partials, xscale);                                            \
     break;
   switch (mode) {
     SAAMG_CSR_CASE(CSR_SPMV)
@@ -99,6 +101,7 @@ __global__ void diag_inverse_k(int n, const int* __restrict__ rowptr, const int*
 
 template <class TI, class TO>
 __global__ void convert_k(const TI* __restrict__ in, TO* __restrict__ out, size_t n) {
+  pdl_wait();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
     out[i] = (TO)in[i];
@@ -149,9 +152,9 @@ void csr_apply(int mode, int n, const int* rowptr, const int* col, const TM* val
     const long long need = ((long long)n + 255) / 256;
     const int blocks = (int)(need < sm_count() * 16 ? need : sm_count() * 16);
     if (mode == CSR_ADD)
-      csr_short_k<TV, TM, CSR_ADD><<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y);
+      launch_pdl(csr_short_k<TV, TM, CSR_ADD>, blocks, 256, 0, s, n, rowptr, col, val, x, y);
     else
-      csr_short_k<TV, TM, CSR_SPMV><<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y);
+      launch_pdl(csr_short_k<TV, TM, CSR_SPMV>, blocks, 256, 0, s, n, rowptr, col, val, x, y);
     SAAMG_LAUNCH();
     return;
   }
@@ -196,13 +199,13 @@ void csr_diag_inverse(const DevCsr& A, double* invd, float* invd32, cudaStream_t
 
 void to_float(const double* in, float* out, size_t n, cudaStream_t s) {
   if (!n) return;
-  convert_k<double, float><<<grid_for(n), 256, 0, s>>>(in, out, n);
+  launch_pdl(convert_k<double, float>, grid_for(n), 256, 0, s, in, out, n);
   SAAMG_LAUNCH();
 }
 
 void to_double(const float* in, double* out, size_t n, cudaStream_t s) {
   if (!n) return;
-  convert_k<float, double><<<grid_for(n), 256, 0, s>>>(in, out, n);
+  launch_pdl(convert_k<float, double>, grid_for(n), 256, 0, s, in, out, n);
   SAAMG_LAUNCH();
 }
 

@@ -1,4 +1,5 @@
 // Kernel launch accounting and opt-in per-class kernel timing (CUDA events).
+#include <cstdlib>
 #include <atomic>
 #include <vector>
 
@@ -52,6 +53,14 @@ namespace {
 thread_local int t_capturing = 0;
 thread_local long long t_captured = 0;
 }  // namespace
+
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("SAAMG_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
 
 void count_launch() {
   if (t_capturing) ++t_captured;

@@ -17,6 +17,7 @@ using rows::sum_fixed;
 template <class TA, class TB>
 __global__ void dot_k(int n, const TA* __restrict__ a, const TB* __restrict__ b,
                       double* __restrict__ part) {
+  pdl_wait();
   const double t = rows::dot_block<TA, TB>(blockIdx.x, n, a, b);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
@@ -26,6 +27,7 @@ template <class TZ>
 __global__ void dot2_k(int n, const double* __restrict__ r, const TZ* __restrict__ z,
                        const double* __restrict__ q, double* __restrict__ part_rz,
                        double* __restrict__ part_zq) {
+  pdl_wait();
   double t1, t2;
   rows::dot2_block<TZ>(blockIdx.x, n, r, z, q, t1, t2);
   if (threadIdx.x == 0) {
@@ -35,6 +37,7 @@ __global__ void dot2_k(int n, const double* __restrict__ r, const TZ* __restrict
 }
 
 __global__ void alpha_k(const double* __restrict__ part, PcgCtl* ctl) {
+  pdl_wait();
   double pq = sum_fixed(part);
   if (threadIdx.x == 0) {
     ctl->pq = pq;
@@ -52,11 +55,13 @@ __global__ void update_k(int n, double* __restrict__ x, double* __restrict__ r,
                          const double* __restrict__ p, const double* __restrict__ q,
                          const PcgCtl* __restrict__ ctl, double* __restrict__ part,
                          float* __restrict__ r32) {
+  pdl_wait();
   const double t = rows::update_block(blockIdx.x, n, ctl->alpha, x, r, p, q, r32);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 __global__ void check_k(const double* __restrict__ part, PcgCtl* ctl) {
+  pdl_wait();
   double rr = sum_fixed(part);
   if (threadIdx.x == 0) {
     ctl->rr = rr;
@@ -68,6 +73,7 @@ __global__ void check_k(const double* __restrict__ part, PcgCtl* ctl) {
 
 __global__ void beta_k(const double* __restrict__ part_rz, const double* __restrict__ part_zq,
                        int rule, PcgCtl* ctl) {
+  pdl_wait();
   double rz = sum_fixed(part_rz);
   double zq = part_zq ? sum_fixed(part_zq) : 0.0;
   if (threadIdx.x == 0 && rule < 0) {  // first direction: only r'z
@@ -91,6 +97,7 @@ __global__ void beta_k(const double* __restrict__ part_rz, const double* __restr
 template <class TZ>
 __global__ void direction_k(int n, const TZ* __restrict__ z, double* __restrict__ p,
                             const PcgCtl* __restrict__ ctl) {
+  pdl_wait();
   const double b = ctl->beta;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     p[i] = (double)z[i] + b * p[i];
@@ -98,18 +105,21 @@ __global__ void direction_k(int n, const TZ* __restrict__ z, double* __restrict_
 
 __global__ void sub_k(int n, const double* __restrict__ b, const double* __restrict__ q,
                       double* __restrict__ r) {
+  pdl_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     r[i] = b[i] - q[i];
 }
 
 template <class TZ>
 __global__ void copy_k(int n, const TZ* __restrict__ z, double* __restrict__ p) {
+  pdl_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     p[i] = (double)z[i];
 }
 
 __global__ void graph_init_k(const double* __restrict__ part_bb, const double* __restrict__ part_rr,
                              PcgCtl* ctl, cudaGraphConditionalHandle cond, int maxit) {
+  pdl_wait();
   const double bb = sum_fixed(part_bb);
   const double rr = sum_fixed(part_rr);
   if (threadIdx.x == 0) {
@@ -128,12 +138,14 @@ __global__ void graph_init_k(const double* __restrict__ part_bb, const double* _
 }
 
 __global__ void zero_if_rhs_zero_k(double* __restrict__ x, int n, const PcgCtl* __restrict__ ctl) {
+  pdl_wait();
   if (ctl->bb != 0.0) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = 0.0;
 }
 
 __global__ void graph_beta_k(const double* __restrict__ part_rz, const double* __restrict__ part_zq,
                              int rule, PcgCtl* ctl) {
+  pdl_wait();
   const double rz = sum_fixed(part_rz);
   const double zq = part_zq ? sum_fixed(part_zq) : 0.0;
   if (threadIdx.x == 0) {
@@ -152,6 +164,7 @@ __global__ void graph_beta_k(const double* __restrict__ part_rz, const double* _
 
 __global__ void graph_check_k(const double* __restrict__ part, PcgCtl* ctl,
                               cudaGraphConditionalHandle cond, int maxit) {
+  pdl_wait();
   const double rr = sum_fixed(part);
   if (threadIdx.x == 0) {
     ctl->rr = rr;
@@ -164,6 +177,7 @@ __global__ void graph_check_k(const double* __restrict__ part, PcgCtl* ctl,
 }
 
 __global__ void store_true_k(const double* __restrict__ part, PcgCtl* ctl) {
+  pdl_wait();
   const double rr = sum_fixed(part);
   if (threadIdx.x == 0) ctl->rr_true = rr;
 }
@@ -177,7 +191,7 @@ inline int vec_blocks(int n) {
 
 template <class TA, class TB>
 void dot_partials(int n, const TA* a, const TB* b, double* partials, cudaStream_t s) {
-  dot_k<TA, TB><<<kRedBlocks, kRedThreads, 0, s>>>(n, a, b, partials);
+  launch_pdl(dot_k<TA, TB>, kRedBlocks, kRedThreads, 0, s, n, a, b, partials);
   SAAMG_LAUNCH();
 }
 template void dot_partials<double, double>(int, const double*, const double*, double*, cudaStream_t);
@@ -187,7 +201,7 @@ template void dot_partials<float, double>(int, const float*, const double*, doub
 template <class TZ>
 void dot2_partials(int n, const double* r, const TZ* z, const double* q, double* part_rz,
                    double* part_zq, cudaStream_t s) {
-  dot2_k<TZ><<<kRedBlocks, kRedThreads, 0, s>>>(n, r, z, q, part_rz, part_zq);
+  launch_pdl(dot2_k<TZ>, kRedBlocks, kRedThreads, 0, s, n, r, z, q, part_rz, part_zq);
   SAAMG_LAUNCH();
 }
 template void dot2_partials<double>(int, const double*, const double*, const double*, double*,
@@ -196,68 +210,68 @@ template void dot2_partials<float>(int, const double*, const float*, const doubl
                                    double*, cudaStream_t);
 
 void pcg_alpha(const double* partials, PcgCtl* ctl, cudaStream_t s) {
-  alpha_k<<<1, kRedThreads, 0, s>>>(partials, ctl);
+  launch_pdl(alpha_k, 1, kRedThreads, 0, s, partials, ctl);
   SAAMG_LAUNCH();
 }
 
 void pcg_update(int n, double* x, double* r, const double* p, const double* q, const PcgCtl* ctl,
                 double* partials, cudaStream_t s, float* r32) {
-  update_k<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, p, q, ctl, partials, r32);
+  launch_pdl(update_k, kRedBlocks, kRedThreads, 0, s, n, x, r, p, q, ctl, partials, r32);
   SAAMG_LAUNCH();
 }
 
 void pcg_check(const double* partials, PcgCtl* ctl, cudaStream_t s) {
-  check_k<<<1, kRedThreads, 0, s>>>(partials, ctl);
+  launch_pdl(check_k, 1, kRedThreads, 0, s, partials, ctl);
   SAAMG_LAUNCH();
 }
 
 void pcg_beta(const double* part_rz, const double* part_zq, int rule, PcgCtl* ctl,
               cudaStream_t s) {
-  beta_k<<<1, kRedThreads, 0, s>>>(part_rz, part_zq, rule, ctl);
+  launch_pdl(beta_k, 1, kRedThreads, 0, s, part_rz, part_zq, rule, ctl);
   SAAMG_LAUNCH();
 }
 
 template <class TZ>
 void pcg_direction(int n, const TZ* z, double* p, const PcgCtl* ctl, cudaStream_t s) {
-  direction_k<TZ><<<vec_blocks(n), 256, 0, s>>>(n, z, p, ctl);
+  launch_pdl(direction_k<TZ>, vec_blocks(n), 256, 0, s, n, z, p, ctl);
   SAAMG_LAUNCH();
 }
 template void pcg_direction<double>(int, const double*, double*, const PcgCtl*, cudaStream_t);
 template void pcg_direction<float>(int, const float*, double*, const PcgCtl*, cudaStream_t);
 
 void vec_sub(int n, const double* b, const double* q, double* r, cudaStream_t s) {
-  sub_k<<<vec_blocks(n), 256, 0, s>>>(n, b, q, r);
+  launch_pdl(sub_k, vec_blocks(n), 256, 0, s, n, b, q, r);
   SAAMG_LAUNCH();
 }
 
 void pcg_graph_init(const double* part_bb, const double* part_rr, PcgCtl* ctl,
                     cudaGraphConditionalHandle cond, int maxit, double* x, int n, cudaStream_t s) {
-  graph_init_k<<<1, kRedThreads, 0, s>>>(part_bb, part_rr, ctl, cond, maxit);
+  launch_pdl(graph_init_k, 1, kRedThreads, 0, s, part_bb, part_rr, ctl, cond, maxit);
   SAAMG_LAUNCH();
-  zero_if_rhs_zero_k<<<vec_blocks(n), 256, 0, s>>>(x, n, ctl);
+  launch_pdl(zero_if_rhs_zero_k, vec_blocks(n), 256, 0, s, x, n, ctl);
   SAAMG_LAUNCH();
 }
 
 void pcg_graph_beta(const double* part_rz, const double* part_zq, int rule, PcgCtl* ctl,
                     cudaStream_t s) {
-  graph_beta_k<<<1, kRedThreads, 0, s>>>(part_rz, part_zq, rule, ctl);
+  launch_pdl(graph_beta_k, 1, kRedThreads, 0, s, part_rz, part_zq, rule, ctl);
   SAAMG_LAUNCH();
 }
 
 void pcg_graph_check(const double* partials, PcgCtl* ctl, cudaGraphConditionalHandle cond,
                      int maxit, cudaStream_t s) {
-  graph_check_k<<<1, kRedThreads, 0, s>>>(partials, ctl, cond, maxit);
+  launch_pdl(graph_check_k, 1, kRedThreads, 0, s, partials, ctl, cond, maxit);
   SAAMG_LAUNCH();
 }
 
 void pcg_store_true(const double* partials, PcgCtl* ctl, cudaStream_t s) {
-  store_true_k<<<1, kRedThreads, 0, s>>>(partials, ctl);
+  launch_pdl(store_true_k, 1, kRedThreads, 0, s, partials, ctl);
   SAAMG_LAUNCH();
 }
 
 template <class TZ>
 void vec_copy_to_double(int n, const TZ* z, double* p, cudaStream_t s) {
-  copy_k<TZ><<<vec_blocks(n), 256, 0, s>>>(n, z, p);
+  launch_pdl(copy_k<TZ>, vec_blocks(n), 256, 0, s, n, z, p);
   SAAMG_LAUNCH();
 }
 template void vec_copy_to_double<double>(int, const double*, double*, cudaStream_t);

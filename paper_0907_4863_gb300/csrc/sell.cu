@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(256) sell_k(int n, int nslices, const int* __r
                                               TV* __restrict__ d, const TV* __restrict__ invd,
                                               TV c1, TV c2, double* __restrict__ partials,
                                               const double* __restrict__ xscale) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   double dacc = 0.0;
@@ -162,13 +163,13 @@ void sell_apply(int mode, const DevSell& S, const TM* val, const TV* x, TV* y, c
 #define SAAMG_SELL_CASE(M)                                                                    \
   case M:                                                                                     \
     if (S.index_bytes == 2)                                                                   \
-      sell_k<TV, TM, M, true><<<blocks, 256, 0, s>>>(S.n, S.nslices, S.perm.p, S.soff.p,      \
-                                                     nullptr, S.dcol.p, val, x, y, b, d, invd, \
-                                                     c1, c2, partials, xscale);               \
+      launch_pdl(sell_k<TV, TM, M, true>, blocks, 256, 0, s, S.n, S.nslices, S.perm.p,       \
+                 S.soff.p, nullptr, S.dcol.p, val, x, y, b, d, invd, c1, c2, partials,        \
+                 xscale);                                                                     \
     else                                                                                      \
-      sell_k<TV, TM, M, false><<<blocks, 256, 0, s>>>(S.n, S.nslices, S.perm.p, S.soff.p,     \
-                                                      S.col.p, nullptr, val, x, y, b, d, invd, \
-                                                      c1, c2, partials, xscale);              \
+      launch_pdl(sell_k<TV, TM, M, false>, blocks, 256, 0, s, S.n, S.nslices, S.perm.p,      \
+                 S.soff.p, S.col.p, nullptr, val, x, y, b, d, invd, c1, c2, partials,         \
+                 xscale);                                                                     \
     break;
   switch (mode) {
     SAAMG_SELL_CASE(CSR_SPMV)

@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(256) stencil_k(StencilDev<T> S, const T* __res
                                                  double* __restrict__ partials,
                                                  const double* __restrict__ xscale,
                                                  const int* __restrict__ agg) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   const int nw = gridDim.x * wpb;
@@ -409,8 +410,8 @@ void launch_shaped(const StencilCfg& cfg, long long units, int blocks_cap, const
   const int blocks = (int)std::max<long long>(1, std::min<long long>(need, blocks_cap));
 #define SAAMG_SHAPE(KK, PP)                                                                  \
   if (cfg.k == KK && (cfg.packed != 0) == PP) {                                              \
-    stencil_k<T, MODE, KK, PP><<<blocks, cfg.block, 0, s>>>(S, x, y, b, d, c1, c2, c2i0,     \
-                                                            partials, xscale, agg);          \
+    launch_pdl(stencil_k<T, MODE, KK, PP>, blocks, cfg.block, 0, s, S, x, y, b, d, c1, c2,   \
+               c2i0, partials, xscale, agg);                                                 \
     return;                                                                                  \
   }
   SAAMG_SHAPE(1, false)
@@ -452,12 +453,13 @@ void stencil_apply(const StencilDev<T>& S, int mode, const T* x, T* y, const T* 
     // reductions: the fixed grid and the default shape, so that partial sums are always
     // taken the same way
     constexpr bool P = packed_rows<T>();
+    const int* no_agg = nullptr;
     if (mode == ST_SPMV_DOT)
-      stencil_k<T, ST_SPMV_DOT, kChunks<T>(), P><<<kRedBlocks, kRedThreads, 0, s>>>(
-          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
+      launch_pdl(stencil_k<T, ST_SPMV_DOT, kChunks<T>(), P>, kRedBlocks, kRedThreads, 0, s, S, x,
+                 y, b, d, c1, c2, c2i0, partials, xscale, no_agg);
     else
-      stencil_k<T, ST_DINV_DOT, kChunks<T>(), P><<<kRedBlocks, kRedThreads, 0, s>>>(
-          S, x, y, b, d, c1, c2, c2i0, partials, xscale, nullptr);
+      launch_pdl(stencil_k<T, ST_DINV_DOT, kChunks<T>(), P>, kRedBlocks, kRedThreads, 0, s, S, x,
+                 y, b, d, c1, c2, c2i0, partials, xscale, no_agg);
     SAAMG_LAUNCH();
     return;
   }
