@@ -10,6 +10,7 @@ mixed-precision, batched and serving legs.  --impl reference times the FP64 CPU 
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -67,6 +68,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default level-0 stencil launch shapes")
+    ap.add_argument("--leg", choices=["batched", "serving"], default=None,
+                    help="run only this leg and print its JSON (no headline line)")
     ap.add_argument("--serve-requests", type=int, default=10000,
                     help="requests of the 10,000-request serving stream to replay")
     return ap.parse_args()
@@ -713,9 +716,16 @@ def batched_leg(S, torch):
     inst = I.batched_instances()
     hs32, hs64, rhos = [], [], []
     degrees = []
+    # stencil launch shape per instance class (geometry kind, grid volume to a factor of 2),
+    # tuned on the class's first instance and reused for the others
+    shapes = {}
     for k, w in enumerate(inst):
         dom, grid = S.make_domain(w.domain), S.make_grid(w.grid)
-        op = shaped_operator(S, dom, grid, w.mode)
+        op = S.build_operator(dom, grid, w.mode)
+        cls = (k % 3, int(math.log2(w.grid.nbox)))
+        if cls not in shapes:
+            shapes[cls] = S.autotune_stencil(op, 1)[0]
+        S.set_stencil_config(op, 1, shapes[cls])
         h32 = S.setup(op, S.params_default(max_coarse=4096, precision=1, beta_rule=1))
         h64 = S.setup(op, S.params_default(max_coarse=4096))
         r = [torch.from_numpy(I.gaussian_bunch(w.grid, w.centre, w.sigma, 1234 + 4 * k + j)).cuda()
@@ -801,6 +811,7 @@ def batched_leg(S, torch):
            "max_rel_err_vs_oracle": err_orc,
            "oracle_sample": f"instances {sample} x 4 rhs ({len(cases)} solves)",
            "autotuned_degrees": {d: degrees.count(d) for d in sorted(set(degrees))},
+           "stencil_shape_classes": len(shapes),
            "iters_fp32_mean": statistics.fmean(i["iters"] for i in infos),
            "iters_fp64_mean": statistics.fmean(its64)}
     for h in hs32 + hs64:
@@ -997,10 +1008,26 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_leg(args):
+    """One extra leg on its own (for profiling it or running it alone)."""
+    import torch
+    from paper_0907_4863_gb300 import saamg as S
+    _, local, _ = dist_env()
+    torch.cuda.set_device(local)
+    S.use_torch_allocator()
+    if args.leg == "batched":
+        out = batched_leg(S, torch)
+    else:
+        out = serving_leg(S, torch, args.serve_requests)
+    print(json.dumps({"leg": args.leg, **out}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.leg:
+        run_leg(args)
     else:
         run_ours(args)
 
