@@ -478,14 +478,14 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
     ProlongState pst;
     SpgemmPlan ap_plan;
     if (PL) {
-      prolongator_start(A, L.agg.p, nagg, pst, s, &PL->P);
+      prolongator_start(A, L.agg.p, nagg, pst, s, &PL->P, l == 0);
       spgemm_symbolic(A, PL->P, ap_plan, s);
       pt.mark("L" + std::to_string(l) + ".early");
     }
     L.lambda = power_lambda_finish(power, s2);
     L.omega = 4.0 / (3.0 * L.lambda);
     pt.mark("L" + std::to_string(l) + ".lambda");
-    if (!PL) prolongator_start(A, L.agg.p, nagg, pst, s);
+    if (!PL) prolongator_start(A, L.agg.p, nagg, pst, s, nullptr, l == 0);
     prolongator_finish(pst, L.invd.p, L.omega, L.P, s);
     pt.mark("L" + std::to_string(l) + ".P");
     if (PL) transpose_known(L.P, PL->R, L.R, s);

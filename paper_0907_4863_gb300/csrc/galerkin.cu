@@ -737,6 +737,49 @@ __global__ void tentative_k(int n, const int* __restrict__ agg, int* __restrict_
   if (i == n) rowptr[n] = n;
 }
 
+// Row i of A T for the level-0 operator (rows of at most 8 entries, the 7-point star): the
+// distinct aggregates of the row's columns in ascending order, each with the sum of its
+// entries in entry order starting from 0 -- the sums of the merge product A T, whose products
+// a_ij * 1 are exact -- a thread per row.  COUNT: the number of distinct aggregates only.  A
+// longer row sets *err and is skipped.
+template <bool COUNT>
+__global__ void at_stencil_k(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                             const double* __restrict__ val, const int* __restrict__ agg,
+                             int* __restrict__ cnt, const int* __restrict__ out_rowptr,
+                             int* __restrict__ out_col, double* __restrict__ out_val,
+                             int* __restrict__ err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int p0 = rowptr[i], len = rowptr[i + 1] - p0;
+  if (len > 8) {
+    *err = 1;
+    return;
+  }
+  int key[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) key[q] = q < len ? agg[col[p0 + q]] : INT_MAX;
+  const int o = COUNT ? 0 : out_rowptr[i];
+  int m = 0, last = -1;
+  for (;;) {
+    int next = INT_MAX;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (key[q] > last && key[q] < next) next = key[q];
+    if (next == INT_MAX) break;
+    if (!COUNT) {
+      double sum = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (key[q] == next) sum += val[p0 + q];
+      out_col[o + m] = next;
+      out_val[o + m] = sum;
+    }
+    ++m;
+    last = next;
+  }
+  if (COUNT) cnt[i] = m;
+}
+
 // --- A T and the smoothed prolongator ------------------------------------------
 // Row i of A T (T(j, agg(j)) = 1) holds the distinct aggregates agg(j) of A's row i, each with
 // the sum of the row's a_ij over it.  A group of G lanes takes one row, G entries at a time:
@@ -1221,7 +1264,7 @@ void smoothed_prolongator(DevCsr& AT, const int* agg, const double* invd, double
                           DevCsr& P, cudaStream_t s);
 
 void prolongator_start(const DevCsr& A, const int* agg, int nagg, ProlongState& st,
-                       cudaStream_t s, const DevCsr* known) {
+                       cudaStream_t s, const DevCsr* known, bool stencil_rows) {
   const int n = A.n;
   st.n = n;
   st.nagg = nagg;
@@ -1229,7 +1272,46 @@ void prolongator_start(const DevCsr& A, const int* agg, int nagg, ProlongState& 
   st.agg = agg;
   const double avg = n > 0 ? (double)A.nnz / n : 0.0;
   st.lists = avg > 8.0;
-  if (!st.lists) {  // short rows (level 0): T and the register k-way merge product
+  if (!st.lists && stencil_rows) {  // the 7-point operator: A T a row at a time
+    DevCsr& AT = st.AT;
+    AT.n = n;
+    AT.m = nagg;
+    AT.rowptr.alloc(n + 1, s);
+    Buf<int> err;
+    err.alloc(1, s);
+    fill_int(err.p, 0, 1, s);
+    if (known) {
+      SAAMG_CUDA(cudaMemcpyAsync(AT.rowptr.p, known->rowptr.p, sizeof(int) * (n + 1),
+                                 cudaMemcpyDeviceToDevice, s));
+      AT.nnz = known->nnz;
+    } else {
+      Buf<int> cnt;
+      cnt.alloc(n + 1, s);
+      {
+        KernelTimer kt(SAAMG_KT_SPGEMM, n, s);
+        at_stencil_k<true><<<blocks_for(n), 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, agg,
+                                                         cnt.p, nullptr, nullptr, nullptr,
+                                                         err.p);
+        SAAMG_LAUNCH();
+      }
+      fill_int(cnt.p + n, 0, 1, s);
+      AT.nnz = exclusive_scan(cnt.p, AT.rowptr.p, n + 1, s);
+    }
+    AT.col.alloc(AT.nnz, s);
+    AT.val.alloc(AT.nnz, s);
+    {
+      KernelTimer kt(SAAMG_KT_SPGEMM, n, s);
+      at_stencil_k<false><<<blocks_for(n), 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, agg,
+                                                        nullptr, AT.rowptr.p, AT.col.p, AT.val.p,
+                                                        err.p);
+      SAAMG_LAUNCH();
+    }
+    int herr = 0;
+    d2h_sync(&herr, err.p, sizeof(int), s);
+    if (herr) fail(SAAMG_ECUDA, "level-0 operator row with more than 8 entries");
+    return;
+  }
+  if (!st.lists) {  // short rows: T and the register k-way merge product
     DevCsr T;
     tentative(agg, n, nagg, T, s);
     SpgemmPlan plan;

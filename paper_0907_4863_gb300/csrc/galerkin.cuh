@@ -71,8 +71,10 @@ struct ProlongState {
   const DevCsr* A = nullptr;
   const int* agg = nullptr;
 };
+// stencil_rows: A is the level-0 operator (rows of at most 8 entries), whose A T is formed a
+// row at a time, with the sums of the general product.
 void prolongator_start(const DevCsr& A, const int* agg, int nagg, ProlongState& st,
-                       cudaStream_t s, const DevCsr* known = nullptr);
+                       cudaStream_t s, const DevCsr* known = nullptr, bool stencil_rows = false);
 void prolongator_finish(ProlongState& st, const double* invd, double omega, DevCsr& P,
                         cudaStream_t s);
 
