@@ -31,6 +31,19 @@ __device__ __forceinline__ void csr_group_row(int row, bool active, int gl,
   if (MODE != CSR_CHEB0 && active) {
     const int p0 = rowptr[row], p1 = rowptr[row + 1];
     int p = p0 + gl;
+    for (; p + 7 * G < p1; p += 8 * G) {
+      int kk[8];
+      TV a[8], xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        kk[u] = col[p + u * G];
+        a[u] = (TV)ldv(val, p + u * G);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) xv[u] = x[kk[u]];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc += a[u] * xv[u];
+    }
     for (; p + 3 * G < p1; p += 4 * G) {
       const int k0 = col[p], k1 = col[p + G], k2 = col[p + 2 * G], k3 = col[p + 3 * G];
       const TV a0 = (TV)ldv(val, p), a1 = (TV)ldv(val, p + G), a2 = (TV)ldv(val, p + 2 * G),
@@ -116,7 +129,21 @@ __device__ __forceinline__ void sell_row(int s, int lane, int n, const int* __re
   if (MODE != CSR_CHEB0) {
     const int e0 = soff[s] + lane, w = (soff[s + 1] - soff[s]) >> 5;
     int k = 0;
-    // four independent (column, value, x) loads in flight per lane
+    // eight independent (column, value, x) loads in flight per lane
+    for (; k + 8 <= w; k += 8) {
+      const int e = e0 + 32 * k;
+      int kk[8];
+      TV a[8], xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        kk[u] = REL ? row + dcol[e + 32 * u] : col[e + 32 * u];
+        a[u] = (TV)ldv(val, e + 32 * u);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) xv[u] = x[kk[u]];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc = fma(a[u], xv[u], acc);
+    }
     for (; k + 4 <= w; k += 4) {
       const int e = e0 + 32 * k;
       const int k0 = REL ? row + dcol[e] : col[e];
