@@ -242,7 +242,10 @@ saamg_status saamg_vcycle(const saamg_hierarchy *h, const double *r, double *z, 
 saamg_status saamg_solve(saamg_hierarchy *h, const double *rho, double *phi, double rtol,
                          void *stream, saamg_solve_info *info);
 
-/* Same as saamg_solve with HOST box arrays; the host<->device copies are part of the call. */
+/* Same as saamg_solve with HOST box arrays; the host<->device transfers are part of the call.
+ * Page-locked (pinned) arrays are read by the gather and written by the scatter kernels
+ * directly through their mapped device addresses (each value crosses the host link once, no
+ * staging copy); pageable arrays are staged through device box arrays allocated for the call. */
 saamg_status saamg_solve_host(saamg_hierarchy *h, const double *rho_host, double *phi_host,
                               double rtol, void *stream, saamg_solve_info *info);
 

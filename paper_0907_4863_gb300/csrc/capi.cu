@@ -1441,6 +1441,17 @@ saamg_status saamg_solve(saamg_hierarchy* h, const double* rho, double* phi, dou
   return g != SAAMG_OK ? g : (saamg_status)st;
 }
 
+// The device address of page-locked host memory mapped into the device's address space, or
+// NULL for other memory.
+static void* mapped_host(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 saamg_status saamg_solve_host(saamg_hierarchy* h, const double* rho_host, double* phi_host,
                               double rtol, void* stream, saamg_solve_info* info) {
   saamg_solve_info local{};
@@ -1454,19 +1465,28 @@ saamg_status saamg_solve_host(saamg_hierarchy* h, const double* rho_host, double
     cudaStream_t s = (cudaStream_t)stream;
     const OperatorData& od = h->op->d;
     size_t nbox = (size_t)od.g.nx * od.g.ny * od.g.nz;
+    // Pinned (page-locked, mapped) host arrays are read by the gather and written by the
+    // scatter directly, through their device addresses: the values cross the host link once,
+    // with no staging copy.  Other host memory is staged through device box arrays.
+    const double* rho_dev = static_cast<const double*>(mapped_host(rho_host));
+    double* phi_dev = static_cast<double*>(mapped_host(phi_host));
     Buf<double> rho, phi;
-    rho.alloc(nbox, s);
-    phi.alloc(nbox, s);
-    SAAMG_CUDA(cudaMemcpyAsync(rho.p, rho_host, nbox * 8, cudaMemcpyHostToDevice, s));
-    SAAMG_CUDA(cudaMemcpyAsync(phi.p, phi_host, nbox * 8, cudaMemcpyHostToDevice, s));
-    if (h->prm.device_loop) {
-      st = solve_device(h, rho.p, phi.p, rtol, s, info);
-    } else {
-      gather_rhs(od, rho.p, phi.p, h->bhat.p, h->xhat.p, s);
-      st = pcg_impl(h, rtol, s, info);
-      scatter_solution(od, h->xhat.p, phi.p, s);
+    if (!rho_dev || !phi_dev) {
+      rho.alloc(nbox, s);
+      phi.alloc(nbox, s);
+      SAAMG_CUDA(cudaMemcpyAsync(rho.p, rho_host, nbox * 8, cudaMemcpyHostToDevice, s));
+      SAAMG_CUDA(cudaMemcpyAsync(phi.p, phi_host, nbox * 8, cudaMemcpyHostToDevice, s));
+      rho_dev = rho.p;
+      phi_dev = phi.p;
     }
-    SAAMG_CUDA(cudaMemcpyAsync(phi_host, phi.p, nbox * 8, cudaMemcpyDeviceToHost, s));
+    if (h->prm.device_loop) {
+      st = solve_device(h, rho_dev, phi_dev, rtol, s, info);
+    } else {
+      gather_rhs(od, rho_dev, phi_dev, h->bhat.p, h->xhat.p, s);
+      st = pcg_impl(h, rtol, s, info);
+      scatter_solution(od, h->xhat.p, phi_dev, s);
+    }
+    if (phi.p) SAAMG_CUDA(cudaMemcpyAsync(phi_host, phi.p, nbox * 8, cudaMemcpyDeviceToHost, s));
     SAAMG_CUDA(cudaStreamSynchronize(s));
   });
   info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

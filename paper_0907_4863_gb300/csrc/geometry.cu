@@ -599,20 +599,23 @@ __global__ void gather_k(GeomParams g, const LineInfo* __restrict__ lines,
   if (xhat) xhat[row] = phi0 ? phi0[box] / si : 0.0;
 }
 
-__global__ void scatter_k(const GeomParams g, const LineInfo* __restrict__ lines,
-                          const int2* __restrict__ chunks, int nchunks,
-                          const double* __restrict__ scale, const double* __restrict__ xhat,
-                          double* __restrict__ phi) {
-  int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (c >= nchunks) return;
-  int2 ch = chunks[c];
-  int L = ch.x;
-  LineInfo me = lines[L];
-  int i = me.lo + ch.y + lane;
-  if (i > me.hi) return;
-  int row = me.start + ch.y + lane;
-  phi[(size_t)i + (size_t)g.nx * (size_t)L] = scale[row] * xhat[row];
+// Every node of the box: the scaled-back unknown on its line run, 0 elsewhere (one pass that
+// writes each element once, so phi may be a box array in device or in pinned host memory).
+__global__ void scatter_full_k(const GeomParams g, const LineInfo* __restrict__ lines,
+                               const double* __restrict__ scale, const double* __restrict__ xhat,
+                               size_t nbox, double* __restrict__ phi) {
+  for (size_t b = blockIdx.x * (size_t)blockDim.x + threadIdx.x; b < nbox;
+       b += (size_t)gridDim.x * blockDim.x) {
+    const int L = (int)(b / (size_t)g.nx);
+    const int i = (int)(b - (size_t)L * g.nx);
+    const LineInfo me = lines[L];
+    double v = 0.0;
+    if (i >= me.lo && i <= me.hi) {
+      const int row = me.start + (i - me.lo);
+      v = scale[row] * xhat[row];
+    }
+    phi[b] = v;
+  }
 }
 
 inline int warp_blocks(long long warps) { return (int)((warps * 32 + 255) / 256); }
@@ -976,10 +979,10 @@ void gather_rhs(const OperatorData& op, const double* rho, const double* phi0, d
 
 void scatter_solution(const OperatorData& op, const double* xhat, double* phi, cudaStream_t s) {
   size_t nbox = (size_t)op.g.nx * op.g.ny * op.g.nz;
-  SAAMG_CUDA(cudaMemsetAsync(phi, 0, nbox * sizeof(double), s));
-  if (op.n == 0) return;
-  scatter_k<<<warp_blocks(op.nchunks), 256, 0, s>>>(op.g, op.lines.p, op.chunks.p, op.nchunks,
-                                                     op.scale.p, xhat, phi);
+  if (nbox == 0) return;
+  const size_t need = (nbox + 255) / 256;
+  const int blocks = (int)(need < (size_t)sm_count() * 16 ? need : (size_t)sm_count() * 16);
+  scatter_full_k<<<blocks, 256, 0, s>>>(op.g, op.lines.p, op.scale.p, xhat, nbox, phi);
   SAAMG_LAUNCH();
 }
 

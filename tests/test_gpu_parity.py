@@ -203,6 +203,14 @@ def test_solve_edge_cases(S):
     infoh = S.solve_host(h, rh, ph)
     assert infoh["iters"] == info["iters"]
     assert np.array_equal(ph, phi.cpu().numpy())
+    # pinned host arrays (read and written in place by the gather and scatter kernels); the
+    # box corner lies outside the pipe: its initial value is ignored and 0 comes back
+    rp = torch.from_numpy(rh).pin_memory()
+    pp = torch.zeros(nbox, dtype=torch.float64).pin_memory()
+    pp[0] = 7.0
+    infop = S.solve_host(h, rp.numpy(), pp.numpy())
+    assert infop["iters"] == info["iters"]
+    assert torch.equal(pp, phi.cpu())
     # single level: the V-cycle is the exact inverse
     w1 = I.cylinder_workload(10, I.QUADRATIC)
     h1 = S.setup(gpu_op(S, w1), S.params_default(max_coarse=10 ** 6))
