@@ -488,13 +488,28 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
     if (!PL) prolongator_start(A, L.agg.p, nagg, pst, s, nullptr, l == 0);
     prolongator_finish(pst, L.invd.p, L.omega, L.P, s);
     pt.mark("L" + std::to_string(l) + ".P");
-    if (PL) transpose_known(L.P, PL->R, L.R, s);
-    else transpose(L.P, L.R, s);
-    pt.mark("L" + std::to_string(l) + ".R");
+    // R = P^T on the second stream (it waits on the host for nothing) while A P runs on s
+    {
+      cudaEvent_t ev;
+      SAAMG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      SAAMG_CUDA(cudaEventRecord(ev, s));
+      SAAMG_CUDA(cudaStreamWaitEvent(s2, ev, 0));
+      cudaEventDestroy(ev);
+    }
+    if (PL) transpose_known(L.P, PL->R, L.R, s2);
+    else transpose(L.P, L.R, s2);
     if (!PL) spgemm_symbolic(A, L.P, ap_plan, s);
     DevCsr AP;
     spgemm_numeric(A, L.P, ap_plan, AP, s);
     pt.mark("L" + std::to_string(l) + ".AP");
+    {
+      cudaEvent_t ev;
+      SAAMG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      SAAMG_CUDA(cudaEventRecord(ev, s2));
+      SAAMG_CUDA(cudaStreamWaitEvent(s, ev, 0));
+      cudaEventDestroy(ev);
+    }
+    pt.mark("L" + std::to_string(l) + ".R");
     auto N = std::make_unique<Level>();
     {
       SpgemmPlan rap_plan;

@@ -251,6 +251,7 @@ constexpr int kRedThreads = 256;
 // ---------------------------------------------------------------------------
 // scan.cu
 long long exclusive_scan(const int* in, int* out, int n, cudaStream_t s);  // returns the total
+void exclusive_scan_async(const int* in, int* out, int n, cudaStream_t s);  // no host wait
 long long exclusive_scan_u8(const unsigned char* in, int* out, int n, cudaStream_t s);
 // Same scan of bytes with caller-provided tile scratch (scan_u8_tiles_needed(n) entries);
 // allocates nothing.

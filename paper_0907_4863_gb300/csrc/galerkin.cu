@@ -1397,7 +1397,7 @@ void transpose(const DevCsr& P, DevCsr& R, cudaStream_t s) {
     SAAMG_LAUNCH();
   }
   R.rowptr.alloc(P.m + 1, s);
-  exclusive_scan(cnt.p, R.rowptr.p, P.m + 1, s);
+  exclusive_scan_async(cnt.p, R.rowptr.p, P.m + 1, s);  // the total is P.nnz
   SAAMG_CUDA(cudaMemcpyAsync(fill.p, R.rowptr.p, sizeof(int) * (P.m + 1), cudaMemcpyDeviceToDevice, s));
   R.col.alloc(P.nnz, s);
   R.val.alloc(P.nnz, s);

@@ -78,7 +78,8 @@ void prolongator_start(const DevCsr& A, const int* agg, int nagg, ProlongState& 
 void prolongator_finish(ProlongState& st, const double* invd, double omega, DevCsr& P,
                         cudaStream_t s);
 
-// R = P^T with ascending columns in every row.
+// R = P^T with ascending columns in every row.  Enqueued on s without any host wait (so it can
+// run on a second stream beside other work).
 void transpose(const DevCsr& P, DevCsr& R, cudaStream_t s);
 // The same when R's pattern is known (`known`, the transpose of a P of the same pattern):
 // the pattern is copied and every value moved to its place (a search in its row of R).

@@ -92,7 +92,7 @@ __global__ void scan_add(int* __restrict__ out, const long long* __restrict__ ti
 }
 
 template <class TIn>
-long long scan_impl(const TIn* in, int* out, int n, cudaStream_t s) {
+long long scan_impl(const TIn* in, int* out, int n, cudaStream_t s, bool readback = true) {
   if (n <= 0) return 0;
   int ntiles = (n + kScanTile - 1) / kScanTile;
   Buf<long long> tiles;
@@ -103,6 +103,7 @@ long long scan_impl(const TIn* in, int* out, int n, cudaStream_t s) {
   SAAMG_LAUNCH();
   scan_add<<<ntiles, 256, 0, s>>>(out, tiles.p, n);
   SAAMG_LAUNCH();
+  if (!readback) return -1;
   long long total = 0;
   d2h_sync(&total, tiles.p + ntiles, sizeof(long long), s);
   return total;
@@ -160,6 +161,10 @@ long long exclusive_scan_u8_into(const unsigned char* in, int* out, int n, long 
 
 long long exclusive_scan(const int* in, int* out, int n, cudaStream_t s) {
   return scan_impl<int>(in, out, n, s);
+}
+
+void exclusive_scan_async(const int* in, int* out, int n, cudaStream_t s) {
+  scan_impl<int>(in, out, n, s, false);
 }
 
 long long exclusive_scan_u8(const unsigned char* in, int* out, int n, cudaStream_t s) {
