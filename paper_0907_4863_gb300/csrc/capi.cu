@@ -479,7 +479,7 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
     SpgemmPlan ap_plan;
     if (PL) {
       prolongator_start(A, L.agg.p, nagg, pst, s, &PL->P, l == 0);
-      spgemm_symbolic(A, PL->P, ap_plan, s);
+      spgemm_symbolic(A, PL->P, ap_plan, s, PL->APpat.n > 0 ? &PL->APpat : nullptr);
       pt.mark("L" + std::to_string(l) + ".early");
     }
     L.lambda = power_lambda_finish(power, s2);
@@ -515,6 +515,13 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
       SpgemmPlan rap_plan;
       spgemm_symbolic(L.R, AP, rap_plan, s, PL ? &prev->lev[l + 1]->A : nullptr);
       spgemm_numeric(L.R, AP, rap_plan, N->A, s);
+    }
+    if (l >= 1) {  // keep the pattern of A P (a level-0 one would cost 8 B per entry of 57 M)
+      L.APpat.n = AP.n;
+      L.APpat.m = AP.m;
+      L.APpat.nnz = AP.nnz;
+      L.APpat.rowptr = std::move(AP.rowptr);
+      L.APpat.col = std::move(AP.col);
     }
     pt.mark("L" + std::to_string(l) + ".RAP");
     N->n = N->A.n;
@@ -571,7 +578,8 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
   pt.flush("setup");
   long long bytes = 0;
   for (auto& L : h->lev) {
-    bytes += L->A.bytes() + L->P.bytes() + L->R.bytes() + L->invd.bytes() + L->invd32.bytes() +
+    bytes += L->A.bytes() + L->P.bytes() + L->R.bytes() + L->APpat.bytes() + L->invd.bytes() +
+             L->invd32.bytes() +
              L->agg.bytes() + L->root.bytes() + L->ids.bytes() + L->As.bytes() + L->P32.bytes() +
              L->R32.bytes();
   }
@@ -627,6 +635,7 @@ static void work_set_impl(const saamg_hierarchy* src, cudaStream_t s, saamg_hier
     for (int k = 0; k < 3; ++k) L->dims[k] = S->dims[k];
     borrow_csr(L->P, S->P);
     borrow_csr(L->R, S->R);
+    borrow_csr(L->APpat, S->APpat);
     L->lambda = S->lambda;
     L->omega = S->omega;
     L->cheb = S->cheb;

@@ -30,6 +30,8 @@ struct Level {
   Buf<unsigned> ids;            // lattice ids of the nodes (cube aggregation, levels >= 1)
   int dims[3] = {0, 0, 0};      // lattice of the ids (cube aggregation)
   DevCsr P, R;                  // to the next level
+  DevCsr APpat;                 // pattern of A_l P_l (levels >= 1): a reusing setup skips its
+                                // symbolic pass
   double lambda = 0, omega = 0;
   ChebCoef cheb;
   // V-cycle work vectors (FP64 and FP32 sets; only the one for the precision is allocated)
