@@ -485,7 +485,11 @@ static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaSt
     L.lambda = power_lambda_finish(power, s2);
     L.omega = 4.0 / (3.0 * L.lambda);
     pt.mark("L" + std::to_string(l) + ".lambda");
-    if (!PL) prolongator_start(A, L.agg.p, nagg, pst, s, nullptr, l == 0);
+    if (!PL) {
+      pst.invd = L.invd.p;
+      pst.omega = L.omega;
+      prolongator_start(A, L.agg.p, nagg, pst, s, nullptr, l == 0);
+    }
     prolongator_finish(pst, L.invd.p, L.omega, L.P, s);
     pt.mark("L" + std::to_string(l) + ".P");
     // R = P^T on the second stream (it waits on the host for nothing) while A P runs on s

@@ -740,44 +740,82 @@ __global__ void tentative_k(int n, const int* __restrict__ agg, int* __restrict_
 // Row i of A T for the level-0 operator (rows of at most 8 entries, the 7-point star): the
 // distinct aggregates of the row's columns in ascending order, each with the sum of its
 // entries in entry order starting from 0 -- the sums of the merge product A T, whose products
-// a_ij * 1 are exact -- a thread per row.  COUNT: the number of distinct aggregates only.  A
-// longer row sets *err and is skipped.
-template <bool COUNT>
-__global__ void at_stencil_k(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
-                             const double* __restrict__ val, const int* __restrict__ agg,
-                             int* __restrict__ cnt, const int* __restrict__ out_rowptr,
-                             int* __restrict__ out_col, double* __restrict__ out_val,
-                             int* __restrict__ err) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int p0 = rowptr[i], len = rowptr[i + 1] - p0;
-  if (len > 8) {
-    *err = 1;
-    return;
-  }
-  int key[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) key[q] = q < len ? agg[col[p0 + q]] : INT_MAX;
-  const int o = COUNT ? 0 : out_rowptr[i];
-  int m = 0, last = -1;
-  for (;;) {
-    int next = INT_MAX;
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (key[q] > last && key[q] < next) next = key[q];
-    if (next == INT_MAX) break;
-    if (!COUNT) {
-      double sum = 0.0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (key[q] == next) sum += val[p0 + q];
-      out_col[o + m] = next;
-      out_val[o + m] = sum;
+// a_ij * 1 are exact -- a lane per row.  A warp takes 32 consecutive rows: their entries
+// (contiguous in A) come into shared memory by coalesced loads, with each column's aggregate,
+// and the rows' outputs (contiguous in the result) go back the same way.  COUNT: the number of
+// distinct aggregates only.  FINAL: P's values [J == agg(i)] - (omega invd_i) (A T)_iJ instead
+// of (A T)_iJ (the expression of prolong_values_k).  A longer row sets *err.
+constexpr int kAtWarps = 4;
+template <bool COUNT, bool FINAL>
+__global__ void __launch_bounds__(32 * kAtWarps) at_stencil_k(
+    int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+    const double* __restrict__ val, const int* __restrict__ agg, const double* __restrict__ invd,
+    double omega, int* __restrict__ cnt, const int* __restrict__ out_rowptr,
+    int* __restrict__ out_col, double* __restrict__ out_val, int* __restrict__ err) {
+  __shared__ int skey[kAtWarps][256];
+  __shared__ double sval[kAtWarps][256];
+  __shared__ int ocol[kAtWarps][256];
+  __shared__ double oval[kAtWarps][256];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int r0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; r0 < n; r0 += nw * 32) {
+    const int rend = min(n, r0 + 32);
+    const int e0 = rowptr[r0], ne = rowptr[rend] - e0;
+    if (ne > 256) {  // some row has more than 8 entries (uniform across the warp)
+      if (lane == 0) *err = 1;
+      continue;
     }
-    ++m;
-    last = next;
+    for (int q = lane; q < ne; q += 32) {
+      skey[wib][q] = agg[col[e0 + q]];
+      if (!COUNT) sval[wib][q] = val[e0 + q];
+    }
+    __syncwarp();
+    const int i = r0 + lane;
+    const int o0 = COUNT ? 0 : out_rowptr[r0];
+    if (i < n) {
+      const int p0 = rowptr[i] - e0, len = rowptr[i + 1] - rowptr[i];
+      if (len > 8) *err = 1;
+      int key[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) key[q] = q < len ? skey[wib][p0 + q] : INT_MAX;
+      int m = 0, last = -1;
+      const int oi = COUNT ? 0 : out_rowptr[i] - o0;
+      const double w = FINAL ? omega * invd[i] : 0.0;
+      const int a = FINAL ? agg[i] : 0;
+      for (;;) {
+        int next = INT_MAX;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (key[q] > last && key[q] < next) next = key[q];
+        if (next == INT_MAX) break;
+        if (!COUNT) {
+          double sum = 0.0;
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (key[q] == next) sum += sval[wib][p0 + q];
+          double v = sum;
+          if (FINAL) {
+            const double tij = (next == a) ? 1.0 : 0.0;
+            v = tij - w * sum;
+          }
+          ocol[wib][oi + m] = next;
+          oval[wib][oi + m] = v;
+        }
+        ++m;
+        last = next;
+      }
+      if (COUNT) cnt[i] = m;
+    }
+    __syncwarp();
+    if (!COUNT) {
+      const int no = out_rowptr[rend] - o0;
+      for (int q = lane; q < no; q += 32) {
+        out_col[o0 + q] = ocol[wib][q];
+        out_val[o0 + q] = oval[wib][q];
+      }
+    }
+    __syncwarp();
   }
-  if (COUNT) cnt[i] = m;
 }
 
 // --- A T and the smoothed prolongator ------------------------------------------
@@ -991,6 +1029,12 @@ __global__ void __launch_bounds__(256) rank_rows_block_k(int n, const int* __res
 }
 
 inline int blocks_for(long long n, int t = 256) { return (int)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1); }
+// blocks of at_stencil_k: a warp per 32 rows, every warp of the grid resident at once
+inline int at_blocks(int n) {
+  const long long warps = (n + 31) / 32;
+  return (int)std::max<long long>(1, std::min<long long>((warps + kAtWarps - 1) / kAtWarps,
+                                                        (long long)sm_count() * 16));
+}
 
 constexpr int kSpgemmWarps = 4;
 // a hash class of at most this many rows runs a block per row
@@ -1289,9 +1333,9 @@ void prolongator_start(const DevCsr& A, const int* agg, int nagg, ProlongState& 
       cnt.alloc(n + 1, s);
       {
         KernelTimer kt(SAAMG_KT_SPGEMM, n, s);
-        at_stencil_k<true><<<blocks_for(n), 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, agg,
-                                                         cnt.p, nullptr, nullptr, nullptr,
-                                                         err.p);
+        at_stencil_k<true, false><<<at_blocks(n), 32 * kAtWarps, 0, s>>>(
+            n, A.rowptr.p, A.col.p, A.val.p, agg, nullptr, 0.0, cnt.p, nullptr, nullptr, nullptr,
+            err.p);
         SAAMG_LAUNCH();
       }
       fill_int(cnt.p + n, 0, 1, s);
@@ -1301,14 +1345,20 @@ void prolongator_start(const DevCsr& A, const int* agg, int nagg, ProlongState& 
     AT.val.alloc(AT.nnz, s);
     {
       KernelTimer kt(SAAMG_KT_SPGEMM, n, s);
-      at_stencil_k<false><<<blocks_for(n), 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, agg,
-                                                        nullptr, AT.rowptr.p, AT.col.p, AT.val.p,
-                                                        err.p);
+      if (st.invd)
+        at_stencil_k<false, true><<<at_blocks(n), 32 * kAtWarps, 0, s>>>(
+            n, A.rowptr.p, A.col.p, A.val.p, agg, st.invd, st.omega, nullptr, AT.rowptr.p,
+            AT.col.p, AT.val.p, err.p);
+      else
+        at_stencil_k<false, false><<<at_blocks(n), 32 * kAtWarps, 0, s>>>(
+            n, A.rowptr.p, A.col.p, A.val.p, agg, nullptr, 0.0, nullptr, AT.rowptr.p, AT.col.p,
+            AT.val.p, err.p);
       SAAMG_LAUNCH();
     }
     int herr = 0;
     d2h_sync(&herr, err.p, sizeof(int), s);
     if (herr) fail(SAAMG_ECUDA, "level-0 operator row with more than 8 entries");
+    st.final_values = st.invd != nullptr;
     return;
   }
   if (!st.lists) {  // short rows: T and the register k-way merge product
@@ -1346,6 +1396,10 @@ void prolongator_start(const DevCsr& A, const int* agg, int nagg, ProlongState& 
 
 void prolongator_finish(ProlongState& st, const double* invd, double omega, DevCsr& P,
                         cudaStream_t s) {
+  if (st.final_values) {  // formed with omega already
+    P = std::move(st.AT);
+    return;
+  }
   if (!st.lists) {
     smoothed_prolongator(st.AT, st.agg, invd, omega, P, s);
     return;

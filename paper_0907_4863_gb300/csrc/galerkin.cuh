@@ -70,6 +70,11 @@ struct ProlongState {
   Buf<double> lval;
   const DevCsr* A = nullptr;
   const int* agg = nullptr;
+  // set before _start when omega is known already: the level-0 row-at-a-time form then writes
+  // P's values at once and _finish only hands P over
+  const double* invd = nullptr;
+  double omega = 0.0;
+  bool final_values = false;
 };
 // stencil_rows: A is the level-0 operator (rows of at most 8 entries), whose A T is formed a
 // row at a time, with the sums of the general product.
