@@ -157,8 +157,8 @@ saamg_status saamg_set_allocator(saamg_alloc_fn alloc, saamg_free_fn free_fn, vo
  * on Gamma_2, the diagonal scaling, a matrix-free stencil description and an explicit
  * CSR copy for the AMG setup.  mode: saamg_boundary_mode.
  * Errors: EINVAL (NULL pointers, sizes < 1, nz < 2 (Robin) or < 3 (Dirichlet), h <= 0,
- * a, b, taper <= 0, more than 2^31 nonzeros, a lattice line whose inside nodes are not
- * contiguous), ENOMEM, ECUDA. */
+ * a, b, taper <= 0, more than 2^31 nonzeros, more than 30000 nodes along x, a lattice line
+ * whose inside nodes are not contiguous), ENOMEM, ECUDA. */
 saamg_status saamg_build_operator(const saamg_domain *domain, const saamg_grid *grid,
                                   int mode, void *stream, saamg_operator **out);
 
