@@ -84,3 +84,13 @@ def test_shape_outside_the_sets_is_rejected(S):
         S.stencil_config(op, 2)
     assert S.stencil_config(op, 1) == before
     op.free()
+
+
+def test_grid_too_long_in_x_is_rejected(S):
+    """Chunk records hold lane offsets within a line in 16 bits: more than 30000 nodes along x
+    is refused before any device work."""
+    w = I.cylinder_workload(24, I.LINEAR)
+    g = I.Grid((30001, 4, 4), (1.0 / 30001, 0.25, 0.25), (-0.5, -0.375, -0.375))
+    with pytest.raises(S.SaamgError) as e:
+        S.build_operator(S.make_domain(w.domain), S.make_grid(g), w.mode)
+    assert e.value.status == S.EINVAL
