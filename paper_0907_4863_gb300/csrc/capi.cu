@@ -372,8 +372,24 @@ static void build_level_sell(saamg_hierarchy* h, Level& L, cudaStream_t s) {
   sell_from_csr(L.A, L.As, f64, f32, bf16, s);
 }
 
+static void setup_levels(const saamg_operator* op, const saamg_params& prm, cudaStream_t s,
+                         saamg_hierarchy* h, const saamg_hierarchy* prev);
+
+// A failed setup waits for both of its streams before the hierarchy's arrays are released (the
+// second stream may still be reading them).
 static void setup_impl(const saamg_operator* op, const saamg_params& prm, cudaStream_t s,
                        saamg_hierarchy* h, const saamg_hierarchy* prev = nullptr) {
+  try {
+    setup_levels(op, prm, s, h, prev);
+  } catch (...) {
+    cudaStreamSynchronize(aux_stream());
+    cudaStreamSynchronize(s);
+    throw;
+  }
+}
+
+static void setup_levels(const saamg_operator* op, const saamg_params& prm, cudaStream_t s,
+                         saamg_hierarchy* h, const saamg_hierarchy* prev) {
   auto t0 = std::chrono::steady_clock::now();
   PhaseTimer pt(s);
   h->op = op;
