@@ -302,7 +302,7 @@ saamg_status saamg_release_batch_cache(void);
 /* Launch shape of the level-0 stencil passes of one precision (the Chebyshev steps, the
  * residual and the matrix-free prolongation; the passes with a reduction keep a fixed shape
  * so that their partial sums never change).  Every row is computed the same way under every
- * shape, so results are identical; only the time changes (the benchmark spec's stencil tile shape). */
+ * shape, so results are identical; only the time changes. */
 typedef struct saamg_stencil_config {
   int chunks_per_step; /* chunks of 32 rows per warp step: 1, 2 or 4 */
   int packed;          /* 1: 32 regular-run rows per warp from the row list, then the table
