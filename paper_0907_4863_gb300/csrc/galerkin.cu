@@ -778,33 +778,54 @@ __global__ void __launch_bounds__(32 * kAtWarps) at_stencil_k(
       int key[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) key[q] = q < len ? skey[wib][p0 + q] : INT_MAX;
-      int m = 0, last = -1;
-      const int oi = COUNT ? 0 : out_rowptr[i] - o0;
-      const double w = FINAL ? omega * invd[i] : 0.0;
-      const int a = FINAL ? agg[i] : 0;
-      for (;;) {
-        int next = INT_MAX;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (key[q] > last && key[q] < next) next = key[q];
-        if (next == INT_MAX) break;
-        if (!COUNT) {
-          double sum = 0.0;
+      if (COUNT) {
+        int m = 0, last = -1;
+        for (;;) {
+          int next = INT_MAX;
 #pragma unroll
           for (int q = 0; q < 8; ++q)
-            if (key[q] == next) sum += sval[wib][p0 + q];
-          double v = sum;
-          if (FINAL) {
-            const double tij = (next == a) ? 1.0 : 0.0;
-            v = tij - w * sum;
-          }
-          ocol[wib][oi + m] = next;
-          oval[wib][oi + m] = v;
+            if (key[q] > last && key[q] < next) next = key[q];
+          if (next == INT_MAX) break;
+          ++m;
+          last = next;
         }
-        ++m;
-        last = next;
+        cnt[i] = m;
+      } else {
+        // the output place of each entry: the number of distinct smaller aggregates (integer
+        // work only); then each entry is added into its place in entry order, from 0 -- one
+        // FP64 add per entry instead of one per (aggregate, entry) pair under a predicate
+        const int oi = out_rowptr[i] - o0, m = min(8, out_rowptr[i + 1] - out_rowptr[i]);
+        bool first[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          first[q] = key[q] != INT_MAX;
+#pragma unroll
+          for (int q2 = 0; q2 < q; ++q2) first[q] = first[q] && key[q2] != key[q];
+        }
+        int dk[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          dk[q] = 0;
+#pragma unroll
+          for (int q2 = 0; q2 < 8; ++q2) dk[q] += (first[q2] && key[q2] < key[q]) ? 1 : 0;
+        }
+        for (int o = 0; o < m; ++o) oval[wib][oi + o] = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (q < len) {
+            ocol[wib][oi + dk[q]] = key[q];
+            oval[wib][oi + dk[q]] += sval[wib][p0 + q];
+          }
+        }
+        if (FINAL) {
+          const double w = omega * invd[i];
+          const int a = agg[i];
+          for (int o = 0; o < m; ++o) {
+            const double tij = (ocol[wib][oi + o] == a) ? 1.0 : 0.0;
+            oval[wib][oi + o] = tij - w * oval[wib][oi + o];
+          }
+        }
       }
-      if (COUNT) cnt[i] = m;
     }
     __syncwarp();
     if (!COUNT) {
