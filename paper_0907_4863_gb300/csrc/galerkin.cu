@@ -846,6 +846,60 @@ __global__ void __launch_bounds__(32 * kAtWarps) at_stencil_k(
 // lane (= entry) order, and the chunk sums are merged into the row's list, kept in scratch
 // arrays laid out like A (a row never has more aggregates than entries), in order of first
 // appearance.  A row of at most G entries is therefore summed strictly in entry order.
+// The list of row i (G lanes of group `sub`; warp-collective) by lane matches, chunk by chunk.
+template <int G>
+__device__ __forceinline__ void at_list_general(int i, bool act, int p0, int len, int maxlen,
+                                                int lane, int sub, int gl, unsigned gmask,
+                                                const int* __restrict__ col,
+                                                const double* __restrict__ val,
+                                                const int* __restrict__ agg,
+                                                int* __restrict__ lcol, double* __restrict__ lval,
+                                                int* __restrict__ cnt) {
+    int m = 0;  // the group's list length
+    for (int cb = 0; cb < maxlen; cb += G) {
+      const bool ok = cb + gl < len;
+      const int p = p0 + cb + gl;
+      const int key = ok ? agg[col[p]] : -1;
+      const double v = ok ? val[p] : 0.0;
+      // the lanes of this group holding the same aggregate
+      const unsigned long long k64 = ((unsigned long long)(unsigned)sub << 32) | (unsigned)key;
+      const unsigned mt = __match_any_sync(0xffffffffu, k64);
+      int cmax = __popc(mt);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+      double sum = 0.0;
+      unsigned rem = mt;
+      for (int t = 0; t < cmax; ++t) {
+        const int src = rem ? __ffs(rem) - 1 : lane;
+        const double sv = __shfl_sync(0xffffffffu, v, src);
+        if (rem) {
+          sum = t == 0 ? sv : sum + sv;
+          rem &= rem - 1u;
+        }
+      }
+      const bool lead = ok && lane == __ffs(mt) - 1;
+      int pos = -1;
+      if (lead)
+        for (int u = 0; u < m; ++u)
+          if (lcol[p0 + u] == key) {
+            pos = u;
+            break;
+          }
+      const bool fresh = lead && pos < 0;
+      const unsigned fm = __ballot_sync(0xffffffffu, fresh) & gmask;
+      if (fresh) {
+        pos = m + __popc(fm & ((1u << lane) - 1u));
+        lcol[p0 + pos] = key;
+        lval[p0 + pos] = sum;
+      } else if (lead) {
+        lval[p0 + pos] += sum;
+      }
+      m += __popc(fm);
+      __syncwarp();
+    }
+    if (act && gl == 0) cnt[i] = m;
+}
+
 template <int G>
 __global__ void __launch_bounds__(256) at_lists_k(int n, const int* __restrict__ rowptr,
                                                   const int* __restrict__ col,
@@ -907,49 +961,91 @@ __global__ void __launch_bounds__(256) at_lists_k(int n, const int* __restrict__
       __syncwarp();
       continue;
     }
-    int m = 0;  // the group's list length
-    for (int cb = 0; cb < maxlen; cb += G) {
-      const bool ok = cb + gl < len;
-      const int p = p0 + cb + gl;
-      const int key = ok ? agg[col[p]] : -1;
-      const double v = ok ? val[p] : 0.0;
-      // the lanes of this group holding the same aggregate
-      const unsigned long long k64 = ((unsigned long long)(unsigned)sub << 32) | (unsigned)key;
-      const unsigned mt = __match_any_sync(0xffffffffu, k64);
-      int cmax = __popc(mt);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
-      double sum = 0.0;
-      unsigned rem = mt;
-      for (int t = 0; t < cmax; ++t) {
-        const int src = rem ? __ffs(rem) - 1 : lane;
-        const double sv = __shfl_sync(0xffffffffu, v, src);
-        if (rem) {
-          sum = t == 0 ? sv : sum + sv;
-          rem &= rem - 1u;
-        }
+    at_list_general<G>(i, act, p0, len, maxlen, lane, sub, gl, gmask, col, val, agg, lcol, lval,
+                       cnt);
+  }
+}
+
+// Rows of at most 64 entries (one row per warp, aggregate numbers below 2^25): the row's
+// (aggregate, entry) pairs are sorted in registers, so that equal aggregates become neighbours
+// in entry order and the list comes out in ascending order -- as in at_lists_k -- but a warp
+// sorts kAtBatch rows into shared memory and then sums all of their runs at once, a lane per
+// run, each run from its first entry in order.  On the coarse levels a row's entries fall in
+// few aggregates (runs of about ten), and one run summed at a time by its head lane issued a
+// warp-wide FP64 add per entry with only the heads of one row active.  Longer rows take the
+// general path.
+constexpr int kAtBatch = 4;
+
+__global__ void __launch_bounds__(256) at_lists_sorted_k(int n, const int* __restrict__ rowptr,
+                                                         const int* __restrict__ col,
+                                                         const double* __restrict__ val,
+                                                         const int* __restrict__ agg,
+                                                         int* __restrict__ lcol,
+                                                         double* __restrict__ lval,
+                                                         int* __restrict__ cnt) {
+  __shared__ int skey[8][kAtBatch * 64];      // aggregate of each sorted entry, -1 past the row
+  __shared__ double sval[8][kAtBatch * 64];   // its value
+  __shared__ short shead[8][kAtBatch * 64];   // batch positions of the runs' first entries
+  __shared__ int sinfo[8][3 * kAtBatch + 1];  // rows, their first entries, first runs (+ total)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  int* srow = sinfo[w];
+  int* sp0 = srow + kAtBatch;
+  int* srun = sp0 + kAtBatch;
+  int nb = 0;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;; i += nw) {
+    const bool have = i < n;
+    const int p0 = have ? rowptr[i] : 0;
+    const int len = have ? rowptr[i + 1] - p0 : 0;
+    const bool sorted = have && len <= 64;
+    if (sorted) {
+      unsigned x0 = 0xffffffffu, x1 = 0xffffffffu;
+      if (lane < len) x0 = ((unsigned)agg[col[p0 + lane]] << 6) | (unsigned)lane;
+      if (lane + 32 < len) x1 = ((unsigned)agg[col[p0 + lane + 32]] << 6) | (unsigned)(lane + 32);
+      bitonic64(x0, x1, lane);
+      const int q = nb * 64 + lane;
+      skey[w][q] = lane < len ? (int)(x0 >> 6) : -1;
+      skey[w][q + 32] = lane + 32 < len ? (int)(x1 >> 6) : -1;
+      sval[w][q] = lane < len ? val[p0 + (x0 & 63u)] : 0.0;
+      sval[w][q + 32] = lane + 32 < len ? val[p0 + (x1 & 63u)] : 0.0;
+      if (lane == 0) {
+        srow[nb] = i;
+        sp0[nb] = p0;
       }
-      const bool lead = ok && lane == __ffs(mt) - 1;
-      int pos = -1;
-      if (lead)
-        for (int u = 0; u < m; ++u)
-          if (lcol[p0 + u] == key) {
-            pos = u;
-            break;
-          }
-      const bool fresh = lead && pos < 0;
-      const unsigned fm = __ballot_sync(0xffffffffu, fresh) & gmask;
-      if (fresh) {
-        pos = m + __popc(fm & ((1u << lane) - 1u));
-        lcol[p0 + pos] = key;
-        lval[p0 + pos] = sum;
-      } else if (lead) {
-        lval[p0 + pos] += sum;
-      }
-      m += __popc(fm);
-      __syncwarp();
+      ++nb;
+      if (nb < kAtBatch) continue;
     }
-    if (act && gl == 0) cnt[i] = m;
+    if (nb > 0) {
+      __syncwarp();
+      int nrun = 0;
+      for (int q0 = 0; q0 < nb * 64; q0 += 32) {
+        if ((q0 & 63) == 0 && lane == 0) srun[q0 >> 6] = nrun;
+        const int q = q0 + lane;
+        const int k = skey[w][q];
+        const bool head = k >= 0 && ((q & 63) == 0 || skey[w][q - 1] != k);
+        const unsigned hm = __ballot_sync(0xffffffffu, head);
+        if (head) shead[w][nrun + __popc(hm & ((1u << lane) - 1u))] = (short)q;
+        nrun += __popc(hm);
+      }
+      if (lane == 0) srun[nb] = nrun;
+      __syncwarp();
+      for (int r = lane; r < nrun; r += 32) {
+        const int q = shead[w][r];
+        const int b = q >> 6, k = skey[w][q];
+        double sum = sval[w][q];
+        for (int t = q + 1; (t & 63) != 0 && skey[w][t] == k; ++t) sum += sval[w][t];
+        const int pos = sp0[b] + (r - srun[b]);
+        lcol[pos] = k;
+        lval[pos] = sum;
+      }
+      if (lane < nb) cnt[srow[lane]] = srun[lane + 1] - srun[lane];
+      __syncwarp();
+      nb = 0;
+    }
+    if (!have) break;
+    if (!sorted)
+      at_list_general<32>(i, true, p0, len, len, lane, 0, lane, 0xffffffffu, col, val, agg, lcol,
+                          lval, cnt);
   }
 }
 
@@ -1406,6 +1502,9 @@ void prolongator_start(const DevCsr& A, const int* agg, int nagg, ProlongState& 
     if (st.G == 16)
       at_lists_k<16><<<blocks, 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, agg, st.lcol.p,
                                             st.lval.p, cnt.p, sortable);
+    else if (sortable)
+      at_lists_sorted_k<<<blocks, 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, agg, st.lcol.p,
+                                               st.lval.p, cnt.p);
     else
       at_lists_k<32><<<blocks, 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, agg, st.lcol.p,
                                             st.lval.p, cnt.p, sortable);
