@@ -402,7 +402,7 @@ static void setup_levels(const saamg_operator* op, const saamg_params& prm, cuda
     L0->avg = od.n ? (double)od.nnz / od.n : 0.0;
     L0->invd.alloc(od.n, s);
     L0->invd32.alloc(od.n, s);
-    csr_diag_inverse(od.A, L0->invd.p, L0->invd32.p, s);
+    stencil_diag_inverse(od, L0->invd.p, L0->invd32.p, s);
     h->lev.push_back(std::move(L0));
   }
   int l = 0;

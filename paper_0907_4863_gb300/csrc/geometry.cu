@@ -969,6 +969,40 @@ void field_gradient(const OperatorData& op, const double* phi, double* ex, doubl
   SAAMG_LAUNCH();
 }
 
+// 1 / a_ii of the scaled operator from the stencil data: the regular-run rows' diagonal is the
+// interior constant (1 / diag formed once), the table rows carry their own 1 / diag -- the same
+// IEEE divisions of the same diagonals as in the CSR, without a pass over it.
+__global__ void invd_fill_k(int n, double invd0, double* __restrict__ invd,
+                            float* __restrict__ invd32) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    invd[i] = invd0;
+    if (invd32) invd32[i] = (float)invd0;
+  }
+}
+
+__global__ void invd_table_k(int ntable, const int* __restrict__ trow,
+                             const double* __restrict__ table, double* __restrict__ invd,
+                             float* __restrict__ invd32) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntable) return;
+  const double v = table[8 * (size_t)t + 7];
+  invd[trow[t]] = v;
+  if (invd32) invd32[trow[t]] = (float)v;
+}
+
+void stencil_diag_inverse(const OperatorData& op, double* invd, float* invd32, cudaStream_t s) {
+  if (op.n == 0) return;
+  const size_t need = ((size_t)op.n + 255) / 256;
+  const int blocks = (int)(need < (size_t)sm_count() * 16 ? need : (size_t)sm_count() * 16);
+  invd_fill_k<<<blocks, 256, 0, s>>>(op.n, op.invd0, invd, invd32);
+  SAAMG_LAUNCH();
+  if (op.ntable > 0) {
+    invd_table_k<<<(op.ntable + 255) / 256, 256, 0, s>>>(op.ntable, op.trow.p, op.table.p, invd,
+                                                          invd32);
+    SAAMG_LAUNCH();
+  }
+}
+
 void gather_rhs(const OperatorData& op, const double* rho, const double* phi0, double* bhat,
                 double* xhat, cudaStream_t s) {
   if (op.n == 0) return;

@@ -61,6 +61,8 @@ void build_operator_data(const GeomParams& g, cudaStream_t s, OperatorData& op);
 // rho (box) -> bhat (compact) = s_i * (bfac_i * rho); phi0 (box) -> xhat0 = phi0 / s_i (if given)
 void gather_rhs(const OperatorData& op, const double* rho, const double* phi0, double* bhat,
                 double* xhat, cudaStream_t s);
+// invd = 1 / a_ii of the scaled operator (and its FP32 copy, if given) from the stencil data
+void stencil_diag_inverse(const OperatorData& op, double* invd, float* invd32, cudaStream_t s);
 // xhat (compact) -> phi (box) = s_i * xhat at unknowns, 0 elsewhere
 void scatter_solution(const OperatorData& op, const double* xhat, double* phi, cudaStream_t s);
 
