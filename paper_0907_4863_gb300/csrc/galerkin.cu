@@ -1099,15 +1099,33 @@ __global__ void transpose_fill_k(int n, const int* __restrict__ rowptr, const in
   }
 }
 
-// Warp per row: every entry's rank among the row's (distinct) columns gives its place.
+// Warp per row: every entry's rank among the row's (distinct) columns gives its place.  Rows of
+// at most 64 entries whose columns fit 26 bits are sorted in registers instead, (column, entry)
+// pairs by a bitonic network: the same order, without a pass over the row per entry.
 __global__ void rank_rows_k(int n, const int* __restrict__ rowptr, const int* __restrict__ tcol,
                             const double* __restrict__ tval, int* __restrict__ col,
-                            double* __restrict__ val) {
+                            double* __restrict__ val, bool sortable) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int i = warp; i < n; i += nw) {
     const int p0 = rowptr[i], p1 = rowptr[i + 1];
+    const int len = p1 - p0;
+    if (sortable && len <= 64) {  // uniform across the warp
+      unsigned x0 = 0xffffffffu, x1 = 0xffffffffu;
+      if (lane < len) x0 = ((unsigned)tcol[p0 + lane] << 6) | (unsigned)lane;
+      if (lane + 32 < len) x1 = ((unsigned)tcol[p0 + lane + 32] << 6) | (unsigned)(lane + 32);
+      bitonic64(x0, x1, lane);
+      if (lane < len) {
+        col[p0 + lane] = (int)(x0 >> 6);
+        val[p0 + lane] = tval[p0 + (x0 & 63u)];
+      }
+      if (lane + 32 < len) {
+        col[p0 + lane + 32] = (int)(x1 >> 6);
+        val[p0 + lane + 32] = tval[p0 + (x1 & 63u)];
+      }
+      continue;
+    }
     for (int p = p0 + lane; p < p1; p += 32) {
       const int c = tcol[p];
       int rank = 0;
@@ -1591,7 +1609,8 @@ void transpose(const DevCsr& P, DevCsr& R, cudaStream_t s) {
   } else if (R.n > 0) {
     long long warps = R.n;
     int blocks = (int)std::min<long long>((warps * 32 + 255) / 256, sm_count() * 32);
-    rank_rows_k<<<blocks, 256, 0, s>>>(R.n, R.rowptr.p, tcol.p, tval.p, R.col.p, R.val.p);
+    rank_rows_k<<<blocks, 256, 0, s>>>(R.n, R.rowptr.p, tcol.p, tval.p, R.col.p, R.val.p,
+                                       P.n < (1 << 26));
     SAAMG_LAUNCH();
   }
 }
