@@ -31,7 +31,12 @@ PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP64 level-0 Chebyshev step
 # on the 256^3 elliptic pipe, from its ncu capture; None for other kernels or sizes, and to be
 # reset whenever that kernel changes
-TRAFFIC_BYTES = {("stencil_smooth", 0, 256): 366.19e6}  # (class, precision, n) -> DRAM bytes per launch (ncu)
+# (class, precision, n) -> DRAM bytes per launch (ncu, dram__bytes_read + dram__bytes_write); the
+# BF16 mode's level-0 passes are the FP32 kernels
+TRAFFIC_BYTES = {("stencil_smooth", 0, 256): 363.9e6,
+                 ("stencil_smooth", 1, 256): 125.1e6, ("stencil_smooth", 2, 256): 125.1e6,
+                 ("stencil_resid", 1, 256): 82.5e6, ("stencil_resid", 2, 256): 82.5e6,
+                 ("prolong0", 1, 256): 81.3e6, ("prolong0", 2, 256): 81.3e6}
 # kernel timing classes of the solve phase (one kernel template each)
 SOLVE_CLASSES = ("stencil_smooth", "stencil_apply", "stencil_resid", "stencil_first",
                  "coarse_csr", "coarse_deep", "transfer", "transfer_deep", "prolong0")
