@@ -840,12 +840,6 @@ __global__ void __launch_bounds__(32 * kAtWarps) at_stencil_k(
 }
 
 // --- A T and the smoothed prolongator ------------------------------------------
-// Row i of A T (T(j, agg(j)) = 1) holds the distinct aggregates agg(j) of A's row i, each with
-// the sum of the row's a_ij over it.  A group of G lanes takes one row, G entries at a time:
-// equal aggregates inside a chunk are found by a match and summed by their lowest lane in
-// lane (= entry) order, and the chunk sums are merged into the row's list, kept in scratch
-// arrays laid out like A (a row never has more aggregates than entries), in order of first
-// appearance.  A row of at most G entries is therefore summed strictly in entry order.
 // The list of row i (G lanes of group `sub`; warp-collective) by lane matches, chunk by chunk.
 template <int G>
 __device__ __forceinline__ void at_list_general(int i, bool act, int p0, int len, int maxlen,
@@ -855,51 +849,58 @@ __device__ __forceinline__ void at_list_general(int i, bool act, int p0, int len
                                                 const int* __restrict__ agg,
                                                 int* __restrict__ lcol, double* __restrict__ lval,
                                                 int* __restrict__ cnt) {
-    int m = 0;  // the group's list length
-    for (int cb = 0; cb < maxlen; cb += G) {
-      const bool ok = cb + gl < len;
-      const int p = p0 + cb + gl;
-      const int key = ok ? agg[col[p]] : -1;
-      const double v = ok ? val[p] : 0.0;
-      // the lanes of this group holding the same aggregate
-      const unsigned long long k64 = ((unsigned long long)(unsigned)sub << 32) | (unsigned)key;
-      const unsigned mt = __match_any_sync(0xffffffffu, k64);
-      int cmax = __popc(mt);
+  int m = 0;  // the group's list length
+  for (int cb = 0; cb < maxlen; cb += G) {
+    const bool ok = cb + gl < len;
+    const int p = p0 + cb + gl;
+    const int key = ok ? agg[col[p]] : -1;
+    const double v = ok ? val[p] : 0.0;
+    // the lanes of this group holding the same aggregate
+    const unsigned long long k64 = ((unsigned long long)(unsigned)sub << 32) | (unsigned)key;
+    const unsigned mt = __match_any_sync(0xffffffffu, k64);
+    int cmax = __popc(mt);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
-      double sum = 0.0;
-      unsigned rem = mt;
-      for (int t = 0; t < cmax; ++t) {
-        const int src = rem ? __ffs(rem) - 1 : lane;
-        const double sv = __shfl_sync(0xffffffffu, v, src);
-        if (rem) {
-          sum = t == 0 ? sv : sum + sv;
-          rem &= rem - 1u;
-        }
+    for (int o = 16; o > 0; o >>= 1) cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    double sum = 0.0;
+    unsigned rem = mt;
+    for (int t = 0; t < cmax; ++t) {
+      const int src = rem ? __ffs(rem) - 1 : lane;
+      const double sv = __shfl_sync(0xffffffffu, v, src);
+      if (rem) {
+        sum = t == 0 ? sv : sum + sv;
+        rem &= rem - 1u;
       }
-      const bool lead = ok && lane == __ffs(mt) - 1;
-      int pos = -1;
-      if (lead)
-        for (int u = 0; u < m; ++u)
-          if (lcol[p0 + u] == key) {
-            pos = u;
-            break;
-          }
-      const bool fresh = lead && pos < 0;
-      const unsigned fm = __ballot_sync(0xffffffffu, fresh) & gmask;
-      if (fresh) {
-        pos = m + __popc(fm & ((1u << lane) - 1u));
-        lcol[p0 + pos] = key;
-        lval[p0 + pos] = sum;
-      } else if (lead) {
-        lval[p0 + pos] += sum;
-      }
-      m += __popc(fm);
-      __syncwarp();
     }
-    if (act && gl == 0) cnt[i] = m;
+    const bool lead = ok && lane == __ffs(mt) - 1;
+    int pos = -1;
+    if (lead)
+      for (int u = 0; u < m; ++u)
+        if (lcol[p0 + u] == key) {
+          pos = u;
+          break;
+        }
+    const bool fresh = lead && pos < 0;
+    const unsigned fm = __ballot_sync(0xffffffffu, fresh) & gmask;
+    if (fresh) {
+      pos = m + __popc(fm & ((1u << lane) - 1u));
+      lcol[p0 + pos] = key;
+      lval[p0 + pos] = sum;
+    } else if (lead) {
+      lval[p0 + pos] += sum;
+    }
+    m += __popc(fm);
+    __syncwarp();
+  }
+  if (act && gl == 0) cnt[i] = m;
 }
 
+// Row i of A T (T(j, agg(j)) = 1) holds the distinct aggregates agg(j) of A's row i, each with
+// the sum of the row's a_ij over it.  A group of G lanes takes one row, G entries at a time:
+// equal aggregates inside a chunk are found by a match and summed by their lowest lane in
+// lane (= entry) order, and the chunk sums are merged into the row's list, kept in scratch
+// arrays laid out like A (a row never has more aggregates than entries), in order of first
+// appearance.  A row of at most G entries is therefore summed strictly in entry order.  (Rows
+// of a 32-lane class whose aggregates sort in 32 bits go to at_lists_sorted_k instead.)
 template <int G>
 __global__ void __launch_bounds__(256) at_lists_k(int n, const int* __restrict__ rowptr,
                                                   const int* __restrict__ col,
@@ -907,7 +908,7 @@ __global__ void __launch_bounds__(256) at_lists_k(int n, const int* __restrict__
                                                   const int* __restrict__ agg,
                                                   int* __restrict__ lcol,
                                                   double* __restrict__ lval,
-                                                  int* __restrict__ cnt, bool sortable) {
+                                                  int* __restrict__ cnt) {
   constexpr int RPW = 32 / G;
   const int lane = threadIdx.x & 31;
   const int sub = lane / G, gl = lane % G;
@@ -921,46 +922,6 @@ __global__ void __launch_bounds__(256) at_lists_k(int n, const int* __restrict__
     int maxlen = len;
 #pragma unroll
     for (int o = G; o < 32; o <<= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
-    if (G == 32 && sortable && len <= 64) {
-      // the row's (aggregate, entry) pairs sorted in registers: equal aggregates become
-      // neighbours in entry order and the list comes out in ascending order
-      __shared__ unsigned skey[8][64];
-      __shared__ double sval[8][64];
-      const int w = threadIdx.x >> 5;
-      unsigned x0 = 0xffffffffu, x1 = 0xffffffffu;
-      if (lane < len) {
-        x0 = ((unsigned)agg[col[p0 + lane]] << 6) | (unsigned)lane;
-        sval[w][lane] = val[p0 + lane];
-      }
-      if (lane + 32 < len) {
-        x1 = ((unsigned)agg[col[p0 + lane + 32]] << 6) | (unsigned)(lane + 32);
-        sval[w][lane + 32] = val[p0 + lane + 32];
-      }
-      bitonic64(x0, x1, lane);
-      skey[w][lane] = x0;
-      skey[w][lane + 32] = x1;
-      __syncwarp();
-      int m = 0;
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int sp = lane + 32 * r;
-        const unsigned x = r ? x1 : x0;
-        const bool head = sp < len && (sp == 0 || (skey[w][sp - 1] >> 6) != (x >> 6));
-        const unsigned hm = __ballot_sync(0xffffffffu, head);
-        if (head) {
-          const unsigned kk = x >> 6;
-          double sum = sval[w][x & 63u];
-          for (int t = sp + 1; t < len && (skey[w][t] >> 6) == kk; ++t) sum += sval[w][skey[w][t] & 63u];
-          const int pos = m + __popc(hm & ((1u << lane) - 1u));
-          lcol[p0 + pos] = (int)kk;
-          lval[p0 + pos] = sum;
-        }
-        m += __popc(hm);
-      }
-      if (lane == 0) cnt[i] = m;
-      __syncwarp();
-      continue;
-    }
     at_list_general<G>(i, act, p0, len, maxlen, lane, sub, gl, gmask, col, val, agg, lcol, lval,
                        cnt);
   }
@@ -1519,13 +1480,13 @@ void prolongator_start(const DevCsr& A, const int* agg, int nagg, ProlongState& 
     KernelTimer kt(SAAMG_KT_SPGEMM, n, s);
     if (st.G == 16)
       at_lists_k<16><<<blocks, 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, agg, st.lcol.p,
-                                            st.lval.p, cnt.p, sortable);
+                                            st.lval.p, cnt.p);
     else if (sortable)
       at_lists_sorted_k<<<blocks, 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, agg, st.lcol.p,
                                                st.lval.p, cnt.p);
     else
       at_lists_k<32><<<blocks, 256, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, agg, st.lcol.p,
-                                            st.lval.p, cnt.p, sortable);
+                                            st.lval.p, cnt.p);
     SAAMG_LAUNCH();
   }
   fill_int(cnt.p + n, 0, 1, s);
