@@ -75,9 +75,11 @@ def _csr_close(rp, cc, vv, rp2, cc2, vv2, rtol):
         assert err < rtol, err
 
 
+# the 64^3 pipe coarsened to 40 rows: level 2 has rows of more than 64 entries (five of 170),
+# which take the general path of the coarse-level A T lists
 HIER = [(I.cylinder_workload(32, I.CONSTANT), 1000, 3), (I.pipe_workload(40, I.LINEAR), 60, 10),
         (I.pipe_workload(28, I.QUADRATIC), 40, 10), (I.taper_workload(30, 26, 44, I.LINEAR), 50, 10),
-        (aniso_workloads()[0], 80, 10)]
+        (aniso_workloads()[0], 80, 10), (I.pipe_workload(64, I.LINEAR), 40, 10)]
 
 
 @pytest.mark.parametrize("w,max_coarse,max_levels", HIER, ids=lambda v: getattr(v, "name", str(v)))
