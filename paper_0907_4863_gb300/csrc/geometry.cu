@@ -969,6 +969,8 @@ void field_gradient(const OperatorData& op, const double* phi, double* ex, doubl
   SAAMG_LAUNCH();
 }
 
+namespace {
+
 // 1 / a_ii of the scaled operator from the stencil data: the regular-run rows' diagonal is the
 // interior constant (1 / diag formed once), the table rows carry their own 1 / diag -- the same
 // IEEE divisions of the same diagonals as in the CSR, without a pass over it.
@@ -989,6 +991,8 @@ __global__ void invd_table_k(int ntable, const int* __restrict__ trow,
   invd[trow[t]] = v;
   if (invd32) invd32[trow[t]] = (float)v;
 }
+
+}  // namespace
 
 void stencil_diag_inverse(const OperatorData& op, double* invd, float* invd32, cudaStream_t s) {
   if (op.n == 0) return;
