@@ -366,10 +366,15 @@ static cudaStream_t aux_stream() {
 }
 
 // SELL copy of a coarse level's operator with the value arrays of the V-cycle's precision.
-static void build_level_sell(saamg_hierarchy* h, Level& L, cudaStream_t s) {
+// like: the same level of a reused hierarchy (same pattern), whose SELL layout is copied
+static void build_level_sell(saamg_hierarchy* h, Level& L, cudaStream_t s,
+                             const Level* like = nullptr) {
   const bool f64 = !mixed(h), f32 = h->prm.precision == SAAMG_PREC_FP32;
   const bool bf16 = h->prm.precision == SAAMG_PREC_FP32_BF16;
-  sell_from_csr(L.A, L.As, f64, f32, bf16, s);
+  if (like && like->As.n == L.n && like->As.nnz == L.A.nnz && like->As.nslices > 0)
+    sell_like(L.A, like->As, L.As, f64, f32, bf16, s);
+  else
+    sell_from_csr(L.A, L.As, f64, f32, bf16, s);
 }
 
 static void setup_levels(const saamg_operator* op, const saamg_params& prm, cudaStream_t s,
@@ -433,7 +438,8 @@ static void setup_levels(const saamg_operator* op, const saamg_params& prm, cuda
     if (coarsen) {
       // a smoothed level >= 1 large enough for SELL gets its SELL copy now (it is not the
       // coarsest), so that in the FP64 V-cycle the power iteration runs on it too
-      if (l >= 1 && L.n >= kSellMinRows && L.As.n == 0) build_level_sell(h, L, s);
+      if (l >= 1 && L.n >= kSellMinRows && L.As.n == 0)
+        build_level_sell(h, L, s, prev ? prev->lev[l].get() : nullptr);
       const StencilDev<double> S0 = od.view<double>();
       cudaEvent_t fork;
       SAAMG_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
@@ -575,7 +581,9 @@ static void setup_levels(const saamg_operator* op, const saamg_params& prm, cuda
     // SELL for the large smoothed levels (built before their spectral bound); a small level
     // runs on CSR with wide row groups
     if (q >= 1 && q < nl - 1 && L.n >= kSellMinRows) {
-      if (L.As.n == 0) build_level_sell(h, L, s);
+      if (L.As.n == 0)
+        build_level_sell(h, L, s,
+                         prev && q < (int)prev->lev.size() ? prev->lev[q].get() : nullptr);
     } else if (q >= 1 && q < nl - 1) {
       if (f32) {
         L.A.val32.alloc(L.A.nnz, s);

@@ -72,6 +72,25 @@ __global__ void sell_fill_k(int n, const int* __restrict__ rowptr, const int* __
   if (far) atomicOr(wide, 1);
 }
 
+// The value arrays of a layout whose structure is already in place (as sell_fill_k writes them).
+__global__ void sell_values_k(int n, const int* __restrict__ rowptr, const double* __restrict__ val,
+                              const int* __restrict__ perm, const int* __restrict__ soff,
+                              double* __restrict__ sval, float* __restrict__ sval32,
+                              __nv_bfloat16* __restrict__ sval16) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int r = perm[p], s = p >> 5, lane = p & 31;
+  const int w = (soff[s + 1] - soff[s]) >> 5;
+  const int p0 = rowptr[r], len = rowptr[r + 1] - p0;
+  for (int k = 0; k < w; ++k) {
+    const int e = soff[s] + 32 * k + lane;
+    const double v = k < len ? val[p0 + k] : 0.0;
+    if (sval) sval[e] = v;
+    if (sval32) sval32[e] = (float)v;
+    if (sval16) sval16[e] = __double2bfloat16(v);
+  }
+}
+
 template <class TV, class TM, int MODE, bool REL>
 __global__ void __launch_bounds__(256) sell_k(int n, int nslices, const int* __restrict__ perm,
                                               const int* __restrict__ soff,
@@ -145,6 +164,36 @@ void sell_from_csr(const DevCsr& A, DevSell& S, bool f64, bool f32, bool bf16, c
     S.col.release();
     S.index_bytes = 2;
   }
+}
+
+void sell_like(const DevCsr& A, const DevSell& like, DevSell& S, bool f64, bool f32, bool bf16,
+               cudaStream_t s) {
+  if (like.n != A.n || like.nnz != A.nnz) fail(SAAMG_EINVAL, "SELL layout of another pattern");
+  S.n = A.n;
+  S.m = A.m;
+  S.nnz = A.nnz;
+  S.nslices = like.nslices;
+  S.nent = like.nent;
+  S.index_bytes = like.index_bytes;
+  auto copy = [&](auto& dst, const auto& src, size_t count) {
+    dst.alloc(count, s);
+    if (count)
+      SAAMG_CUDA(cudaMemcpyAsync(dst.p, src.p, count * sizeof(*src.p), cudaMemcpyDeviceToDevice,
+                                 s));
+  };
+  copy(S.perm, like.perm, (size_t)A.n);
+  copy(S.soff, like.soff, (size_t)like.nslices + 1);
+  if (like.index_bytes == 2) copy(S.dcol, like.dcol, (size_t)like.nent);
+  else copy(S.col, like.col, (size_t)like.nent);
+  if (f64) S.val.alloc(S.nent, s);
+  if (f32) S.val32.alloc(S.nent, s);
+  if (bf16) S.val16.alloc(S.nent, s);
+  if (A.n == 0) return;
+  sell_values_k<<<(A.n + 255) / 256, 256, 0, s>>>(A.n, A.rowptr.p, A.val.p, S.perm.p, S.soff.p,
+                                                  f64 ? S.val.p : nullptr,
+                                                  f32 ? S.val32.p : nullptr,
+                                                  bf16 ? S.val16.p : nullptr);
+  SAAMG_LAUNCH();
 }
 
 template <class TV, class TM>

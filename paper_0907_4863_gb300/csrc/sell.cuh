@@ -43,6 +43,10 @@ struct DevSell {
 
 // S = A in SELL form with the value arrays requested (FP64 / FP32 / BF16 copies of A.val).
 void sell_from_csr(const DevCsr& A, DevSell& S, bool f64, bool f32, bool bf16, cudaStream_t s);
+// The same for an A whose pattern is that of the matrix `like` holds (a reused hierarchy's
+// level): like's layout is copied and only the value arrays are filled.
+void sell_like(const DevCsr& A, const DevSell& like, DevSell& S, bool f64, bool f32, bool bf16,
+               cudaStream_t s);
 
 // The CSR modes of csr_apply (CSR_CHEB with c1 == 0 does not read d; CSR_SPMV_DINV_DOT
 // writes kRedBlocks partial sums of y.y and takes the scale of x from *xscale, 1 if NULL).
