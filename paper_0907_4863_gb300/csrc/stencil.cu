@@ -10,6 +10,8 @@
 // (bound by FP64 issue): first 32 regular-run rows per warp from a (row, line) list, then
 // 32 table rows per warp from the table-row list.
 #include <algorithm>
+#include <cstdint>
+#include <type_traits>
 
 #include "operator.cuh"
 #include "batch.cuh"
@@ -133,6 +135,21 @@ __device__ __forceinline__ void stencil_row(const StencilDev<T>& S, int c, int l
       vyp = x[ar[oyp]];
       vzm = x[ar[ozm]];
       vzp = x[ar[ozp]];
+    } else if (PACKED && !TABLE && (reinterpret_cast<uintptr_t>(x) & (2 * sizeof(T) - 1)) == 0) {
+      // a regular-run row has both x-neighbours: x[row - 1 .. row + 1] as one aligned pair and
+      // one single element (two loads for the same three values)
+      using T2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
+      const T2 v = *reinterpret_cast<const T2*>(x + (row & ~1));
+      const bool odd = (row & 1) != 0;
+      const T v1 = x[odd ? row + 1 : row - 1];
+      vxm = odd ? v.x : v1;
+      xc = odd ? v.y : v.x;
+      vxp = odd ? v1 : v.y;
+      const T* xr = x + row;
+      vym = xr[oym];
+      vyp = xr[oyp];
+      vzm = xr[ozm];
+      vzp = xr[ozp];
     } else {
       const T* xr = x + row;
       xc = xr[0];
