@@ -542,7 +542,7 @@ static void setup_levels(const saamg_operator* op, const saamg_params& prm, cuda
       spgemm_symbolic(L.R, AP, rap_plan, s, PL ? &prev->lev[l + 1]->A : nullptr);
       spgemm_numeric(L.R, AP, rap_plan, N->A, s);
     }
-    if (l >= 1) {  // keep the pattern of A P (a level-0 one would cost 8 B per entry of 57 M)
+    {  // keep the pattern of A P: a reuse of this hierarchy skips its symbolic pass
       L.APpat.n = AP.n;
       L.APpat.m = AP.m;
       L.APpat.nnz = AP.nnz;
