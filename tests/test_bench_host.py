@@ -105,3 +105,23 @@ def test_level1_smoother_counts_its_column_bytes(bench):
         "algorithmic_bytes_per_launch"] == pytest.approx(8e6)
     assert bench.level1_index_bytes({"sell_index_bytes": [0, 2, 0]}) == 2
     assert bench.level1_index_bytes({"sell_index_bytes": [0, 0, 0]}) == 4
+
+
+def test_captured_traffic_is_attached_to_the_256_cube_classes(bench):
+    """The ncu DRAM bytes per launch go with the class, precision and size they were captured
+    on (the BF16 mode's level-0 passes are the FP32 kernels); nothing else carries any, and each
+    capture stays near the class's algorithmic bytes at 7,119,872 rows."""
+    rows = 7_119_872
+    rec = (1.0, 10, 10 * rows)
+    r = bench.roofline("stencil_smooth", rec, 0, n=256)
+    assert r["traffic"] == pytest.approx(364.0e6)
+    assert 1.0 < r["traffic"] / r["algorithmic_bytes_per_launch"] < 1.3  # the (row, line) list
+    for prec in (1, 2):
+        for name in ("stencil_smooth", "stencil_resid", "prolong0"):
+            r = bench.roofline(name, rec, prec, n=256)
+            assert r["traffic"] is not None
+            assert 0.8 < r["traffic"] / r["algorithmic_bytes_per_launch"] < 1.1
+        for name in ("stencil_first", "coarse_csr", "transfer", "coarse_deep"):
+            assert bench.roofline(name, rec, prec, n=256)["traffic"] is None
+    assert bench.roofline("stencil_resid", rec, 0, n=256)["traffic"] is None
+    assert bench.roofline("stencil_smooth", rec, 1, n=512)["traffic"] is None
